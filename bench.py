@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the ghost-celled ideal-MHD patch advance on GB300.
+
+Workload: one periodic 3D patch of 128^3 cells + 2 ghost layers holding a
+blast wave (rho = 1 + 0.01 U(-1,1) seeded noise, p = 10 inside r < 0.1 and 0.1
+outside, B = (1, 1, 0)/sqrt 2, v = 0, [-1/2, 1/2]^3).  One step is one pass of
+the whole single-patch path: periodic ghost fill -> CFL dt reduction (device
+scalar) -> MUSCL-Hancock/HLLD/CT advance of the interior.  Both precisions are
+timed: FP32 bulk arithmetic (the headline) and FP64 (the parity build).
+
+Metric: cell-updates/s = interior cells x steps / device time.  L2 is flushed
+(512 MiB write) before every timed step.  ``--impl reference`` times the FP64
+CPU oracle on the host cores on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s (FP64 vs FP32-mixed, % HBM roofline); patch p50/p99 latency"
+UNIT = "cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# Device-side FP peaks used for the ALU roofline (per GPU).  Derived from the
+# unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x clock, and the
+# FP64 rate measured on this GPU ("ALU peaks").
+FP_PEAK_TFLOPS = {"f32": None, "f64": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    return ap.parse_args()
+
+
+def config(n):
+    return {"workload": "3D ideal-MHD blast wave, one periodic %d^3 patch + 2 ghost layers; "
+                        "step = ghost fill + CFL dt + MUSCL-Hancock/HLLD/CT advance" % n,
+            "cells": n ** 3, "ghost_layers": 2, "steps_per_call": 1,
+            "l2": "flushed before every timed step (512 MiB write)",
+            "parallelism": "replicas (one independent patch per GPU)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def kernel_units(name, n):
+    """Elements one launch of a kernel processes on the n^3 periodic patch
+    (update box = interior, so UB+1 = n+2 and UB+2 = n+4 cells a side)."""
+    return {
+        "k_prim": (n + 4) ** 3,
+        "k_pred": (n + 2) ** 3,
+        "k_edge": 3 * (n + 3) ** 2 * (n + 2),
+        "k_flux": 3 * (n + 1) * (n + 2) ** 2,
+        "k_emf": 3 * n * (n + 1) ** 2,
+        "k_update": n ** 3,
+        "k_cfl": n ** 3,
+        "k_ghost": (n + 4) ** 3 - n ** 3,
+    }.get(name)
+
+
+# Algorithmic values moved per unit by each staged kernel (read + written
+# once): the staged design exchanges intermediates through HBM.
+KERNEL_VALUES = {"k_prim": 8 + 11, "k_pred": 8 + 51, "k_edge": 1 + 1, "k_flux": 16 + 1 + 2 + 8,
+                 "k_emf": 4 + 4 + 4 + 1, "k_update": 16 + 16, "k_cfl": 8, "k_ghost": 16}
+
+
+def time_dtype(dtype, pr, args, local, world, stream, flush):
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.patch import Patch
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+
+    ctx = capi.mhd_ctx_create(device=local)
+    try:
+        p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
+        run = PeriodicRunner(p, ctx, stream)
+        for _ in range(args.warmup):
+            run.step()
+        torch.cuda.synchronize()
+        status = capi.mhd_get_device_status(ctx)
+        capi.mhd_timing_enable(ctx, True)
+        capi.mhd_timing_reset(ctx)
+        l0 = capi.mhd_launch_count(ctx)
+        barrier(world)
+        torch.cuda.synchronize()
+        total_ms = 0.0
+        per_step = []
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run.step()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            per_step.append(ms)
+            total_ms += ms
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = capi.mhd_launch_count(ctx) - l0
+        kt = capi.mhd_timing_read(ctx)
+        capi.mhd_timing_enable(ctx, False)
+        status = status or capi.mhd_get_device_status(ctx)
+
+        # end to end through the public API with host buffers: per step the state
+        # goes host -> device from pinned memory and the new state comes back
+        ne = args.e2e_steps or max(3, args.steps // 2)
+        host = torch.empty_like(p.state, device="cpu").pin_memory()
+        host.copy_(p.state)
+        nbytes = host.numel() * host.element_size()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(ne):
+            with torch.cuda.stream(stream):
+                p.state.copy_(host, non_blocking=True)
+            run.step()
+            with torch.cuda.stream(stream):
+                host.copy_(p.state, non_blocking=True)
+        t1.record(stream)
+        t1.synchronize()
+        e2e_ms = t0.elapsed_time(t1)
+        barrier(world)
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    return {"total_ms": total_ms, "per_step_ms": per_step, "launches": launches, "kernels": kt,
+            "status": status, "e2e_ms": e2e_ms, "e2e_steps": ne, "state_bytes": nbytes}
+
+
+def cpu_baseline(pr, steps):
+    """The FP64 oracle as it stands, on the host cores, on `steps` full steps of
+    the same workload."""
+    from oracle import oracle as O
+    st = pr.state.copy()
+    prm = O.params()
+    t0 = time.perf_counter()
+    O.run_periodic(st, pr.n, pr.g, pr.dx, prm, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": pr.cells * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d full FP64 steps of the %d^3 blast (ghost fill + dt + advance), %.1f s" %
+                      (steps, pr.n[0], dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    pr = synth.blast(args.n)
+    from oracle import oracle as O
+    O.build()
+    st = pr.state.copy()
+    prm = O.params()
+    O.run_periodic(st, pr.n, pr.g, pr.dx, prm, max(1, args.warmup and 1))
+    t0 = time.perf_counter()
+    O.run_periodic(st, pr.n, pr.g, pr.dx, prm, args.steps)
+    dt = time.perf_counter() - t0
+    v = pr.cells * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.n),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d full FP64 steps of the %d^3 blast on the host cores" % (args.steps, args.n)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_1112_1710_gb300 import _build
+    _build.build()
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    pr = synth.blast(args.n)
+    stream = torch.cuda.Stream(device=local)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % local)
+    hbm, hbm_src = peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    res = {}
+    for dtype in ("f32", "f64"):
+        res[dtype] = time_dtype(dtype, pr, args, local, world, stream, flush)
+    clk = clocks.stop()
+    cells = pr.cells
+    out_dt = {}
+    for dtype, r in res.items():
+        tmax = reduce_max(r["total_ms"], world)
+        ncell = reduce_sum(cells * args.steps, world)
+        e2e_max = reduce_max(r["e2e_ms"], world)
+        s = 4 if dtype == "f32" else 8
+        ms_step = tmax / args.steps
+        value = ncell / (tmax * 1e-3)
+        kernels = {}
+        for nm, (ms, cnt) in r["kernels"].items():
+            if cnt:
+                kernels[nm] = {"ms_total": ms, "launches": cnt, "ms_per_launch": ms / cnt}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+        units = kernel_units(dom, args.n)
+        per_launch = kernels[dom]["ms_per_launch"] * 1e-3
+        traffic_alg = units * KERNEL_VALUES[dom] * s
+        achieved = traffic_alg / per_launch / 1e9
+        out_dt[dtype] = {
+            "value": value, "ms_per_step": ms_step,
+            "p50_step_ms": statistics.median(r["per_step_ms"]),
+            "p99_step_ms": sorted(r["per_step_ms"])[max(0, int(0.99 * len(r["per_step_ms"])) - 1)],
+            "hbm_step": {"bytes_per_cell_update": 2 * 8 * s, "achieved_gbs": 2 * 8 * s * cells / (ms_step * 1e-3) / 1e9,
+                         "peak_gbs": hbm, "frac": 2 * 8 * s * cells / (ms_step * 1e-3) / 1e9 / hbm},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "algorithmic_bytes_per_launch": traffic_alg, "units_per_launch": units,
+                         "peak_source": hbm_src},
+            "kernels": kernels,
+            "e2e": {"value": reduce_sum(cells * r["e2e_steps"], world) / (e2e_max * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": r["state_bytes"], "d2h_bytes_per_step": r["state_bytes"]},
+            "gpu_launches": r["launches"], "device_status": r["status"],
+        }
+    if rank != 0:
+        return
+    main = out_dt["f32"]
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(args.n), "roofline": main["roofline"], "hbm_step": main["hbm_step"],
+            "e2e": main["e2e"], "gpu_launches": main["gpu_launches"], "clocks": clk,
+            "fp64": out_dt["f64"], "fp32": {k: v for k, v in main.items() if k not in ("roofline", "e2e")}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pr, args.cpu_steps)
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * mhd_gpu.h -- C ABI of the GB300 (sm_103a) ghost-celled ideal-MHD patch
+ * library: the hyperbolic advance of grid patches and the level operations
+ * that feed it (ghost fill, prolongation/restriction, flux-register
+ * refluxing, CFL time step, conservation sums).
+ *
+ * Method.  The AMR life cycle is that of Carroll-Nellenback et al.,
+ * "Efficient Parallelization for AMR MHD Multiphysics Calculations" (Sec. 2.2:
+ * Overlap, Prolongation, Advance, Synchronisation, Restriction).  Each patch
+ * is advanced independently (Abstract, Sec. 2.3) with extended ghost zones of
+ * width R * n_ghost (Sec. 2.3), updating a box that shrinks by n_ghost per
+ * substep (Sec. 4, worked 4x4 example).  The paper does not state the MHD
+ * solver; the advance is the unsplit MUSCL-Hancock scheme with primitive PLM
+ * reconstruction, the HLLD Riemann solver of Miyoshi & Kusano (2005) and
+ * constrained transport with Gardiner & Stone (2005) upwinded edge EMFs.  One
+ * step consumes n_ghost = 2 ghost layers.
+ *
+ * Memory.  The caller owns every state array and every stream; the library
+ * owns its context, its scratch arena and its device copies of descriptor
+ * and copy lists.  State is structure-of-arrays: five cell arrays (rho, Mx,
+ * My, Mz, E) and three face arrays (Bx on x-faces, By on y-faces, Bz on
+ * z-faces) that share one set of element strides (stride[0] == 1, x fastest).
+ * A patch with interior box [lo, hi] and g ghost layers has N_d = hi_d - lo_d
+ * + 1 + 2g cells per axis; array index a_d = global index - (lo_d - g); face
+ * arrays carry one extra entry (index N_d) along their normal, and face index
+ * a is the lower face of cell a.  Every array must hold at least
+ * stride[2] * (N_2 + 1) elements.  Elements are double (MHD_F64) or float
+ * (MHD_F32); flux registers and conservation sums are always double.
+ *
+ * Execution.  Every call that takes a stream enqueues work on it and returns
+ * without synchronising, except mhd_get_device_status and mhd_ctx_destroy.
+ * Arguments that can be checked on the host are checked before anything is
+ * launched; a failed check returns a negative status and launches nothing.
+ * Errors found on the device (a non-positive density or pressure after an
+ * update) set a status word read by mhd_get_device_status; kernels never trap.
+ * A context may be used from one host thread at a time.
+ */
+#ifndef MHD_GPU_H
+#define MHD_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mhd_status;
+#define MHD_OK 0
+#define MHD_EINVAL (-1)    /* bad argument (host check)                      */
+#define MHD_ENOMEM (-2)    /* the library could not allocate its scratch     */
+#define MHD_ECUDA (-3)     /* a CUDA runtime call failed                     */
+#define MHD_ENEGATIVE (-4) /* device: rho <= 0 or p <= 0 after an update      */
+#define MHD_ETIMEOUT (-5)  /* device: a bounded wait gave up                  */
+
+#define MHD_F64 0
+#define MHD_F32 1
+
+typedef struct mhd_ctx mhd_ctx;
+
+/* Inclusive box of cells in a level's global index space. */
+typedef struct {
+  int32_t lo[3], hi[3];
+} mhd_box;
+
+/* One patch (grid, Sec. 2): its interior box on its level, its ghost width
+ * and its arrays.  Pointers are device pointers to elements of `dtype`. */
+typedef struct {
+  int32_t level;     /* refinement level l (dx_l = dx_0 / R^l, Sec. 2)        */
+  int32_t nghost;    /* g: ghost layers on every side                       */
+  int32_t dtype;     /* MHD_F64 or MHD_F32                                  */
+  int32_t patch_id;  /* caller's id, echoed in error messages               */
+  mhd_box interior;  /* cells owned by the patch                            */
+  void *U[5];        /* rho, Mx, My, Mz, E                                  */
+  void *B[3];        /* Bx, By, Bz                                          */
+  int64_t stride[3]; /* element strides; stride[0] must be 1                */
+  double dx[3];      /* cell widths                                         */
+} mhd_patch_desc;
+
+/* Solver constants.  The paper fixes none of them. */
+typedef struct {
+  double gamma;      /* ratio of specific heats, > 1                        */
+  double cfl;        /* Courant number, in (0, 1]                           */
+  int32_t limiter;   /* 0 van Leer harmonic, 1 minmod, 2 monotonised central */
+  int32_t emf;       /* 0 Gardiner-Stone upwinded, 1 arithmetic mean        */
+  double upwind_eps; /* contact speeds |S_M| <= upwind_eps (S_R - S_L) count as
+                        no upwind side in the EMF upwinding; <= 0 selects
+                        1e-10 for MHD_F64 and 1e-5 for MHD_F32 patches      */
+} mhd_params;
+
+/* One ghost-fill copy (Sec. 2.2 "update ghost cells" and Sec. 2.3): the
+ * cells of `box` (global index space of the destination's level) in patch
+ * `dst` receive the values of patch `src` at index + `offset` (a periodic
+ * image shift, or zero), together with the lower face of every box cell
+ * along each axis (and the array's extra upper face where the box reaches the
+ * last cell of an axis), except faces that belong to dst's interior (normal
+ * index in [lo, hi+1], other indices inside the interior).  Source cells must
+ * lie in src's interior.  Boxes of one call must not overlap; every copy of
+ * one call reads only interiors, so the copies are independent. */
+typedef struct {
+  int32_t src, dst;    /* indices into the descriptor array                 */
+  mhd_box box;         /* destination cells                                 */
+  int32_t offset[3];   /* source global index = destination index + offset  */
+} mhd_copy;
+
+/* Context: owns scratch memory and device copies of small host tables on
+ * CUDA device `device`.  *out is NULL on failure. */
+mhd_status mhd_ctx_create(const mhd_params *params, int32_t device, mhd_ctx **out);
+void mhd_ctx_destroy(mhd_ctx *ctx);
+const char *mhd_last_error(const mhd_ctx *ctx);
+
+/* CFL time step (Sec. 2.2 advances with dt_l = dt_{l-1}/R): writes to the
+ * device double *d_dt_out the minimum over patches p and interior cells of
+ *   scale[p] * cfl * min_d dx_d / (|v_d| + c_f,d),
+ * c_f,d the fast magnetosonic speed along d (Bc = mean of the two faces).
+ * scale (host, length n, may be NULL for all ones) is R^level for the
+ * coarse-step dt of a hierarchy.  The minimum is exact (order independent). */
+mhd_status mhd_cfl_dt(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
+                      const double *scale, double *d_dt_out, void *stream);
+
+/* Advance (A of Sec. 2.2) of n patches by one step of dt_p = (*d_dt) *
+ * dt_scale[p] (d_dt a device double, dt_scale host, may be NULL for ones).
+ * Patch p updates its interior grown by grow[p] layers (host array, may be
+ * NULL for zeros) and the face fields on that box; it needs valid data on
+ * the interior grown by grow[p] + 2 and requires grow[p] + 2 <= nghost
+ * (Sec. 2.3: the update box shrinks by n_ghost = 2 per substep).  Patches
+ * must not share memory.  On return the work is enqueued on `stream`. */
+mhd_status mhd_patch_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
+                             const int32_t *grow, const double *d_dt,
+                             const double *dt_scale, void *stream);
+
+/* Ghost fill (Sec. 2.2 S step "update ghost cells"; periodic images and
+ * same-level neighbours): executes the copies of `list` (host array) in one
+ * launch.  All patches of the call must have one dtype. */
+mhd_status mhd_ghost_fill(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
+                          const mhd_copy *list, int32_t nlist, void *stream);
+
+/* Conservation sums over the interiors of n patches (one dtype):
+ * d_out8[q] = sum of U_q dV (q < 5) and of B_{q-5} dV over the lower faces of
+ * interior cells (q >= 5), accumulated in double in a fixed order (the result
+ * is reproducible run to run).  d_out8 is a device array of 8 doubles. */
+mhd_status mhd_conservation_sums(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
+                                 double *d_out8, void *stream);
+
+/* Synchronises the context's device, then returns (and clears) the device
+ * status word in *out: MHD_OK or the first device error raised since the
+ * last call.  The return value reports CUDA failures of the call itself. */
+mhd_status mhd_get_device_status(mhd_ctx *ctx, int32_t *out);
+
+/* Library version and build flags (for logs). */
+const char *mhd_version(void);
+
+/* Number of kernels this context has enqueued so far (for launch accounting). */
+int64_t mhd_launch_count(const mhd_ctx *ctx);
+
+/* Per-kernel event timer (diagnostics, no counterpart in the paper).  While
+ * enabled, every launch of the context is bracketed by two CUDA events
+ * recorded on the launching stream.  mhd_timing_read synchronises on the
+ * pending events and returns, for kernel id `kernel` (0 <= id < 9, names from
+ * mhd_kernel_name), the summed device time in ms and the number of launches
+ * since the last reset; mhd_timing_reset clears the sums. */
+mhd_status mhd_timing_enable(mhd_ctx *ctx, int32_t on);
+mhd_status mhd_timing_read(mhd_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
+mhd_status mhd_timing_reset(mhd_ctx *ctx);
+const char *mhd_kernel_name(int32_t kernel);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_GPU_H */

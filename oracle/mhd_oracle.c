@@ -362,8 +362,13 @@ static int wrap(int a, int g, int n) {
 }
 
 /* Every element whose index lies outside [g, g+n-1] along some axis is copied
- * from the periodic image inside it; a face array's upper boundary face (index
- * g+n along its normal) is the image of the lower one. */
+ * from the periodic image inside it, except the patch's own faces: a face
+ * whose normal index is in [g, g+n] and whose other indices are in [g, g+n-1]
+ * belongs to the interior and is left as the advance computed it (its upper
+ * boundary face equals the image of the lower one because the update does not
+ * depend on position).  A face array's extra entry (index N along its normal)
+ * is the upper face of the image of cell N-1, which for a patch thinner than
+ * its ghost width is the interior's upper boundary face. */
 ORC_EXPORT void orc_fill_periodic(const orc_patch *P) {
   const int g = P->g;
   const int N0 = P->n[0] + 2 * g, N1 = P->n[1] + 2 * g, N2 = P->n[2] + 2 * g;
@@ -375,7 +380,21 @@ ORC_EXPORT void orc_fill_periodic(const orc_patch *P) {
       for (int j = 0; j < ext[1]; ++j)
         for (int i = 0; i < ext[0]; ++i) {
           int si = wrap(i, g, P->n[0]), sj = wrap(j, g, P->n[1]), sk = wrap(k, g, P->n[2]);
+          /* the extra face at index N along the normal is the upper face of
+           * the image of the last cell N-1 */
+          if (a == 5 && i == N0) si = wrap(N0 - 1, g, P->n[0]) + 1;
+          if (a == 6 && j == N1) sj = wrap(N1 - 1, g, P->n[1]) + 1;
+          if (a == 7 && k == N2) sk = wrap(N2 - 1, g, P->n[2]) + 1;
           if (si == i && sj == j && sk == k) continue;
+          if (a >= 5) {
+            int ax = a - 5, id[3] = {i, j, k};
+            int own = 1;
+            for (int e = 0; e < 3; ++e) {
+              int top = (e == ax) ? g + P->n[e] : g + P->n[e] - 1;
+              if (id[e] < g || id[e] > top) own = 0;
+            }
+            if (own) continue;
+          }
           A[ix(P, i, j, k)] = A[ix(P, si, sj, sk)];
         }
   }

@@ -1,0 +1,202 @@
+"""Thin ctypes binding of ``include/mhd_gpu.h`` (``libmhdgpu.so``).
+
+Argument marshalling only: every step of the patch advance runs in the CUDA
+library.  Functions keep the C names (``mhd_patch_advance`` ...) and raise
+``MHDError`` on a negative status.  There is no CPU fallback: importing this
+module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ENEGATIVE, MHD_ETIMEOUT = 0, -1, -2, -3, -4, -5
+MHD_F64, MHD_F32 = 0, 1
+STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
+                -4: "MHD_ENEGATIVE", -5: "MHD_ETIMEOUT"}
+
+# Exported functions of include/mhd_gpu.h (checked against the header by the tests).
+EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", "mhd_patch_advance",
+           "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
+           "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
+           "mhd_kernel_name")
+N_KERNELS = 9
+
+
+class MHDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class mhd_box(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3)]
+
+
+class mhd_patch_desc(C.Structure):
+    _fields_ = [("level", C.c_int32), ("nghost", C.c_int32), ("dtype", C.c_int32),
+                ("patch_id", C.c_int32), ("interior", mhd_box), ("U", C.c_void_p * 5),
+                ("B", C.c_void_p * 3), ("stride", C.c_int64 * 3), ("dx", C.c_double * 3)]
+
+
+class mhd_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
+                ("emf", C.c_int32), ("upwind_eps", C.c_double)]
+
+
+class mhd_copy(C.Structure):
+    _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("box", mhd_box), ("offset", C.c_int32 * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libmhdgpu.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError("libmhdgpu.so is not built: run __graft_entry__.build() "
+                              "(nvcc for sm_103a); there is no CPU fallback")
+        _build.build()
+    L = C.CDLL(_build.LIB)
+    P = C.c_void_p
+    i32, i64 = C.c_int32, C.c_int64
+    dp = C.POINTER(C.c_double)
+    L.mhd_ctx_create.restype = i32
+    L.mhd_ctx_create.argtypes = [C.POINTER(mhd_params), i32, C.POINTER(P)]
+    L.mhd_ctx_destroy.restype = None
+    L.mhd_ctx_destroy.argtypes = [P]
+    L.mhd_last_error.restype = C.c_char_p
+    L.mhd_last_error.argtypes = [P]
+    L.mhd_cfl_dt.restype = i32
+    L.mhd_cfl_dt.argtypes = [P, C.POINTER(mhd_patch_desc), i32, dp, P, P]
+    L.mhd_patch_advance.restype = i32
+    L.mhd_patch_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), P, dp, P]
+    L.mhd_ghost_fill.restype = i32
+    L.mhd_ghost_fill.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_copy), i32, P]
+    L.mhd_conservation_sums.restype = i32
+    L.mhd_conservation_sums.argtypes = [P, C.POINTER(mhd_patch_desc), i32, P, P]
+    L.mhd_get_device_status.restype = i32
+    L.mhd_get_device_status.argtypes = [P, C.POINTER(i32)]
+    L.mhd_version.restype = C.c_char_p
+    L.mhd_version.argtypes = []
+    L.mhd_launch_count.restype = i64
+    L.mhd_launch_count.argtypes = [P]
+    L.mhd_timing_enable.restype = i32
+    L.mhd_timing_enable.argtypes = [P, i32]
+    L.mhd_timing_read.restype = i32
+    L.mhd_timing_read.argtypes = [P, i32, dp, C.POINTER(i64)]
+    L.mhd_timing_reset.restype = i32
+    L.mhd_timing_reset.argtypes = [P]
+    L.mhd_kernel_name.restype = C.c_char_p
+    L.mhd_kernel_name.argtypes = [i32]
+    _lib = L
+    return L
+
+
+def _check(ctx, r):
+    if r != MHD_OK:
+        msg = load().mhd_last_error(ctx).decode() if ctx else ""
+        raise MHDError(r, msg)
+
+
+def _arr(ctype, seq):
+    seq = list(seq)
+    a = (ctype * max(1, len(seq)))()
+    for i, v in enumerate(seq):
+        a[i] = v
+    return a
+
+
+def _descs(patches):
+    ds = list(patches)
+    arr = (mhd_patch_desc * max(1, len(ds)))(*ds)
+    return arr, len(ds)
+
+
+# ------------------------------------------------------------------ C names
+def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0):
+    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps)
+    out = C.c_void_p()
+    r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
+    _check(None, r)
+    return out.value
+
+
+def mhd_ctx_destroy(ctx) -> None:
+    load().mhd_ctx_destroy(ctx)
+
+
+def mhd_last_error(ctx) -> str:
+    return load().mhd_last_error(ctx).decode()
+
+
+def mhd_version() -> str:
+    return load().mhd_version().decode()
+
+
+def mhd_launch_count(ctx) -> int:
+    return int(load().mhd_launch_count(ctx))
+
+
+def mhd_cfl_dt(ctx, patches, d_dt_out: int, stream: int = 0, scale=None) -> None:
+    arr, n = _descs(patches)
+    sc = _arr(C.c_double, scale) if scale is not None else None
+    _check(ctx, load().mhd_cfl_dt(ctx, arr, n, sc, d_dt_out, stream))
+
+
+def mhd_patch_advance(ctx, patches, d_dt: int, stream: int = 0, grow=None, dt_scale=None) -> None:
+    arr, n = _descs(patches)
+    gr = _arr(C.c_int32, grow) if grow is not None else None
+    sc = _arr(C.c_double, dt_scale) if dt_scale is not None else None
+    _check(ctx, load().mhd_patch_advance(ctx, arr, n, gr, d_dt, sc, stream))
+
+
+def mhd_ghost_fill(ctx, patches, copies, stream: int = 0) -> None:
+    arr, n = _descs(patches)
+    cl = list(copies)
+    carr = (mhd_copy * max(1, len(cl)))(*cl)
+    _check(ctx, load().mhd_ghost_fill(ctx, arr, n, carr, len(cl), stream))
+
+
+def mhd_conservation_sums(ctx, patches, d_out8: int, stream: int = 0) -> None:
+    arr, n = _descs(patches)
+    _check(ctx, load().mhd_conservation_sums(ctx, arr, n, d_out8, stream))
+
+
+def mhd_get_device_status(ctx) -> int:
+    v = C.c_int32(0)
+    _check(ctx, load().mhd_get_device_status(ctx, C.byref(v)))
+    return int(v.value)
+
+
+def mhd_timing_enable(ctx, on: bool = True) -> None:
+    _check(ctx, load().mhd_timing_enable(ctx, 1 if on else 0))
+
+
+def mhd_timing_reset(ctx) -> None:
+    _check(ctx, load().mhd_timing_reset(ctx))
+
+
+def mhd_kernel_name(kernel: int) -> str:
+    return load().mhd_kernel_name(kernel).decode()
+
+
+def mhd_timing_read(ctx) -> dict:
+    """{kernel name: (total ms, launches)} since the last reset."""
+    out = {}
+    for k in range(N_KERNELS):
+        ms = C.c_double(0.0)
+        n = C.c_int64(0)
+        _check(ctx, load().mhd_timing_read(ctx, k, C.byref(ms), C.byref(n)))
+        out[mhd_kernel_name(k)] = (float(ms.value), int(n.value))
+    return out

@@ -1,0 +1,370 @@
+// advance.cuh -- the staged patch advance (A of the paper's Sec. 2.2 life
+// cycle) over a batch of patches, templated on the arithmetic type R.
+//
+// One step of a patch updates the cells of its update box UB = interior grown
+// by k layers (Sec. 2.3 extended ghosts) and the faces of those cells; it reads
+// data on UB grown by 2.  Six kernels, each one thread per element, every
+// block working inside one patch (BlockTask):
+//   k_prim    UB+2 cells : primitives W, cell EMF E^n = -v x Bc
+//   k_pred    UB+1 cells : limited slopes, face values, positivity rule,
+//                          Hancock predictor, predicted face states, E_ref
+//   k_edge    edges      : E^n at cell edges (mean of the four cells)
+//   k_flux    faces      : CT half-step normal field, HLLD flux, contact side
+//   k_emf     UB edges   : Gardiner-Stone (or arithmetic) edge EMF
+//   k_update  UB         : conservative cell update and CT face update
+// Intermediates live in a per-patch scratch region with the patch's own
+// strides, so every stage addresses them like the state arrays.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "physics.cuh"
+
+namespace mhd {
+
+template <typename R> struct SolverConsts {
+  R gamma, gm1, igm1, eps_up;
+  int limiter, emf;
+};
+
+struct Cell {
+  int i, j, k;
+};
+
+// Decomposes element e of the UB+2 launch region of patch p; false if e is
+// beyond the region.
+__device__ __forceinline__ bool launch_cell(const DPatch& p, int e, Cell& c) {
+  const int ex = p.n[0] + 2 * p.k + 4, ey = p.n[1] + 2 * p.k + 4, ez = p.n[2] + 2 * p.k + 4;
+  if (e >= ex * ey * ez) return false;
+  const int lo = p.g - p.k - 2;
+  c.i = lo + e % ex;
+  c.j = lo + (e / ex) % ey;
+  c.k = lo + e / (ex * ey);
+  return true;
+}
+
+// Is index v along axis d inside [lo_d + a, hi_d + b] of the update box?
+__device__ __forceinline__ bool in_ub(const DPatch& p, int d, int v, int a, int b) {
+  const int lo = p.g - p.k, hi = p.g + p.n[d] - 1 + p.k;
+  return v >= lo + a && v <= hi + b;
+}
+
+__device__ __forceinline__ int64_t lin(const DPatch& p, const Cell& c) {
+  return (int64_t)c.i + (int64_t)c.j * p.s1 + (int64_t)c.k * p.s2;
+}
+
+__device__ __forceinline__ int64_t stride_of(const DPatch& p, int d) {
+  return d == 0 ? (int64_t)1 : (d == 1 ? p.s1 : p.s2);
+}
+
+template <typename R> __device__ __forceinline__ R* arr(R* scr, const DPatch& p, int a) {
+  return scr + p.scr + (int64_t)a * p.nelem;
+}
+
+__device__ __forceinline__ void raise_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+template <typename R> struct StepDt {
+  R dt, hdtdx[3], dtdx[3];
+  __device__ __forceinline__ StepDt(const DPatch& p, const double* d_dt) {
+    dt = (R)((*d_dt) * p.dt_scale);
+    R hdt = R(0.5) * dt;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      hdtdx[d] = hdt / (R)p.dx[d];
+      dtdx[d] = dt / (R)p.dx[d];
+    }
+  }
+};
+
+// ---------------------------------------------------------------- k_prim
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr,
+                                                   SolverConsts<R> sc, int* status) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const int64_t x = lin(p, c);
+  const R* U0 = (const R*)p.U[0];
+  R u[8];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = ((const R*)p.U[q])[x];
+  u[5] = R(0.5) * (((const R*)p.B[0])[x] + ((const R*)p.B[0])[x + 1]);
+  u[6] = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
+  u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
+  (void)U0;
+  R w[8];
+  cons2prim(u, sc.gm1, w);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) arr(scr, p, SC_W + q)[x] = w[q];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    arr(scr, p, SC_EN + a)[x] = w[1 + cc] * w[5 + b] - w[1 + b] * w[5 + cc];
+  }
+  if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
+}
+
+// ---------------------------------------------------------------- k_pred
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr,
+                                                   SolverConsts<R> sc, const double* d_dt) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1)) return;
+  const StepDt<R> st(p, d_dt);
+  const int64_t x = lin(p, c);
+  R w[8], dw[3][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) w[q] = arr(scr, p, SC_W + q)[x];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t sd = stride_of(p, d);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const R* Wq = arr(scr, p, SC_W + q);
+      R a = w[q] - Wq[x - sd];
+      R b = Wq[x + sd] - w[q];
+      dw[d][q] = limiter(sc.limiter, a, b);
+    }
+  }
+  // first positivity rule on the face values of rho and p
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R rm = w[0] - R(0.5) * dw[d][0], rp = w[0] + R(0.5) * dw[d][0];
+    R pm = w[4] - R(0.5) * dw[d][4], pp = w[4] + R(0.5) * dw[d][4];
+    if (!(rm > R(0)) || !(rp > R(0)) || !(pm > R(0)) || !(pp > R(0))) bad = true;
+  }
+  // Hancock increment
+  R du[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) du[q] = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R fwm[8], fwp[8], fm[8], fp[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      fwm[q] = bad ? w[q] : w[q] - R(0.5) * dw[d][q];
+      fwp[q] = bad ? w[q] : w[q] + R(0.5) * dw[d][q];
+    }
+    flux_xyz(d, fwp, sc.igm1, fp);
+    flux_xyz(d, fwm, sc.igm1, fm);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) du[q] = du[q] - st.hdtdx[d] * (fp[q] - fm[q]);
+  }
+  // predicted face states and the second positivity rule
+  bool bad2 = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      R fw[8], u[8], pw[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        fw[q] = bad ? w[q] : (sd ? w[q] + R(0.5) * dw[d][q] : w[q] - R(0.5) * dw[d][q]);
+      prim2cons(fw, sc.igm1, u);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) u[q] = u[q] + du[q];
+      cons2prim(u, sc.gm1, pw);
+      if (!(pw[0] > R(0)) || !(pw[4] > R(0))) bad2 = true;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + (d * 2 + sd) * 8 + q)[x] = pw[q];
+    }
+  }
+  if (bad2) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + f * 8 + q)[x] = w[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) du[q] = R(0);
+  }
+  // reference cell EMF from U^{n+1/2}
+  R uc[8], uh[8];
+  prim2cons(w, sc.igm1, uc);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) uh[q] = uc[q] + du[q];
+  R ir = R(1) / uh[0];
+  R v[3] = {uh[1] * ir, uh[2] * ir, uh[3] * ir};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    arr(scr, p, SC_ER + a)[x] = v[cc] * uh[5 + b] - v[b] * uh[5 + cc];
+  }
+}
+
+// ---------------------------------------------------------------- k_edge
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const int a = blockIdx.y;
+  const int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
+  const int64_t x = lin(p, c);
+  const int64_t sb = stride_of(p, b), sc_ = stride_of(p, cc);
+  const R* En = arr(scr, p, SC_EN + a);
+  R e00 = En[x - sb - sc_];
+  R e10 = En[x - sc_];
+  R e01 = En[x - sb];
+  R e11 = En[x];
+  arr(scr, p, SC_EE + a)[x] = R(0.25) * (e00 + e10 + e01 + e11);
+}
+
+// ---------------------------------------------------------------- k_flux
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr,
+                                                   SolverConsts<R> sc, const double* d_dt) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const int d = blockIdx.y;
+  const int b = (d + 1) % 3, cc = (d + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  if (!in_ub(p, d, id[d], 0, 1) || !in_ub(p, b, id[b], -1, 1) || !in_ub(p, cc, id[cc], -1, 1)) return;
+  const StepDt<R> st(p, d_dt);
+  const int64_t x = lin(p, c);
+  const int64_t sd = stride_of(p, d), sb = stride_of(p, b), scc = stride_of(p, cc);
+  // CT half step of the face-normal field
+  R dEc = arr(scr, p, SC_EE + cc)[x + sb] - arr(scr, p, SC_EE + cc)[x];
+  R dEb = arr(scr, p, SC_EE + b)[x + scc] - arr(scr, p, SC_EE + b)[x];
+  R bh = ((const R*)p.B[d])[x] - (st.hdtdx[b] * dEc - st.hdtdx[cc] * dEb);
+  R wl[8], wr[8], L[8], Rr[8], fr[8], f[8], upw;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    wl[q] = arr(scr, p, SC_WF + (d * 2 + 1) * 8 + q)[x - sd];
+    wr[q] = arr(scr, p, SC_WF + (d * 2 + 0) * 8 + q)[x];
+  }
+  rot_in(d, wl, L);
+  rot_in(d, wr, Rr);
+  hlld(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
+  rot_out(d, fr, f);
+  f[5 + d] = upw;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) arr(scr, p, SC_F + d * 8 + q)[x] = f[q];
+}
+
+// ---------------------------------------------------------------- k_emf
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
+                                                  const BlockTask* __restrict__ T, R* scr,
+                                                  SolverConsts<R> sc) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const int a = blockIdx.y;
+  const int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  if (!in_ub(p, a, id[a], 0, 0) || !in_ub(p, b, id[b], 0, 1) || !in_ub(p, cc, id[cc], 0, 1)) return;
+  const int64_t x = lin(p, c);
+  const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
+  const R* Fbc = arr(scr, p, SC_F + b * 8 + 5 + cc);
+  const R* Fcb = arr(scr, p, SC_F + cc * 8 + 5 + b);
+  R eb_lo = -Fbc[x - scc];
+  R eb_hi = -Fbc[x];
+  R ec_lo = Fcb[x - sb];
+  R ec_hi = Fcb[x];
+  R avg = R(0.25) * (eb_lo + eb_hi + ec_lo + ec_hi);
+  R* Ed = arr(scr, p, SC_ED + a);
+  if (sc.emf == 1) {
+    Ed[x] = avg;
+    return;
+  }
+  const R* Er = arr(scr, p, SC_ER + a);
+  R r00 = Er[x - sb - scc];
+  R r10 = Er[x - scc];
+  R r01 = Er[x - sb];
+  R r11 = Er[x];
+  const R* Ub = arr(scr, p, SC_F + b * 8 + 5 + b);
+  const R* Uc = arr(scr, p, SC_F + cc * 8 + 5 + cc);
+  R mb_lo = Ub[x - scc];
+  R mb_hi = Ub[x];
+  R mc_lo = Uc[x - sb];
+  R mc_hi = Uc[x];
+  R dc14, dc34, db14, db34;
+  if (mb_hi > R(0)) dc14 = r01 - ec_lo;
+  else if (mb_hi < R(0)) dc14 = r11 - ec_hi;
+  else dc14 = R(0.5) * ((r01 - ec_lo) + (r11 - ec_hi));
+  if (mb_lo > R(0)) dc34 = ec_lo - r00;
+  else if (mb_lo < R(0)) dc34 = ec_hi - r10;
+  else dc34 = R(0.5) * ((ec_lo - r00) + (ec_hi - r10));
+  if (mc_hi > R(0)) db14 = r10 - eb_lo;
+  else if (mc_hi < R(0)) db14 = r11 - eb_hi;
+  else db14 = R(0.5) * ((r10 - eb_lo) + (r11 - eb_hi));
+  if (mc_lo > R(0)) db34 = eb_lo - r00;
+  else if (mc_lo < R(0)) db34 = eb_hi - r01;
+  else db34 = R(0.5) * ((eb_lo - r00) + (eb_hi - r01));
+  Ed[x] = avg + R(0.25) * (dc34 - dc14 + db34 - db14);
+}
+
+// ---------------------------------------------------------------- k_update
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ P,
+                                                     const BlockTask* __restrict__ T, R* scr,
+                                                     const double* d_dt) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const StepDt<R> st(p, d_dt);
+  const int64_t x = lin(p, c);
+  const int id[3] = {c.i, c.j, c.k};
+  if (in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const R* F0 = arr(scr, p, SC_F + 0 * 8 + q);
+      const R* F1 = arr(scr, p, SC_F + 1 * 8 + q);
+      const R* F2 = arr(scr, p, SC_F + 2 * 8 + q);
+      R* Uq = (R*)p.U[q];
+      R u = Uq[x];
+      u = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + p.s1] - F1[x]) -
+          st.dtdx[2] * (F2[x + p.s2] - F2[x]);
+      Uq[x] = u;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    if (!in_ub(p, a, id[a], 0, 1) || !in_ub(p, b, id[b], 0, 0) || !in_ub(p, cc, id[cc], 0, 0)) continue;
+    const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
+    const R* Ec = arr(scr, p, SC_ED + cc);
+    const R* Eb = arr(scr, p, SC_ED + b);
+    R dEc = Ec[x + sb] - Ec[x];
+    R dEb = Eb[x + scc] - Eb[x];
+    R* Ba = (R*)p.B[a];
+    Ba[x] = Ba[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
+  }
+}
+
+// Enqueues the six stages for the patches of one call.
+template <typename R>
+cudaError_t launch_advance(const DPatch* d_patches, const BlockTask* d_tasks, int nblocks, R* scr,
+                           const SolverConsts<R>& sc, const double* d_dt, int* d_status,
+                           const KernelTimer* tm, cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  dim3 g1(nblocks), g3(nblocks, 3);
+  MHD_TIMED(tm, K_PRIM, s, (k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
+  MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_dt)));
+  MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
+  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_dt)));
+  MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
+  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, d_dt)));
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

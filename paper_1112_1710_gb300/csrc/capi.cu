@@ -1,0 +1,504 @@
+// capi.cu -- the C ABI of include/mhd_gpu.h: argument checks, the context
+// (scratch arena, status word, device copies of descriptor tables), and the
+// dispatch to the kernel translation units.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+#include "mhd_gpu.h"
+
+using namespace mhd;
+
+namespace {
+
+// A device copy of a small host table, keyed by its bytes.  Entries are
+// immutable once uploaded, so a launch may still be reading one while the
+// host prepares the next call; repeated calls with the same descriptors
+// (every step of a static hierarchy) upload nothing.
+struct TableEntry {
+  std::vector<char> bytes;
+  void* dev = nullptr;
+};
+
+uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* c = (const unsigned char*)p;
+  uint64_t h = 1469598103934665603ULL;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+}  // namespace
+
+struct mhd_ctx {
+  mhd_params prm;
+  int device = 0;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double* partials = nullptr;
+  size_t partials_n = 0;
+  int* d_status = nullptr;
+  std::string err;
+  std::unordered_multimap<uint64_t, TableEntry> tables;
+  size_t table_bytes = 0;
+  int64_t launches = 0;
+  // per-kernel event timer
+  bool timing = false;
+  struct Mark {
+    int kernel;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Mark> marks;
+  double kernel_ms[K_COUNT] = {};
+  int64_t kernel_n[K_COUNT] = {};
+  KernelTimer timer{};
+};
+
+namespace {
+
+constexpr size_t kTableCacheLimit = size_t(256) << 20;
+
+mhd_status fail(mhd_ctx* c, mhd_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+mhd_status cuda_fail(mhd_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, MHD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Returns a device pointer holding `n` bytes equal to `host`.
+mhd_status table(mhd_ctx* c, const void* host, size_t n, void** out) {
+  if (n == 0) {
+    *out = nullptr;
+    return MHD_OK;
+  }
+  const uint64_t h = fnv1a(host, n);
+  auto range = c->tables.equal_range(h);
+  for (auto it = range.first; it != range.second; ++it) {
+    if (it->second.bytes.size() == n && std::memcmp(it->second.bytes.data(), host, n) == 0) {
+      *out = it->second.dev;
+      return MHD_OK;
+    }
+  }
+  if (c->table_bytes + n > kTableCacheLimit) {
+    // drop every cached table; launches in flight may still read them
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "table cache flush");
+    for (auto& kv : c->tables) cudaFree(kv.second.dev);
+    c->tables.clear();
+    c->table_bytes = 0;
+  }
+  TableEntry t;
+  t.bytes.assign((const char*)host, (const char*)host + n);
+  cudaError_t e = cudaMalloc(&t.dev, n);
+  if (e != cudaSuccess) return fail(c, MHD_ENOMEM, "table alloc of %zu bytes: %s", n, cudaGetErrorString(e));
+  // synchronous copy: the entry is immutable from here on
+  e = cudaMemcpy(t.dev, host, n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(t.dev);
+    return cuda_fail(c, e, "table upload");
+  }
+  *out = t.dev;
+  c->table_bytes += n;
+  c->tables.emplace(h, std::move(t));
+  return MHD_OK;
+}
+
+mhd_status ensure_scratch(mhd_ctx* c, size_t bytes) {
+  if (bytes <= c->scratch_bytes) return MHD_OK;
+  if (c->scratch) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "scratch resize");
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&c->scratch, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MHD_ENOMEM, "scratch alloc of %zu bytes: %s", want, cudaGetErrorString(e));
+  }
+  c->scratch_bytes = want;
+  return MHD_OK;
+}
+
+mhd_status ensure_partials(mhd_ctx* c, size_t n) {
+  if (n <= c->partials_n) return MHD_OK;
+  if (c->partials) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "partials resize");
+    cudaFree(c->partials);
+    c->partials = nullptr;
+  }
+  cudaError_t e = cudaMalloc(&c->partials, n * 8 * sizeof(double));
+  if (e != cudaSuccess) return fail(c, MHD_ENOMEM, "partials alloc: %s", cudaGetErrorString(e));
+  c->partials_n = n;
+  return MHD_OK;
+}
+
+size_t elem_size(int dtype) { return dtype == MHD_F64 ? 8 : 4; }
+
+// Host checks of one descriptor and its conversion to the device form.
+mhd_status convert(mhd_ctx* c, const mhd_patch_desc& d, int idx, DPatch& o) {
+  if (d.dtype != MHD_F64 && d.dtype != MHD_F32)
+    return fail(c, MHD_EINVAL, "patch %d (id %d): dtype %d", idx, d.patch_id, d.dtype);
+  if (d.nghost < 0 || d.nghost > 64)
+    return fail(c, MHD_EINVAL, "patch %d (id %d): nghost %d", idx, d.patch_id, d.nghost);
+  if (d.stride[0] != 1)
+    return fail(c, MHD_EINVAL, "patch %d (id %d): stride[0] must be 1", idx, d.patch_id);
+  std::memset(&o, 0, sizeof o);
+  int64_t N[3];
+  for (int a = 0; a < 3; ++a) {
+    int64_t n = (int64_t)d.interior.hi[a] - d.interior.lo[a] + 1;
+    if (n < 1 || n > (1 << 20))
+      return fail(c, MHD_EINVAL, "patch %d (id %d): empty or huge interior along axis %d", idx, d.patch_id, a);
+    N[a] = n + 2 * d.nghost;
+    o.n[a] = (int32_t)n;
+    o.N[a] = (int32_t)N[a];
+    o.glo[a] = d.interior.lo[a] - d.nghost;
+    if (!(d.dx[a] > 0.0))
+      return fail(c, MHD_EINVAL, "patch %d (id %d): dx[%d] must be > 0", idx, d.patch_id, a);
+    o.dx[a] = d.dx[a];
+  }
+  if (d.stride[1] < N[0] + 1 || d.stride[2] < d.stride[1] * (N[1] + 1))
+    return fail(c, MHD_EINVAL, "patch %d (id %d): strides too small for the face arrays", idx, d.patch_id);
+  if (N[0] * N[1] * N[2] > (int64_t)1 << 31)
+    return fail(c, MHD_EINVAL, "patch %d (id %d): more than 2^31 cells", idx, d.patch_id);
+  for (int q = 0; q < 5; ++q) {
+    if (!d.U[q]) return fail(c, MHD_EINVAL, "patch %d (id %d): U[%d] is NULL", idx, d.patch_id, q);
+    o.U[q] = d.U[q];
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (!d.B[a]) return fail(c, MHD_EINVAL, "patch %d (id %d): B[%d] is NULL", idx, d.patch_id, a);
+    o.B[a] = d.B[a];
+  }
+  o.s1 = d.stride[1];
+  o.s2 = d.stride[2];
+  o.nelem = d.stride[2] * (N[2] + 1);
+  o.g = d.nghost;
+  o.dt_scale = 1.0;
+  o.cfl_scale = 1.0;
+  return MHD_OK;
+}
+
+mhd_status begin(mhd_ctx* c) {
+  if (!c) return MHD_EINVAL;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return MHD_OK;
+}
+
+// block table over a per-patch element count
+void tasks_for(const std::vector<int64_t>& counts, std::vector<BlockTask>& out) {
+  out.clear();
+  for (size_t p = 0; p < counts.size(); ++p)
+    for (int64_t s = 0; s < counts[p]; s += kThreads) out.push_back(BlockTask{(int32_t)p, (int32_t)s});
+}
+
+double eps_for(const mhd_params& prm, int dtype) {
+  if (prm.upwind_eps > 0.0) return prm.upwind_eps;
+  return dtype == MHD_F64 ? 1e-10 : 1e-5;
+}
+
+void timer_mark(void* self, int kernel, int phase, cudaStream_t s) {
+  mhd_ctx* c = (mhd_ctx*)self;
+  if (phase == 0) {
+    mhd_ctx::Mark m{kernel, nullptr, nullptr};
+    cudaEventCreate(&m.start);
+    cudaEventCreate(&m.stop);
+    cudaEventRecord(m.start, s);
+    c->marks.push_back(m);
+  } else {
+    cudaEventRecord(c->marks.back().stop, s);
+  }
+}
+
+const KernelTimer* timer_of(mhd_ctx* c) { return c->timing ? &c->timer : nullptr; }
+
+const char* const kKernelNames[K_COUNT] = {"k_prim", "k_pred", "k_edge", "k_flux", "k_emf",
+                                            "k_update", "k_cfl", "k_ghost", "k_sums"};
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_version(void) {
+  return "mhdgpu 0.1 sm_103a (fp64 --fmad=false, fp32 --fmad=true)";
+}
+
+mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** out) {
+  if (!out) return MHD_EINVAL;
+  *out = nullptr;
+  if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
+      params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1)
+    return MHD_EINVAL;
+  mhd_ctx* c = new mhd_ctx();
+  c->prm = *params;
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return MHD_ECUDA;
+  }
+  *out = c;
+  return MHD_OK;
+}
+
+void mhd_ctx_destroy(mhd_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : c->tables) cudaFree(kv.second.dev);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->partials) cudaFree(c->partials);
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+}
+
+const char* mhd_last_error(const mhd_ctx* c) {
+  return c ? c->err.c_str() : "no context";
+}
+
+int64_t mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : 0; }
+
+mhd_status mhd_timing_enable(mhd_ctx* c, int32_t on) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  c->timing = on != 0;
+  c->timer.self = c;
+  c->timer.mark = timer_mark;
+  return MHD_OK;
+}
+
+mhd_status mhd_timing_read(mhd_ctx* c, int32_t kernel, double* total_ms, int64_t* launches) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (kernel < 0 || kernel >= K_COUNT || !total_ms || !launches) return fail(c, MHD_EINVAL, "bad kernel id");
+  for (auto& m : c->marks) {
+    cudaError_t e = cudaEventSynchronize(m.stop);
+    if (e != cudaSuccess) return cuda_fail(c, e, "timing event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m.start, m.stop);
+    c->kernel_ms[m.kernel] += ms;
+    c->kernel_n[m.kernel] += 1;
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
+  c->marks.clear();
+  *total_ms = c->kernel_ms[kernel];
+  *launches = c->kernel_n[kernel];
+  return MHD_OK;
+}
+
+mhd_status mhd_timing_reset(mhd_ctx* c) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  double ms;
+  int64_t n;
+  if ((r = mhd_timing_read(c, 0, &ms, &n))) return r;
+  for (int k = 0; k < K_COUNT; ++k) {
+    c->kernel_ms[k] = 0.0;
+    c->kernel_n[k] = 0;
+  }
+  return MHD_OK;
+}
+
+const char* mhd_kernel_name(int32_t kernel) {
+  return (kernel >= 0 && kernel < K_COUNT) ? kKernelNames[kernel] : "";
+}
+
+mhd_status mhd_get_device_status(mhd_ctx* c, int32_t* out) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (!out) return fail(c, MHD_EINVAL, "out is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "device status sync");
+  int v = 0;
+  e = cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(c, e, "device status read");
+  *out = v;
+  return MHD_OK;
+}
+
+mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n,
+                             const int32_t* grow, const double* d_dt, const double* dt_scale,
+                             void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
+  if (!d_dt) return fail(c, MHD_EINVAL, "d_dt is NULL");
+  if (n == 0) return MHD_OK;
+  std::vector<DPatch> dp(n);
+  std::vector<int64_t> counts(n);
+  const int dtype = patches[0].dtype;
+  int64_t off = 0;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+    const int k = grow ? grow[p] : 0;
+    if (k < 0 || k + 2 > patches[p].nghost)
+      return fail(c, MHD_EINVAL, "patch %d (id %d): grow %d needs grow + 2 <= nghost (%d)", p,
+                  patches[p].patch_id, k, patches[p].nghost);
+    if (dt_scale && !(dt_scale[p] > 0.0)) return fail(c, MHD_EINVAL, "dt_scale[%d] must be > 0", p);
+    dp[p].k = k;
+    dp[p].dt_scale = dt_scale ? dt_scale[p] : 1.0;
+    dp[p].scr = off;
+    off += (int64_t)SC_COUNT * dp[p].nelem;
+    counts[p] = (int64_t)(dp[p].n[0] + 2 * k + 4) * (dp[p].n[1] + 2 * k + 4) * (dp[p].n[2] + 2 * k + 4);
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  if ((r = ensure_scratch(c, (size_t)off * elem_size(dtype)))) return r;
+  void *d_p = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  AdvanceArgs a;
+  a.patches = (const DPatch*)d_p;
+  a.tasks = (const BlockTask*)d_t;
+  a.nblocks = (int)tasks.size();
+  a.scratch = c->scratch;
+  a.gamma = c->prm.gamma;
+  a.eps_up = eps_for(c->prm, dtype);
+  a.limiter = c->prm.limiter;
+  a.emf = c->prm.emf;
+  a.d_dt = d_dt;
+  a.d_status = c->d_status;
+  a.timer = timer_of(c);
+  cudaError_t e = dtype == MHD_F64 ? advance_f64(a, (cudaStream_t)stream) : advance_f32(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
+  c->launches += 6;
+  return MHD_OK;
+}
+
+mhd_status mhd_cfl_dt(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const double* scale,
+                      double* d_dt_out, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches) return fail(c, MHD_EINVAL, "cfl_dt needs at least one patch");
+  if (!d_dt_out) return fail(c, MHD_EINVAL, "d_dt_out is NULL");
+  std::vector<DPatch> dp(n);
+  std::vector<int64_t> counts(n);
+  const int dtype = patches[0].dtype;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+    if (scale && !(scale[p] > 0.0)) return fail(c, MHD_EINVAL, "scale[%d] must be > 0", p);
+    dp[p].cfl_scale = scale ? scale[p] : 1.0;
+    counts[p] = (int64_t)dp[p].n[0] * dp[p].n[1] * dp[p].n[2];
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_p = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = cfl_dt_launch(dtype, (const DPatch*)d_p, (const BlockTask*)d_t, (int)tasks.size(),
+                                c->prm.gamma, c->prm.cfl, d_dt_out, c->d_status, timer_of(c),
+                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cfl_dt launch");
+  c->launches += tasks.empty() ? 1 : 2;
+  return MHD_OK;
+}
+
+mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const mhd_copy* list,
+                          int32_t nlist, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !patches) || nlist < 0 || (nlist > 0 && !list))
+    return fail(c, MHD_EINVAL, "bad arguments");
+  if (nlist == 0) return MHD_OK;
+  std::vector<DPatch> dp(n);
+  const int dtype = n > 0 ? patches[0].dtype : 0;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  std::vector<DCopy> dc(nlist);
+  std::vector<int64_t> counts(nlist);
+  for (int t = 0; t < nlist; ++t) {
+    const mhd_copy& m = list[t];
+    if (m.src < 0 || m.src >= n || m.dst < 0 || m.dst >= n)
+      return fail(c, MHD_EINVAL, "copy %d: patch index out of range", t);
+    const DPatch& D = dp[m.dst];
+    const DPatch& S = dp[m.src];
+    DCopy& o = dc[t];
+    o.src = m.src;
+    o.dst = m.dst;
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a] - D.glo[a], hi = m.box.hi[a] - D.glo[a];
+      if (hi < lo || lo < 0 || hi >= D.N[a])
+        return fail(c, MHD_EINVAL, "copy %d: box outside the destination's arrays along axis %d", t, a);
+      // source cells (and the upper face of the last one) must lie in src's interior
+      const int slo = m.box.lo[a] + m.offset[a] - S.glo[a], shi = m.box.hi[a] + m.offset[a] - S.glo[a];
+      if (slo < S.g || shi > S.g + S.n[a] - 1)
+        return fail(c, MHD_EINVAL, "copy %d: source outside the source interior along axis %d", t, a);
+      o.lo[a] = lo;
+      o.ext[a] = hi - lo + 1;
+      o.off[a] = (m.box.lo[a] + m.offset[a] - S.glo[a]) - lo;
+      cnt *= o.ext[a];
+    }
+    o.start = 0;
+    counts[t] = cnt;
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_p = nullptr, *d_c = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, dc.data(), dc.size() * sizeof(DCopy), &d_c))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = ghost_fill_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, (const BlockTask*)d_t,
+                                    (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ghost fill launch");
+  c->launches += 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_conservation_sums(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, double* d_out8,
+                                 void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches || !d_out8) return fail(c, MHD_EINVAL, "bad arguments");
+  std::vector<DPatch> dp(n);
+  std::vector<int64_t> counts(n);
+  const int dtype = patches[0].dtype;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+    counts[p] = (int64_t)dp[p].n[0] * dp[p].n[1] * dp[p].n[2];
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  if ((r = ensure_partials(c, tasks.size()))) return r;
+  void *d_p = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = sums_launch(dtype, (const DPatch*)d_p, (const BlockTask*)d_t, (int)tasks.size(),
+                              c->partials, d_out8, timer_of(c), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sums launch");
+  c->launches += 2;
+  return MHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// common.cuh -- device-side descriptors shared by the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mhd {
+
+// Device copy of one patch for a launch.  Array index a_d of a cell runs over
+// [0, N_d); the interior is [g, g + n_d).  All eight arrays share s1 (y
+// stride) and s2 (z stride); the x stride is 1.
+struct DPatch {
+  void* U[5];
+  void* B[3];
+  int64_t s1, s2;
+  int64_t nelem;     // elements of one array (s2 * (N_2 + 1))
+  int64_t scr;       // offset of this patch's scratch in the arena (elements)
+  int32_t n[3];      // interior cells
+  int32_t N[3];      // cells including ghosts
+  int32_t g;         // ghost layers
+  int32_t k;         // update box = interior grown by k
+  int32_t glo[3];    // global index of array index 0 (interior lo - g)
+  int32_t pad;
+  double dx[3];
+  double dt_scale;   // dt of this patch = (*d_dt) * dt_scale
+  double cfl_scale;  // scale factor of the CFL candidate dt
+};
+
+// One block of a batched launch: the patch it works on and the first linear
+// element (within that patch's launch region) of its threads.
+struct BlockTask {
+  int32_t patch;
+  int32_t start;
+};
+
+// One ghost-fill copy, resolved to array indices of both patches.
+struct DCopy {
+  int32_t src, dst;
+  int32_t lo[3];     // destination array indices of the box corner
+  int32_t ext[3];    // box extents
+  int32_t off[3];    // source array index = destination array index + off
+  int32_t start;     // first linear element of this copy in the launch
+};
+
+// scratch arrays of the staged advance (offsets in units of one array)
+enum : int {
+  SC_W = 0,      // 8 primitives on UB+2
+  SC_EN = 8,     // 3 cell-centred E^n = -v x Bc on UB+2
+  SC_WF = 11,    // 48 predicted face states (d, side, q) on UB+1
+  SC_ER = 59,    // 3 reference cell EMFs from U^{n+1/2} on UB+1
+  SC_EE = 62,    // 3 edge E^n averages
+  SC_F = 65,     // 24 face fluxes (d, q); slot 5+d holds the contact side
+  SC_ED = 89,    // 3 edge EMFs of the update
+  SC_COUNT = 92
+};
+
+constexpr int kThreads = 256;
+
+// Kernel ids of the per-kernel event timer (mhd_timing_*).
+enum KernelId : int {
+  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_COUNT
+};
+
+// Optional hook that records CUDA events around each launch on its stream.
+struct KernelTimer {
+  void* self;
+  void (*mark)(void* self, int kernel, int phase, cudaStream_t s);
+};
+
+#define MHD_TIMED(tm, id, s, launch)                      \
+  do {                                                     \
+    if (tm) (tm)->mark((tm)->self, (id), 0, (s));          \
+    launch;                                                \
+    if (tm) (tm)->mark((tm)->self, (id), 1, (s));          \
+  } while (0)
+
+}  // namespace mhd

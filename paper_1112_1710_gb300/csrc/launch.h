@@ -1,0 +1,39 @@
+// launch.h -- host entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mhd {
+
+struct AdvanceArgs {
+  const DPatch* patches;   // device
+  const BlockTask* tasks;  // device
+  int nblocks;
+  void* scratch;           // device arena of the call's element type
+  double gamma, eps_up;
+  int limiter, emf;
+  const double* d_dt;      // device
+  int* d_status;           // device
+  const KernelTimer* timer;  // nullable
+};
+
+cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);
+cudaError_t advance_f32(const AdvanceArgs& a, cudaStream_t s);
+
+// CFL candidate minimum over the interiors (tasks span interiors).
+cudaError_t cfl_dt_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks,
+                          double gamma, double cfl, double* d_out, int* d_status,
+                          const KernelTimer* tm, cudaStream_t s);
+
+// Ghost copies (tasks: patch field = copy index).
+cudaError_t ghost_fill_launch(int dtype, const DPatch* patches, const DCopy* copies,
+                              const BlockTask* tasks, int nblocks, const KernelTimer* tm,
+                              cudaStream_t s);
+
+// Conservation sums (tasks span interiors); partials holds nblocks*8 doubles.
+cudaError_t sums_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks,
+                        double* partials, double* d_out8, const KernelTimer* tm, cudaStream_t s);
+
+}  // namespace mhd

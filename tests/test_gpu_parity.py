@@ -1,0 +1,260 @@
+"""GPU (sm_103a) vs FP64 oracle parity through the C ABI.
+
+FP64: the GPU build has no multiply-add contraction and evaluates every
+expression in the oracle's order, so results are expected to be identical;
+the bar is L-infinity relative error <= 1e-11 per variable after 10 steps.
+Integer metadata and copies are bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import random_state, rel_l1, rel_linf, to_patch
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1112_1710_gb300 import _build, capi as C
+    _build.build()
+    C.load()
+    return C
+
+
+@pytest.fixture
+def ctx(capi):
+    c = capi.mhd_ctx_create()
+    yield c
+    capi.mhd_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("n,g", [((8, 6, 5), 2), ((128, 128, 1), 2), ((3, 5, 2), 4), ((1, 1, 1), 2),
+                                 ((37, 29, 23), 4)])
+def test_periodic_ghost_fill_bitexact(capi, ctx, orc, n, g):
+    from paper_1112_1710_gb300.patch import periodic_copies
+    st = random_state(n, g, seed=11)
+    p = to_patch(st, n, g, (1.0, 1.0, 1.0))
+    capi.mhd_ghost_fill(ctx, [p.desc()], periodic_copies(n, g))
+    P = orc.patch(st, n, g, (1.0, 1.0, 1.0))
+    orc.fill_periodic(P)
+    got = p.state.cpu().numpy()
+    # every cell array element and every face element the fill defines
+    assert np.array_equal(got[:5, :n[2] + 2 * g, :n[1] + 2 * g, :n[0] + 2 * g],
+                          st[:5, :n[2] + 2 * g, :n[1] + 2 * g, :n[0] + 2 * g])
+    N = [v + 2 * g for v in n]
+    for a in range(3):
+        ext = list(N)
+        ext[a] += 1
+        assert np.array_equal(got[5 + a, :ext[2], :ext[1], :ext[0]], st[5 + a, :ext[2], :ext[1], :ext[0]])
+
+
+@pytest.mark.parametrize("problem", ["blast", "ot", "random"])
+def test_cfl_dt_bitexact(capi, ctx, orc, problem):
+    if problem == "blast":
+        pr = synth.blast(24)
+        st, n, g, dx = pr.state, pr.n, pr.g, pr.dx
+    elif problem == "ot":
+        pr = synth.orszag_tang(40)
+        st, n, g, dx = pr.state, pr.n, pr.g, pr.dx
+    else:
+        n, g, dx = (21, 17, 13), 2, (0.1, 0.07, 0.13)
+        st = random_state(n, g, seed=3)
+    P = orc.patch(st, n, g, dx)
+    orc.fill_periodic(P)
+    want = orc.cfl_dt(P, orc.params())
+    p = to_patch(st, n, g, dx)
+    d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    capi.mhd_cfl_dt(ctx, [p.desc()], d.data_ptr())
+    assert d.item() == want
+    # the scale factor of a hierarchy level is an exact power of two
+    capi.mhd_cfl_dt(ctx, [p.desc()], d.data_ptr(), scale=[4.0])
+    assert d.item() == 4.0 * want
+
+
+@pytest.mark.parametrize("emf,lim", [(0, 0), (1, 0), (0, 1), (0, 2)])
+@pytest.mark.parametrize("k", [0, 2])
+def test_one_step_random_state_ragged(capi, orc, emf, lim, k):
+    """One step on a ragged patch (several blocks, partial tail) from random
+    data, including the extended update box (k = 2, g = 4)."""
+    n, g, dx = (19, 13, 11), 4, (0.05, 0.07, 0.06)
+    st = random_state(n, g, seed=5 + k)
+    ctx = capi.mhd_ctx_create(limiter=lim, emf=emf)
+    try:
+        p = to_patch(st, n, g, dx)
+        d = torch.full((1,), 1.3e-3, dtype=torch.float64, device="cuda")
+        capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr(), grow=[k])
+        assert capi.mhd_get_device_status(ctx) == 0
+        got = p.state.cpu().numpy()
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    P = orc.patch(st, n, g, dx)
+    assert orc.advance(P, orc.params(limiter=lim, emf=emf), 1.3e-3, k) == 0
+    # compare the update box and its faces
+    lo, hi = g - k, g + np.array(n) - 1 + k
+    for q in range(8):
+        ext_hi = hi.copy()
+        if q >= 5:
+            ext_hi[q - 5] += 1
+        a = got[q, lo:ext_hi[2] + 1, lo:ext_hi[1] + 1, lo:ext_hi[0] + 1]
+        b = st[q, lo:ext_hi[2] + 1, lo:ext_hi[1] + 1, lo:ext_hi[0] + 1]
+        assert np.abs(a - b).max() <= TOL * np.abs(b).max(), (q, np.abs(a - b).max())
+    # outside the update box nothing changed
+    untouched = got.copy()
+    untouched[:, lo:hi[2] + 2, lo:hi[1] + 2, lo:hi[0] + 2] = 0
+    ref = st.copy()
+    ref[:, lo:hi[2] + 2, lo:hi[1] + 2, lo:hi[0] + 2] = 0
+    assert np.array_equal(untouched, ref)
+
+
+def _run_both(capi, ctx, orc, pr, steps, dtype="f64", dt=None):
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    st0 = pr.state.copy()
+    p = to_patch(st0, pr.n, pr.g, pr.dx, dtype=dtype)
+    run = PeriodicRunner(p, ctx)
+    gdts = run.run(steps, dt=dt, record_dt=True)
+    got = p.state.cpu().numpy()
+    odts = orc.run_periodic(pr.state, pr.n, pr.g, pr.dx, orc.params(), steps, dt=dt)
+    return got, pr.state, gdts, odts
+
+
+def test_orszag_tang_128_fp64_10_steps(capi, ctx, orc):
+    """2D Orszag-Tang, 128^2 + 2 ghosts, FP64, CFL 0.4 (the full-size 2D case)."""
+    pr = synth.orszag_tang(128)
+    got, want, gdts, odts = _run_both(capi, ctx, orc, pr, 10)
+    assert gdts == odts
+    err = rel_linf(got, want, pr.n, pr.g)
+    assert np.all(err <= TOL), err
+    assert capi.mhd_get_device_status(ctx) == 0
+
+
+def test_blast_128_fp64_10_steps(capi, ctx, orc):
+    """3D blast, 128^3 + 2 ghosts, FP64 (the full-size 3D case, same launch
+    configuration as the bench)."""
+    pr = synth.blast(128)
+    got, want, gdts, odts = _run_both(capi, ctx, orc, pr, 10)
+    assert gdts == odts
+    err = rel_linf(got, want, pr.n, pr.g)
+    assert np.all(err <= TOL), err
+
+
+def test_blast_fp32_error_report(capi, ctx, orc, capsys):
+    """FP32 bulk arithmetic against the FP64 oracle with the oracle's dt
+    sequence: the error is reported per variable (no parity bar), with loose
+    sanity bounds."""
+    pr = synth.blast(64)
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    st0 = pr.state.copy()
+    p = to_patch(st0, pr.n, pr.g, pr.dx, dtype="f32")
+    run = PeriodicRunner(p, ctx)
+    want = pr.state
+    P = orc.patch(want, pr.n, pr.g, pr.dx)
+    rows = []
+    for step in range(1, 11):
+        orc.fill_periodic(P)
+        dt = orc.cfl_dt(P, orc.params())
+        assert orc.advance(P, orc.params(), dt, 0) == 0
+        run.step(dt)
+        if step in (1, 10):
+            run.fill()
+            orc.fill_periodic(P)
+            got = p.state.cpu().numpy()
+            rows.append((step, rel_linf(got, want, pr.n, pr.g), rel_l1(got, want, pr.n, pr.g)))
+    with capsys.disabled():
+        for step, li, l1 in rows:
+            print("\nFP32 vs FP64 oracle, blast 64^3, step %d" % step)
+            print("  Linf rel:", " ".join("%.2e" % v for v in li))
+            print("  L1   rel:", " ".join("%.2e" % v for v in l1))
+    li = rows[-1][1]
+    l1 = rows[-1][2]
+    assert np.all(l1[[0, 4, 5, 6]] < 1e-4) and np.all(li[[0, 4]] < 1e-2)
+
+
+def test_batched_patches_equal_single_and_oracle(capi, ctx, orc):
+    """Independent periodic patches of uneven sizes advanced in one call give
+    the same bits as one call per patch, and match the oracle."""
+    from paper_1112_1710_gb300.patch import periodic_copies
+    sizes = [(8, 8, 8), (13, 9, 7), (24, 16, 12), (5, 5, 5)]
+    probs = [random_state(n, 2, seed=20 + i) for i, n in enumerate(sizes)]
+    dx = (0.05, 0.05, 0.05)
+    batch = [to_patch(s, n, 2, dx, pid=i) for i, (s, n) in enumerate(zip(probs, sizes))]
+    alone = [to_patch(s, n, 2, dx, pid=i) for i, (s, n) in enumerate(zip(probs, sizes))]
+    d = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    descs = [p.desc() for p in batch]
+    copies = []
+    for i, n in enumerate(sizes):
+        for c in periodic_copies(n, 2):
+            c.src = c.dst = i
+            copies.append(c)
+    for _ in range(3):
+        capi.mhd_ghost_fill(ctx, descs, copies)
+        capi.mhd_patch_advance(ctx, descs, d.data_ptr())
+        for p in alone:
+            capi.mhd_ghost_fill(ctx, [p.desc()], periodic_copies(p.n, 2))
+            capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr())
+    for i, (s, n) in enumerate(zip(probs, sizes)):
+        a = batch[i].state.cpu().numpy()
+        b = alone[i].state.cpu().numpy()
+        assert np.array_equal(a, b)
+        orc.run_periodic(s, n, 2, dx, orc.params(), 3, dt=1e-3)
+        capi.mhd_ghost_fill(ctx, [batch[i].desc()], periodic_copies(n, 2))
+        err = rel_linf(batch[i].state.cpu().numpy(), s, n, 2)
+        assert np.all(err <= TOL), (i, err)
+
+
+def test_conservation_sums_within_summation_bound(capi, ctx, orc):
+    pr = synth.blast(48)
+    P = orc.patch(pr.state, pr.n, pr.g, pr.dx)
+    orc.fill_periodic(P)
+    want = orc.sums(P)
+    p = to_patch(pr.state, pr.n, pr.g, pr.dx)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    capi.mhd_conservation_sums(ctx, [p.desc()], out.data_ptr())
+    got = out.cpu().numpy()
+    dv = pr.dx[0] * pr.dx[1] * pr.dx[2]
+    absum = np.abs(pr.state[:, pr.g:pr.g + 48, pr.g:pr.g + 48, pr.g:pr.g + 48]).reshape(8, -1).sum(1) * dv
+    ncell = 48 ** 3
+    bound = 2 * ncell * np.finfo(np.float64).eps * absum
+    assert np.all(np.abs(got - want) <= bound + 1e-300)
+    # reproducible bit for bit
+    out2 = torch.zeros(8, dtype=torch.float64, device="cuda")
+    capi.mhd_conservation_sums(ctx, [p.desc()], out2.data_ptr())
+    assert np.array_equal(out2.cpu().numpy(), got)
+
+
+def test_negative_pressure_sets_status_without_trapping(capi, ctx):
+    pr = synth.blast(16)
+    st = pr.state.copy()
+    st[4, 5, 6, 7] = -1.0  # total energy below the magnetic energy: p < 0
+    p = to_patch(st, pr.n, pr.g, pr.dx)
+    d = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
+    capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr())
+    assert capi.mhd_get_device_status(ctx) == capi.MHD_ENEGATIVE
+    assert capi.mhd_get_device_status(ctx) == 0  # cleared by the read
+    # the context still works
+    q = to_patch(pr.state, pr.n, pr.g, pr.dx)
+    capi.mhd_patch_advance(ctx, [q.desc()], d.data_ptr())
+    torch.cuda.synchronize()
+
+
+def test_host_checks_reject_without_launch(capi, ctx):
+    pr = synth.blast(8)
+    p = to_patch(pr.state, pr.n, pr.g, pr.dx)
+    d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    before = capi.mhd_launch_count(ctx)
+    with pytest.raises(capi.MHDError) as e:
+        capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr(), grow=[1])  # 1 + 2 > g = 2
+    assert e.value.status == capi.MHD_EINVAL
+    bad = p.desc()
+    bad.stride[1] = 3
+    with pytest.raises(capi.MHDError):
+        capi.mhd_patch_advance(ctx, [bad], d.data_ptr())
+    bad = p.desc()
+    bad.dtype = 7
+    with pytest.raises(capi.MHDError):
+        capi.mhd_cfl_dt(ctx, [bad], d.data_ptr())
+    assert capi.mhd_launch_count(ctx) == before
+    # an empty advance is valid and launches nothing
+    capi.mhd_patch_advance(ctx, [], d.data_ptr())
+    assert capi.mhd_launch_count(ctx) == before
