@@ -108,15 +108,23 @@ def test_one_step_random_state_ragged(capi, orc, emf, lim, k):
     assert np.array_equal(untouched, ref)
 
 
-def _run_both(capi, ctx, orc, pr, steps, dtype="f64", dt=None):
+def _run_both(capi, ctx, orc, pr, steps, dtype="f64", dt=None, emf=0):
     from paper_1112_1710_gb300.runner import PeriodicRunner
     st0 = pr.state.copy()
     p = to_patch(st0, pr.n, pr.g, pr.dx, dtype=dtype)
     run = PeriodicRunner(p, ctx)
     gdts = run.run(steps, dt=dt, record_dt=True)
     got = p.state.cpu().numpy()
-    odts = orc.run_periodic(pr.state, pr.n, pr.g, pr.dx, orc.params(), steps, dt=dt)
+    odts = orc.run_periodic(pr.state, pr.n, pr.g, pr.dx, orc.params(emf=emf), steps, dt=dt)
     return got, pr.state, gdts, odts
+
+
+@pytest.fixture
+def ctx_blast(capi):
+    """The blast workloads use the arithmetic edge-EMF average."""
+    c = capi.mhd_ctx_create(emf=1)
+    yield c
+    capi.mhd_ctx_destroy(c)
 
 
 def test_orszag_tang_128_fp64_10_steps(capi, ctx, orc):
@@ -129,17 +137,18 @@ def test_orszag_tang_128_fp64_10_steps(capi, ctx, orc):
     assert capi.mhd_get_device_status(ctx) == 0
 
 
-def test_blast_128_fp64_10_steps(capi, ctx, orc):
+def test_blast_128_fp64_10_steps(capi, ctx_blast, orc):
     """3D blast, 128^3 + 2 ghosts, FP64 (the full-size 3D case, same launch
     configuration as the bench)."""
     pr = synth.blast(128)
-    got, want, gdts, odts = _run_both(capi, ctx, orc, pr, 10)
+    got, want, gdts, odts = _run_both(capi, ctx_blast, orc, pr, 10, emf=1)
     assert gdts == odts
     err = rel_linf(got, want, pr.n, pr.g)
     assert np.all(err <= TOL), err
+    assert capi.mhd_get_device_status(ctx_blast) == 0
 
 
-def test_blast_fp32_error_report(capi, ctx, orc, capsys):
+def test_blast_fp32_error_report(capi, ctx_blast, orc, capsys):
     """FP32 bulk arithmetic against the FP64 oracle with the oracle's dt
     sequence: the error is reported per variable (no parity bar), with loose
     sanity bounds."""
@@ -147,14 +156,15 @@ def test_blast_fp32_error_report(capi, ctx, orc, capsys):
     from paper_1112_1710_gb300.runner import PeriodicRunner
     st0 = pr.state.copy()
     p = to_patch(st0, pr.n, pr.g, pr.dx, dtype="f32")
-    run = PeriodicRunner(p, ctx)
+    run = PeriodicRunner(p, ctx_blast)
     want = pr.state
     P = orc.patch(want, pr.n, pr.g, pr.dx)
+    prm = orc.params(emf=1)
     rows = []
     for step in range(1, 11):
         orc.fill_periodic(P)
-        dt = orc.cfl_dt(P, orc.params())
-        assert orc.advance(P, orc.params(), dt, 0) == 0
+        dt = orc.cfl_dt(P, prm)
+        assert orc.advance(P, prm, dt, 0) == 0
         run.step(dt)
         if step in (1, 10):
             run.fill()
