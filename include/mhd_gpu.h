@@ -51,6 +51,7 @@ typedef int32_t mhd_status;
 #define MHD_ECUDA (-3)     /* a CUDA runtime call failed                     */
 #define MHD_ENEGATIVE (-4) /* device: rho <= 0 or p <= 0 after an update      */
 #define MHD_ETIMEOUT (-5)  /* device: a bounded wait gave up                  */
+#define MHD_ETOOBIG (-6)   /* request exceeds a fixed static capacity        */
 
 #define MHD_F64 0
 #define MHD_F32 1
@@ -140,6 +141,28 @@ mhd_status mhd_ghost_fill(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n
  * is reproducible run to run).  d_out8 is a device array of 8 doubles. */
 mhd_status mhd_conservation_sums(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
                                  double *d_out8, void *stream);
+
+/* The same conservation sums, for callers that cannot allocate memory (the
+ * paper has no counterpart).  Some callers own no device memory of their own:
+ * their process's memory is reserved by another allocator (a serving
+ * framework's caching pool), or they must not call cudaMalloc/cudaFree because
+ * those calls can synchronise the device and stall other streams, or they run
+ * as a plugin that is not allowed to allocate.  This entry point needs no
+ * context and allocates nothing, on the device or the host: the partial sums
+ * live in a fixed array inside the library (1 MiB per GPU, held by every GPU
+ * that loads the library until the process exits) and the descriptors travel
+ * as a kernel argument.  The caller passes the patches (host array) and
+ * d_out8 (device, 8 doubles), as for mhd_conservation_sums, and gets the same
+ * values bit for bit; the work is enqueued on `stream` of the current device.
+ * Limits: at most 16 patches and 4,194,304 interior cells in total (16384
+ * blocks of 256 cells); larger requests return MHD_ETOOBIG and launch
+ * nothing; bad descriptors return MHD_EINVAL.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU (different streams
+ * without ordering between them) race and may return wrong sums. */
+mhd_status mhd_conservation_sums_static(const mhd_patch_desc *patches, int32_t n,
+                                        double *d_out8, void *stream);
 
 /* Synchronises the context's device, then returns (and clears) the device
  * status word in *out: MHD_OK or the first device error raised since the

@@ -23,6 +23,7 @@ UNITS = {
     "level_ops.cu": ["--fmad=false"],
     "advance_f64.cu": ["--fmad=false"],
     "advance_f32.cu": ["--fmad=true"],
+    "noalloc.cu": ["--fmad=false"],
 }
 
 

@@ -13,15 +13,16 @@ import os
 from . import _build
 
 MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_ENEGATIVE, MHD_ETIMEOUT = 0, -1, -2, -3, -4, -5
+MHD_ETOOBIG = -6
 MHD_F64, MHD_F32 = 0, 1
 STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA",
-                -4: "MHD_ENEGATIVE", -5: "MHD_ETIMEOUT"}
+                -4: "MHD_ENEGATIVE", -5: "MHD_ETIMEOUT", -6: "MHD_ETOOBIG"}
 
 # Exported functions of include/mhd_gpu.h (checked against the header by the tests).
 EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", "mhd_patch_advance",
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
-           "mhd_kernel_name")
+           "mhd_kernel_name", "mhd_conservation_sums_static")
 N_KERNELS = 9
 
 
@@ -99,6 +100,8 @@ def load(build_if_missing: bool = False):
     L.mhd_timing_reset.argtypes = [P]
     L.mhd_kernel_name.restype = C.c_char_p
     L.mhd_kernel_name.argtypes = [i32]
+    L.mhd_conservation_sums_static.restype = i32
+    L.mhd_conservation_sums_static.argtypes = [C.POINTER(mhd_patch_desc), i32, P, P]
     _lib = L
     return L
 
@@ -171,6 +174,14 @@ def mhd_ghost_fill(ctx, patches, copies, stream: int = 0) -> None:
 def mhd_conservation_sums(ctx, patches, d_out8: int, stream: int = 0) -> None:
     arr, n = _descs(patches)
     _check(ctx, load().mhd_conservation_sums(ctx, arr, n, d_out8, stream))
+
+
+def mhd_conservation_sums_static(patches, d_out8: int, stream: int = 0) -> None:
+    """Allocation-free conservation sums (no context; fixed capacity)."""
+    arr, n = _descs(patches)
+    r = load().mhd_conservation_sums_static(arr, n, d_out8, stream)
+    if r != MHD_OK:
+        raise MHDError(r, "mhd_conservation_sums_static rejected the request")
 
 
 def mhd_get_device_status(ctx) -> int:
