@@ -355,49 +355,38 @@ static void cell_prim(const orc_patch *P, int i, int j, int k, double gm1, doubl
 /* ------------------------------------------------------------------ */
 /* periodic ghost fill (single patch covering a periodic domain)        */
 /* ------------------------------------------------------------------ */
-static int wrap(int a, int g, int n) {
-  int r = (a - g) % n;
-  if (r < 0) r += n;
-  return g + r;
-}
+ORC_EXPORT void orc_copy(const orc_patch *Ps, const int32_t *sglo, const orc_patch *Pd,
+                         const int32_t *dglo, const int32_t *lo, const int32_t *hi,
+                         const int32_t *off, int32_t pass);
 
-/* Every element whose index lies outside [g, g+n-1] along some axis is copied
- * from the periodic image inside it, except the patch's own faces: a face
- * whose normal index is in [g, g+n] and whose other indices are in [g, g+n-1]
- * belongs to the interior and is left as the advance computed it (its upper
- * boundary face equals the image of the lower one because the update does not
- * depend on position).  A face array's extra entry (index N along its normal)
- * is the upper face of the image of cell N-1, which for a patch thinner than
- * its ghost width is the interior's upper boundary face. */
+/* Periodic ghost fill of one patch that covers its periodic domain: every
+ * periodic image of the interior (offsets of up to ceil((g+1)/n) periods
+ * along each axis) that overlaps the ghost-extended box grown by one cell is
+ * copied with the rule of orc_copy (cells and lower faces in pass 0, upper
+ * faces in pass 1; the patch's own interior faces are never written). */
 ORC_EXPORT void orc_fill_periodic(const orc_patch *P) {
   const int g = P->g;
-  const int N0 = P->n[0] + 2 * g, N1 = P->n[1] + 2 * g, N2 = P->n[2] + 2 * g;
-  for (int a = 0; a < 8; ++a) {
-    double *A = (a < 5) ? P->U[a] : P->B[a - 5];
-    int ext[3] = {N0, N1, N2};
-    if (a >= 5) ext[a - 5] += 1;
-    for (int k = 0; k < ext[2]; ++k)
-      for (int j = 0; j < ext[1]; ++j)
-        for (int i = 0; i < ext[0]; ++i) {
-          int si = wrap(i, g, P->n[0]), sj = wrap(j, g, P->n[1]), sk = wrap(k, g, P->n[2]);
-          /* the extra face at index N along the normal is the upper face of
-           * the image of the last cell N-1 */
-          if (a == 5 && i == N0) si = wrap(N0 - 1, g, P->n[0]) + 1;
-          if (a == 6 && j == N1) sj = wrap(N1 - 1, g, P->n[1]) + 1;
-          if (a == 7 && k == N2) sk = wrap(N2 - 1, g, P->n[2]) + 1;
-          if (si == i && sj == j && sk == k) continue;
-          if (a >= 5) {
-            int ax = a - 5, id[3] = {i, j, k};
-            int own = 1;
-            for (int e = 0; e < 3; ++e) {
-              int top = (e == ax) ? g + P->n[e] : g + P->n[e] - 1;
-              if (id[e] < g || id[e] > top) own = 0;
-            }
-            if (own) continue;
+  const int32_t glo[3] = {0, 0, 0};
+  int r[3];
+  for (int d = 0; d < 3; ++d) r[d] = (g + P->n[d]) / P->n[d];
+  for (int pass = 0; pass < 2; ++pass)
+    for (int oz = -r[2]; oz <= r[2]; ++oz)
+      for (int oy = -r[1]; oy <= r[1]; ++oy)
+        for (int ox = -r[0]; ox <= r[0]; ++ox) {
+          int o[3] = {ox, oy, oz};
+          if (!ox && !oy && !oz) continue;
+          int32_t lo[3], hi[3], off[3];
+          int empty = 0;
+          for (int d = 0; d < 3; ++d) {
+            int a = o[d] * P->n[d], b = a + P->n[d] - 1;
+            lo[d] = a > -g - 1 ? a : -g - 1;
+            hi[d] = b < P->n[d] + g ? b : P->n[d] + g;
+            off[d] = -o[d] * P->n[d];
+            if (lo[d] > hi[d]) empty = 1;
           }
-          A[ix(P, i, j, k)] = A[ix(P, si, sj, sk)];
+          if (empty) continue;
+          orc_copy(P, glo, P, glo, lo, hi, off, pass);
         }
-  }
 }
 
 /* ------------------------------------------------------------------ */
@@ -803,4 +792,365 @@ ORC_EXPORT double orc_divb_max(const orc_patch *P) {
         m = mx(m, fabs(dvb));
       }
   return m;
+}
+
+/* ================================================================== */
+/* AMR level operations (Sec. 2.2: Prolongation, Restriction, flux      */
+/* synchronisation), refinement ratio R = 2.  A fine patch is aligned   */
+/* to its coarse level (even lower index, even extent); fine global     */
+/* index = 2 * coarse global index + {0, 1}.                            */
+/* ================================================================== */
+
+/* global -> array index of a patch whose interior starts at global lo */
+static int gidx(int global, int lo, int g) { return global - lo + g; }
+
+static double minmod2(double a, double b) { return orc_limiter(1, a, b); }
+
+/* Prolongation of the coarse cells of box [clo, chi] (coarse global index)
+ * of coarse patch Pc (interior starting at global cglo) into fine patch Pf
+ * (interior starting at fglo): for each coarse cell, the 8 fine cells and
+ * the lower faces of those fine cells (plus the extra upper face where a fine
+ * cell is the last of its array), skipping the fine patch's own interior
+ * faces.  Cells: U_f = U_c + (+-h_x) + (+-h_y) + (+-h_z), h_d = 0.25 *
+ * minmod of the coarse one-sided differences (conservative limited linear).
+ * Faces: divergence-free reconstruction inside the coarse cell (Balsara
+ * 2001 for R = 2): each coarse face gives its mean and its minmod transverse
+ * quarter-slopes; the quadratic field Bx = a0 + ax x + ay y + az z + axx x^2 +
+ * axy xy + axz xz (and cyclic) matching those traces with div B = 0
+ * identically yields the inner faces.  Fine units: the coarse cell is
+ * [-1, 1]^3, fine cells have unit width. */
+ORC_EXPORT void orc_prolong(const orc_patch *Pc, const int32_t *cglo, const orc_patch *Pf,
+                            const int32_t *fglo, const int32_t *clo, const int32_t *chi) {
+  const int gc = Pc->g, gf = Pf->g;
+  const int64_t *sc = Pc->s, *sf = Pf->s;
+  int Nf[3];
+  for (int d = 0; d < 3; ++d) Nf[d] = Pf->n[d] + 2 * gf;
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int ci[3] = {gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc)};
+        int64_t c = ix(Pc, ci[0], ci[1], ci[2]);
+        /* cells */
+        double uc[5], h[5][3];
+        for (int q = 0; q < 5; ++q) {
+          uc[q] = Pc->U[q][c];
+          for (int d = 0; d < 3; ++d) {
+            double a = uc[q] - Pc->U[q][c - sc[d]];
+            double b = Pc->U[q][c + sc[d]] - uc[q];
+            h[q][d] = 0.25 * minmod2(a, b);
+          }
+        }
+        /* faces: mean and transverse quarter-slopes of the six coarse faces */
+        double m[3][2], qs[3][2][3];  /* qs[normal][side][transverse axis] */
+        for (int a = 0; a < 3; ++a)
+          for (int sd = 0; sd < 2; ++sd) {
+            int64_t f = c + (sd ? sc[a] : 0);
+            m[a][sd] = Pc->B[a][f];
+            for (int t = 0; t < 3; ++t) {
+              if (t == a) { qs[a][sd][t] = 0.0; continue; }
+              double lo = m[a][sd] - Pc->B[a][f - sc[t]];
+              double hi = Pc->B[a][f + sc[t]] - m[a][sd];
+              qs[a][sd][t] = 0.25 * minmod2(lo, hi);
+            }
+          }
+        /* polynomial coefficients: lin[a][t] = coefficient of x_t in B_a
+         * (t != a), crs[a][t] = coefficient of x_a x_t in B_a */
+        double lin[3][3], crs[3][3], sq[3], c0[3];
+        for (int a = 0; a < 3; ++a)
+          for (int t = 0; t < 3; ++t) {
+            if (t == a) { lin[a][t] = 0.0; crs[a][t] = 0.0; continue; }
+            lin[a][t] = qs[a][1][t] + qs[a][0][t];
+            crs[a][t] = qs[a][1][t] - qs[a][0][t];
+          }
+        for (int a = 0; a < 3; ++a) {
+          int b = (a + 1) % 3, cc = (a + 2) % 3;
+          sq[a] = -0.5 * (crs[b][a] + crs[cc][a]);
+          c0[a] = 0.5 * (m[a][0] + m[a][1]) - sq[a];
+        }
+        /* the 8 fine cells */
+        for (int fc = 0; fc < 2; ++fc)
+          for (int fb = 0; fb < 2; ++fb)
+            for (int fa = 0; fa < 2; ++fa) {
+              int sub[3] = {fa, fb, fc};
+              int fi[3];
+              for (int d = 0; d < 3; ++d) fi[d] = gidx(2 * (d == 0 ? I : d == 1 ? J : K) + sub[d], fglo[d], gf);
+              int64_t x = ix(Pf, fi[0], fi[1], fi[2]);
+              for (int q = 0; q < 5; ++q) {
+                double u = uc[q];
+                u = u + (fa ? h[q][0] : -h[q][0]);
+                u = u + (fb ? h[q][1] : -h[q][1]);
+                u = u + (fc ? h[q][2] : -h[q][2]);
+                Pf->U[q][x] = u;
+              }
+              for (int a = 0; a < 3; ++a) {
+                int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+                int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+                /* lower face of this fine cell along a, and (if last) the upper */
+                for (int up = 0; up < 2; ++up) {
+                  int fidx[3] = {fi[0], fi[1], fi[2]};
+                  if (up) {
+                    if (fi[a] != Nf[a] - 1) continue;
+                    fidx[a] += 1;
+                  }
+                  int own = 1;
+                  for (int e = 0; e < 3; ++e) {
+                    int top = (e == a) ? gf + Pf->n[e] : gf + Pf->n[e] - 1;
+                    if (fidx[e] < gf || fidx[e] > top) own = 0;
+                  }
+                  if (own) continue;
+                  int pos = sub[a] + up; /* 0 lower coarse face, 1 inner, 2 upper */
+                  double v;
+                  if (pos == 1) {
+                    double sl = sub[lo_t] ? 0.5 * lin[a][lo_t] : -0.5 * lin[a][lo_t];
+                    double sh = sub[hi_t] ? 0.5 * lin[a][hi_t] : -0.5 * lin[a][hi_t];
+                    v = c0[a] + sl + sh;
+                  } else {
+                    int sd = pos == 2;
+                    double sl = sub[lo_t] ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
+                    double sh = sub[hi_t] ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
+                    v = m[a][sd] + sl + sh;
+                  }
+                  Pf->B[a][ix(Pf, fidx[0], fidx[1], fidx[2])] = v;
+                }
+              }
+            }
+      }
+}
+
+/* Restriction of fine patch Pf onto coarse patch Pc for the coarse cells of
+ * box [clo, chi] (the coarsened fine interior clipped to Pc's interior grown
+ * by one cell): every box cell inside Pc's interior = 0.125 * (sum of its 8
+ * fine cells, x fastest); every face of a box cell that is a face of Pc's
+ * interior (normal index in [lo, hi+1], others in [lo, hi]) = 0.25 * (sum of
+ * its 4 fine sub-faces, lower transverse axis fastest).  Pass 0 writes the
+ * cells and the lower faces, pass 1 the upper faces of the box's top layer,
+ * so a coarse face shared by two coarse patches, or by two fine patches,
+ * receives the same value everywhere. */
+static int own_face_c(const orc_patch *P, const int *ai, int a) {
+  for (int e = 0; e < 3; ++e) {
+    int top = (e == a) ? P->g + P->n[e] : P->g + P->n[e] - 1;
+    if (ai[e] < P->g || ai[e] > top) return 0;
+  }
+  return 1;
+}
+
+ORC_EXPORT void orc_restrict(const orc_patch *Pf, const int32_t *fglo, const orc_patch *Pc,
+                             const int32_t *cglo, const int32_t *clo, const int32_t *chi,
+                             int32_t pass) {
+  const int gc = Pc->g, gf = Pf->g;
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int C3[3] = {I, J, K};
+        int ca0[3] = {gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc)};
+        int inside = 1;
+        for (int e = 0; e < 3; ++e)
+          if (ca0[e] < gc || ca0[e] > gc + Pc->n[e] - 1) inside = 0;
+        int64_t c = ix(Pc, ca0[0], ca0[1], ca0[2]);
+        for (int q = 0; q < 5 && pass == 0 && inside; ++q) {
+          double s = 0.0;
+          int first = 1;
+          for (int fc = 0; fc < 2; ++fc)
+            for (int fb = 0; fb < 2; ++fb)
+              for (int fa = 0; fa < 2; ++fa) {
+                double v = Pf->U[q][ix(Pf, gidx(2 * I + fa, fglo[0], gf), gidx(2 * J + fb, fglo[1], gf),
+                                        gidx(2 * K + fc, fglo[2], gf))];
+                s = first ? v : s + v;
+                first = 0;
+              }
+          Pc->U[q][c] = 0.125 * s;
+        }
+        for (int a = 0; a < 3; ++a) {
+          int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+          int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+          for (int up = 0; up < 2; ++up) {
+            if (up != pass) continue;
+            if (up && C3[a] != chi[a]) continue;
+            int cf[3] = {ca0[0], ca0[1], ca0[2]};
+            cf[a] += up;
+            if (!own_face_c(Pc, cf, a)) continue;
+            double s = 0.0;
+            int first = 1;
+            for (int j2 = 0; j2 < 2; ++j2)
+              for (int j1 = 0; j1 < 2; ++j1) {
+                int f[3];
+                f[a] = 2 * (C3[a] + up);
+                f[lo_t] = 2 * C3[lo_t] + j1;
+                f[hi_t] = 2 * C3[hi_t] + j2;
+                double v = Pf->B[a][ix(Pf, gidx(f[0], fglo[0], gf), gidx(f[1], fglo[1], gf), gidx(f[2], fglo[2], gf))];
+                s = first ? v : s + v;
+                first = 0;
+              }
+            int ca[3] = {gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc)};
+            ca[a] += up;
+            Pc->B[a][ix(Pc, ca[0], ca[1], ca[2])] = 0.25 * s;
+          }
+        }
+      }
+}
+
+/* Flux-register deposit of coarse faces: for each axis-d face of the coarse
+ * box [clo, chi] (face index = index of its upper cell), the correction
+ * dF_q = 0.25 * (sum of the 4 fine sub-face registers, lower transverse axis
+ * fastest) - (coarse register), written into the correction planes corr[d*5+q]
+ * (laid out with the coarse patch's strides).  fine: 5 planes over the fine
+ * box [flo, fhi] (x fastest); coarse: 5 planes over [clo, chi]. */
+ORC_EXPORT void orc_deposit_faces(const orc_patch *Pc, const int32_t *cglo, double *const *corr,
+                                  int32_t d, const int32_t *clo, const int32_t *chi,
+                                  const double *fine, const int32_t *flo, const int32_t *fhi,
+                                  const double *coarse) {
+  const int gc = Pc->g;
+  int fe[3], ce[3];
+  for (int e = 0; e < 3; ++e) { fe[e] = fhi[e] - flo[e] + 1; ce[e] = chi[e] - clo[e] + 1; }
+  int64_t fn = (int64_t)fe[0] * fe[1] * fe[2], cn = (int64_t)ce[0] * ce[1] * ce[2];
+  int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int C3[3] = {I, J, K};
+        int64_t co = (int64_t)(I - clo[0]) + (int64_t)ce[0] * ((J - clo[1]) + (int64_t)ce[1] * (K - clo[2]));
+        int64_t c = ix(Pc, gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc));
+        for (int q = 0; q < 5; ++q) {
+          double s = 0.0;
+          int first = 1;
+          for (int j2 = 0; j2 < 2; ++j2)
+            for (int j1 = 0; j1 < 2; ++j1) {
+              int f[3];
+              f[d] = 2 * C3[d];
+              f[lo_t] = 2 * C3[lo_t] + j1;
+              f[hi_t] = 2 * C3[hi_t] + j2;
+              int64_t fo = (int64_t)(f[0] - flo[0]) + (int64_t)fe[0] * ((f[1] - flo[1]) + (int64_t)fe[1] * (f[2] - flo[2]));
+              double v = fine[q * fn + fo];
+              s = first ? v : s + v;
+              first = 0;
+            }
+          corr[d * 5 + q][c] = 0.25 * s - coarse[q * cn + co];
+        }
+      }
+}
+
+/* EMF deposit of coarse axis-a edges of box [clo, chi] (an edge is stored at
+ * the cell whose lower corner lines it lies on): dE = 0.5 * (sum of the two
+ * fine segments) - (coarse register), into corr[15 + a]. */
+ORC_EXPORT void orc_deposit_edges(const orc_patch *Pc, const int32_t *cglo, double *const *corr,
+                                  int32_t a, const int32_t *clo, const int32_t *chi,
+                                  const double *fine, const int32_t *flo, const int32_t *fhi,
+                                  const double *coarse) {
+  const int gc = Pc->g;
+  int fe[3], ce[3];
+  for (int e = 0; e < 3; ++e) { fe[e] = fhi[e] - flo[e] + 1; ce[e] = chi[e] - clo[e] + 1; }
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int C3[3] = {I, J, K};
+        int64_t co = (int64_t)(I - clo[0]) + (int64_t)ce[0] * ((J - clo[1]) + (int64_t)ce[1] * (K - clo[2]));
+        int64_t c = ix(Pc, gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc));
+        double s = 0.0;
+        for (int seg = 0; seg < 2; ++seg) {
+          int f[3] = {2 * C3[0], 2 * C3[1], 2 * C3[2]};
+          f[a] += seg;
+          int64_t fo = (int64_t)(f[0] - flo[0]) + (int64_t)fe[0] * ((f[1] - flo[1]) + (int64_t)fe[1] * (f[2] - flo[2]));
+          s = seg ? s + fine[fo] : fine[fo];
+        }
+        corr[15 + a][c] = 0.5 * s - coarse[co];
+      }
+}
+
+/* Applies the correction planes to every interior cell and every interior
+ * face of coarse patch P:
+ *   U_q -= (dF_x(+x) - dF_x)/dx - ... (x, y, z in order),
+ *   B_a -= ((dE_c(+b) - dE_c)/dx_b - (dE_b(+c) - dE_b)/dx_c)
+ * (planes are zero away from coarse-fine boundaries). */
+ORC_EXPORT void orc_correct(const orc_patch *P, double *const *corr) {
+  const int g = P->g;
+  const int64_t *s = P->s;
+  for (int k = g; k < g + P->n[2]; ++k)
+    for (int j = g; j < g + P->n[1]; ++j)
+      for (int i = g; i < g + P->n[0]; ++i) {
+        int64_t c = ix(P, i, j, k);
+        for (int q = 0; q < 5; ++q) {
+          double u = P->U[q][c];
+          u = u - (corr[0 * 5 + q][c + s[0]] - corr[0 * 5 + q][c]) / P->dx[0]
+                - (corr[1 * 5 + q][c + s[1]] - corr[1 * 5 + q][c]) / P->dx[1]
+                - (corr[2 * 5 + q][c + s[2]] - corr[2 * 5 + q][c]) / P->dx[2];
+          P->U[q][c] = u;
+        }
+      }
+  for (int a = 0; a < 3; ++a) {
+    int b = (a + 1) % 3, cc = (a + 2) % 3;
+    int hi[3] = {g + P->n[0] - 1, g + P->n[1] - 1, g + P->n[2] - 1};
+    hi[a] += 1;
+    for (int k = g; k <= hi[2]; ++k)
+      for (int j = g; j <= hi[1]; ++j)
+        for (int i = g; i <= hi[0]; ++i) {
+          int64_t c = ix(P, i, j, k);
+          double dEc = corr[15 + cc][c + s[b]] - corr[15 + cc][c];
+          double dEb = corr[15 + b][c + s[cc]] - corr[15 + b][c];
+          P->B[a][c] = P->B[a][c] - (dEc / P->dx[b] - dEb / P->dx[cc]);
+        }
+  }
+}
+
+/* Ghost copy (Sec. 2.2 "update ghost cells"), two passes over all copies of
+ * a fill.  Box [lo, hi] (destination global index) is a source interior
+ * image clipped to the destination's ghost-extended box grown by one cell:
+ * the box cells inside the destination's arrays take the values of Ps at
+ * global index + off, and so does every face of a box cell that exists in
+ * the destination's face arrays (the extra cell layer supplies the faces on
+ * the array's outer planes): pass 0 writes cells and lower faces, pass 1 the
+ * upper faces of the box's top layer along each axis.  No pass writes a face
+ * of Pd's interior (normal index in [g, g+n], others in [g, g+n-1]).
+ * Within one pass the copies of a fill write disjoint elements; a face that
+ * is the top face of one box and the bottom face of another gets the pass-1
+ * value (both sources hold the same face). */
+static int dst_own_face(const orc_patch *Pd, const int *di, int a) {
+  for (int e = 0; e < 3; ++e) {
+    int top = (e == a) ? Pd->g + Pd->n[e] : Pd->g + Pd->n[e] - 1;
+    if (di[e] < Pd->g || di[e] > top) return 0;
+  }
+  return 1;
+}
+
+/* does the axis-a face with array index di exist in P's face arrays? */
+static int face_exists(const orc_patch *P, const int *di, int a) {
+  for (int e = 0; e < 3; ++e) {
+    int N = P->n[e] + 2 * P->g;
+    int top = (e == a) ? N : N - 1;
+    if (di[e] < 0 || di[e] > top) return 0;
+  }
+  return 1;
+}
+
+ORC_EXPORT void orc_copy(const orc_patch *Ps, const int32_t *sglo, const orc_patch *Pd,
+                         const int32_t *dglo, const int32_t *lo, const int32_t *hi,
+                         const int32_t *off, int32_t pass) {
+  const int gs = Ps->g, gd = Pd->g;
+  int Nd[3];
+  for (int d = 0; d < 3; ++d) Nd[d] = Pd->n[d] + 2 * gd;
+  for (int k = lo[2]; k <= hi[2]; ++k)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int i = lo[0]; i <= hi[0]; ++i) {
+        int gl[3] = {i, j, k};
+        int di[3] = {gidx(i, dglo[0], gd), gidx(j, dglo[1], gd), gidx(k, dglo[2], gd)};
+        int si[3] = {gidx(i + off[0], sglo[0], gs), gidx(j + off[1], sglo[1], gs), gidx(k + off[2], sglo[2], gs)};
+        int64_t xd = ix(Pd, di[0], di[1], di[2]), xs = ix(Ps, si[0], si[1], si[2]);
+        int cell_in = 1;
+        for (int e = 0; e < 3; ++e)
+          if (di[e] < 0 || di[e] > Nd[e] - 1) cell_in = 0;
+        if (pass == 0) {
+          if (cell_in)
+            for (int q = 0; q < 5; ++q) Pd->U[q][xd] = Ps->U[q][xs];
+          for (int a = 0; a < 3; ++a)
+            if (face_exists(Pd, di, a) && !dst_own_face(Pd, di, a)) Pd->B[a][xd] = Ps->B[a][xs];
+        } else {
+          for (int a = 0; a < 3; ++a) {
+            if (gl[a] != hi[a]) continue;
+            int du[3] = {di[0], di[1], di[2]};
+            du[a] += 1;
+            if (!face_exists(Pd, du, a) || dst_own_face(Pd, du, a)) continue;
+            Pd->B[a][xd + Pd->s[a]] = Ps->B[a][xs + Ps->s[a]];
+          }
+        }
+      }
 }

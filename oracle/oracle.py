@@ -81,6 +81,20 @@ def lib():
             L.orc_sums.argtypes = [C.POINTER(_Patch), dp]
             L.orc_divb_max.restype = C.c_double
             L.orc_divb_max.argtypes = [C.POINTER(_Patch)]
+            i3 = C.POINTER(C.c_int32)
+            pp = C.POINTER(C.c_void_p)
+            L.orc_prolong.restype = None
+            L.orc_prolong.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3]
+            L.orc_restrict.restype = None
+            L.orc_restrict.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, C.c_int32]
+            for nm in ("orc_deposit_faces", "orc_deposit_edges"):
+                f = getattr(L, nm)
+                f.restype = None
+                f.argtypes = [C.POINTER(_Patch), i3, pp, C.c_int32, i3, i3, dp, i3, i3, dp]
+            L.orc_correct.restype = None
+            L.orc_correct.argtypes = [C.POINTER(_Patch), pp]
+            L.orc_copy.restype = None
+            L.orc_copy.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, i3, C.c_int32]
             _lib = L
     return _lib
 
@@ -196,6 +210,42 @@ def sums(P: _Patch) -> np.ndarray:
 
 def divb_max(P: _Patch) -> float:
     return lib().orc_divb_max(C.byref(P))
+
+
+def _i3(v):
+    return (C.c_int32 * 3)(*[int(x) for x in v])
+
+
+def prolong(Pc: _Patch, cglo, Pf: _Patch, fglo, clo, chi) -> None:
+    lib().orc_prolong(C.byref(Pc), _i3(cglo), C.byref(Pf), _i3(fglo), _i3(clo), _i3(chi))
+
+
+def restrict(Pf: _Patch, fglo, Pc: _Patch, cglo, clo, chi, pass_) -> None:
+    lib().orc_restrict(C.byref(Pf), _i3(fglo), C.byref(Pc), _i3(cglo), _i3(clo), _i3(chi), int(pass_))
+
+
+def _planes(corr: np.ndarray):
+    assert corr.dtype == np.float64 and corr.flags.c_contiguous and corr.shape[0] == 18
+    arr = (C.c_void_p * 18)(*[corr.ctypes.data + q * corr.strides[0] for q in range(18)])
+    return arr
+
+
+def deposit_faces(Pc, cglo, corr, d, clo, chi, fine, flo, fhi, coarse) -> None:
+    lib().orc_deposit_faces(C.byref(Pc), _i3(cglo), _planes(corr), int(d), _i3(clo), _i3(chi),
+                            _dp(fine), _i3(flo), _i3(fhi), _dp(coarse))
+
+
+def deposit_edges(Pc, cglo, corr, a, clo, chi, fine, flo, fhi, coarse) -> None:
+    lib().orc_deposit_edges(C.byref(Pc), _i3(cglo), _planes(corr), int(a), _i3(clo), _i3(chi),
+                            _dp(fine), _i3(flo), _i3(fhi), _dp(coarse))
+
+
+def correct(P, corr) -> None:
+    lib().orc_correct(C.byref(P), _planes(corr))
+
+
+def copy(Ps, sglo, Pd, dglo, lo, hi, off, pass_) -> None:
+    lib().orc_copy(C.byref(Ps), _i3(sglo), C.byref(Pd), _i3(dglo), _i3(lo), _i3(hi), _i3(off), int(pass_))
 
 
 def run_periodic(state: np.ndarray, n, g: int, dx, prm: _Params, steps: int,

@@ -79,11 +79,13 @@ class Patch:
 
 
 def periodic_copies(n, g: int, lo=(0, 0, 0), index: int = 0):
-    """Ghost-fill copies of one patch that covers a periodic domain: every ghost
-    cell receives its periodic image, as boxes with image offsets (offsets of
-    up to ceil(g/n) periods, so a patch thinner than its ghost width works)."""
+    """Ghost-fill copies of one patch that covers a periodic domain: every
+    periodic image of the interior, clipped to the ghost-extended box grown by
+    one cell (the outer layer carries the faces on the outer planes of the face
+    arrays), as a box with its image offset (up to ceil((g+1)/n) periods, so a
+    patch thinner than its ghost width works)."""
     out = []
-    reach = [-(-g // int(n[d])) for d in range(3)]
+    reach = [(g + int(n[d])) // int(n[d]) for d in range(3)]
     ranges = [range(-reach[d], reach[d] + 1) for d in range(3)]
     for o in itertools.product(*ranges):
         if o == (0, 0, 0):
@@ -93,7 +95,7 @@ def periodic_copies(n, g: int, lo=(0, 0, 0), index: int = 0):
         for d in range(3):
             a = lo[d] + o[d] * n[d]
             b = a + n[d] - 1
-            a2, b2 = max(a, lo[d] - g), min(b, lo[d] + n[d] - 1 + g)
+            a2, b2 = max(a, lo[d] - g - 1), min(b, lo[d] + n[d] + g)
             if a2 > b2:
                 ok = False
                 break

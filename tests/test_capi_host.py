@@ -38,24 +38,25 @@ def test_binding_struct_layouts_match_header():
 
 @pytest.mark.parametrize("n,g", [((8, 6, 5), 2), ((128, 128, 1), 2), ((3, 5, 2), 4), ((1, 1, 1), 2), ((13, 7, 9), 4)])
 def test_periodic_copy_list_partitions_ghosts_like_the_wrap(n, g):
-    """Every ghost cell is written exactly once, from its periodic image inside
-    the interior -- the element-wise wrap the oracle's periodic fill uses."""
+    """Every cell of the ghost-extended box grown by one, except the interior,
+    is in exactly one copy box, and its source is its periodic image inside
+    the interior."""
     from paper_1112_1710_gb300.patch import periodic_copies
     cop = periodic_copies(n, g)
-    N = [n[d] + 2 * g for d in range(3)]
+    N = [n[d] + 2 * g + 2 for d in range(3)]
     hits = np.zeros(N[::-1], dtype=int)
     for c in cop:
         lo, hi, off = list(c.box.lo), list(c.box.hi), list(c.offset)
         for k in range(lo[2], hi[2] + 1):
             for j in range(lo[1], hi[1] + 1):
                 for i in range(lo[0], hi[0] + 1):
-                    hits[k + g, j + g, i + g] += 1
+                    hits[k + g + 1, j + g + 1, i + g + 1] += 1
                     src = (i + off[0], j + off[1], k + off[2])
                     for d, s in enumerate(src):
                         assert 0 <= s < n[d]
                         assert (s - (i, j, k)[d]) % n[d] == 0
     inter = np.zeros_like(hits)
-    inter[g:g + n[2], g:g + n[1], g:g + n[0]] = 1
+    inter[g + 1:g + 1 + n[2], g + 1:g + 1 + n[1], g + 1:g + 1 + n[0]] = 1
     assert np.array_equal(hits, 1 - inter)
 
 
@@ -80,26 +81,42 @@ def test_extended_ghost_cell_update_accounting():
 
 def apply_copies_numpy(st, n, g, copies):
     """The copy semantics documented for mhd_copy in include/mhd_gpu.h, written
-    out on a numpy patch (single patch, src = dst)."""
+    out on a numpy patch (single patch, src = dst): pass 0 cells and lower
+    faces, pass 1 upper faces of each box's top layer; only elements that exist
+    in the destination arrays; never the destination's interior faces."""
     N = [v + 2 * g for v in n]
     src = st.copy()
-    for c in copies:
-        lo, hi, off = list(c.box.lo), list(c.box.hi), list(c.offset)
-        for k in range(lo[2], hi[2] + 1):
-            for j in range(lo[1], hi[1] + 1):
-                for i in range(lo[0], hi[0] + 1):
-                    d = (i + g, j + g, k + g)
-                    s = (i + off[0] + g, j + off[1] + g, k + off[2] + g)
-                    st[:5, d[2], d[1], d[0]] = src[:5, s[2], s[1], s[0]]
-                    for a in range(3):
-                        interior = all(g <= d[b] <= (g + n[b] if b == a else g + n[b] - 1) for b in range(3))
-                        if not interior:
-                            st[5 + a, d[2], d[1], d[0]] = src[5 + a, s[2], s[1], s[0]]
-                        if d[a] == N[a] - 1:
-                            du, su = list(d), list(s)
-                            du[a] += 1
-                            su[a] += 1
-                            st[5 + a, du[2], du[1], du[0]] = src[5 + a, su[2], su[1], su[0]]
+
+    def interior_face(d, a):
+        return all(g <= d[b] <= (g + n[b] if b == a else g + n[b] - 1) for b in range(3))
+
+    def face_exists(d, a):
+        return all(0 <= d[b] <= (N[b] if b == a else N[b] - 1) for b in range(3))
+
+    for pass_ in (0, 1):
+        for c in copies:
+            lo, hi, off = list(c.box.lo), list(c.box.hi), list(c.offset)
+            for k in range(lo[2], hi[2] + 1):
+                for j in range(lo[1], hi[1] + 1):
+                    for i in range(lo[0], hi[0] + 1):
+                        gl = (i, j, k)
+                        d = (i + g, j + g, k + g)
+                        s = (i + off[0] + g, j + off[1] + g, k + off[2] + g)
+                        if pass_ == 0:
+                            if all(0 <= d[b] < N[b] for b in range(3)):
+                                st[:5, d[2], d[1], d[0]] = src[:5, s[2], s[1], s[0]]
+                            for a in range(3):
+                                if face_exists(d, a) and not interior_face(d, a):
+                                    st[5 + a, d[2], d[1], d[0]] = src[5 + a, s[2], s[1], s[0]]
+                        else:
+                            for a in range(3):
+                                if gl[a] != hi[a]:
+                                    continue
+                                du, su = list(d), list(s)
+                                du[a] += 1
+                                su[a] += 1
+                                if face_exists(du, a) and not interior_face(du, a):
+                                    st[5 + a, du[2], du[1], du[0]] = src[5 + a, su[2], su[1], su[0]]
 
 
 @pytest.mark.parametrize("n,g", [((6, 5, 4), 2), ((7, 3, 1), 2), ((2, 3, 2), 4), ((1, 1, 1), 2)])
