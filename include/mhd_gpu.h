@@ -88,20 +88,74 @@ typedef struct {
                         1e-10 for MHD_F64 and 1e-5 for MHD_F32 patches      */
 } mhd_params;
 
-/* One ghost-fill copy (Sec. 2.2 "update ghost cells" and Sec. 2.3): the
- * cells of `box` (global index space of the destination's level) in patch
- * `dst` receive the values of patch `src` at index + `offset` (a periodic
- * image shift, or zero), together with the lower face of every box cell
- * along each axis (and the array's extra upper face where the box reaches the
- * last cell of an axis), except faces that belong to dst's interior (normal
- * index in [lo, hi+1], other indices inside the interior).  Source cells must
- * lie in src's interior.  Boxes of one call must not overlap; every copy of
- * one call reads only interiors, so the copies are independent. */
+/* One ghost-fill copy (Sec. 2.2 "synchronise ... and update ghost cells",
+ * Sec. 2.3): `box` (global index space of the destination's level) is an
+ * image of src's interior (source index = destination index + `offset`, a
+ * periodic shift or zero) clipped to dst's ghost-extended box grown by one
+ * cell.  Every box cell that lies in dst's arrays takes src's values, and so
+ * does every face of a box cell that exists in dst's face arrays (the outer
+ * cell layer supplies the faces on the outer planes of those arrays), except
+ * faces of dst's interior (normal index in [lo, hi+1], other indices inside
+ * the interior).  A call writes cells and lower faces in a first pass and the
+ * upper faces of each box's top layer in a second, so copies of one call
+ * never write the same element in one pass; where the top face of one box is
+ * the bottom face of another, the second pass wins (both sources hold that
+ * face).  Source boxes must lie in src's interior and copies of one call must
+ * read only interiors. */
 typedef struct {
   int32_t src, dst;    /* indices into the descriptor array                 */
   mhd_box box;         /* destination cells                                 */
   int32_t offset[3];   /* source global index = destination index + offset  */
 } mhd_copy;
+
+/* AMR items (refinement ratio 2; fine global index = 2 x coarse + {0, 1};
+ * fine patches are aligned: even lower corner, even extent). */
+typedef struct {
+  int32_t coarse, fine; /* indices into the coarse / fine descriptor arrays  */
+  mhd_box box;          /* coarse cells, coarse global index                 */
+} mhd_prolong_item;
+
+typedef struct {
+  int32_t fine, coarse;
+  mhd_box box;          /* coarse cells: the coarsened fine interior clipped
+                           to the coarse interior grown by one cell          */
+} mhd_restrict_item;
+
+#define MHD_CAP_FACE 0
+#define MHD_CAP_EDGE 1
+
+/* Flux-register capture of an advance (FP64): kind MHD_CAP_FACE stores
+ * dt * F (rho, Mx, My, Mz, E: 5 planes over the box, x fastest) on the
+ * axis-normal faces of `box` (face index = index of the cell above the
+ * face); MHD_CAP_EDGE stores dt * E_axis (1 plane) on the axis edges of `box`
+ * (an edge is indexed by the cell at whose lower corner lines it lies).
+ * mode 0 writes, 1 adds (accumulation over substeps).  box: global index of
+ * the patch's level; it must lie within the faces / edges the advance
+ * computes (faces: normal index in [lo-k, hi+k+1], others in
+ * [lo-k-1, hi+k+1]; edges: along axis [lo-k, hi+k], others [lo-k, hi+k+1]). */
+typedef struct {
+  int32_t patch, kind, axis, mode;
+  mhd_box box;
+  double *dst;          /* device                                            */
+} mhd_capture;
+
+/* One flux-register deposit (Sec. 2.2: restriction of fluxes from the fine
+ * level and synchronisation at coarse-fine faces): for each coarse face of
+ * `box` (kind MHD_CAP_FACE, normal `axis`) the correction
+ *   dF_q = 0.25 * (sum of the 4 fine sub-face registers) - coarse register,
+ * for each coarse edge (kind MHD_CAP_EDGE, along `axis`)
+ *   dE = 0.5 * (sum of the 2 fine segment registers) - coarse register,
+ * is written into the coarse patch's correction planes (18 FP64 planes with
+ * the patch's strides: plane 5 d + q holds dF_q of axis-d faces, plane 15 + a
+ * the axis-a dE).  fine: register over fine_box (fine global index, x
+ * fastest); coarse_reg: register over box. */
+typedef struct {
+  int32_t coarse, kind, axis, pad;
+  mhd_box box;          /* coarse global index                               */
+  mhd_box fine_box;
+  const double *fine;   /* device                                            */
+  const double *coarse_reg;
+} mhd_deposit;
 
 /* Context: owns scratch memory and device copies of small host tables on
  * CUDA device `device`.  *out is NULL on failure. */
@@ -124,10 +178,52 @@ mhd_status mhd_cfl_dt(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
  * NULL for zeros) and the face fields on that box; it needs valid data on
  * the interior grown by grow[p] + 2 and requires grow[p] + 2 <= nghost
  * (Sec. 2.3: the update box shrinks by n_ghost = 2 per substep).  Patches
- * must not share memory.  On return the work is enqueued on `stream`. */
+ * must not share memory.  caps (host, ncap entries, may be NULL) capture
+ * dt * F and dt * E of this step into FP64 flux registers (mhd_capture).  On
+ * return the work is enqueued on `stream`. */
 mhd_status mhd_patch_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
                              const int32_t *grow, const double *d_dt,
-                             const double *dt_scale, void *stream);
+                             const double *dt_scale, const mhd_capture *caps,
+                             int32_t ncap, void *stream);
+
+/* Prolongation (P of Sec. 2.2: pre-advance coarse data into the fine ghost
+ * zones, Sec. 2.3) of the coarse cells of each item into its fine patch: the
+ * 8 fine cells get U_c + (+-h_x) + (+-h_y) + (+-h_z), h_d = 0.25 minmod of the
+ * coarse one-sided differences (conservative limited linear); the faces of
+ * those fine cells (lower faces, plus the array's extra upper face) get a
+ * divergence-free reconstruction inside the coarse cell (Balsara 2001 for
+ * R = 2): each coarse face contributes its value and its minmod transverse
+ * quarter-slopes, and the quadratic field matching those traces with
+ * div B = 0 gives the inner faces.  The fine patch's own interior faces are
+ * never written.  The coarse cells and their one-cell stencil must lie in the
+ * coarse arrays, the fine cells in the fine arrays.  Coarse and fine patches
+ * share one dtype. */
+mhd_status mhd_prolong(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc,
+                       const mhd_patch_desc *fine, int32_t nf,
+                       const mhd_prolong_item *items, int32_t n, void *stream);
+
+/* Restriction (R of Sec. 2.2): every item cell inside the coarse interior =
+ * 0.125 (sum of its 8 fine cells); every face of an item cell that is a face
+ * of the coarse interior = 0.25 (sum of its 4 fine sub-faces).  Lower faces
+ * are written in a first pass and upper faces in a second, so a coarse face
+ * covered by two fine patches, or owned by two coarse patches, gets one
+ * value. */
+mhd_status mhd_restrict(mhd_ctx *ctx, const mhd_patch_desc *fine, int32_t nf,
+                        const mhd_patch_desc *coarse, int32_t nc,
+                        const mhd_restrict_item *items, int32_t n, void *stream);
+
+/* Refluxing (Sec. 2.2: fine fluxes restricted to the coarse level at the
+ * coarse-fine boundary): zeroes the correction planes corr[p] (host array of
+ * nc device pointers, NULL for coarse patches without children; 18 FP64
+ * planes each, see mhd_deposit), executes the deposits, then corrects every
+ * interior cell and face of those coarse patches:
+ *   U_q -= (dF_x(+x) - dF_x)/dx - (dF_y(+y) - dF_y)/dy - (dF_z(+z) - dF_z)/dz,
+ *   B_a -= (dE_c(+b) - dE_c)/dx_b - (dE_b(+c) - dE_b)/dx_c   (b, c = a+1, a+2),
+ * in FP64 (FP32 state is rounded once).  Call mhd_restrict afterwards: it
+ * overwrites the covered cells and faces. */
+mhd_status mhd_reflux(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc,
+                      double *const *corr, const mhd_deposit *deps, int32_t nd,
+                      void *stream);
 
 /* Ghost fill (Sec. 2.2 S step "update ghost cells"; periodic images and
  * same-level neighbours): executes the copies of `list` (host array) in one
@@ -178,7 +274,7 @@ int64_t mhd_launch_count(const mhd_ctx *ctx);
 /* Per-kernel event timer (diagnostics, no counterpart in the paper).  While
  * enabled, every launch of the context is bracketed by two CUDA events
  * recorded on the launching stream.  mhd_timing_read synchronises on the
- * pending events and returns, for kernel id `kernel` (0 <= id < 9, names from
+ * pending events and returns, for kernel id `kernel` (0 <= id < 10, names from
  * mhd_kernel_name), the summed device time in ms and the number of launches
  * since the last reset; mhd_timing_reset clears the sums. */
 mhd_status mhd_timing_enable(mhd_ctx *ctx, int32_t on);

@@ -806,13 +806,47 @@ static int gidx(int global, int lo, int g) { return global - lo + g; }
 
 static double minmod2(double a, double b) { return orc_limiter(1, a, b); }
 
+/* thermal energy E - |M|^2/(2 rho) - |Bc|^2/2 of cell c (Bc = face means) */
+static double thermal(const orc_patch *P, int64_t c) {
+  double rho = P->U[0][c];
+  double ke = 0.5 * (P->U[1][c] * P->U[1][c] + P->U[2][c] * P->U[2][c] + P->U[3][c] * P->U[3][c]) / rho;
+  double bx = 0.5 * (P->B[0][c] + P->B[0][c + P->s[0]]);
+  double by = 0.5 * (P->B[1][c] + P->B[1][c + P->s[1]]);
+  double bz = 0.5 * (P->B[2][c] + P->B[2][c + P->s[2]]);
+  double me = 0.5 * (bx * bx + by * by + bz * bz);
+  return P->U[4][c] - ke - me;
+}
+
+/* fine axis-a face at position pos (0 lower coarse face, 1 inner, 2 upper)
+ * and transverse sub-indices sub[] of the reconstruction in one coarse cell */
+static double pface(int a, int pos, const int *sub, double m[3][2], double qs[3][2][3],
+                    double lin[3][3], const double *c0) {
+  int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+  if (pos == 1) {
+    double sl = sub[lo_t] ? 0.5 * lin[a][lo_t] : -0.5 * lin[a][lo_t];
+    double sh = sub[hi_t] ? 0.5 * lin[a][hi_t] : -0.5 * lin[a][hi_t];
+    return c0[a] + sl + sh;
+  }
+  int sd = pos == 2;
+  double sl = sub[lo_t] ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
+  double sh = sub[hi_t] ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
+  return m[a][sd] + sl + sh;
+}
+
+
 /* Prolongation of the coarse cells of box [clo, chi] (coarse global index)
  * of coarse patch Pc (interior starting at global cglo) into fine patch Pf
  * (interior starting at fglo): for each coarse cell, the 8 fine cells and
  * the lower faces of those fine cells (plus the extra upper face where a fine
  * cell is the last of its array), skipping the fine patch's own interior
- * faces.  Cells: U_f = U_c + (+-h_x) + (+-h_y) + (+-h_z), h_d = 0.25 *
- * minmod of the coarse one-sided differences (conservative limited linear).
+ * faces.  Density and momentum: U_f = U_c + (+-h_x) + (+-h_y) + (+-h_z), h_d =
+ * 0.25 * minmod of the coarse one-sided differences (conservative limited
+ * linear).  Total energy: the thermal energy e = E - |M|^2/(2 rho) - |Bc|^2/2
+ * is prolonged the same way (so e_f >= e_c / 4 > 0) and E_f = (e_f +
+ * |M_f|^2/(2 rho_f)) + |Bc_f|^2/2, Bc_f the mean of the fine cell's two faces
+ * of the reconstruction below; prolonging E itself left negative pressure in
+ * low-beta ghost cells.
  * Faces: divergence-free reconstruction inside the coarse cell (Balsara
  * 2001 for R = 2): each coarse face gives its mean and its minmod transverse
  * quarter-slopes; the quadratic field Bx = a0 + ax x + ay y + az z + axx x^2 +
@@ -831,14 +865,20 @@ ORC_EXPORT void orc_prolong(const orc_patch *Pc, const int32_t *cglo, const orc_
         int ci[3] = {gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc)};
         int64_t c = ix(Pc, ci[0], ci[1], ci[2]);
         /* cells */
-        double uc[5], h[5][3];
-        for (int q = 0; q < 5; ++q) {
+        double uc[4], h[4][3], ec, he[3];
+        for (int q = 0; q < 4; ++q) {
           uc[q] = Pc->U[q][c];
           for (int d = 0; d < 3; ++d) {
             double a = uc[q] - Pc->U[q][c - sc[d]];
             double b = Pc->U[q][c + sc[d]] - uc[q];
             h[q][d] = 0.25 * minmod2(a, b);
           }
+        }
+        ec = thermal(Pc, c);
+        for (int d = 0; d < 3; ++d) {
+          double a = ec - thermal(Pc, c - sc[d]);
+          double b = thermal(Pc, c + sc[d]) - ec;
+          he[d] = 0.25 * minmod2(a, b);
         }
         /* faces: mean and transverse quarter-slopes of the six coarse faces */
         double m[3][2], qs[3][2][3];  /* qs[normal][side][transverse axis] */
@@ -875,13 +915,31 @@ ORC_EXPORT void orc_prolong(const orc_patch *Pc, const int32_t *cglo, const orc_
               int fi[3];
               for (int d = 0; d < 3; ++d) fi[d] = gidx(2 * (d == 0 ? I : d == 1 ? J : K) + sub[d], fglo[d], gf);
               int64_t x = ix(Pf, fi[0], fi[1], fi[2]);
-              for (int q = 0; q < 5; ++q) {
+              double uf[4];
+              for (int q = 0; q < 4; ++q) {
                 double u = uc[q];
                 u = u + (fa ? h[q][0] : -h[q][0]);
                 u = u + (fb ? h[q][1] : -h[q][1]);
                 u = u + (fc ? h[q][2] : -h[q][2]);
+                uf[q] = u;
                 Pf->U[q][x] = u;
               }
+              /* face-averaged field of the reconstruction (a function of the
+               * coarse data only, so every patch that prolongs this cell gets
+               * the same energy) */
+              double bc[3];
+              for (int a = 0; a < 3; ++a) {
+                double f0 = pface(a, sub[a], sub, m, qs, lin, c0);
+                double f1 = pface(a, sub[a] + 1, sub, m, qs, lin, c0);
+                bc[a] = 0.5 * (f0 + f1);
+              }
+              double e = ec;
+              e = e + (fa ? he[0] : -he[0]);
+              e = e + (fb ? he[1] : -he[1]);
+              e = e + (fc ? he[2] : -he[2]);
+              double kef = 0.5 * (uf[1] * uf[1] + uf[2] * uf[2] + uf[3] * uf[3]) / uf[0];
+              double mef = 0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+              Pf->U[4][x] = e + kef + mef;
               for (int a = 0; a < 3; ++a) {
                 int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
                 int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;

@@ -24,6 +24,7 @@ UNITS = {
     "advance_f64.cu": ["--fmad=false"],
     "advance_f32.cu": ["--fmad=true"],
     "noalloc.cu": ["--fmad=false"],
+    "amr_ops.cu": ["--fmad=false"],
 }
 
 

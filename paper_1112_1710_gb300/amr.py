@@ -1,0 +1,326 @@
+"""Static AMR hierarchy on the GPU: metadata (ghost copies, prolongation and
+restriction items, FP64 flux registers and their deposits) and the subcycled
+coarse step of the paper's life cycle (Sec. 2.2) with extended ghost zones
+(Sec. 2.3), refinement ratio 2.  Every level operation is one batched call of
+``libmhdgpu.so`` over all patches of a level.
+
+One coarse step (AMR(0) of Sec. 2.2):
+  dt_0 = min over levels of 2^l * (CFL dt of level l)      (device scalar)
+  fill level 0 (periodic images, same-level copies);  step(0, 0)
+step(l, k):
+  P: prolong level l (pre-advance) into the ghost zones of level l+1, then
+     same-level copies on level l+1
+  A: advance level l (update box = interior grown by k, dt_l = dt_0 / 2^l),
+     capturing dt*F and dt*E on coarse-fine faces and edges (FP64)
+  step(l+1, 2); S: same-level copies on l+1; step(l+1, 0)
+  reflux level l from the registers; R: restrict l+1 onto l
+"""
+from __future__ import annotations
+
+import ctypes as C
+import itertools
+
+import numpy as np
+import torch
+
+from . import capi
+from .patch import Patch
+
+
+def _isect(alo, ahi, blo, bhi):
+    """Vectorised box intersection: alo/ahi (M, 3) with one box (3,)."""
+    lo = np.maximum(alo, blo)
+    hi = np.minimum(ahi, bhi)
+    ok = np.all(lo <= hi, axis=1)
+    return lo, hi, ok
+
+
+def _vol(lo, hi):
+    return int(np.prod(np.asarray(hi) - np.asarray(lo) + 1))
+
+
+class Hierarchy:
+    def __init__(self, boxes, n0, states, dx0, g=4, dtype="f32", ctx=None, stream=None, device="cuda"):
+        """boxes[l] = [(lo, hi)]; states[l][i] = float64 numpy array (synth layout)."""
+        self.n0, self.g, self.dtype = n0, g, dtype
+        self.device = torch.device(device)
+        self.gpu = self.device.type == "cuda"  # on the CPU only the metadata is built (tests)
+        self.ctx = ctx if (ctx is not None or not self.gpu) else capi.mhd_ctx_create()
+        self.own_ctx = ctx is None and self.gpu
+        self.stream = (stream or torch.cuda.current_stream(self.device)) if self.gpu else None
+        self.levels = []
+        for l, bl in enumerate(boxes):
+            dx = tuple(v / 2 ** l for v in dx0)
+            pats = []
+            for i, (lo, hi) in enumerate(bl):
+                n = tuple(hi[d] - lo[d] + 1 for d in range(3))
+                pats.append(Patch.from_array(states[l][i], lo, n, g, dx, dtype=dtype, device=self.device,
+                                             level=l, patch_id=i))
+            self.levels.append(pats)
+        self.descs = [[p.desc() for p in pats] for pats in self.levels] if self.gpu else None
+        self.lo = [np.array([p.lo for p in pats], dtype=np.int64) for pats in self.levels]
+        self.hi = [np.array([p.hi for p in pats], dtype=np.int64) for pats in self.levels]
+        self.d_dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self._build()
+
+    @property
+    def sp(self) -> int:
+        return self.stream.cuda_stream
+
+    @property
+    def nlev(self) -> int:
+        return len(self.levels)
+
+    # ------------------------------------------------------------------ metadata
+    def _copies(self, l):
+        n = self.n0 * 2 ** l
+        g = self.g
+        lo, hi = self.lo[l], self.hi[l]
+        near = np.any(lo <= g + 1, axis=1) | np.any(hi >= n - g - 2, axis=1)
+        shifts = [(0, 0, 0)]
+        if near.any():
+            shifts = [s for s in itertools.product((-n, 0, n), repeat=3)]
+        out = []
+        for di in range(len(lo)):
+            elo = lo[di] - g - 1
+            ehi = hi[di] + g + 1
+            for sh in shifts:
+                sh = np.array(sh)
+                blo, bhi, ok = _isect(lo + sh, hi + sh, elo, ehi)
+                if sh.any():
+                    pass
+                else:
+                    ok[di] = False
+                for si in np.nonzero(ok)[0]:
+                    c = capi.mhd_copy()
+                    c.src = int(si)
+                    c.dst = int(di)
+                    c.box.lo[:] = [int(v) for v in blo[si]]
+                    c.box.hi[:] = [int(v) for v in bhi[si]]
+                    c.offset[:] = [int(-v) for v in sh]
+                    out.append(c)
+        return out
+
+    def _prolongs(self, l):
+        g = self.g
+        clo, chi = self.lo[l], self.hi[l]
+        out = []
+        for fi, (flo, fhi) in enumerate(zip(self.lo[l + 1], self.hi[l + 1])):
+            el, eh = flo - g, fhi + g
+            slabs = [((el[0], el[1], el[2]), (eh[0], eh[1], flo[2] - 1)),
+                     ((el[0], el[1], fhi[2] + 1), (eh[0], eh[1], eh[2])),
+                     ((el[0], el[1], flo[2]), (eh[0], flo[1] - 1, fhi[2])),
+                     ((el[0], fhi[1] + 1, flo[2]), (eh[0], eh[1], fhi[2])),
+                     ((el[0], flo[1], flo[2]), (flo[0] - 1, fhi[1], fhi[2])),
+                     ((fhi[0] + 1, flo[1], flo[2]), (eh[0], fhi[1], fhi[2]))]
+            for (slo, shi) in slabs:
+                cl = np.array(slo) // 2
+                ch = np.array(shi) // 2
+                blo, bhi, ok = _isect(clo, chi, cl, ch)
+                for ci in np.nonzero(ok)[0]:
+                    it = capi.mhd_prolong_item()
+                    it.coarse = int(ci)
+                    it.fine = int(fi)
+                    it.box = capi.box(blo[ci], bhi[ci])
+                    out.append(it)
+        return out
+
+    def _restricts(self, l):
+        clo, chi = self.lo[l], self.hi[l]
+        out = []
+        for fi, (flo, fhi) in enumerate(zip(self.lo[l + 1], self.hi[l + 1])):
+            cl, ch = flo // 2, (fhi + 1) // 2 - 1
+            blo, bhi, ok = _isect(clo - 1, chi + 1, cl, ch)
+            for ci in np.nonzero(ok)[0]:
+                it = capi.mhd_restrict_item()
+                it.fine = int(fi)
+                it.coarse = int(ci)
+                it.box = capi.box(blo[ci], bhi[ci])
+                out.append(it)
+        return out
+
+    def _build(self):
+        L = self.nlev
+        self.copy_lists = [self._copies(l) for l in range(L)]
+        self.prolong_lists = [self._prolongs(l) for l in range(L - 1)]
+        self.restrict_lists = [self._restricts(l) for l in range(L - 1)]
+        # flux registers: (size, owner) records, then one FP64 buffer
+        regs = []          # (values,)
+        fine_caps = {l: [] for l in range(L)}     # (patch, kind, axis, lo, hi, reg)
+        coarse_caps = {l: [] for l in range(L)}
+        deposits = {l: [] for l in range(L)}      # (coarse, kind, axis, lo, hi, fine reg, fine lo, fine hi, coarse reg)
+
+        def new_reg(nvals):
+            regs.append(nvals)
+            return len(regs) - 1
+
+        for l in range(1, L):
+            clo_all, chi_all = self.lo[l - 1], self.hi[l - 1]
+            for fi, (flo, fhi) in enumerate(zip(self.lo[l], self.hi[l])):
+                for d in range(3):
+                    for side in (0, 1):
+                        fidx = int(flo[d]) if side == 0 else int(fhi[d]) + 1
+                        cidx = fidx // 2
+                        outc = cidx - 1 if side == 0 else cidx
+                        # fine faces of the side
+                        rlo, rhi = flo.copy(), fhi.copy()
+                        rlo[d] = rhi[d] = fidx
+                        rf = new_reg(5 * _vol(rlo, rhi))
+                        fine_caps[l].append((fi, 0, d, rlo, rhi, rf))
+                        cl, ch = flo // 2, (fhi + 1) // 2 - 1
+                        cl = cl.copy()
+                        ch = ch.copy()
+                        cl[d] = ch[d] = cidx
+                        for ci in range(len(clo_all)):
+                            if not (clo_all[ci][d] <= outc <= chi_all[ci][d]):
+                                continue
+                            blo, bhi = cl.copy(), ch.copy()
+                            ok = True
+                            for e in range(3):
+                                if e == d:
+                                    continue
+                                blo[e] = max(cl[e], clo_all[ci][e])
+                                bhi[e] = min(ch[e], chi_all[ci][e])
+                                ok = ok and blo[e] <= bhi[e]
+                            if not ok:
+                                continue
+                            rc = new_reg(5 * _vol(blo, bhi))
+                            coarse_caps[l - 1].append((ci, 0, d, blo, bhi, rc))
+                            deposits[l - 1].append((ci, 0, d, blo, bhi, rf, rlo, rhi, rc))
+                        # edges in the side plane
+                        for a in range(3):
+                            if a == d:
+                                continue
+                            tt = 3 - a - d
+                            elo, ehi = flo.copy(), fhi.copy()
+                            elo[d] = ehi[d] = fidx
+                            ehi[tt] = fhi[tt] + 1
+                            re = new_reg(_vol(elo, ehi))
+                            fine_caps[l].append((fi, 1, a, elo, ehi, re))
+                            cl, ch = (flo // 2).copy(), ((fhi + 1) // 2 - 1).copy()
+                            cl[d] = ch[d] = cidx
+                            ch[tt] = (fhi[tt] + 1) // 2
+                            top = chi_all + 1
+                            top[:, a] -= 1
+                            blo, bhi, ok = _isect(clo_all, top, cl, ch)
+                            for ci in np.nonzero(ok)[0]:
+                                rc = new_reg(_vol(blo[ci], bhi[ci]))
+                                coarse_caps[l - 1].append((int(ci), 1, a, blo[ci], bhi[ci], rc))
+                                deposits[l - 1].append((int(ci), 1, a, blo[ci], bhi[ci], re, elo, ehi, rc))
+        offs = np.concatenate([[0], np.cumsum(regs)]).astype(np.int64)
+        self.regbuf = torch.zeros(max(1, int(offs[-1])), dtype=torch.float64, device=self.device)
+        base = self.regbuf.data_ptr()
+        ptr = lambda r: base + 8 * int(offs[r])
+
+        def cap_array(items, mode_fine):
+            arr = (capi.mhd_capture * max(1, len(items)))()
+            for t, (p, kind, ax, lo, hi, r, fine_side) in enumerate(items):
+                arr[t].patch = int(p)
+                arr[t].kind = kind
+                arr[t].axis = ax
+                arr[t].mode = mode_fine if fine_side else 0
+                arr[t].box = capi.box(lo, hi)
+                arr[t].dst = ptr(r)
+            return arr, len(items)
+
+        self.caps = {}
+        for l in range(L):
+            items = [c + (True,) for c in fine_caps[l]] + [c + (False,) for c in coarse_caps[l]]
+            self.caps[(l, True)] = cap_array(items, 0) if items else None
+            self.caps[(l, False)] = cap_array(items, 1) if items else None
+        self.deps = {}
+        self.corr = {}
+        for l in range(L - 1):
+            dl = deposits[l]
+            arr = (capi.mhd_deposit * max(1, len(dl)))()
+            need = sorted({int(x[0]) for x in dl})
+            corr = {}
+            for ci in need:
+                nelem = int(np.prod(self.levels[l][ci].state.shape[1:]))
+                corr[ci] = torch.zeros(18 * nelem, dtype=torch.float64, device=self.device)
+            for t, (ci, kind, ax, lo, hi, rf, flo, fhi, rc) in enumerate(dl):
+                arr[t].coarse = int(ci)
+                arr[t].kind = kind
+                arr[t].axis = ax
+                arr[t].box = capi.box(lo, hi)
+                arr[t].fine_box = capi.box(flo, fhi)
+                arr[t].fine = ptr(rf)
+                arr[t].coarse_reg = ptr(rc)
+            self.deps[l] = (arr, len(dl))
+            self.corr[l] = [corr[ci].data_ptr() if ci in corr else None for ci in range(len(self.levels[l]))]
+            self._corr_keep = getattr(self, "_corr_keep", []) + list(corr.values())
+        self.fine_caps, self.coarse_caps, self.deposit_list = fine_caps, coarse_caps, deposits
+        # prebuilt ctypes arrays of the static lists
+        self._copy_arr = [capi._structs(capi.mhd_copy, cl) for cl in self.copy_lists]
+        self._prolong_arr = [capi._structs(capi.mhd_prolong_item, pl) for pl in self.prolong_lists]
+        self._restrict_arr = [capi._structs(capi.mhd_restrict_item, rl) for rl in self.restrict_lists]
+        if not self.gpu:
+            return
+        self._desc_arr = [capi._descs(d) for d in self.descs]
+        self._all_descs = capi._descs([d for dl in self.descs for d in dl])
+        self._all_scale = capi._arr(C.c_double, [2.0 ** l for l, dl in enumerate(self.descs) for _ in dl])
+        self._dt_scale = [capi._arr(C.c_double, [0.5 ** l] * len(dl)) for l, dl in enumerate(self.descs)]
+
+    # ------------------------------------------------------------------ operations
+    def fill(self, l):
+        arr, n = self._desc_arr[l]
+        ca, nc = self._copy_arr[l]
+        if nc:
+            capi._check(self.ctx, capi.load().mhd_ghost_fill(self.ctx, arr, n, ca, nc, self.sp))
+
+    def prolong(self, l):
+        capi.mhd_prolong(self.ctx, self.descs[l], self.descs[l + 1], self._prolong_arr[l], self.sp)
+
+    def restrict(self, l):
+        capi.mhd_restrict(self.ctx, self.descs[l + 1], self.descs[l], self._restrict_arr[l], self.sp)
+
+    def advance(self, l, k, first):
+        arr, n = self._desc_arr[l]
+        grow = capi._arr(C.c_int32, [k] * n)
+        caps = self.caps[(l, first)]
+        ca, nca = caps if caps is not None else (None, 0)
+        capi._check(self.ctx, capi.load().mhd_patch_advance(self.ctx, arr, n, grow, self.d_dt.data_ptr(),
+                                                            self._dt_scale[l], ca, nca, self.sp))
+
+    def reflux(self, l):
+        capi.mhd_reflux(self.ctx, self.descs[l], self.corr[l], self.deps[l], self.sp)
+
+    def cfl(self):
+        arr, n = self._all_descs
+        capi._check(self.ctx, capi.load().mhd_cfl_dt(self.ctx, arr, n, self._all_scale, self.d_dt.data_ptr(),
+                                                     self.sp))
+
+    def step(self, l, k, first=True):
+        last = l + 1 >= self.nlev
+        if not last:
+            self.prolong(l)
+            self.fill(l + 1)
+        self.advance(l, k, first)
+        if not last:
+            self.step(l + 1, 2, True)
+            self.fill(l + 1)
+            self.step(l + 1, 0, False)
+            self.reflux(l)
+            self.restrict(l)
+
+    def initialise(self):
+        for l in range(self.nlev - 2, -1, -1):
+            self.restrict(l)
+        self.fill(0)
+
+    def coarse_step(self, dt: float | None = None):
+        if dt is None:
+            self.cfl()
+        else:
+            with torch.cuda.stream(self.stream):
+                self.d_dt.fill_(float(dt))
+        self.fill(0)
+        self.step(0, 0)
+
+    def cell_updates_per_coarse_step(self) -> int:
+        return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)
+
+    def close(self):
+        if self.own_ctx and self.ctx:
+            capi.mhd_ctx_destroy(self.ctx)
+            self.ctx = None

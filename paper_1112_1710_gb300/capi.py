@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA"
 EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", "mhd_patch_advance",
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
-           "mhd_kernel_name", "mhd_conservation_sums_static")
-N_KERNELS = 9
+           "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux")
+N_KERNELS = 10
+MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 
 
 class MHDError(RuntimeError):
@@ -49,6 +50,31 @@ class mhd_params(C.Structure):
 
 class mhd_copy(C.Structure):
     _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("box", mhd_box), ("offset", C.c_int32 * 3)]
+
+
+class mhd_prolong_item(C.Structure):
+    _fields_ = [("coarse", C.c_int32), ("fine", C.c_int32), ("box", mhd_box)]
+
+
+class mhd_restrict_item(C.Structure):
+    _fields_ = [("fine", C.c_int32), ("coarse", C.c_int32), ("box", mhd_box)]
+
+
+class mhd_capture(C.Structure):
+    _fields_ = [("patch", C.c_int32), ("kind", C.c_int32), ("axis", C.c_int32), ("mode", C.c_int32),
+                ("box", mhd_box), ("dst", C.c_void_p)]
+
+
+class mhd_deposit(C.Structure):
+    _fields_ = [("coarse", C.c_int32), ("kind", C.c_int32), ("axis", C.c_int32), ("pad", C.c_int32),
+                ("box", mhd_box), ("fine_box", mhd_box), ("fine", C.c_void_p), ("coarse_reg", C.c_void_p)]
+
+
+def box(lo, hi) -> mhd_box:
+    b = mhd_box()
+    b.lo[:] = tuple(int(v) for v in lo)
+    b.hi[:] = tuple(int(v) for v in hi)
+    return b
 
 
 _lib = None
@@ -81,7 +107,17 @@ def load(build_if_missing: bool = False):
     L.mhd_cfl_dt.restype = i32
     L.mhd_cfl_dt.argtypes = [P, C.POINTER(mhd_patch_desc), i32, dp, P, P]
     L.mhd_patch_advance.restype = i32
-    L.mhd_patch_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), P, dp, P]
+    L.mhd_patch_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), P, dp,
+                                    C.POINTER(mhd_capture), i32, P]
+    L.mhd_prolong.restype = i32
+    L.mhd_prolong.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
+                              C.POINTER(mhd_prolong_item), i32, P]
+    L.mhd_restrict.restype = i32
+    L.mhd_restrict.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
+                               C.POINTER(mhd_restrict_item), i32, P]
+    L.mhd_reflux.restype = i32
+    L.mhd_reflux.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(C.c_void_p),
+                             C.POINTER(mhd_deposit), i32, P]
     L.mhd_ghost_fill.restype = i32
     L.mhd_ghost_fill.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_copy), i32, P]
     L.mhd_conservation_sums.restype = i32
@@ -157,11 +193,43 @@ def mhd_cfl_dt(ctx, patches, d_dt_out: int, stream: int = 0, scale=None) -> None
     _check(ctx, load().mhd_cfl_dt(ctx, arr, n, sc, d_dt_out, stream))
 
 
-def mhd_patch_advance(ctx, patches, d_dt: int, stream: int = 0, grow=None, dt_scale=None) -> None:
+def _structs(ctype, items):
+    items = list(items)
+    return (ctype * max(1, len(items)))(*items), len(items)
+
+
+def mhd_patch_advance(ctx, patches, d_dt: int, stream: int = 0, grow=None, dt_scale=None, caps=None) -> None:
     arr, n = _descs(patches)
     gr = _arr(C.c_int32, grow) if grow is not None else None
     sc = _arr(C.c_double, dt_scale) if dt_scale is not None else None
-    _check(ctx, load().mhd_patch_advance(ctx, arr, n, gr, d_dt, sc, stream))
+    if caps is None:
+        ca, nca = None, 0
+    elif isinstance(caps, tuple):  # (prebuilt ctypes array, count)
+        ca, nca = caps
+    else:
+        ca, nca = _structs(mhd_capture, caps)
+    _check(ctx, load().mhd_patch_advance(ctx, arr, n, gr, d_dt, sc, ca, nca, stream))
+
+
+def mhd_prolong(ctx, coarse, fine, items, stream: int = 0) -> None:
+    ca, nc = _descs(coarse)
+    fa, nf = _descs(fine)
+    it, ni = items if isinstance(items, tuple) else _structs(mhd_prolong_item, items)
+    _check(ctx, load().mhd_prolong(ctx, ca, nc, fa, nf, it, ni, stream))
+
+
+def mhd_restrict(ctx, fine, coarse, items, stream: int = 0) -> None:
+    fa, nf = _descs(fine)
+    ca, nc = _descs(coarse)
+    it, ni = items if isinstance(items, tuple) else _structs(mhd_restrict_item, items)
+    _check(ctx, load().mhd_restrict(ctx, fa, nf, ca, nc, it, ni, stream))
+
+
+def mhd_reflux(ctx, coarse, corr_ptrs, deposits, stream: int = 0) -> None:
+    ca, nc = _descs(coarse)
+    cp = (C.c_void_p * max(1, nc))(*[p or None for p in corr_ptrs])
+    dp_, nd = deposits if isinstance(deposits, tuple) else _structs(mhd_deposit, deposits)
+    _check(ctx, load().mhd_reflux(ctx, ca, nc, cp, dp_, nd, stream))
 
 
 def mhd_ghost_fill(ctx, patches, copies, stream: int = 0) -> None:

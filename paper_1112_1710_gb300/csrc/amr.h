@@ -1,0 +1,59 @@
+// amr.h -- device descriptors and launchers of the AMR level operations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace mhd {
+
+// One box item between two patch arrays: prolongation (a = coarse, b = fine)
+// or restriction (a = fine, b = coarse); box in coarse global cell index.
+struct DBoxItem {
+  int32_t a, b;
+  int32_t lo[3], ext[3];
+};
+
+// One flux-register capture on a patch: kind 0 = axis-normal faces (5 FP64
+// planes over the box), kind 1 = axis edges (1 plane); box in the patch's
+// array index space; mode 0 set, 1 add.
+struct DCapture {
+  int32_t patch, kind, axis, mode;
+  int32_t lo[3], ext[3];
+  double* dst;
+};
+
+// One deposit into a coarse patch's correction planes: box in coarse global
+// index (faces: face index = index of the upper cell; edges: storing cell).
+struct DDeposit {
+  int32_t coarse, kind, axis, pad;
+  int32_t lo[3], ext[3];
+  int32_t flo[3], fext[3];  // fine register box (fine global index)
+  const double* fine;       // fine register (5 planes for faces, 1 for edges)
+  const double* creg;       // coarse register over the box
+  double* corr;             // correction planes of the coarse patch (18 planes)
+};
+
+// Correction planes of one coarse patch.
+struct DCorr {
+  int32_t patch, pad;
+  int64_t count;  // 18 * nelem
+  double* base;
+};
+
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const BlockTask* tasks,
+                               int nblocks, const KernelTimer* tm, cudaStream_t s);
+cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, const DBoxItem* items,
+                           const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s);
+cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse, const DBoxItem* items,
+                            const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s);
+cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const BlockTask* tasks,
+                           int nblocks, const void* scratch, const double* d_dt, const KernelTimer* tm,
+                           cudaStream_t s);
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const BlockTask* zero_tasks,
+                          int nzero, const DDeposit* deps, const BlockTask* dep_tasks, int ndep,
+                          const BlockTask* corr_tasks, int ncorr, const KernelTimer* tm, cudaStream_t s);
+
+}  // namespace mhd

@@ -1,0 +1,500 @@
+// amr_ops.cu -- level operations of the subcycled AMR step (refinement ratio
+// 2; Sec. 2.2 Prolongation, Restriction, flux synchronisation): prolongation
+// into ghost zones, restriction, FP64 flux-register capture, deposit of the
+// register differences into correction planes, and the correction itself.
+// Built with --fmad=false; every expression follows one fixed evaluation
+// order.  A fine patch is aligned to its coarse level: fine global index =
+// 2 * coarse global index + {0, 1}.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "amr.h"
+#include "common.cuh"
+#include "physics.cuh"
+
+namespace mhd {
+
+namespace {
+
+__device__ __forceinline__ int64_t lin3(const DPatch& p, int i, int j, int k) {
+  return (int64_t)i + (int64_t)j * p.s1 + (int64_t)k * p.s2;
+}
+__device__ __forceinline__ int64_t sof(const DPatch& p, int d) {
+  return d == 0 ? (int64_t)1 : (d == 1 ? p.s1 : p.s2);
+}
+// is the axis-a face with array index ai a face of p's interior?
+__device__ __forceinline__ bool own_face(const DPatch& p, const int* ai, int a) {
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int top = (e == a) ? p.g + p.n[e] : p.g + p.n[e] - 1;
+    if (ai[e] < p.g || ai[e] > top) return false;
+  }
+  return true;
+}
+// does the axis-a face with array index ai exist in p's arrays?
+__device__ __forceinline__ bool face_exists(const DPatch& p, const int* ai, int a) {
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int top = (e == a) ? p.N[e] : p.N[e] - 1;
+    if (ai[e] < 0 || ai[e] > top) return false;
+  }
+  return true;
+}
+template <typename R> __device__ __forceinline__ R minmod(R a, R b) { return limiter<R>(1, a, b); }
+
+// thermal energy E - |M|^2/(2 rho) - |Bc|^2/2 of cell x (Bc = face means)
+template <typename R> __device__ __forceinline__ R thermal(const DPatch& p, int64_t x) {
+  const R rho = ((const R*)p.U[0])[x];
+  const R mx = ((const R*)p.U[1])[x], my = ((const R*)p.U[2])[x], mz = ((const R*)p.U[3])[x];
+  R ke = R(0.5) * (mx * mx + my * my + mz * mz) / rho;
+  R bx = R(0.5) * (((const R*)p.B[0])[x] + ((const R*)p.B[0])[x + 1]);
+  R by = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
+  R bz = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
+  R me = R(0.5) * (bx * bx + by * by + bz * bz);
+  return ((const R*)p.U[4])[x] - ke - me;
+}
+
+// fine axis-a face at position pos (0 lower coarse face, 1 inner, 2 upper)
+// and transverse sub-indices sub[] of the reconstruction in one coarse cell
+template <typename R>
+__device__ __forceinline__ R pface(int a, int pos, const int* sub, const R (&m)[3][2], const R (&qs)[3][2][3],
+                                   const R (&lin)[3][3], const R (&c0)[3]) {
+  const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+  if (pos == 1) {
+    R sl = sub[lo_t] ? R(0.5) * lin[a][lo_t] : R(-0.5) * lin[a][lo_t];
+    R sh = sub[hi_t] ? R(0.5) * lin[a][hi_t] : R(-0.5) * lin[a][hi_t];
+    return c0[a] + sl + sh;
+  }
+  const int sd = pos == 2;
+  R sl = sub[lo_t] ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
+  R sh = sub[hi_t] ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
+  return m[a][sd] + sl + sh;
+}
+
+__device__ __forceinline__ void box_cell(const int32_t* lo, const int32_t* ext, int e, int* c) {
+  c[0] = lo[0] + e % ext[0];
+  c[1] = lo[1] + (e / ext[0]) % ext[1];
+  c[2] = lo[2] + e / (ext[0] * ext[1]);
+}
+
+// ---------------------------------------------------------------- ghost copy
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_ghost2(const DPatch* __restrict__ P, const DCopy* __restrict__ C,
+                                                     const BlockTask* __restrict__ T, int pass) {
+  const BlockTask t = T[blockIdx.x];
+  const DCopy cp = C[t.patch];
+  const int e = t.start + threadIdx.x;
+  if (e >= cp.ext[0] * cp.ext[1] * cp.ext[2]) return;
+  int di[3];
+  box_cell(cp.lo, cp.ext, e, di);
+  const DPatch& d = P[cp.dst];
+  const DPatch& s = P[cp.src];
+  const int si[3] = {di[0] + cp.off[0], di[1] + cp.off[1], di[2] + cp.off[2]};
+  const int64_t xd = lin3(d, di[0], di[1], di[2]);
+  const int64_t xs = lin3(s, si[0], si[1], si[2]);
+  if (pass == 0) {
+    const bool cell_in = di[0] >= 0 && di[0] < d.N[0] && di[1] >= 0 && di[1] < d.N[1] && di[2] >= 0 && di[2] < d.N[2];
+    if (cell_in)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd] = ((const R*)s.U[q])[xs];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (face_exists(d, di, a) && !own_face(d, di, a)) ((R*)d.B[a])[xd] = ((const R*)s.B[a])[xs];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (di[a] != cp.lo[a] + cp.ext[a] - 1) continue;
+      int du[3] = {di[0], di[1], di[2]};
+      du[a] += 1;
+      if (!face_exists(d, du, a) || own_face(d, du, a)) continue;
+      ((R*)d.B[a])[xd + sof(d, a)] = ((const R*)s.B[a])[xs + sof(s, a)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- prolongation
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_prolong(const DPatch* __restrict__ PC, const DPatch* __restrict__ PF,
+                                                      const DBoxItem* __restrict__ items,
+                                                      const BlockTask* __restrict__ T) {
+  const BlockTask t = T[blockIdx.x];
+  const DBoxItem it = items[t.patch];
+  const int e = t.start + threadIdx.x;
+  if (e >= it.ext[0] * it.ext[1] * it.ext[2]) return;
+  int C3[3];
+  box_cell(it.lo, it.ext, e, C3);
+  const DPatch& pc = PC[it.a];
+  const DPatch& pf = PF[it.b];
+  const int ci[3] = {C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]};
+  const int64_t c = lin3(pc, ci[0], ci[1], ci[2]);
+  R uc[4], h[4][3], he[3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R* Uq = (const R*)pc.U[q];
+    uc[q] = Uq[c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R a = uc[q] - Uq[c - sof(pc, d)];
+      R b = Uq[c + sof(pc, d)] - uc[q];
+      h[q][d] = R(0.25) * minmod(a, b);
+    }
+  }
+  const R ec = thermal<R>(pc, c);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R a = ec - thermal<R>(pc, c - sof(pc, d));
+    R b = thermal<R>(pc, c + sof(pc, d)) - ec;
+    he[d] = R(0.25) * minmod(a, b);
+  }
+  R m[3][2], qs[3][2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R* Ba = (const R*)pc.B[a];
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const int64_t f = c + (sd ? sof(pc, a) : 0);
+      m[a][sd] = Ba[f];
+#pragma unroll
+      for (int tt = 0; tt < 3; ++tt) {
+        if (tt == a) {
+          qs[a][sd][tt] = R(0);
+          continue;
+        }
+        R lo = m[a][sd] - Ba[f - sof(pc, tt)];
+        R hi = Ba[f + sof(pc, tt)] - m[a][sd];
+        qs[a][sd][tt] = R(0.25) * minmod(lo, hi);
+      }
+    }
+  }
+  R lin[3][3], crs[3][3], sq[3], c0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int tt = 0; tt < 3; ++tt) {
+      if (tt == a) {
+        lin[a][tt] = R(0);
+        crs[a][tt] = R(0);
+        continue;
+      }
+      lin[a][tt] = qs[a][1][tt] + qs[a][0][tt];
+      crs[a][tt] = qs[a][1][tt] - qs[a][0][tt];
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    sq[a] = R(-0.5) * (crs[b][a] + crs[cc][a]);
+    c0[a] = R(0.5) * (m[a][0] + m[a][1]) - sq[a];
+  }
+  for (int fc = 0; fc < 2; ++fc)
+    for (int fb = 0; fb < 2; ++fb)
+      for (int fa = 0; fa < 2; ++fa) {
+        const int sub[3] = {fa, fb, fc};
+        int fi[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fi[d] = 2 * C3[d] + sub[d] - pf.glo[d];
+        const int64_t x = lin3(pf, fi[0], fi[1], fi[2]);
+        R uf[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          R u = uc[q];
+          u = u + (fa ? h[q][0] : -h[q][0]);
+          u = u + (fb ? h[q][1] : -h[q][1]);
+          u = u + (fc ? h[q][2] : -h[q][2]);
+          uf[q] = u;
+          ((R*)pf.U[q])[x] = u;
+        }
+        R bc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          R f0 = pface<R>(a, sub[a], sub, m, qs, lin, c0);
+          R f1 = pface<R>(a, sub[a] + 1, sub, m, qs, lin, c0);
+          bc[a] = R(0.5) * (f0 + f1);
+        }
+        R en = ec;
+        en = en + (fa ? he[0] : -he[0]);
+        en = en + (fb ? he[1] : -he[1]);
+        en = en + (fc ? he[2] : -he[2]);
+        R kef = R(0.5) * (uf[1] * uf[1] + uf[2] * uf[2] + uf[3] * uf[3]) / uf[0];
+        R mef = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        ((R*)pf.U[4])[x] = en + kef + mef;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+          const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+          for (int up = 0; up < 2; ++up) {
+            int fidx[3] = {fi[0], fi[1], fi[2]};
+            if (up) {
+              if (fi[a] != pf.N[a] - 1) continue;
+              fidx[a] += 1;
+            }
+            if (own_face(pf, fidx, a)) continue;
+            const int pos = sub[a] + up;
+            R v;
+            if (pos == 1) {
+              R sl = sub[lo_t] ? R(0.5) * lin[a][lo_t] : R(-0.5) * lin[a][lo_t];
+              R sh = sub[hi_t] ? R(0.5) * lin[a][hi_t] : R(-0.5) * lin[a][hi_t];
+              v = c0[a] + sl + sh;
+            } else {
+              const int sd = pos == 2;
+              R sl = sub[lo_t] ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
+              R sh = sub[hi_t] ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
+              v = m[a][sd] + sl + sh;
+            }
+            ((R*)pf.B[a])[lin3(pf, fidx[0], fidx[1], fidx[2])] = v;
+          }
+        }
+      }
+}
+
+// ---------------------------------------------------------------- restriction
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_restrict(const DPatch* __restrict__ PF, const DPatch* __restrict__ PC,
+                                                       const DBoxItem* __restrict__ items,
+                                                       const BlockTask* __restrict__ T, int pass) {
+  const BlockTask t = T[blockIdx.x];
+  const DBoxItem it = items[t.patch];
+  const int e = t.start + threadIdx.x;
+  if (e >= it.ext[0] * it.ext[1] * it.ext[2]) return;
+  int C3[3];
+  box_cell(it.lo, it.ext, e, C3);
+  const DPatch& pf = PF[it.a];
+  const DPatch& pc = PC[it.b];
+  const int ca0[3] = {C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]};
+  const bool inside = ca0[0] >= pc.g && ca0[0] < pc.g + pc.n[0] && ca0[1] >= pc.g && ca0[1] < pc.g + pc.n[1] &&
+                      ca0[2] >= pc.g && ca0[2] < pc.g + pc.n[2];
+  if (pass == 0 && inside) {
+    const int64_t c = lin3(pc, ca0[0], ca0[1], ca0[2]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const R* Fq = (const R*)pf.U[q];
+      R s = R(0);
+      bool first = true;
+      for (int fc = 0; fc < 2; ++fc)
+        for (int fb = 0; fb < 2; ++fb)
+          for (int fa = 0; fa < 2; ++fa) {
+            R v = Fq[lin3(pf, 2 * C3[0] + fa - pf.glo[0], 2 * C3[1] + fb - pf.glo[1], 2 * C3[2] + fc - pf.glo[2])];
+            s = first ? v : s + v;
+            first = false;
+          }
+      ((R*)pc.U[q])[c] = R(0.125) * s;
+    }
+  }
+  const int chi[3] = {it.lo[0] + it.ext[0] - 1, it.lo[1] + it.ext[1] - 1, it.lo[2] + it.ext[2] - 1};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+    const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+    const int up = pass;
+    if (up && C3[a] != chi[a]) continue;
+    int cf[3] = {ca0[0], ca0[1], ca0[2]};
+    cf[a] += up;
+    if (!own_face(pc, cf, a)) continue;
+    const R* Fa = (const R*)pf.B[a];
+    R s = R(0);
+    bool first = true;
+    for (int j2 = 0; j2 < 2; ++j2)
+      for (int j1 = 0; j1 < 2; ++j1) {
+        int f[3];
+        f[a] = 2 * (C3[a] + up);
+        f[lo_t] = 2 * C3[lo_t] + j1;
+        f[hi_t] = 2 * C3[hi_t] + j2;
+        R v = Fa[lin3(pf, f[0] - pf.glo[0], f[1] - pf.glo[1], f[2] - pf.glo[2])];
+        s = first ? v : s + v;
+        first = false;
+      }
+    ((R*)pc.B[a])[lin3(pc, cf[0], cf[1], cf[2])] = R(0.25) * s;
+  }
+}
+
+// ---------------------------------------------------------------- capture
+// dst = (or +=) dt * F_q on the axis faces (5 planes) / dt * E_axis on edges
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__ P, const DCapture* __restrict__ C,
+                                                      const BlockTask* __restrict__ T, const R* scr,
+                                                      const double* d_dt) {
+  const BlockTask t = T[blockIdx.x];
+  const DCapture cp = C[t.patch];
+  const int e = t.start + threadIdx.x;
+  const int64_t nv = (int64_t)cp.ext[0] * cp.ext[1] * cp.ext[2];
+  if (e >= nv) return;
+  int ai[3];
+  box_cell(cp.lo, cp.ext, e, ai);
+  const DPatch& p = P[cp.patch];
+  const double dt = (*d_dt) * p.dt_scale;
+  const int64_t x = lin3(p, ai[0], ai[1], ai[2]);
+  if (cp.kind == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8 + q) * p.nelem;
+      const double v = dt * (double)F[x];
+      double* o = cp.dst + (int64_t)q * nv + e;
+      *o = cp.mode ? *o + v : v;
+    }
+  } else {
+    const R* Ed = scr + p.scr + (int64_t)(SC_ED + cp.axis) * p.nelem;
+    const double v = dt * (double)Ed[x];
+    double* o = cp.dst + e;
+    *o = cp.mode ? *o + v : v;
+  }
+}
+
+// ---------------------------------------------------------------- reflux
+__global__ void __launch_bounds__(kThreads) k_zero(const DCorr* __restrict__ C, const BlockTask* __restrict__ T) {
+  const BlockTask t = T[blockIdx.x];
+  const DCorr cr = C[t.patch];
+  const int64_t e = (int64_t)t.start + threadIdx.x;
+  if (e < cr.count) cr.base[e] = 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__ PC,
+                                                      const DDeposit* __restrict__ D,
+                                                      const BlockTask* __restrict__ T) {
+  const BlockTask t = T[blockIdx.x];
+  const DDeposit dp = D[t.patch];
+  const int e = t.start + threadIdx.x;
+  const int64_t cn = (int64_t)dp.ext[0] * dp.ext[1] * dp.ext[2];
+  if (e >= cn) return;
+  int C3[3];
+  box_cell(dp.lo, dp.ext, e, C3);
+  const DPatch& pc = PC[dp.coarse];
+  const int64_t c = lin3(pc, C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]);
+  const int64_t fn = (int64_t)dp.fext[0] * dp.fext[1] * dp.fext[2];
+  if (dp.kind == 0) {
+    const int d = dp.axis;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+    for (int q = 0; q < 5; ++q) {
+      double s = 0.0;
+      bool first = true;
+      for (int j2 = 0; j2 < 2; ++j2)
+        for (int j1 = 0; j1 < 2; ++j1) {
+          int f[3];
+          f[d] = 2 * C3[d];
+          f[lo_t] = 2 * C3[lo_t] + j1;
+          f[hi_t] = 2 * C3[hi_t] + j2;
+          const int64_t fo = (int64_t)(f[0] - dp.flo[0]) +
+                             (int64_t)dp.fext[0] * ((f[1] - dp.flo[1]) + (int64_t)dp.fext[1] * (f[2] - dp.flo[2]));
+          const double v = dp.fine[q * fn + fo];
+          s = first ? v : s + v;
+          first = false;
+        }
+      dp.corr[(int64_t)(d * 5 + q) * pc.nelem + c] = 0.25 * s - dp.creg[q * cn + e];
+    }
+  } else {
+    const int a = dp.axis;
+    double s = 0.0;
+    for (int seg = 0; seg < 2; ++seg) {
+      int f[3] = {2 * C3[0], 2 * C3[1], 2 * C3[2]};
+      f[a] += seg;
+      const int64_t fo = (int64_t)(f[0] - dp.flo[0]) +
+                         (int64_t)dp.fext[0] * ((f[1] - dp.flo[1]) + (int64_t)dp.fext[1] * (f[2] - dp.flo[2]));
+      s = seg ? s + dp.fine[fo] : dp.fine[fo];
+    }
+    dp.corr[(int64_t)(15 + a) * pc.nelem + c] = 0.5 * s - dp.creg[e];
+  }
+}
+
+// Applies the correction planes to the interior cells and faces of a coarse
+// patch: launch region = interior grown by one on the upper side.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_correct(const DPatch* __restrict__ PC, const DCorr* __restrict__ C,
+                                                      const BlockTask* __restrict__ T) {
+  const BlockTask t = T[blockIdx.x];
+  const DCorr cr = C[t.patch];
+  const DPatch& p = PC[cr.patch];
+  const int e = t.start + threadIdx.x;
+  const int ex = p.n[0] + 1, ey = p.n[1] + 1, ez = p.n[2] + 1;
+  if (e >= ex * ey * ez) return;
+  const int ai[3] = {p.g + e % ex, p.g + (e / ex) % ey, p.g + e / (ex * ey)};
+  const int64_t c = lin3(p, ai[0], ai[1], ai[2]);
+  const double* K = cr.base;
+  const int64_t ne = p.nelem;
+  const bool cell = ai[0] < p.g + p.n[0] && ai[1] < p.g + p.n[1] && ai[2] < p.g + p.n[2];
+  if (cell) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      R* Uq = (R*)p.U[q];
+      double u = (double)Uq[c];
+      u = u - (K[(0 * 5 + q) * ne + c + 1] - K[(0 * 5 + q) * ne + c]) / p.dx[0] -
+          (K[(1 * 5 + q) * ne + c + p.s1] - K[(1 * 5 + q) * ne + c]) / p.dx[1] -
+          (K[(2 * 5 + q) * ne + c + p.s2] - K[(2 * 5 + q) * ne + c]) / p.dx[2];
+      Uq[c] = (R)u;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!own_face(p, ai, a)) continue;
+    const int b = (a + 1) % 3, cc = (a + 2) % 3;
+    const double dEc = K[(15 + cc) * ne + c + sof(p, b)] - K[(15 + cc) * ne + c];
+    const double dEb = K[(15 + b) * ne + c + sof(p, cc)] - K[(15 + b) * ne + c];
+    R* Ba = (R*)p.B[a];
+    Ba[c] = (R)((double)Ba[c] - (dEc / p.dx[b] - dEb / p.dx[cc]));
+  }
+}
+
+}  // namespace
+
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const BlockTask* tasks,
+                               int nblocks, const KernelTimer* tm, cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (dtype == 0)
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks, pass)));
+    else
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks, pass)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, const DBoxItem* items,
+                           const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  if (dtype == 0)
+    MHD_TIMED(tm, K_AMR, s, (k_prolong<double><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+  else
+    MHD_TIMED(tm, K_AMR, s, (k_prolong<float><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+  return cudaGetLastError();
+}
+
+cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse, const DBoxItem* items,
+                            const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (dtype == 0)
+      MHD_TIMED(tm, K_AMR, s, (k_restrict<double><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+    else
+      MHD_TIMED(tm, K_AMR, s, (k_restrict<float><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const BlockTask* tasks,
+                           int nblocks, const void* scratch, const double* d_dt, const KernelTimer* tm,
+                           cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  if (dtype == 0)
+    MHD_TIMED(tm, K_AMR, s, (k_capture<double><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
+                                                                            (const double*)scratch, d_dt)));
+  else
+    MHD_TIMED(tm, K_AMR, s, (k_capture<float><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
+                                                                           (const float*)scratch, d_dt)));
+  return cudaGetLastError();
+}
+
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const BlockTask* zero_tasks,
+                          int nzero, const DDeposit* deps, const BlockTask* dep_tasks, int ndep,
+                          const BlockTask* corr_tasks, int ncorr, const KernelTimer* tm, cudaStream_t s) {
+  if (nzero) MHD_TIMED(tm, K_AMR, s, (k_zero<<<nzero, kThreads, 0, s>>>(corr, zero_tasks)));
+  if (ndep) MHD_TIMED(tm, K_AMR, s, (k_deposit<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
+  if (ncorr) {
+    if (dtype == 0)
+      MHD_TIMED(tm, K_AMR, s, (k_correct<double><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+    else
+      MHD_TIMED(tm, K_AMR, s, (k_correct<float><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -10,6 +10,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "amr.h"
 #include "common.cuh"
 #include "launch.h"
 #include "mhd_gpu.h"
@@ -232,7 +233,21 @@ void timer_mark(void* self, int kernel, int phase, cudaStream_t s) {
 const KernelTimer* timer_of(mhd_ctx* c) { return c->timing ? &c->timer : nullptr; }
 
 const char* const kKernelNames[K_COUNT] = {"k_prim", "k_pred", "k_edge", "k_flux", "k_emf",
-                                            "k_update", "k_cfl", "k_ghost", "k_sums"};
+                                            "k_update", "k_cfl", "k_ghost", "k_sums", "k_amr"};
+
+// converts a descriptor array (all of one dtype) to device form
+mhd_status convert_all(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, std::vector<DPatch>& dp,
+                       int* dtype) {
+  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
+  dp.resize(n);
+  for (int p = 0; p < n; ++p) {
+    mhd_status r = convert(c, patches[p], p, dp[p]);
+    if (r) return r;
+    if (p == 0 && *dtype < 0) *dtype = patches[0].dtype;
+    if (patches[p].dtype != *dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  return MHD_OK;
+}
 
 }  // namespace
 
@@ -343,7 +358,7 @@ mhd_status mhd_get_device_status(mhd_ctx* c, int32_t* out) {
 
 mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n,
                              const int32_t* grow, const double* d_dt, const double* dt_scale,
-                             void* stream) {
+                             const mhd_capture* caps, int32_t ncap, void* stream) {
   mhd_status r = begin(c);
   if (r) return r;
   if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
@@ -386,9 +401,56 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   a.d_dt = d_dt;
   a.d_status = c->d_status;
   a.timer = timer_of(c);
+  // flux-register captures: checked against the faces / edges this call computes
+  if (ncap < 0 || (ncap > 0 && !caps)) return fail(c, MHD_EINVAL, "bad capture list");
+  std::vector<DCapture> dc(ncap);
+  std::vector<int64_t> ccounts(ncap);
+  for (int t = 0; t < ncap; ++t) {
+    const mhd_capture& m = caps[t];
+    if (m.patch < 0 || m.patch >= n || (m.kind != 0 && m.kind != 1) || m.axis < 0 || m.axis > 2 ||
+        (m.mode != 0 && m.mode != 1) || !m.dst)
+      return fail(c, MHD_EINVAL, "capture %d: bad patch, kind, axis, mode or dst", t);
+    const DPatch& p = dp[m.patch];
+    DCapture& o = dc[t];
+    o.patch = m.patch;
+    o.kind = m.kind;
+    o.axis = m.axis;
+    o.mode = m.mode;
+    o.dst = m.dst;
+    int64_t cnt = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int lo = m.box.lo[d] - p.glo[d], hi = m.box.hi[d] - p.glo[d];
+      const int ulo = p.g - p.k, uhi = p.g + p.n[d] - 1 + p.k;
+      int alo, ahi;  // computed range along d
+      if (m.kind == 0) {
+        alo = d == m.axis ? ulo : ulo - 1;
+        ahi = d == m.axis ? uhi + 1 : uhi + 1;
+      } else {
+        alo = ulo;
+        ahi = d == m.axis ? uhi : uhi + 1;
+      }
+      if (hi < lo || lo < alo || hi > ahi)
+        return fail(c, MHD_EINVAL, "capture %d: box outside the elements the advance computes (axis %d)", t, d);
+      o.lo[d] = lo;
+      o.ext[d] = hi - lo + 1;
+      cnt *= o.ext[d];
+    }
+    ccounts[t] = cnt;
+  }
   cudaError_t e = dtype == MHD_F64 ? advance_f64(a, (cudaStream_t)stream) : advance_f32(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
   c->launches += 6;
+  if (ncap > 0) {
+    std::vector<BlockTask> ctasks;
+    tasks_for(ccounts, ctasks);
+    void *d_c = nullptr, *d_ct = nullptr;
+    if ((r = table(c, dc.data(), dc.size() * sizeof(DCapture), &d_c))) return r;
+    if ((r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) return r;
+    e = capture_launch(dtype, (const DPatch*)d_p, (const DCapture*)d_c, (const BlockTask*)d_ct, (int)ctasks.size(),
+                       c->scratch, d_dt, timer_of(c), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capture launch");
+    c->launches += 1;
+  }
   return MHD_OK;
 }
 
@@ -448,8 +510,8 @@ mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, 
     int64_t cnt = 1;
     for (int a = 0; a < 3; ++a) {
       const int lo = m.box.lo[a] - D.glo[a], hi = m.box.hi[a] - D.glo[a];
-      if (hi < lo || lo < 0 || hi >= D.N[a])
-        return fail(c, MHD_EINVAL, "copy %d: box outside the destination's arrays along axis %d", t, a);
+      if (hi < lo || lo < -1 || hi > D.N[a])
+        return fail(c, MHD_EINVAL, "copy %d: box outside the destination's arrays grown by one along axis %d", t, a);
       // source cells (and the upper face of the last one) must lie in src's interior
       const int slo = m.box.lo[a] + m.offset[a] - S.glo[a], shi = m.box.hi[a] + m.offset[a] - S.glo[a];
       if (slo < S.g || shi > S.g + S.n[a] - 1)
@@ -468,10 +530,10 @@ mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, 
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DCopy), &d_c))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
-  cudaError_t e = ghost_fill_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, (const BlockTask*)d_t,
-                                    (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = ghost_fill2_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, (const BlockTask*)d_t,
+                                     (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ghost fill launch");
-  c->launches += 1;
+  c->launches += 2;
   return MHD_OK;
 }
 
@@ -498,6 +560,178 @@ mhd_status mhd_conservation_sums(mhd_ctx* c, const mhd_patch_desc* patches, int3
                               c->partials, d_out8, timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "sums launch");
   c->launches += 2;
+  return MHD_OK;
+}
+
+mhd_status mhd_prolong(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, const mhd_patch_desc* fine,
+                       int32_t nf, const mhd_prolong_item* items, int32_t n, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !items)) return fail(c, MHD_EINVAL, "bad item list");
+  if (n == 0) return MHD_OK;
+  int dtype = -1;
+  std::vector<DPatch> dc, df;
+  if ((r = convert_all(c, coarse, nc, dc, &dtype))) return r;
+  if ((r = convert_all(c, fine, nf, df, &dtype))) return r;
+  std::vector<DBoxItem> di(n);
+  std::vector<int64_t> counts(n);
+  for (int t = 0; t < n; ++t) {
+    const mhd_prolong_item& m = items[t];
+    if (m.coarse < 0 || m.coarse >= nc || m.fine < 0 || m.fine >= nf)
+      return fail(c, MHD_EINVAL, "prolong item %d: patch index out of range", t);
+    const DPatch& C = dc[m.coarse];
+    const DPatch& F = df[m.fine];
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a], hi = m.box.hi[a];
+      // coarse cells and their one-cell stencil inside the coarse arrays
+      if (hi < lo || lo - C.glo[a] < 1 || hi - C.glo[a] > C.N[a] - 2)
+        return fail(c, MHD_EINVAL, "prolong item %d: coarse box or its stencil outside the coarse arrays", t);
+      // the fine cells inside the fine arrays
+      if (2 * lo - F.glo[a] < 0 || 2 * hi + 1 - F.glo[a] > F.N[a] - 1)
+        return fail(c, MHD_EINVAL, "prolong item %d: fine cells outside the fine arrays", t);
+      di[t].lo[a] = lo;
+      di[t].ext[a] = hi - lo + 1;
+      cnt *= hi - lo + 1;
+    }
+    di[t].a = m.coarse;
+    di[t].b = m.fine;
+    counts[t] = cnt;
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr, *d_t = nullptr;
+  if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
+  if ((r = table(c, df.data(), df.size() * sizeof(DPatch), &d_f))) return r;
+  if ((r = table(c, di.data(), di.size() * sizeof(DBoxItem), &d_i))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = prolong_launch(dtype, (const DPatch*)d_c, (const DPatch*)d_f, (const DBoxItem*)d_i,
+                                 (const BlockTask*)d_t, (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "prolong launch");
+  c->launches += 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_restrict(mhd_ctx* c, const mhd_patch_desc* fine, int32_t nf, const mhd_patch_desc* coarse,
+                        int32_t nc, const mhd_restrict_item* items, int32_t n, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !items)) return fail(c, MHD_EINVAL, "bad item list");
+  if (n == 0) return MHD_OK;
+  int dtype = -1;
+  std::vector<DPatch> dc, df;
+  if ((r = convert_all(c, fine, nf, df, &dtype))) return r;
+  if ((r = convert_all(c, coarse, nc, dc, &dtype))) return r;
+  std::vector<DBoxItem> di(n);
+  std::vector<int64_t> counts(n);
+  for (int t = 0; t < n; ++t) {
+    const mhd_restrict_item& m = items[t];
+    if (m.coarse < 0 || m.coarse >= nc || m.fine < 0 || m.fine >= nf)
+      return fail(c, MHD_EINVAL, "restrict item %d: patch index out of range", t);
+    const DPatch& C = dc[m.coarse];
+    const DPatch& F = df[m.fine];
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a], hi = m.box.hi[a];
+      const int flo = F.glo[a] + F.g, fhi = flo + F.n[a] - 1;
+      const int clo = C.glo[a] + C.g, chi = clo + C.n[a] - 1;
+      if (hi < lo || 2 * lo < flo || 2 * hi + 1 > fhi || lo < clo - 1 || hi > chi + 1)
+        return fail(c, MHD_EINVAL, "restrict item %d: box not inside the coarsened fine interior and the "
+                                   "coarse interior grown by one", t);
+      di[t].lo[a] = lo;
+      di[t].ext[a] = hi - lo + 1;
+      cnt *= hi - lo + 1;
+    }
+    di[t].a = m.fine;
+    di[t].b = m.coarse;
+    counts[t] = cnt;
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr, *d_t = nullptr;
+  if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
+  if ((r = table(c, df.data(), df.size() * sizeof(DPatch), &d_f))) return r;
+  if ((r = table(c, di.data(), di.size() * sizeof(DBoxItem), &d_i))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = restrict_launch(dtype, (const DPatch*)d_f, (const DPatch*)d_c, (const DBoxItem*)d_i,
+                                  (const BlockTask*)d_t, (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "restrict launch");
+  c->launches += 2;
+  return MHD_OK;
+}
+
+mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, double* const* corr,
+                      const mhd_deposit* deps, int32_t nd, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (nc < 1 || !corr || nd < 0 || (nd > 0 && !deps)) return fail(c, MHD_EINVAL, "bad arguments");
+  int dtype = -1;
+  std::vector<DPatch> dc;
+  if ((r = convert_all(c, coarse, nc, dc, &dtype))) return r;
+  std::vector<DCorr> cr;
+  std::vector<int64_t> zc, kc;
+  for (int p = 0; p < nc; ++p) {
+    if (!corr[p]) continue;
+    DCorr k;
+    k.patch = p;
+    k.pad = 0;
+    k.count = 18 * dc[p].nelem;
+    k.base = corr[p];
+    cr.push_back(k);
+    zc.push_back(k.count);
+    kc.push_back((int64_t)(dc[p].n[0] + 1) * (dc[p].n[1] + 1) * (dc[p].n[2] + 1));
+  }
+  std::vector<DDeposit> dd(nd);
+  std::vector<int64_t> dcount(nd);
+  for (int t = 0; t < nd; ++t) {
+    const mhd_deposit& m = deps[t];
+    if (m.coarse < 0 || m.coarse >= nc || !corr[m.coarse] || (m.kind != 0 && m.kind != 1) || m.axis < 0 ||
+        m.axis > 2 || !m.fine || !m.coarse_reg)
+      return fail(c, MHD_EINVAL, "deposit %d: bad coarse patch, kind, axis or register", t);
+    const DPatch& C = dc[m.coarse];
+    DDeposit& o = dd[t];
+    o.coarse = m.coarse;
+    o.kind = m.kind;
+    o.axis = m.axis;
+    o.pad = 0;
+    o.fine = m.fine;
+    o.creg = m.coarse_reg;
+    o.corr = corr[m.coarse];
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a], hi = m.box.hi[a];
+      // the elements (face / edge index up to hi + 1) inside the coarse arrays
+      if (hi < lo || lo - C.glo[a] < 0 || hi - C.glo[a] > C.N[a] - 1)
+        return fail(c, MHD_EINVAL, "deposit %d: box outside the coarse arrays", t);
+      // the fine elements read: 2 lo .. 2 hi + (1 along the sub-face / segment axes)
+      const bool sub = (m.kind == 0) ? (a != m.axis) : (a == m.axis);
+      const int f0 = 2 * lo, f1 = 2 * hi + (sub ? 1 : 0);
+      if (f0 < m.fine_box.lo[a] || f1 > m.fine_box.hi[a])
+        return fail(c, MHD_EINVAL, "deposit %d: fine register box does not hold the fine elements", t);
+      o.lo[a] = lo;
+      o.ext[a] = hi - lo + 1;
+      o.flo[a] = m.fine_box.lo[a];
+      o.fext[a] = m.fine_box.hi[a] - m.fine_box.lo[a] + 1;
+      cnt *= o.ext[a];
+    }
+    dcount[t] = cnt;
+  }
+  std::vector<BlockTask> tz, td, tk;
+  tasks_for(zc, tz);
+  tasks_for(dcount, td);
+  tasks_for(kc, tk);
+  void *d_c = nullptr, *d_r = nullptr, *d_d = nullptr, *d_tz = nullptr, *d_td = nullptr, *d_tk = nullptr;
+  if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
+  if ((r = table(c, cr.data(), cr.size() * sizeof(DCorr), &d_r))) return r;
+  if ((r = table(c, dd.data(), dd.size() * sizeof(DDeposit), &d_d))) return r;
+  if ((r = table(c, tz.data(), tz.size() * sizeof(BlockTask), &d_tz))) return r;
+  if ((r = table(c, td.data(), td.size() * sizeof(BlockTask), &d_td))) return r;
+  if ((r = table(c, tk.data(), tk.size() * sizeof(BlockTask), &d_tk))) return r;
+  cudaError_t e = reflux_launch(dtype, (const DPatch*)d_c, (const DCorr*)d_r, (const BlockTask*)d_tz,
+                                (int)tz.size(), (const DDeposit*)d_d, (const BlockTask*)d_td, (int)td.size(),
+                                (const BlockTask*)d_tk, (int)tk.size(), timer_of(c), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reflux launch");
+  c->launches += 3;
   return MHD_OK;
 }
 

@@ -59,7 +59,7 @@ constexpr int kThreads = 256;
 
 // Kernel ids of the per-kernel event timer (mhd_timing_*).
 enum KernelId : int {
-  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_COUNT
+  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_AMR, K_COUNT
 };
 
 // Optional hook that records CUDA events around each launch on its stream.

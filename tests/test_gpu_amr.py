@@ -1,0 +1,140 @@
+"""AMR level operations and the subcycled coarse step: GPU (sm_103a) vs the
+FP64 oracle through the C ABI.  FP64 results are expected bit-identical (bar
+1e-11); the FP32 run reports its conservation drift and div B."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import synth.amr as SA
+from gpu_util import random_state, to_patch
+
+pytestmark = pytest.mark.gpu
+G = 4
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1112_1710_gb300 import _build, capi as C
+    _build.build()
+    C.load()
+    return C
+
+
+def _states(H, n0, p_in=10.0):
+    return [[SA.blast_patch(lo, hi, l, n0, G, p_in=p_in)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+
+
+def test_prolong_and_restrict_random_data(capi, orc):
+    """Prolongation of random coarse data into a fine patch's ghost zone and the
+    restriction of random fine data, against the oracle."""
+    ctx = capi.mhd_ctx_create()
+    try:
+        nc, lo_c = (12, 12, 12), (0, 0, 0)
+        stc = random_state(nc, G, seed=31)
+        nf, lo_f = (8, 6, 10), (6, 8, 4)
+        stf = random_state(nf, G, seed=32)
+        pc = to_patch(stc, nc, G, (0.1,) * 3, lo=lo_c)
+        pf = to_patch(stf, nf, G, (0.05,) * 3, lo=lo_f, level=1)
+        clo = tuple((v - G) // 2 for v in lo_f)
+        chi = tuple((v + nf[d] + G) // 2 - 1 for d, v in enumerate(lo_f))
+        it = capi.mhd_prolong_item()
+        it.coarse, it.fine = 0, 0
+        it.box = capi.box(clo, chi)
+        capi.mhd_prolong(ctx, [pc.desc()], [pf.desc()], [it])
+        Pc = orc.patch(stc, nc, G, (0.1,) * 3)
+        a = stf.copy()
+        Pf = orc.patch(a, nf, G, (0.05,) * 3)
+        orc.prolong(Pc, lo_c, Pf, lo_f, clo, chi)
+        assert np.array_equal(pf.state.cpu().numpy(), a)
+        # restriction onto the coarse patch (box grown by one around the interior)
+        b = stc.copy()
+        Pc2 = orc.patch(b, nc, G, (0.1,) * 3)
+        rlo = tuple(v // 2 for v in lo_f)
+        rhi = tuple((v + nf[d]) // 2 - 1 for d, v in enumerate(lo_f))
+        for pass_ in (0, 1):
+            orc.restrict(Pf, lo_f, Pc2, lo_c, rlo, rhi, pass_)
+        ri = capi.mhd_restrict_item()
+        ri.fine, ri.coarse = 0, 0
+        ri.box = capi.box(rlo, rhi)
+        capi.mhd_restrict(ctx, [pf.desc()], [pc.desc()], [ri])
+        assert np.array_equal(pc.state.cpu().numpy(), b)
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("split", [1, 2])
+def test_amr_coarse_steps_fp64_parity(capi, orc, split):
+    """Three subcycled coarse steps of a 3-level shell hierarchy (1 + 47 + 42
+    patches of 4^3-8^3 cells, 4 ghost layers): every patch array equals the
+    oracle's."""
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8, level0_split=split)
+    st = _states(H, n0)
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        oh.initialise()
+        oh.fill(0)
+        ph.initialise()
+        for _ in range(3):
+            odt = oh.coarse_step()
+            ph.coarse_step()
+            assert ph.d_dt.item() == odt
+        assert capi.mhd_get_device_status(ctx) == 0
+        worst = 0.0
+        for l in range(3):
+            for P, Q in zip(oh.levels[l], ph.levels[l]):
+                got = Q.state.cpu().numpy()
+                n = P.n
+                for q in range(8):
+                    ext = list(n)
+                    if q >= 5:
+                        ext[q - 5] += 1
+                    a = got[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                    b = P.state[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                    worst = max(worst, float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)))
+        assert worst <= TOL, worst
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+
+
+def test_amr_fp32_conservation_and_divb(capi, capsys):
+    """FP32 state with FP64 flux registers and sums: composite totals and the
+    face divergence after five coarse steps (reported)."""
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
+    ctx = capi.mhd_ctx_create(emf=1)
+    try:
+        ph = Hierarchy(H, n0, _states(H, n0), (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
+        ph.initialise()
+        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s0 = out.cpu().numpy().copy()
+        for _ in range(5):
+            ph.coarse_step()
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s1 = out.cpu().numpy()
+        divb = 0.0
+        for l, pats in enumerate(ph.levels):
+            for p in pats:
+                s = p.state.double().cpu().numpy()
+                nx, ny, nz = p.n
+                d = ((s[5, G:G + nz, G:G + ny, G + 1:G + nx + 1] - s[5, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[6, G:G + nz, G + 1:G + ny + 1, G:G + nx] - s[6, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[7, G + 1:G + nz + 1, G:G + ny, G:G + nx] - s[7, G:G + nz, G:G + ny, G:G + nx]))
+                divb = max(divb, float(np.abs(d).max()))
+        rel = np.abs(s1 - s0) / np.maximum(np.abs(s0), 1e-12)
+        with capsys.disabled():
+            print("\nFP32 AMR, 5 coarse steps: relative drift of (rho, E, Bx, By):",
+                  " ".join("%.2e" % v for v in rel[[0, 4, 5, 6]]), " max |div B| dx:", "%.2e" % divb)
+        assert rel[0] < 1e-5 and rel[4] < 1e-5 and divb < 1e-4
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        ph.close()
+        capi.mhd_ctx_destroy(ctx)

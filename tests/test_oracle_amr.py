@@ -34,15 +34,43 @@ def _fill_linear(st, n, lo, dx, cell_fn, face_fns):
         st[q, :N[2], :N[1], :N[0]] = np.transpose(cell_fn(q, X, Y, Z), (2, 1, 0))
 
 
+def _set_energy_from_thermal(st, n, lo, dx, efn):
+    """E = e + |M|^2/(2 rho) + |Bc|^2/2 with e linear (cell centres)."""
+    N = [v + 2 * G for v in n]
+    c = [(np.arange(N[d]) - G + lo[d] + 0.5) * dx[d] for d in range(3)]
+    X, Y, Z = np.meshgrid(c[0], c[1], c[2], indexing="ij")
+    e = np.transpose(efn(X, Y, Z), (2, 1, 0))
+    sl = (slice(0, N[2]), slice(0, N[1]), slice(0, N[0]))
+    rho, m = st[(0,) + sl], st[1:4, :N[2], :N[1], :N[0]]
+    bx = 0.5 * (st[5, :N[2], :N[1], :N[0]] + st[5, :N[2], :N[1], 1:N[0] + 1])
+    by = 0.5 * (st[6, :N[2], :N[1], :N[0]] + st[6, :N[2], 1:N[1] + 1, :N[0]])
+    bz = 0.5 * (st[7, :N[2], :N[1], :N[0]] + st[7, 1:N[2] + 1, :N[1], :N[0]])
+    st[(4,) + sl] = e + 0.5 * (m ** 2).sum(0) / rho + 0.5 * (bx * bx + by * by + bz * bz)
+    return e
+
+
+def _thermal(st, n):
+    N = [v + 2 * G for v in n]
+    rho, m = st[0, :N[2], :N[1], :N[0]], st[1:4, :N[2], :N[1], :N[0]]
+    bx = 0.5 * (st[5, :N[2], :N[1], :N[0]] + st[5, :N[2], :N[1], 1:N[0] + 1])
+    by = 0.5 * (st[6, :N[2], :N[1], :N[0]] + st[6, :N[2], 1:N[1] + 1, :N[0]])
+    bz = 0.5 * (st[7, :N[2], :N[1], :N[0]] + st[7, 1:N[2] + 1, :N[1], :N[0]])
+    return st[4, :N[2], :N[1], :N[0]] - 0.5 * (m ** 2).sum(0) / rho - 0.5 * (bx * bx + by * by + bz * bz)
+
+
 def test_prolongation_exact_for_linear_data_and_divergence_free(orc):
+    """Linear rho, M, thermal energy and a linear divergence-free field are
+    reproduced exactly (rounding) by the prolongation."""
     nc, lo_c = (8, 8, 8), (0, 0, 0)
     dxc = (1.0, 1.0, 1.0)
     stc, Pc = _patch(orc, nc, lo_c, dxc)
-    cell = lambda q, x, y, z: 1.0 + 0.1 * q + 0.3 * x - 0.2 * y + 0.05 * z
+    cell = lambda q, x, y, z: 3.0 + 0.1 * q + 0.3 * x - 0.2 * y + 0.05 * z
+    efn = lambda x, y, z: 5.0 + 0.1 * x + 0.2 * y - 0.3 * z
     faces = [lambda x, y, z: 0.2 + 0.3 * y - 0.1 * z,
              lambda x, y, z: -0.4 + 0.2 * x + 0.25 * z,
              lambda x, y, z: 0.1 - 0.15 * x + 0.35 * y]
     _fill_linear(stc, nc, lo_c, dxc, cell, faces)
+    _set_energy_from_thermal(stc, nc, lo_c, dxc, efn)
     nf, lo_f = (8, 8, 8), (4, 4, 4)
     dxf = (0.5, 0.5, 0.5)
     stf, Pf = _patch(orc, nf, lo_f, dxf)
@@ -54,10 +82,12 @@ def test_prolongation_exact_for_linear_data_and_divergence_free(orc):
     # every face holds the linear field
     ref = np.zeros_like(stf)
     _fill_linear(ref, nf, lo_f, dxf, cell, faces)
+    e_ref = _set_energy_from_thermal(ref, nf, lo_f, dxf, efn)
     stf[5:8] = ref[5:8]
     orc.prolong(Pc, lo_c, Pf, lo_f, clo, chi)
     N = [v + 2 * G for v in nf]
-    assert np.abs(stf[:5, :N[2], :N[1], :N[0]] - ref[:5, :N[2], :N[1], :N[0]]).max() < 1e-13
+    assert np.abs(stf[:4, :N[2], :N[1], :N[0]] - ref[:4, :N[2], :N[1], :N[0]]).max() < 1e-13
+    assert np.abs(_thermal(stf, nf) - e_ref).max() < 1e-12
     for a in range(3):
         ext = list(N)
         ext[a] += 1
@@ -100,7 +130,8 @@ def test_prolongation_of_divergence_free_random_field(orc):
     # compare the coarse cells x in [0,1] and their faces except the x-face at
     # x = 2 (it is the fine patch's own, unset, boundary face)
     cs = (slice(G, G + 8), slice(G, G + 8), slice(G, G + 2))
-    assert np.abs(stc[(slice(0, 5),) + cs] - back[(slice(0, 5),) + cs]).max() < 1e-13 * np.abs(back[:5]).max()
+    # rho and M are prolonged conservatively; E through the thermal energy
+    assert np.abs(stc[(slice(0, 4),) + cs] - back[(slice(0, 4),) + cs]).max() < 1e-13 * np.abs(back[:4]).max()
     fx = (slice(G, G + 8), slice(G, G + 8), slice(G, G + 2))
     fy = (slice(G, G + 8), slice(G, G + 9), slice(G, G + 2))
     fz = (slice(G, G + 9), slice(G, G + 8), slice(G, G + 2))
