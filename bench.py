@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
+    ap.add_argument("--workload", default="patch", choices=["patch", "amr"])
     return ap.parse_args()
 
 
@@ -358,10 +359,89 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def amr_hierarchy():
+    """The AMR workload: base 64^3 (one periodic patch) + 3 refined levels
+    covering the blast shell r in [0.25, 0.35] (jittered per level) with
+    seeded uneven patches of 8^3-48^3 cells, 4 ghost layers, ratio 2."""
+    import synth.amr as SA
+    H = SA.shell_hierarchy(n0=64, levels=4, seed=1112, size_min=8, size_max=48)
+    states = [[SA.blast_patch(lo, hi, l, 64, 4)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    return H, states
+
+
+def time_amr(H, states, dtype, steps, mode, local):
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.amr import Hierarchy
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    stream = torch.cuda.Stream(device=local)
+    h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
+                  device="cuda:%d" % local)
+    try:
+        h.initialise()
+        if mode == "per_patch":
+            h.batched = False
+        if mode == "graph":
+            h.capture_graph()
+        else:
+            h.coarse_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = capi.mhd_launch_count(ctx)
+        e0.record(stream)
+        for _ in range(steps):
+            if mode == "graph":
+                h.replay()
+            else:
+                h.coarse_step()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        status = capi.mhd_get_device_status(ctx)
+        upd = h.cell_updates_per_coarse_step()
+        launches = capi.mhd_launch_count(ctx) - l0
+    finally:
+        h.close()
+        capi.mhd_ctx_destroy(ctx)
+    return {"dtype": dtype, "mode": mode, "coarse_steps": steps, "ms_per_coarse_step": ms / steps,
+            "cell_updates_per_coarse_step": upd, "value": upd * steps / (ms * 1e-3),
+            "library_launches_per_step": (launches / steps) if mode != "graph" else None,
+            "device_status": status}
+
+
+def run_amr(args):
+    import torch
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1112_1710_gb300 import _build
+    _build.build()
+    H, states = amr_hierarchy()
+    res = [time_amr(H, states, "f32", args.steps, "graph", local),
+           time_amr(H, states, "f32", args.steps, "batched", local),
+           time_amr(H, states, "f64", max(1, args.steps // 2), "graph", local),
+           time_amr(H, states, "f64", 1, "per_patch", local)]
+    if rank != 0:
+        return
+    main = res[0]
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": 1, "ms_per_step": main["ms_per_coarse_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "AMR blast-shell hierarchy: base 64^3 + 3 levels (ratio 2, subcycled), "
+                                   "%d patches of 8^3-48^3, 4 ghost layers; step = one coarse step" %
+                                   sum(len(l) for l in H),
+                       "patches_per_level": [len(l) for l in H],
+                       "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
+            "runs": res}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "amr":
+        run_amr(args)
     else:
         run_ours(args)
 

@@ -33,7 +33,12 @@
  * launched; a failed check returns a negative status and launches nothing.
  * Errors found on the device (a non-positive density or pressure after an
  * update) set a status word read by mhd_get_device_status; kernels never trap.
- * A context may be used from one host thread at a time.
+ * A context may be used from one host thread at a time.  All calls of a
+ * context share its scratch arena: calls on different streams must be ordered
+ * by the caller (events), or use one context per stream.  Device tables are
+ * cached by content, so after one warm-up call with the same arguments a call
+ * uploads nothing and can be captured in a CUDA graph; a captured graph holds
+ * the scratch address, which changes only when a larger call grows the arena.
  */
 #ifndef MHD_GPU_H
 #define MHD_GPU_H

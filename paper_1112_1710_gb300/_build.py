@@ -22,7 +22,7 @@ UNITS = {
     "capi.cu": [],
     "level_ops.cu": ["--fmad=false"],
     "advance_f64.cu": ["--fmad=false"],
-    "advance_f32.cu": ["--fmad=true"],
+    "advance_f32.cu": ["--fmad=true", "--use_fast_math"],
     "noalloc.cu": ["--fmad=false"],
     "amr_ops.cu": ["--fmad=false"],
 }

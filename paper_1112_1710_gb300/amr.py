@@ -275,12 +275,40 @@ class Hierarchy:
         capi.mhd_restrict(self.ctx, self.descs[l + 1], self.descs[l], self._restrict_arr[l], self.sp)
 
     def advance(self, l, k, first):
+        if not self.batched:
+            return self._advance_per_patch(l, k, first)
         arr, n = self._desc_arr[l]
         grow = capi._arr(C.c_int32, [k] * n)
         caps = self.caps[(l, first)]
         ca, nca = caps if caps is not None else (None, 0)
         capi._check(self.ctx, capi.load().mhd_patch_advance(self.ctx, arr, n, grow, self.d_dt.data_ptr(),
                                                             self._dt_scale[l], ca, nca, self.sp))
+
+    batched = True
+
+    def _advance_per_patch(self, l, k, first):
+        """The plain path: one advance call (six kernels) per patch."""
+        if not hasattr(self, "_pp"):
+            self._pp = {}
+        key = (l, first)
+        if key not in self._pp:
+            caps = self.caps[(l, first)]
+            per = [[] for _ in self.descs[l]]
+            if caps is not None:
+                arr, n = caps
+                for t in range(n):
+                    c = capi.mhd_capture()
+                    C.memmove(C.byref(c), C.byref(arr[t]), C.sizeof(c))
+                    p = c.patch
+                    c.patch = 0
+                    per[p].append(c)
+            self._pp[key] = [(capi._descs([d]), capi._structs(capi.mhd_capture, cl)) for d, cl in
+                             zip(self.descs[l], per)]
+        grow = capi._arr(C.c_int32, [k])
+        scale = capi._arr(C.c_double, [0.5 ** l])
+        for (arr, n), (ca, nca) in self._pp[key]:
+            capi._check(self.ctx, capi.load().mhd_patch_advance(self.ctx, arr, n, grow, self.d_dt.data_ptr(),
+                                                                scale, ca if nca else None, nca, self.sp))
 
     def reflux(self, l):
         capi.mhd_reflux(self.ctx, self.descs[l], self.corr[l], self.deps[l], self.sp)
@@ -316,6 +344,27 @@ class Hierarchy:
                 self.d_dt.fill_(float(dt))
         self.fill(0)
         self.step(0, 0)
+
+    def capture_graph(self):
+        """Captures one whole coarse step (CFL dt, ghost fills, subcycled
+        advances, refluxing, restriction) as a CUDA graph.  dt lives in device
+        memory, so the graph stays valid across steps.  One eager step is run
+        first so that every descriptor table is already on the device (the
+        capture issues no uploads)."""
+        self.coarse_step()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.cfl()
+            self.fill(0)
+            self.step(0, 0)
+        self.graph = g
+        return g
+
+    def replay(self):
+        # CUDAGraph.replay launches on the current stream
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
 
     def cell_updates_per_coarse_step(self) -> int:
         return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)

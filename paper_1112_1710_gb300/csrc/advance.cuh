@@ -32,15 +32,40 @@ struct Cell {
   int i, j, k;
 };
 
+// q = floor(e / d) and e - q d for 0 <= e < 2^24 without an integer
+// division: the single-precision quotient is within one of the true one and
+// is corrected.
+__device__ __forceinline__ int divmod24(int e, int d, int& r) {
+  int q = __float2int_rz(__int2float_rn(e) * __frcp_rn(__int2float_rn(d)));
+  r = e - q * d;
+  if (r < 0) {
+    q -= 1;
+    r += d;
+  } else if (r >= d) {
+    q += 1;
+    r -= d;
+  }
+  return q;
+}
+
 // Decomposes element e of the UB+2 launch region of patch p; false if e is
 // beyond the region.
 __device__ __forceinline__ bool launch_cell(const DPatch& p, int e, Cell& c) {
   const int ex = p.n[0] + 2 * p.k + 4, ey = p.n[1] + 2 * p.k + 4, ez = p.n[2] + 2 * p.k + 4;
   if (e >= ex * ey * ez) return false;
   const int lo = p.g - p.k - 2;
-  c.i = lo + e % ex;
-  c.j = lo + (e / ex) % ey;
-  c.k = lo + e / (ex * ey);
+  if (ex * ey * ez < (1 << 24)) {
+    int rx, ry;
+    const int qx = divmod24(e, ex, rx);
+    const int qy = divmod24(qx, ey, ry);
+    c.i = lo + rx;
+    c.j = lo + ry;
+    c.k = lo + qy;
+  } else {  // very large patches: exact integer division
+    c.i = lo + e % ex;
+    c.j = lo + (e / ex) % ey;
+    c.k = lo + e / (ex * ey);
+  }
   return true;
 }
 
@@ -202,6 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
 }
 
 // ---------------------------------------------------------------- k_edge
+template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr);
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr) {
@@ -209,8 +236,15 @@ __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  const int a = blockIdx.y;
-  const int b = (a + 1) % 3, cc = (a + 2) % 3;
+  switch (blockIdx.y) {
+    case 0: edge_avg<R, 0>(p, c, scr); break;
+    case 1: edge_avg<R, 1>(p, c, scr); break;
+    default: edge_avg<R, 2>(p, c, scr); break;
+  }
+}
+
+template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
   const int id[3] = {c.i, c.j, c.k};
   if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
   const int64_t x = lin(p, c);
@@ -224,16 +258,12 @@ __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
 }
 
 // ---------------------------------------------------------------- k_flux
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
-                                                   const BlockTask* __restrict__ T, R* scr,
-                                                   SolverConsts<R> sc, const double* d_dt) {
-  const BlockTask t = T[blockIdx.x];
-  const DPatch& p = P[t.patch];
-  Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  const int d = blockIdx.y;
-  const int b = (d + 1) % 3, cc = (d + 2) % 3;
+// The face direction is a template parameter so that every array index below
+// is a compile-time constant (no local-memory arrays).
+template <typename R, int d>
+__device__ __forceinline__ void flux_face(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc,
+                                          const double* d_dt) {
+  constexpr int b = (d + 1) % 3, cc = (d + 2) % 3;
   const int id[3] = {c.i, c.j, c.k};
   if (!in_ub(p, d, id[d], 0, 1) || !in_ub(p, b, id[b], -1, 1) || !in_ub(p, cc, id[cc], -1, 1)) return;
   const StepDt<R> st(p, d_dt);
@@ -258,7 +288,25 @@ __global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
   for (int q = 0; q < 8; ++q) arr(scr, p, SC_F + d * 8 + q)[x] = f[q];
 }
 
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr,
+                                                   SolverConsts<R> sc, const double* d_dt) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  switch (blockIdx.y) {
+    case 0: flux_face<R, 0>(p, c, scr, sc, d_dt); break;
+    case 1: flux_face<R, 1>(p, c, scr, sc, d_dt); break;
+    default: flux_face<R, 2>(p, c, scr, sc, d_dt); break;
+  }
+}
+
 // ---------------------------------------------------------------- k_emf
+template <typename R, int a>
+__device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc);
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
                                                   const BlockTask* __restrict__ T, R* scr,
@@ -267,8 +315,16 @@ __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  const int a = blockIdx.y;
-  const int b = (a + 1) % 3, cc = (a + 2) % 3;
+  switch (blockIdx.y) {
+    case 0: edge_emf<R, 0>(p, c, scr, sc); break;
+    case 1: edge_emf<R, 1>(p, c, scr, sc); break;
+    default: edge_emf<R, 2>(p, c, scr, sc); break;
+  }
+}
+
+template <typename R, int a>
+__device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
   const int id[3] = {c.i, c.j, c.k};
   if (!in_ub(p, a, id[a], 0, 0) || !in_ub(p, b, id[b], 0, 1) || !in_ub(p, cc, id[cc], 0, 1)) return;
   const int64_t x = lin(p, c);
