@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,11 +36,6 @@ SOLVER = {"gamma": 5.0 / 3.0, "cfl": 0.4, "limiter": 0, "emf": 1}
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
-# Device-side FP peaks used for the ALU roofline (per GPU).  Derived from the
-# unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x clock, and the
-# FP64 rate measured on this GPU ("ALU peaks").
-FP_PEAK_TFLOPS = {"f32": None, "f64": None}
-
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -52,7 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
-    ap.add_argument("--workload", default="patch", choices=["patch", "amr"])
+    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve"])
+    ap.add_argument("--requests", type=int, default=10000, help="serve: requests per offered load")
+    ap.add_argument("--slots", type=int, default=3, help="serve: streams (one context each)")
+    ap.add_argument("--batch-cells", type=int, default=4 << 20, help="serve: cell budget of one batch")
     return ap.parse_args()
 
 
@@ -436,10 +435,112 @@ def run_amr(args):
     print(json.dumps(line))
 
 
+def per_patch_f64(tpl, reqs, local):
+    """The plain per-patch FP64 launch path over the same requests (each as
+    FP64): one patch per ghost fill and per advance, one stream, no batching."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.patch import Patch, periodic_copies
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    stream = torch.cuda.Stream(device=local)
+    one = torch.ones(1, dtype=torch.float64, device="cuda:%d" % local)
+    copies = {}
+    try:
+        def go(rs):
+            for r in rs:
+                p0, dt = tpl[(r.n, "f64")]
+                cl = copies.get(r.n)
+                if cl is None:
+                    cl = copies[r.n] = periodic_copies(p0.n, p0.g)
+                with torch.cuda.stream(stream):
+                    p = Patch(p0.state.clone(), p0.lo, p0.n, p0.g, p0.dx, r.level, r.rid)
+                capi.mhd_ghost_fill(ctx, [p.desc()], cl, stream.cuda_stream)
+                capi.mhd_patch_advance(ctx, [p.desc()], one.data_ptr(), stream.cuda_stream, dt_scale=[dt])
+        go(reqs[:20])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        go(reqs)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    cells = sum(r.cells for r in reqs)
+    return {"requests": len(reqs), "ms": ms, "cell_updates_per_s": cells / (ms * 1e-3)}
+
+
+def run_serve(args):
+    """Serving stream: Poisson arrivals of single-step patch requests, cube
+    edges log-uniform 16-128 (even), 4 ghost layers, levels 0-7 served finer
+    first, FP32/FP64 50/50, resident state under a 64 GB HBM budget.  First the
+    saturation throughput (all requests at t = 0), then offered loads of 0.5,
+    0.8 and 0.95 of it, each with p50/p99 latency."""
+    import torch
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1112_1710_gb300 import _build, capi
+    _build.build()
+    from paper_1112_1710_gb300.serve import GpuBackend, Scheduler, latency_stats, make_templates, poisson_requests
+    G = 4
+    budget = 64 << 30
+    t_setup = time.time()
+    tpl = make_templates(range(16, 129, 2), g=G, solver=SOLVER, device="cuda:%d" % local)
+    be = GpuBackend(tpl, n_slots=args.slots, g=G, solver=SOLVER, device="cuda:%d" % local)
+    clk = ClockSampler(local)
+    launches0 = 0
+
+    def serve(reqs):
+        sch = Scheduler(be, n_slots=args.slots, budget_bytes=budget, max_batch_cells=args.batch_cells, g=G)
+        out = sch.run(reqs, t_limit=900.0)
+        torch.cuda.synchronize()
+        st = latency_stats(out)
+        st["batches"] = len(sch.batches)
+        st["peak_resident_gb"] = sch.peak_resident / 2 ** 30
+        return st
+
+    try:
+        serve(poisson_requests(max(200, args.requests // 10), math.inf, seed=1))     # warm-up: arenas sized
+        setup_s = time.time() - t_setup
+        launches0 = sum(capi.mhd_launch_count(c) for c in be.ctxs)
+        clk.start()
+        sat = serve(poisson_requests(args.requests, math.inf, seed=4242))
+        loads = {}
+        for f in (0.5, 0.8, 0.95):
+            loads[str(f)] = serve(poisson_requests(args.requests, f * sat["requests_per_s"], seed=4242))
+        clocks = clk.stop()
+        launches = sum(capi.mhd_launch_count(c) for c in be.ctxs) - launches0
+        status = max(capi.mhd_get_device_status(c) for c in be.ctxs)
+        sample = poisson_requests(args.requests, math.inf, seed=4242)[: max(50, args.requests // 10)]
+        pp = per_patch_f64(tpl, sample, local)
+        served64 = serve([type(r)(r.rid, 0.0, r.n, r.level, "f64") for r in sample])
+    finally:
+        be.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": sat["cell_updates_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.requests, "warmup": max(200, args.requests // 10),
+            "ms_per_step": sat["span_s"] * 1e3 / args.requests, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving stream: single-step requests on periodic blast-wave cubes, edges "
+                                   "log-uniform 16-128 (even) + 4 ghost layers, levels 0-7 finer first, FP32/FP64 "
+                                   "50/50, 64 GB HBM budget, seed 4242; step = one request",
+                       "slots": args.slots, "batch_cells": args.batch_cells, "setup_s": setup_s,
+                       "l2": "batches of up to %d cells: working set above L2" % args.batch_cells,
+                       "parallelism": "replicas"},
+            "saturation": sat, "offered_load": loads,
+            "fp64_sample": {"served_batched": served64, "plain_per_patch": pp},
+            "gpu_launches": launches, "device_status": status, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     elif args.workload == "amr":
         run_amr(args)
     else:

@@ -234,9 +234,8 @@ def mhd_reflux(ctx, coarse, corr_ptrs, deposits, stream: int = 0) -> None:
 
 def mhd_ghost_fill(ctx, patches, copies, stream: int = 0) -> None:
     arr, n = _descs(patches)
-    cl = list(copies)
-    carr = (mhd_copy * max(1, len(cl)))(*cl)
-    _check(ctx, load().mhd_ghost_fill(ctx, arr, n, carr, len(cl), stream))
+    carr, nc = copies if isinstance(copies, tuple) else _structs(mhd_copy, copies)
+    _check(ctx, load().mhd_ghost_fill(ctx, arr, n, carr, nc, stream))
 
 
 def mhd_conservation_sums(ctx, patches, d_out8: int, stream: int = 0) -> None:
