@@ -68,9 +68,16 @@ def peaks():
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, "fallback", 2070.0
+
+
+def alu_peak_tflops(dtype, sm_mhz):
+    """Plain-ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flop (FMA) per clock; FP64: 152 SMs x 2 FP64 FMA per clock x 2 flop."""
+    lanes = 128 if dtype == "f32" else 2
+    return 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -178,10 +185,18 @@ def kernel_units(name, n):
     }.get(name)
 
 
-# Algorithmic values moved per unit by each staged kernel (read + written
-# once): the staged design exchanges intermediates through HBM.
-KERNEL_VALUES = {"k_prim": 8 + 11, "k_pred": 8 + 51, "k_edge": 1 + 1, "k_flux": 16 + 1 + 2 + 8,
-                 "k_emf": 4 + 4 + 4 + 1, "k_update": 16 + 16, "k_cfl": 8, "k_ghost": 16}
+# Algorithmic floating-point operations per unit of each kernel (add, sub,
+# mul, div and sqrt each counted once): the oracle's own arithmetic, counted
+# by oracle/opcount.py (`python -m oracle.opcount 128`) on the first step of
+# this workload; k_flux = CT half step + HLLD.  Data-dependent branches (HLLD
+# regions) move the per-unit figures by well under 1%.
+KERNEL_FLOPS = {"k_prim": 35.0, "k_pred": 835.0, "k_edge": 4.0, "k_flux": 376.0, "k_emf": 4.0,
+                "k_update": 89.14, "k_cfl": 92.0, "k_ghost": 0.0}
+
+# DRAM bytes (read + write) per launch of the dominant kernels on this
+# workload, from one ncu capture of the current kernels
+# (profiles/k_pred_k_flux_blast128_full.md); None where no capture exists.
+KERNEL_TRAFFIC = {("f32", "k_pred"): 542.4e6, ("f32", "k_flux"): 682.6e6}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush):
@@ -304,7 +319,7 @@ def run_ours(args):
     pr = synth.blast(args.n)
     stream = torch.cuda.Stream(device=local)
     flush = torch.empty(max(1, args.flush_mb) * 256 * 1024, dtype=torch.float32, device="cuda:%d" % local)
-    hbm, hbm_src = peaks()
+    hbm, hbm_src, sm_mhz = peaks()
     clocks = ClockSampler(local)
     clocks.start()
     res = {}
@@ -327,18 +342,30 @@ def run_ours(args):
         dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
         units = kernel_units(dom, args.n)
         per_launch = kernels[dom]["ms_per_launch"] * 1e-3
-        traffic_alg = units * KERNEL_VALUES[dom] * s
-        achieved = traffic_alg / per_launch / 1e9
+        step_bytes = 8 * s * ((args.n + 4) ** 3 + args.n ** 3)
+        flops = units * KERNEL_FLOPS[dom]
+        achieved = flops / per_launch / 1e12
+        peak = alu_peak_tflops(dtype, sm_mhz)
+        traffic = KERNEL_TRAFFIC.get((dtype, dom))
         out_dt[dtype] = {
             "value": value, "ms_per_step": ms_step,
             "p50_step_ms": statistics.median(r["per_step_ms"]),
             "p99_step_ms": sorted(r["per_step_ms"])[max(0, int(0.99 * len(r["per_step_ms"])) - 1)],
-            "hbm_step": {"bytes_per_cell_update": 2 * 8 * s, "achieved_gbs": 2 * 8 * s * cells / (ms_step * 1e-3) / 1e9,
-                         "peak_gbs": hbm, "frac": 2 * 8 * s * cells / (ms_step * 1e-3) / 1e9 / hbm},
-            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "algorithmic_bytes_per_launch": traffic_alg, "units_per_launch": units,
-                         "peak_source": hbm_src},
+            "hbm_step": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
+                         "peak_gbs": hbm, "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+                         "peak_source": hbm_src,
+                         "definition": "8 arrays x %d B x ((n+4)^3 read + n^3 written)" % s},
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_flops_per_launch": flops, "units_per_launch": units,
+                         "flops_per_unit": KERNEL_FLOPS[dom],
+                         "dram_gbs": (traffic / per_launch / 1e9) if traffic else None,
+                         "peak_source": "derived: 152 SMs x %s x 2 flop x %.0f MHz" %
+                                        ("128 FP32 lanes" if dtype == "f32" else "2 FP64 FMA/clk", sm_mhz)},
+            "step_flops": {"flops_per_cell_update": sum(KERNEL_FLOPS[k] * kernel_units(k, args.n)
+                                                        for k in KERNEL_FLOPS) / cells,
+                           "achieved_tflops": sum(KERNEL_FLOPS[k] * kernel_units(k, args.n) for k in KERNEL_FLOPS)
+                           / (ms_step * 1e-3) / 1e12, "peak_tflops": peak},
             "kernels": kernels,
             "e2e": {"value": reduce_sum(cells * r["e2e_steps"], world) / (e2e_max * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": r["state_bytes"], "d2h_bytes_per_step": r["state_bytes"]},

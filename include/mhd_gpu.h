@@ -217,6 +217,25 @@ mhd_status mhd_restrict(mhd_ctx *ctx, const mhd_patch_desc *fine, int32_t nf,
                         const mhd_patch_desc *coarse, int32_t nc,
                         const mhd_restrict_item *items, int32_t n, void *stream);
 
+#define MHD_PROLONG 0
+#define MHD_RESTRICT 1
+
+/* One coarse-fine item of mhd_restrict_prolong: `box` holds coarse cells
+ * (coarse global index) under the rules of mhd_prolong (mode MHD_PROLONG) or
+ * mhd_restrict (mode MHD_RESTRICT). */
+typedef struct {
+  int32_t fine, coarse; /* indices into the fine / coarse descriptor arrays  */
+  mhd_box box;
+} mhd_level_item;
+
+/* The P and R operations of Sec. 2.2 behind one entry point: mode
+ * MHD_PROLONG runs mhd_prolong (coarse -> fine ghost zones), MHD_RESTRICT
+ * runs mhd_restrict (fine -> covered coarse cells and faces), with the same
+ * checks, results and errors; any other mode is MHD_EINVAL. */
+mhd_status mhd_restrict_prolong(mhd_ctx *ctx, int32_t mode, const mhd_patch_desc *fine,
+                                int32_t nf, const mhd_patch_desc *coarse, int32_t nc,
+                                const mhd_level_item *items, int32_t n, void *stream);
+
 /* Refluxing (Sec. 2.2: fine fluxes restricted to the coarse level at the
  * coarse-fine boundary): zeroes the correction planes corr[p] (host array of
  * nc device pointers, NULL for coarse patches without children; 18 FP64

@@ -42,6 +42,12 @@
 
 #define ORC_EXPORT __attribute__((visibility("default")))
 
+/* Marks the start of stage k of the advance (and of the other operations)
+ * for the operation-counting build (opcount.cpp); a no-op here. */
+#ifndef ORC_STAGE
+#define ORC_STAGE(k) ((void)0)
+#endif
+
 typedef struct {
   int32_t n[3];    /* interior cells per axis                          */
   int32_t g;       /* ghost layers on every side                       */
@@ -398,6 +404,7 @@ ORC_EXPORT double orc_cfl_dt(const orc_patch *P, const orc_params *prm) {
   const int g = P->g;
   const double gm1 = prm->gamma - 1.0;
   double m = INFINITY;
+  ORC_STAGE(8);
 #pragma omp parallel for collapse(2) reduction(min : m)
   for (int k = g; k < g + P->n[2]; ++k)
     for (int j = g; j < g + P->n[1]; ++j)
@@ -467,6 +474,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
     dtdx[d] = dt / P->dx[d];
   }
 
+
+  ORC_STAGE(1);
   /* ---- stage 1: primitives and cell-centred E^n = -v x Bc on UB+2 ---- */
   double *W[8], *En[3];
   for (int q = 0; q < 8; ++q) W[q] = tmp(P);
@@ -485,6 +494,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
       }
 
+
+  ORC_STAGE(2);
   /* ---- stage 2: slopes, face values, Hancock predictor on UB+1 ---- */
   /* Wf[(d*2+side)*8+q]: side 0 = lower face of the cell, 1 = upper face */
   double *Wf[48], *Er[3];
@@ -557,6 +568,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
       }
 
+
+  ORC_STAGE(3);
   /* ---- stage 3: edge E^n = mean of the four neighbouring cell values ---- */
   /* Ee[a] at cell index c is the axis-a edge at the lower b and lower c corner */
   double *Ee[3];
@@ -579,6 +592,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
   }
 
+
+  ORC_STAGE(4);
   /* ---- stage 4: face-normal B at n+1/2 (CT half step) ---- */
   double *Bh[3];
   for (int a = 0; a < 3; ++a) Bh[a] = tmp(P);
@@ -598,6 +613,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
   }
 
+
+  ORC_STAGE(5);
   /* ---- stage 5: HLLD fluxes on the faces ---- */
   double *F[3][8], *Up[3];
   for (int d = 0; d < 3; ++d) {
@@ -624,6 +641,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
   }
 
+
+  ORC_STAGE(6);
   /* ---- stage 6: edge EMFs on the edges of the update box ---- */
   double *Ed[3];
   for (int a = 0; a < 3; ++a) Ed[a] = tmp(P);
@@ -707,6 +726,8 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         }
   }
 
+
+  ORC_STAGE(7);
   /* ---- stage 7: conservative cell update and CT face update ---- */
   int64_t nneg = 0;
 #pragma omp parallel for collapse(2) reduction(+ : nneg)

@@ -52,50 +52,54 @@ class _Capture(C.Structure):
                 ("mode", C.c_int32), ("dst", C.c_void_p)]
 
 
+def bind(L):
+    """Declares the C signatures of the oracle's exports on a loaded library."""
+    dp = C.POINTER(C.c_double)
+    L.orc_limiter.restype = C.c_double
+    L.orc_limiter.argtypes = [C.c_int32, C.c_double, C.c_double]
+    L.orc_fast_speed.restype = C.c_double
+    L.orc_fast_speed.argtypes = [C.c_double] * 6
+    L.orc_flux.restype = None
+    L.orc_flux.argtypes = [C.c_int32, dp, C.c_double, dp]
+    L.orc_hlld.restype = None
+    L.orc_hlld.argtypes = [C.c_int32, dp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
+    L.orc_hlld_fan.restype = None
+    L.orc_hlld_fan.argtypes = [C.c_int32, dp, dp, C.c_double, C.c_double, dp, dp, dp]
+    L.orc_fill_periodic.restype = None
+    L.orc_fill_periodic.argtypes = [C.POINTER(_Patch)]
+    L.orc_cfl_dt.restype = C.c_double
+    L.orc_cfl_dt.argtypes = [C.POINTER(_Patch), C.POINTER(_Params)]
+    L.orc_advance.restype = C.c_int64
+    L.orc_advance.argtypes = [C.POINTER(_Patch), C.POINTER(_Params), C.c_double,
+                              C.c_int32, C.POINTER(_Capture), C.c_int32,
+                              C.POINTER(_Capture), C.c_int32]
+    L.orc_sums.restype = None
+    L.orc_sums.argtypes = [C.POINTER(_Patch), dp]
+    L.orc_divb_max.restype = C.c_double
+    L.orc_divb_max.argtypes = [C.POINTER(_Patch)]
+    i3 = C.POINTER(C.c_int32)
+    pp = C.POINTER(C.c_void_p)
+    L.orc_prolong.restype = None
+    L.orc_prolong.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3]
+    L.orc_restrict.restype = None
+    L.orc_restrict.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, C.c_int32]
+    for nm in ("orc_deposit_faces", "orc_deposit_edges"):
+        f = getattr(L, nm)
+        f.restype = None
+        f.argtypes = [C.POINTER(_Patch), i3, pp, C.c_int32, i3, i3, dp, i3, i3, dp]
+    L.orc_correct.restype = None
+    L.orc_correct.argtypes = [C.POINTER(_Patch), pp]
+    L.orc_copy.restype = None
+    L.orc_copy.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, i3, C.c_int32]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = C.CDLL(_LIB)
-            dp = C.POINTER(C.c_double)
-            L.orc_limiter.restype = C.c_double
-            L.orc_limiter.argtypes = [C.c_int32, C.c_double, C.c_double]
-            L.orc_fast_speed.restype = C.c_double
-            L.orc_fast_speed.argtypes = [C.c_double] * 6
-            L.orc_flux.restype = None
-            L.orc_flux.argtypes = [C.c_int32, dp, C.c_double, dp]
-            L.orc_hlld.restype = None
-            L.orc_hlld.argtypes = [C.c_int32, dp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
-            L.orc_hlld_fan.restype = None
-            L.orc_hlld_fan.argtypes = [C.c_int32, dp, dp, C.c_double, C.c_double, dp, dp, dp]
-            L.orc_fill_periodic.restype = None
-            L.orc_fill_periodic.argtypes = [C.POINTER(_Patch)]
-            L.orc_cfl_dt.restype = C.c_double
-            L.orc_cfl_dt.argtypes = [C.POINTER(_Patch), C.POINTER(_Params)]
-            L.orc_advance.restype = C.c_int64
-            L.orc_advance.argtypes = [C.POINTER(_Patch), C.POINTER(_Params), C.c_double,
-                                      C.c_int32, C.POINTER(_Capture), C.c_int32,
-                                      C.POINTER(_Capture), C.c_int32]
-            L.orc_sums.restype = None
-            L.orc_sums.argtypes = [C.POINTER(_Patch), dp]
-            L.orc_divb_max.restype = C.c_double
-            L.orc_divb_max.argtypes = [C.POINTER(_Patch)]
-            i3 = C.POINTER(C.c_int32)
-            pp = C.POINTER(C.c_void_p)
-            L.orc_prolong.restype = None
-            L.orc_prolong.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3]
-            L.orc_restrict.restype = None
-            L.orc_restrict.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, C.c_int32]
-            for nm in ("orc_deposit_faces", "orc_deposit_edges"):
-                f = getattr(L, nm)
-                f.restype = None
-                f.argtypes = [C.POINTER(_Patch), i3, pp, C.c_int32, i3, i3, dp, i3, i3, dp]
-            L.orc_correct.restype = None
-            L.orc_correct.argtypes = [C.POINTER(_Patch), pp]
-            L.orc_copy.restype = None
-            L.orc_copy.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, i3, C.c_int32]
-            _lib = L
+            _lib = bind(C.CDLL(_LIB))
     return _lib
 
 

@@ -22,9 +22,11 @@ STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA"
 EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", "mhd_patch_advance",
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
-           "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux")
+           "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
+           "mhd_restrict_prolong")
 N_KERNELS = 10
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
+MHD_PROLONG, MHD_RESTRICT = 0, 1
 
 
 class MHDError(RuntimeError):
@@ -54,6 +56,10 @@ class mhd_copy(C.Structure):
 
 class mhd_prolong_item(C.Structure):
     _fields_ = [("coarse", C.c_int32), ("fine", C.c_int32), ("box", mhd_box)]
+
+
+class mhd_level_item(C.Structure):
+    _fields_ = [("fine", C.c_int32), ("coarse", C.c_int32), ("box", mhd_box)]
 
 
 class mhd_restrict_item(C.Structure):
@@ -115,6 +121,9 @@ def load(build_if_missing: bool = False):
     L.mhd_restrict.restype = i32
     L.mhd_restrict.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
                                C.POINTER(mhd_restrict_item), i32, P]
+    L.mhd_restrict_prolong.restype = i32
+    L.mhd_restrict_prolong.argtypes = [P, i32, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
+                                       C.POINTER(mhd_level_item), i32, P]
     L.mhd_reflux.restype = i32
     L.mhd_reflux.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(C.c_void_p),
                              C.POINTER(mhd_deposit), i32, P]
@@ -223,6 +232,13 @@ def mhd_restrict(ctx, fine, coarse, items, stream: int = 0) -> None:
     ca, nc = _descs(coarse)
     it, ni = items if isinstance(items, tuple) else _structs(mhd_restrict_item, items)
     _check(ctx, load().mhd_restrict(ctx, fa, nf, ca, nc, it, ni, stream))
+
+
+def mhd_restrict_prolong(ctx, mode, fine, coarse, items, stream: int = 0) -> None:
+    fa, nf = _descs(fine)
+    ca, nc = _descs(coarse)
+    it, ni = items if isinstance(items, tuple) else _structs(mhd_level_item, items)
+    _check(ctx, load().mhd_restrict_prolong(ctx, mode, fa, nf, ca, nc, it, ni, stream))
 
 
 def mhd_reflux(ctx, coarse, corr_ptrs, deposits, stream: int = 0) -> None:

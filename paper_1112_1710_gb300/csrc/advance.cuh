@@ -32,22 +32,6 @@ struct Cell {
   int i, j, k;
 };
 
-// q = floor(e / d) and e - q d for 0 <= e < 2^24 without an integer
-// division: the single-precision quotient is within one of the true one and
-// is corrected.
-__device__ __forceinline__ int divmod24(int e, int d, int& r) {
-  int q = __float2int_rz(__int2float_rn(e) * __frcp_rn(__int2float_rn(d)));
-  r = e - q * d;
-  if (r < 0) {
-    q -= 1;
-    r += d;
-  } else if (r >= d) {
-    q += 1;
-    r -= d;
-  }
-  return q;
-}
-
 // Decomposes element e of the UB+2 launch region of patch p; false if e is
 // beyond the region.
 __device__ __forceinline__ bool launch_cell(const DPatch& p, int e, Cell& c) {
@@ -91,15 +75,36 @@ __device__ __forceinline__ void raise_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }
 
+// Per-patch step constants dt, dt/(2 dx_d), dt/dx_d, computed once per call by
+// k_stepc (one thread per patch) so that no stage thread touches the double
+// dt scalar, the double dt scale or the double cell widths (on this GPU the
+// FP64 pipe is 64x narrower than the FP32 one).
+constexpr int kStepConsts = 8;
+
+template <typename R>
+__global__ void k_stepc(const DPatch* __restrict__ P, int npatch, const double* d_dt, R* K) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npatch) return;
+  const R dt = (R)((*d_dt) * P[p].dt_scale);
+  const R hdt = R(0.5) * dt;
+  R* k = K + (int64_t)p * kStepConsts;
+  k[0] = dt;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    k[1 + d] = hdt / (R)P[p].dx[d];
+    k[4 + d] = dt / (R)P[p].dx[d];
+  }
+}
+
 template <typename R> struct StepDt {
   R dt, hdtdx[3], dtdx[3];
-  __device__ __forceinline__ StepDt(const DPatch& p, const double* d_dt) {
-    dt = (R)((*d_dt) * p.dt_scale);
-    R hdt = R(0.5) * dt;
+  __device__ __forceinline__ StepDt(const R* __restrict__ K, int patch) {
+    const R* k = K + (int64_t)patch * kStepConsts;
+    dt = k[0];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      hdtdx[d] = hdt / (R)p.dx[d];
-      dtdx[d] = dt / (R)p.dx[d];
+      hdtdx[d] = k[1 + d];
+      dtdx[d] = k[4 + d];
     }
   }
 };
@@ -138,13 +143,13 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
-                                                   SolverConsts<R> sc, const double* d_dt) {
+                                                   SolverConsts<R> sc, const R* __restrict__ K) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
   if (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1)) return;
-  const StepDt<R> st(p, d_dt);
+  const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   R w[8], dw[3][8];
 #pragma unroll
@@ -261,12 +266,12 @@ template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPat
 // The face direction is a template parameter so that every array index below
 // is a compile-time constant (no local-memory arrays).
 template <typename R, int d>
-__device__ __forceinline__ void flux_face(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc,
-                                          const double* d_dt) {
+__device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell& c, R* scr,
+                                          const SolverConsts<R>& sc, const R* __restrict__ K) {
   constexpr int b = (d + 1) % 3, cc = (d + 2) % 3;
   const int id[3] = {c.i, c.j, c.k};
   if (!in_ub(p, d, id[d], 0, 1) || !in_ub(p, b, id[b], -1, 1) || !in_ub(p, cc, id[cc], -1, 1)) return;
-  const StepDt<R> st(p, d_dt);
+  const StepDt<R> st(K, patch);
   const int64_t x = lin(p, c);
   const int64_t sd = stride_of(p, d), sb = stride_of(p, b), scc = stride_of(p, cc);
   // CT half step of the face-normal field
@@ -291,15 +296,15 @@ __device__ __forceinline__ void flux_face(const DPatch& p, const Cell& c, R* scr
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
-                                                   SolverConsts<R> sc, const double* d_dt) {
+                                                   SolverConsts<R> sc, const R* __restrict__ K) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
   switch (blockIdx.y) {
-    case 0: flux_face<R, 0>(p, c, scr, sc, d_dt); break;
-    case 1: flux_face<R, 1>(p, c, scr, sc, d_dt); break;
-    default: flux_face<R, 2>(p, c, scr, sc, d_dt); break;
+    case 0: flux_face<R, 0>(p, t.patch, c, scr, sc, K); break;
+    case 1: flux_face<R, 1>(p, t.patch, c, scr, sc, K); break;
+    default: flux_face<R, 2>(p, t.patch, c, scr, sc, K); break;
   }
 }
 
@@ -372,12 +377,12 @@ __device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr,
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ P,
                                                      const BlockTask* __restrict__ T, R* scr,
-                                                     const double* d_dt) {
+                                                     const R* __restrict__ K) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  const StepDt<R> st(p, d_dt);
+  const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   const int id[3] = {c.i, c.j, c.k};
   if (in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0)) {
@@ -407,19 +412,22 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
   }
 }
 
-// Enqueues the six stages for the patches of one call.
+// Enqueues the step constants and the six stages for the patches of one
+// call; K (npatch x kStepConsts elements) is scratch.
 template <typename R>
-cudaError_t launch_advance(const DPatch* d_patches, const BlockTask* d_tasks, int nblocks, R* scr,
-                           const SolverConsts<R>& sc, const double* d_dt, int* d_status,
+cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks, R* scr,
+                           R* K, const SolverConsts<R>& sc, const double* d_dt, int* d_status,
                            const KernelTimer* tm, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   dim3 g1(nblocks), g3(nblocks, 3);
-  MHD_TIMED(tm, K_PRIM, s, (k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
-  MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_dt)));
+  MHD_TIMED(tm, K_PRIM, s,
+            (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
+             k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
+  MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
-  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_dt)));
+  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
-  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, d_dt)));
+  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, K)));
   return cudaGetLastError();
 }
 

@@ -14,8 +14,8 @@ cudaError_t advance_f32(const AdvanceArgs& a, cudaStream_t s) {
   sc.eps_up = (float)a.eps_up;
   sc.limiter = a.limiter;
   sc.emf = a.emf;
-  return launch_advance<float>(a.patches, a.tasks, a.nblocks, (float*)a.scratch, sc, a.d_dt,
-                               a.d_status, a.timer, s);
+  return launch_advance<float>(a.patches, a.npatches, a.tasks, a.nblocks, (float*)a.scratch,
+                               (float*)a.stepc, sc, a.d_dt, a.d_status, a.timer, s);
 }
 
 }  // namespace mhd

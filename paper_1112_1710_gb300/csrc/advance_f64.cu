@@ -14,8 +14,8 @@ cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s) {
   sc.eps_up = a.eps_up;
   sc.limiter = a.limiter;
   sc.emf = a.emf;
-  return launch_advance<double>(a.patches, a.tasks, a.nblocks, (double*)a.scratch, sc, a.d_dt,
-                                a.d_status, a.timer, s);
+  return launch_advance<double>(a.patches, a.npatches, a.tasks, a.nblocks, (double*)a.scratch,
+                                (double*)a.stepc, sc, a.d_dt, a.d_status, a.timer, s);
 }
 
 }  // namespace mhd

@@ -176,6 +176,7 @@ mhd_status convert(mhd_ctx* c, const mhd_patch_desc& d, int idx, DPatch& o) {
     if (!(d.dx[a] > 0.0))
       return fail(c, MHD_EINVAL, "patch %d (id %d): dx[%d] must be > 0", idx, d.patch_id, a);
     o.dx[a] = d.dx[a];
+    o.dxf[a] = (float)d.dx[a];
   }
   if (d.stride[1] < N[0] + 1 || d.stride[2] < d.stride[1] * (N[1] + 1))
     return fail(c, MHD_EINVAL, "patch %d (id %d): strides too small for the face arrays", idx, d.patch_id);
@@ -385,15 +386,19 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   std::vector<BlockTask> tasks;
   tasks_for(counts, tasks);
   if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
-  if ((r = ensure_scratch(c, (size_t)off * elem_size(dtype)))) return r;
+  // the per-patch step constants follow the stage planes in the arena
+  const int64_t stepc_off = off;
+  if ((r = ensure_scratch(c, (size_t)(off + 8 * (int64_t)n) * elem_size(dtype)))) return r;
   void *d_p = nullptr, *d_t = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
   AdvanceArgs a;
   a.patches = (const DPatch*)d_p;
+  a.npatches = n;
   a.tasks = (const BlockTask*)d_t;
   a.nblocks = (int)tasks.size();
   a.scratch = c->scratch;
+  a.stepc = (char*)c->scratch + (size_t)stepc_off * elem_size(dtype);
   a.gamma = c->prm.gamma;
   a.eps_up = eps_for(c->prm, dtype);
   a.limiter = c->prm.limiter;
@@ -439,7 +444,7 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   }
   cudaError_t e = dtype == MHD_F64 ? advance_f64(a, (cudaStream_t)stream) : advance_f32(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
-  c->launches += 6;
+  c->launches += 7;
   if (ncap > 0) {
     std::vector<BlockTask> ctasks;
     tasks_for(ccounts, ctasks);
@@ -658,6 +663,31 @@ mhd_status mhd_restrict(mhd_ctx* c, const mhd_patch_desc* fine, int32_t nf, cons
   if (e != cudaSuccess) return cuda_fail(c, e, "restrict launch");
   c->launches += 2;
   return MHD_OK;
+}
+
+mhd_status mhd_restrict_prolong(mhd_ctx* c, int32_t mode, const mhd_patch_desc* fine, int32_t nf,
+                                const mhd_patch_desc* coarse, int32_t nc, const mhd_level_item* items, int32_t n,
+                                void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (mode != MHD_PROLONG && mode != MHD_RESTRICT) return fail(c, MHD_EINVAL, "mode %d", mode);
+  if (n < 0 || (n > 0 && !items)) return fail(c, MHD_EINVAL, "bad item list");
+  if (mode == MHD_PROLONG) {
+    std::vector<mhd_prolong_item> it(n);
+    for (int t = 0; t < n; ++t) {
+      it[t].coarse = items[t].coarse;
+      it[t].fine = items[t].fine;
+      it[t].box = items[t].box;
+    }
+    return mhd_prolong(c, coarse, nc, fine, nf, it.data(), n, stream);
+  }
+  std::vector<mhd_restrict_item> it(n);
+  for (int t = 0; t < n; ++t) {
+    it[t].fine = items[t].fine;
+    it[t].coarse = items[t].coarse;
+    it[t].box = items[t].box;
+  }
+  return mhd_restrict(c, fine, nf, coarse, nc, it.data(), n, stream);
 }
 
 mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, double* const* corr,

@@ -25,7 +25,30 @@ struct DPatch {
   double dx[3];
   double dt_scale;   // dt of this patch = (*d_dt) * dt_scale
   double cfl_scale;  // scale factor of the CFL candidate dt
+  float dxf[3];      // dx rounded to FP32 (FP32 kernels read no doubles per thread)
+  int32_t pad2;
 };
+
+// Cell width along d in the arithmetic type of a kernel.
+template <typename R> __device__ __forceinline__ R dx_of(const DPatch& p, int d);
+template <> __device__ __forceinline__ double dx_of<double>(const DPatch& p, int d) { return p.dx[d]; }
+template <> __device__ __forceinline__ float dx_of<float>(const DPatch& p, int d) { return p.dxf[d]; }
+
+// q = floor(e / d) and e - q d for 0 <= e < 2^24 without an integer
+// division: the single-precision quotient is within one of the true one and
+// is corrected.
+__device__ __forceinline__ int divmod24(int e, int d, int& r) {
+  int q = __float2int_rz(__int2float_rn(e) * __frcp_rn(__int2float_rn(d)));
+  r = e - q * d;
+  if (r < 0) {
+    q -= 1;
+    r += d;
+  } else if (r >= d) {
+    q += 1;
+    r -= d;
+  }
+  return q;
+}
 
 // One block of a batched launch: the patch it works on and the first linear
 // element (within that patch's launch region) of its threads.

@@ -9,9 +9,11 @@ namespace mhd {
 
 struct AdvanceArgs {
   const DPatch* patches;   // device
+  int npatches;
   const BlockTask* tasks;  // device
   int nblocks;
   void* scratch;           // device arena of the call's element type
+  void* stepc;             // device, npatches x 8 elements of that type (in the arena)
   double gamma, eps_up;
   int limiter, emf;
   const double* d_dt;      // device

@@ -12,10 +12,12 @@
 namespace mhd {
 
 // ---------------------------------------------------------------- CFL dt
-// Per interior cell: t = min_d dx_d / (|v_d| + c_f,d); candidate
-// (cfl * t) * scale.  The minimum over cells is reduced with warp shuffles,
-// then per block, then one atomicMin on the IEEE bits (the candidates are
-// positive, so integer order is value order).
+// Per interior cell: t = min_d dx_d / (|v_d| + c_f,d), in the patch's
+// arithmetic type.  The block minimum of t (warp shuffles, then shared
+// memory; a block lies in one patch) becomes the candidate (cfl * t) * scale
+// in FP64 once per block, and one atomicMin on its IEEE bits (positive, so
+// integer order is value order) reduces over blocks.  x -> (cfl x) scale is
+// monotone, so this equals the minimum of the per-cell candidates.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_cfl(const DPatch* __restrict__ P,
                                                   const BlockTask* __restrict__ T, double gamma_d,
@@ -24,10 +26,22 @@ __global__ void __launch_bounds__(kThreads) k_cfl(const DPatch* __restrict__ P,
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   const int e = t.start + threadIdx.x;
-  double v = __longlong_as_double(0x7FF0000000000000LL);  // +inf
+  const R inf = R(1) / R(0);
+  R m = inf;
   if (e < p.n[0] * p.n[1] * p.n[2]) {
-    const int i = p.g + e % p.n[0], j = p.g + (e / p.n[0]) % p.n[1], k = p.g + e / (p.n[0] * p.n[1]);
-    const int64_t x = (int64_t)i + (int64_t)j * p.s1 + (int64_t)k * p.s2;
+    int i, j, k;
+    if (p.n[0] * p.n[1] * p.n[2] < (1 << 24)) {
+      int ri, rj;
+      const int q = divmod24(e, p.n[0], ri);
+      k = divmod24(q, p.n[1], rj);
+      i = ri;
+      j = rj;
+    } else {
+      i = e % p.n[0];
+      j = (e / p.n[0]) % p.n[1];
+      k = e / (p.n[0] * p.n[1]);
+    }
+    const int64_t x = (int64_t)(p.g + i) + (int64_t)(p.g + j) * p.s1 + (int64_t)(p.g + k) * p.s2;
     const R gamma = (R)gamma_d, gm1 = gamma - R(1);
     R u[8], w[8];
 #pragma unroll
@@ -36,31 +50,32 @@ __global__ void __launch_bounds__(kThreads) k_cfl(const DPatch* __restrict__ P,
     u[6] = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
     u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
     cons2prim(u, gm1, w);
-    R m = R(1) / R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
       R cf = fast_speed(w[0], w[4], w[5 + d], w[5 + t1], w[5 + t2], gamma);
-      R tt = (R)p.dx[d] / (Tr<R>::abs(w[1 + d]) + cf);
+      R tt = dx_of<R>(p, d) / (Tr<R>::abs(w[1 + d]) + cf);
       m = rmin(m, tt);
     }
-    v = (cfl * (double)m) * p.cfl_scale;
     if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicCAS(status, 0, -4);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    double u2 = __shfl_down_sync(0xffffffffu, v, o);
-    v = (u2 < v) ? u2 : v;
+    R u2 = __shfl_down_sync(0xffffffffu, m, o);
+    m = (u2 < m) ? u2 : m;
   }
-  __shared__ double red[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __shared__ R red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x < 32) {
-    v = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : __longlong_as_double(0x7FF0000000000000LL);
+    m = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : inf;
     for (int o = 16; o > 0; o >>= 1) {
-      double u2 = __shfl_down_sync(0xffffffffu, v, o);
-      v = (u2 < v) ? u2 : v;
+      R u2 = __shfl_down_sync(0xffffffffu, m, o);
+      m = (u2 < m) ? u2 : m;
     }
-    if (threadIdx.x == 0 && v == v) atomicMin(out, (unsigned long long)__double_as_longlong(v));
+    if (threadIdx.x == 0) {
+      const double v = (cfl * (double)m) * p.cfl_scale;
+      if (v == v) atomicMin(out, (unsigned long long)__double_as_longlong(v));
+    }
   }
 }
 

@@ -5,10 +5,10 @@ A hierarchy is a list of levels; level l is a list of interior boxes
 ``(lo, hi)`` (inclusive, level-l global cell index; the level-l domain has
 ``n0 * 2**l`` cells per side on the periodic cube [-1/2, 1/2]^3).  Every fine
 box is aligned to its level (even lower corner, even extent) and lies inside
-one parent box shrunk by ``margin`` parent cells, so a fine patch's ghost
-region and the slope stencil of its prolongation stay inside its parent's
-interior, and fine patches are at least ``margin`` cells away from the domain
-boundary.
+the union of the parent level's boxes eroded by ``margin`` parent cells (a
+cube erosion), so a fine patch's ghost region and the slope stencil of its
+prolongation stay inside parent interiors, and fine patches are at least
+``margin`` parent cells away from the domain boundary.
 """
 from __future__ import annotations
 

@@ -34,6 +34,7 @@ def test_binding_struct_layouts_match_header():
     assert ctypes.sizeof(capi.mhd_patch_desc) == 16 + 24 + 64 + 24 + 24
     assert ctypes.sizeof(capi.mhd_params) == 32
     assert ctypes.sizeof(capi.mhd_copy) == 8 + 24 + 12
+    assert ctypes.sizeof(capi.mhd_level_item) == ctypes.sizeof(capi.mhd_prolong_item) == 8 + 24
 
 
 @pytest.mark.parametrize("n,g", [((8, 6, 5), 2), ((128, 128, 1), 2), ((3, 5, 2), 4), ((1, 1, 1), 2), ((13, 7, 9), 4)])

@@ -60,6 +60,20 @@ def test_prolong_and_restrict_random_data(capi, orc):
         ri.box = capi.box(rlo, rhi)
         capi.mhd_restrict(ctx, [pf.desc()], [pc.desc()], [ri])
         assert np.array_equal(pc.state.cpu().numpy(), b)
+        # the combined entry point gives the same bits in both modes
+        pc2 = to_patch(stc, nc, G, (0.1,) * 3, lo=lo_c)
+        pf2 = to_patch(stf, nf, G, (0.05,) * 3, lo=lo_f, level=1)
+        li = capi.mhd_level_item()
+        li.fine, li.coarse = 0, 0
+        li.box = capi.box(clo, chi)
+        capi.mhd_restrict_prolong(ctx, capi.MHD_PROLONG, [pf2.desc()], [pc2.desc()], [li])
+        assert torch.equal(pf2.state, pf.state)
+        li.box = capi.box(rlo, rhi)
+        capi.mhd_restrict_prolong(ctx, capi.MHD_RESTRICT, [pf2.desc()], [pc2.desc()], [li])
+        assert torch.equal(pc2.state, pc.state)
+        with pytest.raises(capi.MHDError) as ei:
+            capi.mhd_restrict_prolong(ctx, 2, [pf2.desc()], [pc2.desc()], [li])
+        assert ei.value.status == capi.MHD_EINVAL
     finally:
         capi.mhd_ctx_destroy(ctx)
 
