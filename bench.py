@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
-    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve"])
+    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve", "ot2d"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests per offered load")
     ap.add_argument("--slots", type=int, default=3, help="serve: streams (one context each)")
     ap.add_argument("--batch-cells", type=int, default=4 << 20, help="serve: cell budget of one batch")
@@ -195,18 +195,20 @@ KERNEL_FLOPS = {"k_prim": 35.0, "k_pred": 835.0, "k_edge": 4.0, "k_flux": 376.0,
 
 # DRAM bytes (read + write) per launch of the dominant kernels on this
 # workload, from one ncu capture of the current kernels
-# (profiles/k_pred_k_flux_blast128_full.md); None where no capture exists.
-KERNEL_TRAFFIC = {("f32", "k_pred"): 542.4e6, ("f32", "k_flux"): 682.6e6}
+# (profiles/k_pred_k_flux_blast128_full.md).  Keys: bench pass, kernel.
+KERNEL_TRAFFIC = {("f32", "k_pred"): 542.4e6, ("f32", "k_flux"): 682.6e6,
+                  ("f64", "k_pred"): 1052.3e6, ("f64", "k_flux"): 1359.5e6,
+                  ("f64_exact", "k_pred"): 1051.9e6, ("f64_exact", "k_flux"): 1358.4e6}
 
 
-def time_dtype(dtype, pr, args, local, world, stream, flush):
+def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
     import torch
 
     from paper_1112_1710_gb300 import capi
     from paper_1112_1710_gb300.patch import Patch
     from paper_1112_1710_gb300.runner import PeriodicRunner
 
-    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER)
     try:
         p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
         run = PeriodicRunner(p, ctx, stream)
@@ -323,12 +325,14 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     res = {}
-    for dtype in ("f32", "f64"):
-        res[dtype] = time_dtype(dtype, pr, args, local, world, stream, flush)
+    # FP32 bulk (headline); FP64 with fused multiply-adds (the production FP64
+    # build); FP64 parity build (bit-identical to the oracle)
+    for key, dtype, contract in (("f32", "f32", 0), ("f64", "f64", 1), ("f64_exact", "f64", 0)):
+        res[key] = (dtype, time_dtype(dtype, pr, args, local, world, stream, flush, contract))
     clk = clocks.stop()
     cells = pr.cells
     out_dt = {}
-    for dtype, r in res.items():
+    for key, (dtype, r) in res.items():
         tmax = reduce_max(r["total_ms"], world)
         ncell = reduce_sum(cells * args.steps, world)
         e2e_max = reduce_max(r["e2e_ms"], world)
@@ -346,8 +350,8 @@ def run_ours(args):
         flops = units * KERNEL_FLOPS[dom]
         achieved = flops / per_launch / 1e12
         peak = alu_peak_tflops(dtype, sm_mhz)
-        traffic = KERNEL_TRAFFIC.get((dtype, dom))
-        out_dt[dtype] = {
+        traffic = KERNEL_TRAFFIC.get((key, dom))
+        out_dt[key] = {
             "value": value, "ms_per_step": ms_step,
             "p50_step_ms": statistics.median(r["per_step_ms"]),
             "p99_step_ms": sorted(r["per_step_ms"])[max(0, int(0.99 * len(r["per_step_ms"])) - 1)],
@@ -379,7 +383,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config(args.n), "roofline": main["roofline"], "hbm_step": main["hbm_step"],
             "e2e": main["e2e"], "gpu_launches": main["gpu_launches"], "clocks": clk,
-            "fp64": out_dt["f64"], "fp32": {k: v for k, v in main.items() if k not in ("roofline", "e2e")}}
+            "fp64": out_dt["f64"], "fp64_exact": out_dt["f64_exact"],
+            "fp32": {k: v for k, v in main.items() if k not in ("roofline", "e2e")}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_steps)
     print(json.dumps(line))
@@ -459,6 +464,63 @@ def run_amr(args):
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
             "runs": res}
+    print(json.dumps(line))
+
+
+def run_ot2d(args):
+    """2D Orszag-Tang vortex, one periodic 128^2 patch + 2 ghost layers, FP64,
+    CFL 0.4, 100 steps through the plain per-patch launch (ghost fill, CFL dt,
+    advance per step).  The state (2.6 MB) lives in L2, so the run is latency
+    and launch bound: it reports steps/s and cell-updates/s, no roofline."""
+    import torch
+
+    import synth
+    from paper_1112_1710_gb300 import _build, capi
+    from paper_1112_1710_gb300.patch import Patch
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    _build.build()
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    steps = 100
+    pr = synth.orszag_tang(128)
+    stream = torch.cuda.Stream(device=local)
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for key, contract in (("f64_exact", 0), ("f64", 1)):
+        ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0)
+        try:
+            p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype="f64", device="cuda:%d" % local)
+            run = PeriodicRunner(p, ctx, stream)
+            for _ in range(max(3, args.warmup)):
+                run.step()
+            torch.cuda.synchronize()
+            p.state.copy_(torch.as_tensor(pr.state, device=p.state.device))
+            torch.cuda.synchronize()
+            l0 = capi.mhd_launch_count(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                run.step()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[key] = {"ms": ms, "steps_per_s": steps / (ms * 1e-3),
+                        "value": pr.cells * steps / (ms * 1e-3), "launches": capi.mhd_launch_count(ctx) - l0,
+                        "device_status": capi.mhd_get_device_status(ctx)}
+        finally:
+            capi.mhd_ctx_destroy(ctx)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    main = out["f64_exact"]
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": max(3, args.warmup), "ms_per_step": main["ms"] / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2D Orszag-Tang vortex, one periodic 128^2 patch + 2 ghost layers, FP64, "
+                                   "CFL 0.4, 100 steps, plain per-patch launch (fill + CFL dt + advance)",
+                       "l2": "state (2.6 MB) resident in L2: no roofline claim", "parallelism": "replicas"},
+            "runs": out, "gpu_launches": main["launches"], "clocks": clk}
     print(json.dumps(line))
 
 
@@ -568,6 +630,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "ot2d":
+        run_ot2d(args)
     elif args.workload == "amr":
         run_amr(args)
     else:

@@ -91,6 +91,11 @@ typedef struct {
   double upwind_eps; /* contact speeds |S_M| <= upwind_eps (S_R - S_L) count as
                         no upwind side in the EMF upwinding; <= 0 selects
                         1e-10 for MHD_F64 and 1e-5 for MHD_F32 patches      */
+  int32_t fp64_contract; /* MHD_F64 advance: 0 the parity build (no fused
+                        multiply-add; every operation rounded as written, in
+                        the oracle's order), 1 the build with multiply-adds
+                        fused (about 1.25x faster; differs from 0 by rounding) */
+  int32_t reserved;  /* must be 0                                           */
 } mhd_params;
 
 /* One ghost-fill copy (Sec. 2.2 "synchronise ... and update ghost cells",

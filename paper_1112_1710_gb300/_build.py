@@ -1,8 +1,8 @@
 """Builds the CUDA library ``libmhdgpu.so`` in-tree for sm_103a with nvcc.
 
-Each translation unit is compiled in parallel; the FP64 kernels and the level
-operations use --fmad=false (bit-reproducible, parity build), the FP32
-kernels --fmad=true.
+Each translation unit is compiled in parallel; the FP64 parity kernels and the
+level operations use --fmad=false (bit-reproducible), the contracted FP64
+kernels --fmad=true, the FP32 kernels --fmad=true --use_fast_math.
 """
 from __future__ import annotations
 
@@ -22,6 +22,7 @@ UNITS = {
     "capi.cu": [],
     "level_ops.cu": ["--fmad=false"],
     "advance_f64.cu": ["--fmad=false"],
+    "advance_f64c.cu": ["--fmad=true"],
     "advance_f32.cu": ["--fmad=true", "--use_fast_math"],
     "noalloc.cu": ["--fmad=false"],
     "amr_ops.cu": ["--fmad=false"],

@@ -47,7 +47,8 @@ class mhd_patch_desc(C.Structure):
 
 class mhd_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
-                ("emf", C.c_int32), ("upwind_eps", C.c_double)]
+                ("emf", C.c_int32), ("upwind_eps", C.c_double), ("fp64_contract", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class mhd_copy(C.Structure):
@@ -172,8 +173,8 @@ def _descs(patches):
 
 
 # ------------------------------------------------------------------ C names
-def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0):
-    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps)
+def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0, fp64_contract=0):
+    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, 0)
     out = C.c_void_p()
     r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
     _check(None, r)

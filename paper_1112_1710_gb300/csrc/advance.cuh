@@ -19,9 +19,19 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "launch.h"
 #include "physics.cuh"
 
+// Each translation unit that instantiates the advance names its own inner
+// namespace, so that instantiations built with different floating-point
+// flags (FP64 with and without multiply-add contraction) never share a
+// symbol.
+#ifndef MHD_ADVANCE_NS
+#error "define MHD_ADVANCE_NS before including advance.cuh"
+#endif
+
 namespace mhd {
+namespace MHD_ADVANCE_NS {
 
 template <typename R> struct SolverConsts {
   R gamma, gm1, igm1, eps_up;
@@ -431,4 +441,18 @@ cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask*
   return cudaGetLastError();
 }
 
+// Solver constants in the arithmetic type, then the launches.
+template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t s) {
+  SolverConsts<R> sc;
+  sc.gamma = (R)a.gamma;
+  sc.gm1 = sc.gamma - R(1);
+  sc.igm1 = R(1) / sc.gm1;
+  sc.eps_up = (R)a.eps_up;
+  sc.limiter = a.limiter;
+  sc.emf = a.emf;
+  return launch_advance<R>(a.patches, a.npatches, a.tasks, a.nblocks, (R*)a.scratch, (R*)a.stepc, sc, a.d_dt,
+                           a.d_status, a.timer, s);
+}
+
+}  // namespace MHD_ADVANCE_NS
 }  // namespace mhd

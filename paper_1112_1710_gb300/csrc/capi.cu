@@ -262,7 +262,8 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   if (!out) return MHD_EINVAL;
   *out = nullptr;
   if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
-      params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1)
+      params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1 ||
+      params->fp64_contract < 0 || params->fp64_contract > 1 || params->reserved != 0)
     return MHD_EINVAL;
   mhd_ctx* c = new mhd_ctx();
   c->prm = *params;
@@ -442,7 +443,9 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     }
     ccounts[t] = cnt;
   }
-  cudaError_t e = dtype == MHD_F64 ? advance_f64(a, (cudaStream_t)stream) : advance_f32(a, (cudaStream_t)stream);
+  cudaError_t e = dtype == MHD_F32           ? advance_f32(a, (cudaStream_t)stream)
+                  : c->prm.fp64_contract ? advance_f64c(a, (cudaStream_t)stream)
+                                         : advance_f64(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
   c->launches += 7;
   if (ncap > 0) {

@@ -22,6 +22,7 @@ struct AdvanceArgs {
 };
 
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);
+cudaError_t advance_f64c(const AdvanceArgs& a, cudaStream_t s);
 cudaError_t advance_f32(const AdvanceArgs& a, cudaStream_t s);
 
 // CFL candidate minimum over the interiors (tasks span interiors).

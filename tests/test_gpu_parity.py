@@ -148,6 +148,36 @@ def test_blast_128_fp64_10_steps(capi, ctx_blast, orc):
     assert capi.mhd_get_device_status(ctx_blast) == 0
 
 
+@pytest.mark.parametrize("case", ["orszag_tang", "blast"])
+def test_contracted_fp64_within_tolerance(capi, orc, case, capsys):
+    """The FP64 build with fused multiply-adds (fp64_contract = 1) against the
+    oracle after 10 steps at full size, on the oracle's dt sequence: relative
+    L-infinity error <= 1e-11 per variable (rounding differences only)."""
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    emf = 1 if case == "blast" else 0
+    pr = synth.blast(128) if case == "blast" else synth.orszag_tang(128)
+    ctx = capi.mhd_ctx_create(emf=emf, fp64_contract=1)
+    try:
+        p = to_patch(pr.state.copy(), pr.n, pr.g, pr.dx)
+        run = PeriodicRunner(p, ctx)
+        want = pr.state
+        P = orc.patch(want, pr.n, pr.g, pr.dx)
+        prm = orc.params(emf=emf)
+        for _ in range(10):
+            orc.fill_periodic(P)
+            dt = orc.cfl_dt(P, prm)
+            assert orc.advance(P, prm, dt, 0) == 0
+            run.step(dt)
+        got = p.state.cpu().numpy()
+        err = rel_linf(got, want, pr.n, pr.g)
+        with capsys.disabled():
+            print("\ncontracted FP64 vs oracle, %s, 10 steps: max rel Linf %.2e" % (case, err.max()))
+        assert np.all(err <= TOL), err
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+
+
 def test_blast_fp32_error_report(capi, ctx_blast, orc, capsys):
     """FP32 bulk arithmetic against the FP64 oracle with the oracle's dt
     sequence: the error is reported per variable (no parity bar), with loose
