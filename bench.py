@@ -170,9 +170,13 @@ def reduce_sum(x, world):
     return float(t.item())
 
 
+STAGES = ("k_prim", "k_pred", "k_edge", "k_flux", "k_emf", "k_update")
+
+
 def kernel_units(name, n):
     """Elements one launch of a kernel processes on the n^3 periodic patch
-    (update box = interior, so UB+1 = n+2 and UB+2 = n+4 cells a side)."""
+    (update box = interior, so UB+1 = n+2 and UB+2 = n+4 cells a side); the
+    fused advance and its copy-back count cell updates."""
     return {
         "k_prim": (n + 4) ** 3,
         "k_pred": (n + 2) ** 3,
@@ -182,6 +186,8 @@ def kernel_units(name, n):
         "k_update": n ** 3,
         "k_cfl": n ** 3,
         "k_ghost": (n + 4) ** 3 - n ** 3,
+        "k_fused": n ** 3,
+        "k_commit": n ** 3,
     }.get(name)
 
 
@@ -191,7 +197,16 @@ def kernel_units(name, n):
 # this workload; k_flux = CT half step + HLLD.  Data-dependent branches (HLLD
 # regions) move the per-unit figures by well under 1%.
 KERNEL_FLOPS = {"k_prim": 35.0, "k_pred": 835.0, "k_edge": 4.0, "k_flux": 376.0, "k_emf": 4.0,
-                "k_update": 89.14, "k_cfl": 92.0, "k_ghost": 0.0}
+                "k_update": 89.14, "k_cfl": 92.0, "k_ghost": 0.0, "k_commit": 0.0}
+
+
+def kernel_flops(name, n):
+    """Algorithmic flops of one launch; the fused kernel does the work of all
+    six stages (its halo recomputation is not algorithmic work)."""
+    if name == "k_fused":
+        return sum(KERNEL_FLOPS[k] * kernel_units(k, n) for k in STAGES)
+    return KERNEL_FLOPS[name] * kernel_units(name, n)
+
 
 # DRAM bytes (read + write) per launch of the dominant kernels on this
 # workload, from one ncu capture of the current kernels
@@ -215,6 +230,9 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         for _ in range(args.warmup):
             run.step()
         torch.cuda.synchronize()
+        # the advance (staged kernels or a fused shape) as picked by the autotuner on this patch
+        v, cz, tms = capi.mhd_autotune_advance(ctx, run.descs, run.d_dt.data_ptr(), reps=3, stream=stream.cuda_stream)
+        tuned = {"choice": "staged" if v < 0 else "fused variant %d" % v, "chunk": cz, "ms_per_advance": tms}
         status = capi.mhd_get_device_status(ctx)
         capi.mhd_timing_enable(ctx, True)
         capi.mhd_timing_reset(ctx)
@@ -266,7 +284,7 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
     finally:
         capi.mhd_ctx_destroy(ctx)
     return {"total_ms": total_ms, "per_step_ms": per_step, "launches": launches, "kernels": kt,
-            "status": status, "e2e_ms": e2e_ms, "e2e_steps": ne, "state_bytes": nbytes}
+            "status": status, "e2e_ms": e2e_ms, "e2e_steps": ne, "state_bytes": nbytes, "autotune": tuned}
 
 
 def cpu_baseline(pr, steps):
@@ -347,10 +365,11 @@ def run_ours(args):
         units = kernel_units(dom, args.n)
         per_launch = kernels[dom]["ms_per_launch"] * 1e-3
         step_bytes = 8 * s * ((args.n + 4) ** 3 + args.n ** 3)
-        flops = units * KERNEL_FLOPS[dom]
+        flops = kernel_flops(dom, args.n)
         achieved = flops / per_launch / 1e12
         peak = alu_peak_tflops(dtype, sm_mhz)
         traffic = KERNEL_TRAFFIC.get((key, dom))
+        step_fl = sum(kernel_flops(k, args.n) for k in STAGES + ("k_cfl",))
         out_dt[key] = {
             "value": value, "ms_per_step": ms_step,
             "p50_step_ms": statistics.median(r["per_step_ms"]),
@@ -362,18 +381,16 @@ def run_ours(args):
             "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_flops_per_launch": flops, "units_per_launch": units,
-                         "flops_per_unit": KERNEL_FLOPS[dom],
+                         "flops_per_unit": flops / units,
                          "dram_gbs": (traffic / per_launch / 1e9) if traffic else None,
                          "peak_source": "derived: 152 SMs x %s x 2 flop x %.0f MHz" %
                                         ("128 FP32 lanes" if dtype == "f32" else "2 FP64 FMA/clk", sm_mhz)},
-            "step_flops": {"flops_per_cell_update": sum(KERNEL_FLOPS[k] * kernel_units(k, args.n)
-                                                        for k in KERNEL_FLOPS) / cells,
-                           "achieved_tflops": sum(KERNEL_FLOPS[k] * kernel_units(k, args.n) for k in KERNEL_FLOPS)
-                           / (ms_step * 1e-3) / 1e12, "peak_tflops": peak},
+            "step_flops": {"flops_per_cell_update": step_fl / cells,
+                           "achieved_tflops": step_fl / (ms_step * 1e-3) / 1e12, "peak_tflops": peak},
             "kernels": kernels,
             "e2e": {"value": reduce_sum(cells * r["e2e_steps"], world) / (e2e_max * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": r["state_bytes"], "d2h_bytes_per_step": r["state_bytes"]},
-            "gpu_launches": r["launches"], "device_status": r["status"],
+            "gpu_launches": r["launches"], "device_status": r["status"], "autotune": r["autotune"],
         }
     if rank != 0:
         return

@@ -23,8 +23,8 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
-           "mhd_restrict_prolong")
-N_KERNELS = 10
+           "mhd_restrict_prolong", "mhd_autotune_advance")
+N_KERNELS = 12
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
 
@@ -48,7 +48,7 @@ class mhd_patch_desc(C.Structure):
 class mhd_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
                 ("emf", C.c_int32), ("upwind_eps", C.c_double), ("fp64_contract", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("advance_kernel", C.c_int32), ("fused_chunk", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mhd_copy(C.Structure):
@@ -125,6 +125,9 @@ def load(build_if_missing: bool = False):
     L.mhd_restrict_prolong.restype = i32
     L.mhd_restrict_prolong.argtypes = [P, i32, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
                                        C.POINTER(mhd_level_item), i32, P]
+    L.mhd_autotune_advance.restype = i32
+    L.mhd_autotune_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), P, i32, C.POINTER(i32),
+                                     C.POINTER(i32), C.POINTER(C.c_float), P]
     L.mhd_reflux.restype = i32
     L.mhd_reflux.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(C.c_void_p),
                              C.POINTER(mhd_deposit), i32, P]
@@ -173,8 +176,9 @@ def _descs(patches):
 
 
 # ------------------------------------------------------------------ C names
-def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0, fp64_contract=0):
-    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, 0)
+def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0, fp64_contract=0,
+                   advance_kernel=0, fused_chunk=0):
+    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, advance_kernel, fused_chunk, 0)
     out = C.c_void_p()
     r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
     _check(None, r)
@@ -240,6 +244,17 @@ def mhd_restrict_prolong(ctx, mode, fine, coarse, items, stream: int = 0) -> Non
     ca, nc = _descs(coarse)
     it, ni = items if isinstance(items, tuple) else _structs(mhd_level_item, items)
     _check(ctx, load().mhd_restrict_prolong(ctx, mode, fa, nf, ca, nc, it, ni, stream))
+
+
+def mhd_autotune_advance(ctx, patches, d_dt: int, reps: int = 3, grow=None, stream: int = 0):
+    """Returns (choice, chunk, ms per advance): choice -1 = staged kernels,
+    else the fused variant."""
+    arr, n = _descs(patches)
+    gr = _arr(C.c_int32, grow) if grow is not None else None
+    v, cz, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(ctx, load().mhd_autotune_advance(ctx, arr, n, gr, d_dt, reps, C.byref(v), C.byref(cz), C.byref(ms),
+                                            stream))
+    return int(v.value), int(cz.value), float(ms.value)
 
 
 def mhd_reflux(ctx, coarse, corr_ptrs, deposits, stream: int = 0) -> None:

@@ -387,7 +387,7 @@ __device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr,
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ P,
                                                      const BlockTask* __restrict__ T, R* scr,
-                                                     const R* __restrict__ K) {
+                                                     const R* __restrict__ K, int commit) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
       R u = Uq[x];
       u = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + p.s1] - F1[x]) -
           st.dtdx[2] * (F2[x + p.s2] - F2[x]);
-      Uq[x] = u;
+      // without commit the new state goes to the (by now unused) primitive planes
+      (commit ? Uq : arr(scr, p, SC_W + q))[x] = u;
     }
   }
 #pragma unroll
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
     R dEc = Ec[x + sb] - Ec[x];
     R dEb = Eb[x + scc] - Eb[x];
     R* Ba = (R*)p.B[a];
-    Ba[x] = Ba[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
+    (commit ? Ba : arr(scr, p, SC_W + 5 + a))[x] = Ba[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
   }
 }
 
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
 template <typename R>
 cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks, R* scr,
                            R* K, const SolverConsts<R>& sc, const double* d_dt, int* d_status,
-                           const KernelTimer* tm, cudaStream_t s) {
+                           const KernelTimer* tm, bool commit, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   dim3 g1(nblocks), g3(nblocks, 3);
   MHD_TIMED(tm, K_PRIM, s,
@@ -437,8 +438,61 @@ cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask*
   MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
   MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
-  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, K)));
+  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, K, commit ? 1 : 0)));
   return cudaGetLastError();
+}
+
+#include "fused.cuh"
+
+// Enqueues the step constants, the fused kernel (as many CTAs as fit on the
+// device, at most one per item) and the copy-back of the new state.
+template <typename R, int BX, int BY, int NT>
+cudaError_t launch_fused(const AdvanceArgs& a, const SolverConsts<R>& sc, cudaStream_t s) {
+  if (a.nitems == 0) return cudaSuccess;
+  const size_t smem = sizeof(R) * FusedLayout<BX, BY>::TOTAL;
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    e = cudaFuncSetAttribute(k_fused<R, BX, BY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
+  }
+  int nsm = 0, per_sm = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<R, BX, BY, NT>, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = a.nitems < nsm * per_sm ? a.nitems : nsm * per_sm;
+  R* K = (R*)a.stepc;
+  MHD_TIMED(a.timer, K_FUSED, s,
+            (k_stepc<R><<<(a.npatches + 127) / 128, 128, 0, s>>>(a.patches, a.npatches, a.d_dt, K),
+             cudaMemsetAsync(a.counter, 0, sizeof(int), s),
+             k_fused<R, BX, BY, NT><<<grid, NT, smem, s>>>(a.patches, a.items, a.nitems, a.counter, (R*)a.scratch,
+                                                           K, sc, a.d_status)));
+  if (a.commit)
+    MHD_TIMED(a.timer, K_COMMIT, s,
+              (k_commit<R><<<a.nctasks, kThreads, 0, s>>>(a.patches, a.ctasks, (const R*)a.scratch)));
+  return cudaGetLastError();
+}
+
+template <typename R> cudaError_t launch_fused_variant(const AdvanceArgs& a, const SolverConsts<R>& sc, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    static_assert(kNumFused32 == 4, "variant table and dispatch must match");
+    switch (a.variant) {
+      case 0: return launch_fused<R, 16, 16, 512>(a, sc, s);
+      case 1: return launch_fused<R, 16, 16, 384>(a, sc, s);
+      case 2: return launch_fused<R, 16, 12, 384>(a, sc, s);
+      case 3: return launch_fused<R, 24, 8, 384>(a, sc, s);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    static_assert(kNumFused64 == 1, "variant table and dispatch must match");
+    if (a.variant != 0) return cudaErrorInvalidValue;
+    return launch_fused<R, 8, 8, 128>(a, sc, s);
+  }
 }
 
 // Solver constants in the arithmetic type, then the launches.
@@ -450,8 +504,9 @@ template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t
   sc.eps_up = (R)a.eps_up;
   sc.limiter = a.limiter;
   sc.emf = a.emf;
+  if (a.fused) return launch_fused_variant<R>(a, sc, s);
   return launch_advance<R>(a.patches, a.npatches, a.tasks, a.nblocks, (R*)a.scratch, (R*)a.stepc, sc, a.d_dt,
-                           a.d_status, a.timer, s);
+                           a.d_status, a.timer, a.commit, s);
 }
 
 }  // namespace MHD_ADVANCE_NS

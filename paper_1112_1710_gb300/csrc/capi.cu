@@ -3,6 +3,7 @@
 // dispatch to the kernel translation units.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -52,6 +53,12 @@ struct mhd_ctx {
   std::unordered_multimap<uint64_t, TableEntry> tables;
   size_t table_bytes = 0;
   int64_t launches = 0;
+  // advance path per element type (index MHD_F64 / MHD_F32) as picked by the
+  // autotuner: staged or fused, the fused variant and its z-chunk length (0:
+  // chosen per call); staged until the autotuner measured otherwise
+  bool use_fused[2] = {false, false};
+  int fused_variant[2] = {0, 0};
+  int fused_chunk[2] = {0, 0};
   // per-kernel event timer
   bool timing = false;
   struct Mark {
@@ -233,8 +240,8 @@ void timer_mark(void* self, int kernel, int phase, cudaStream_t s) {
 
 const KernelTimer* timer_of(mhd_ctx* c) { return c->timing ? &c->timer : nullptr; }
 
-const char* const kKernelNames[K_COUNT] = {"k_prim", "k_pred", "k_edge", "k_flux", "k_emf",
-                                            "k_update", "k_cfl", "k_ghost", "k_sums", "k_amr"};
+const char* const kKernelNames[K_COUNT] = {"k_prim", "k_pred",  "k_edge", "k_flux", "k_emf",   "k_update",
+                                            "k_cfl",  "k_ghost", "k_sums", "k_amr",  "k_fused", "k_commit"};
 
 // converts a descriptor array (all of one dtype) to device form
 mhd_status convert_all(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, std::vector<DPatch>& dp,
@@ -263,7 +270,8 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   *out = nullptr;
   if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
       params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1 ||
-      params->fp64_contract < 0 || params->fp64_contract > 1 || params->reserved != 0)
+      params->fp64_contract < 0 || params->fp64_contract > 1 || params->advance_kernel < 0 ||
+      params->advance_kernel > 2 || params->fused_chunk < 0 || params->reserved != 0)
     return MHD_EINVAL;
   mhd_ctx* c = new mhd_ctx();
   c->prm = *params;
@@ -358,18 +366,84 @@ mhd_status mhd_get_device_status(mhd_ctx* c, int32_t* out) {
   return MHD_OK;
 }
 
-mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n,
-                             const int32_t* grow, const double* d_dt, const double* dt_scale,
-                             const mhd_capture* caps, int32_t ncap, void* stream) {
-  mhd_status r = begin(c);
-  if (r) return r;
-  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
-  if (!d_dt) return fail(c, MHD_EINVAL, "d_dt is NULL");
-  if (n == 0) return MHD_OK;
-  std::vector<DPatch> dp(n);
-  std::vector<int64_t> counts(n);
+// Planes per z-chunk of the fused advance: the largest length whose work
+// (including the two-plane pipeline start of every chunk) spreads over the
+// device's resident CTAs with the smallest estimated makespan, i.e. total
+// work / CTAs + one item.
+int fused_chunk_auto(const std::vector<DPatch>& dp, int bx, int by, int ctas) {
+  static const int cand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 256};
+  int best = 8;
+  double best_t = 1e300;
+  for (int cz : cand) {
+    double work = 0.0;
+    int zmax = 0;
+    for (const DPatch& p : dp) {
+      const int ux = p.n[0] + 2 * p.k, uy = p.n[1] + 2 * p.k, uz = p.n[2] + 2 * p.k;
+      const int tiles = ((ux + bx - 1) / bx) * ((uy + by - 1) / by);
+      const int nch = (uz + cz - 1) / cz;
+      work += (double)tiles * (uz + 3.0 * nch);
+      zmax = uz > zmax ? uz : zmax;
+    }
+    const double t = work / ctas + (cz < zmax ? cz : zmax) + 3.0;
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = cz;
+    }
+  }
+  return best;
+}
+
+const FusedVariant& fused_variant_of(int dtype, int v) {
+  return dtype == MHD_F32 ? kFusedVariants32[v] : kFusedVariants64[v];
+}
+
+// Work items (x-y tiles x z-chunks, largest first) and k_commit blocks of a
+// fused call.
+void fused_items(const std::vector<DPatch>& dp, int bx, int by, int cz, std::vector<FusedItem>& items,
+                 std::vector<BlockTask>& ctasks) {
+  items.clear();
+  std::vector<int64_t> ccnt(dp.size());
+  for (size_t p = 0; p < dp.size(); ++p) {
+    const DPatch& q = dp[p];
+    const int lo = q.g - q.k;
+    const int ux = q.n[0] + 2 * q.k, uy = q.n[1] + 2 * q.k, uz = q.n[2] + 2 * q.k;
+    for (int z0 = 0; z0 < uz; z0 += cz)
+      for (int y0 = 0; y0 < uy; y0 += by)
+        for (int x0 = 0; x0 < ux; x0 += bx) {
+          FusedItem it{};
+          it.patch = (int32_t)p;
+          it.x0 = lo + x0;
+          it.y0 = lo + y0;
+          it.z0 = lo + z0;
+          it.z1 = lo + (z0 + cz < uz ? z0 + cz : uz);
+          items.push_back(it);
+        }
+    ccnt[p] = (int64_t)(ux + 1) * (uy + 1) * (uz + 1);
+  }
+  // largest items first (longest chunks, widest tiles), so the queue ends on short ones
+  const auto work = [&](const FusedItem& w) {
+    const DPatch& q = dp[w.patch];
+    const int hx = q.g + q.n[0] + q.k, hy = q.g + q.n[1] + q.k;
+    const int tx = hx - w.x0 < bx ? hx - w.x0 : bx, ty = hy - w.y0 < by ? hy - w.y0 : by;
+    return (int64_t)(tx + 2) * (ty + 2) * (w.z1 - w.z0 + 3);
+  };
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const FusedItem& u, const FusedItem& v) { return work(u) > work(v); });
+  tasks_for(ccnt, ctasks);
+}
+
+int sm_count(int dev) {
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+  return nsm;
+}
+
+// Host checks of an advance's patch array and their device descriptors.
+mhd_status advance_patches(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
+                           const double* dt_scale, std::vector<DPatch>& dp) {
+  dp.assign(n, DPatch{});
   const int dtype = patches[0].dtype;
-  int64_t off = 0;
+  mhd_status r;
   for (int p = 0; p < n; ++p) {
     if ((r = convert(c, patches[p], p, dp[p]))) return r;
     if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
@@ -380,35 +454,31 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     if (dt_scale && !(dt_scale[p] > 0.0)) return fail(c, MHD_EINVAL, "dt_scale[%d] must be > 0", p);
     dp[p].k = k;
     dp[p].dt_scale = dt_scale ? dt_scale[p] : 1.0;
-    dp[p].scr = off;
-    off += (int64_t)SC_COUNT * dp[p].nelem;
-    counts[p] = (int64_t)(dp[p].n[0] + 2 * k + 4) * (dp[p].n[1] + 2 * k + 4) * (dp[p].n[2] + 2 * k + 4);
   }
-  std::vector<BlockTask> tasks;
-  tasks_for(counts, tasks);
-  if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
-  // the per-patch step constants follow the stage planes in the arena
-  const int64_t stepc_off = off;
-  if ((r = ensure_scratch(c, (size_t)(off + 8 * (int64_t)n) * elem_size(dtype)))) return r;
-  void *d_p = nullptr, *d_t = nullptr;
-  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
-  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
-  AdvanceArgs a;
-  a.patches = (const DPatch*)d_p;
-  a.npatches = n;
-  a.tasks = (const BlockTask*)d_t;
-  a.nblocks = (int)tasks.size();
-  a.scratch = c->scratch;
-  a.stepc = (char*)c->scratch + (size_t)stepc_off * elem_size(dtype);
-  a.gamma = c->prm.gamma;
-  a.eps_up = eps_for(c->prm, dtype);
-  a.limiter = c->prm.limiter;
-  a.emf = c->prm.emf;
-  a.d_dt = d_dt;
-  a.d_status = c->d_status;
-  a.timer = timer_of(c);
-  // flux-register captures: checked against the faces / edges this call computes
+  return MHD_OK;
+}
+
+cudaError_t run_advance_args(mhd_ctx* c, int dtype, const AdvanceArgs& a, cudaStream_t s) {
+  return dtype == MHD_F32           ? advance_f32(a, s)
+         : c->prm.fp64_contract ? advance_f64c(a, s)
+                                : advance_f64(a, s);
+}
+
+mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n,
+                             const int32_t* grow, const double* d_dt, const double* dt_scale,
+                             const mhd_capture* caps, int32_t ncap, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
+  if (!d_dt) return fail(c, MHD_EINVAL, "d_dt is NULL");
   if (ncap < 0 || (ncap > 0 && !caps)) return fail(c, MHD_EINVAL, "bad capture list");
+  if (n == 0) return MHD_OK;
+  std::vector<DPatch> dp;
+  const int dtype = patches[0].dtype;
+  if ((r = advance_patches(c, patches, n, grow, dt_scale, dp))) return r;
+  // which advance: the context's (autotuned) choice, or forced staged / fused
+  bool fused = c->prm.advance_kernel == 2 || (c->prm.advance_kernel == 0 && c->use_fused[dtype == MHD_F32 ? 1 : 0]);
+  // flux-register captures: checked against the faces / edges this call computes
   std::vector<DCapture> dc(ncap);
   std::vector<int64_t> ccounts(ncap);
   for (int t = 0; t < ncap; ++t) {
@@ -416,7 +486,7 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     if (m.patch < 0 || m.patch >= n || (m.kind != 0 && m.kind != 1) || m.axis < 0 || m.axis > 2 ||
         (m.mode != 0 && m.mode != 1) || !m.dst)
       return fail(c, MHD_EINVAL, "capture %d: bad patch, kind, axis, mode or dst", t);
-    const DPatch& p = dp[m.patch];
+    DPatch& p = dp[m.patch];
     DCapture& o = dc[t];
     o.patch = m.patch;
     o.kind = m.kind;
@@ -437,28 +507,218 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
       }
       if (hi < lo || lo < alo || hi > ahi)
         return fail(c, MHD_EINVAL, "capture %d: box outside the elements the advance computes (axis %d)", t, d);
+      // the fused kernel stores the face fluxes of the update box only
+      if (m.kind == 0 && d != m.axis && (lo < ulo || hi > uhi)) fused = false;
       o.lo[d] = lo;
       o.ext[d] = hi - lo + 1;
       cnt *= o.ext[d];
     }
     ccounts[t] = cnt;
+    p.flags |= 1;
   }
-  cudaError_t e = dtype == MHD_F32           ? advance_f32(a, (cudaStream_t)stream)
-                  : c->prm.fp64_contract ? advance_f64c(a, (cudaStream_t)stream)
-                                         : advance_f64(a, (cudaStream_t)stream);
+  // arena: per patch its stage planes (staged) or its output copy, plus the
+  // flux planes when it feeds captures (fused); then the step constants, then
+  // the work-queue head
+  int64_t off = 0;
+  for (int p = 0; p < n; ++p) {
+    dp[p].scr = off;
+    off += (int64_t)((!fused || (dp[p].flags & 1)) ? SC_COUNT : 8) * dp[p].nelem;
+  }
+  const int64_t stepc_off = off;
+  off += 8 * (int64_t)n;
+  const size_t es = elem_size(dtype);
+  const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
+  if ((r = ensure_scratch(c, counter_byte + 16))) return r;
+  std::vector<BlockTask> tasks;
+  std::vector<FusedItem> items;
+  std::vector<BlockTask> ctasks;
+  if (!fused) {
+    std::vector<int64_t> counts(n);
+    for (int p = 0; p < n; ++p)
+      counts[p] = (int64_t)(dp[p].n[0] + 2 * dp[p].k + 4) * (dp[p].n[1] + 2 * dp[p].k + 4) *
+                  (dp[p].n[2] + 2 * dp[p].k + 4);
+    tasks_for(counts, tasks);
+    if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  } else {
+    const int di = dtype == MHD_F32 ? 1 : 0;
+    const FusedVariant& v = fused_variant_of(dtype, c->fused_variant[di]);
+    const int cz = c->prm.fused_chunk > 0   ? c->prm.fused_chunk
+                   : c->fused_chunk[di] > 0 ? c->fused_chunk[di]
+                                            : fused_chunk_auto(dp, v.bx, v.by, sm_count(c->device));
+    fused_items(dp, v.bx, v.by, cz, items, ctasks);
+    if (items.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  }
+  void *d_p = nullptr, *d_t = nullptr, *d_i = nullptr, *d_ct = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i))) return r;
+  if ((r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) return r;
+  AdvanceArgs a;
+  a.patches = (const DPatch*)d_p;
+  a.npatches = n;
+  a.tasks = (const BlockTask*)d_t;
+  a.nblocks = (int)tasks.size();
+  a.scratch = c->scratch;
+  a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
+  a.gamma = c->prm.gamma;
+  a.eps_up = eps_for(c->prm, dtype);
+  a.limiter = c->prm.limiter;
+  a.emf = c->prm.emf;
+  a.d_dt = d_dt;
+  a.d_status = c->d_status;
+  a.timer = timer_of(c);
+  a.fused = fused;
+  a.items = (const FusedItem*)d_i;
+  a.nitems = (int)items.size();
+  a.counter = (int*)((char*)c->scratch + counter_byte);
+  a.ctasks = (const BlockTask*)d_ct;
+  a.nctasks = (int)ctasks.size();
+  a.variant = c->fused_variant[dtype == MHD_F32 ? 1 : 0];
+  a.commit = true;
+  cudaError_t e = run_advance_args(c, dtype, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
-  c->launches += 7;
+  c->launches += fused ? 3 : 7;
   if (ncap > 0) {
-    std::vector<BlockTask> ctasks;
-    tasks_for(ccounts, ctasks);
-    void *d_c = nullptr, *d_ct = nullptr;
+    std::vector<BlockTask> cptasks;
+    tasks_for(ccounts, cptasks);
+    void *d_c = nullptr, *d_cpt = nullptr;
     if ((r = table(c, dc.data(), dc.size() * sizeof(DCapture), &d_c))) return r;
-    if ((r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) return r;
-    e = capture_launch(dtype, (const DPatch*)d_p, (const DCapture*)d_c, (const BlockTask*)d_ct, (int)ctasks.size(),
-                       c->scratch, d_dt, timer_of(c), (cudaStream_t)stream);
+    if ((r = table(c, cptasks.data(), cptasks.size() * sizeof(BlockTask), &d_cpt))) return r;
+    e = capture_launch(dtype, (const DPatch*)d_p, (const DCapture*)d_c, (const BlockTask*)d_cpt,
+                       (int)cptasks.size(), c->scratch, d_dt, timer_of(c), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "capture launch");
     c->launches += 1;
   }
+  return MHD_OK;
+}
+
+mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
+                                const double* d_dt, int32_t reps, int32_t* variant_out, int32_t* chunk_out,
+                                float* ms_out, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches || !d_dt || reps < 1 || reps > 1000) return fail(c, MHD_EINVAL, "autotune: bad arguments");
+  std::vector<DPatch> dp;
+  const int dtype = patches[0].dtype;
+  if ((r = advance_patches(c, patches, n, grow, nullptr, dp))) return r;
+  // arena as for a staged call (the staged candidate needs its 92 planes; the
+  // fused ones use the first 8 of them as output copies)
+  int64_t off = 0;
+  int zmax = 1;
+  std::vector<int64_t> counts(n);
+  for (int p = 0; p < n; ++p) {
+    dp[p].scr = off;
+    off += (int64_t)SC_COUNT * dp[p].nelem;
+    const int uz = dp[p].n[2] + 2 * dp[p].k;
+    zmax = uz > zmax ? uz : zmax;
+    counts[p] = (int64_t)(dp[p].n[0] + 2 * dp[p].k + 4) * (dp[p].n[1] + 2 * dp[p].k + 4) * (uz + 4);
+  }
+  const int64_t stepc_off = off;
+  off += 8 * (int64_t)n;
+  const size_t es = elem_size(dtype);
+  const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
+  if ((r = ensure_scratch(c, counter_byte + 16))) return r;
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  void *d_p = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  const int di = dtype == MHD_F32 ? 1 : 0;
+  const int nv = dtype == MHD_F32 ? kNumFused32 : kNumFused64;
+  const int nsm = sm_count(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(c, e, "autotune events");
+  }
+  float best = 3.4e38f;
+  int bv = -2, bcz = 0;
+  std::vector<FusedItem> items;
+  std::vector<BlockTask> ctasks;
+  // candidate -1: the staged kernels; then every fused variant x chunk length
+  for (int v = -1; v < nv; ++v) {
+    std::vector<int> chunks;
+    if (v < 0) {
+      chunks.push_back(0);
+    } else {
+      const FusedVariant& fv = fused_variant_of(dtype, v);
+      for (int cz : {fused_chunk_auto(dp, fv.bx, fv.by, nsm), 4, 8, 16, 32, 64}) {
+        cz = cz > zmax ? zmax : cz;
+        if (std::find(chunks.begin(), chunks.end(), cz) == chunks.end()) chunks.push_back(cz);
+      }
+    }
+    for (int cz : chunks) {
+      AdvanceArgs a{};
+      a.patches = (const DPatch*)d_p;
+      a.npatches = n;
+      a.tasks = (const BlockTask*)d_t;
+      a.nblocks = (int)tasks.size();
+      a.scratch = c->scratch;
+      a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
+      a.gamma = c->prm.gamma;
+      a.eps_up = eps_for(c->prm, dtype);
+      a.limiter = c->prm.limiter;
+      a.emf = c->prm.emf;
+      a.d_dt = d_dt;
+      a.d_status = c->d_status;
+      a.timer = nullptr;
+      a.commit = false;  // both paths leave the patch state as it is
+      a.fused = v >= 0;
+      if (a.fused) {
+        const FusedVariant& fv = fused_variant_of(dtype, v);
+        fused_items(dp, fv.bx, fv.by, cz, items, ctasks);
+        void *d_i = nullptr, *d_ct = nullptr;
+        if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i)) ||
+            (r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return r;
+        }
+        a.items = (const FusedItem*)d_i;
+        a.nitems = (int)items.size();
+        a.counter = (int*)((char*)c->scratch + counter_byte);
+        a.ctasks = (const BlockTask*)d_ct;
+        a.nctasks = (int)ctasks.size();
+        a.variant = v;
+      }
+      e = run_advance_args(c, dtype, a, s);
+      if (e != cudaSuccess) {  // a shape this device cannot run: skip it
+        cudaGetLastError();
+        break;
+      }
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = run_advance_args(c, dtype, a, s);
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(c, e, "autotune run");
+      }
+      c->launches += (a.fused ? 2 : 7) * (reps + 1);
+      ms /= reps;
+      if (ms < best) {
+        best = ms;
+        bv = v;
+        bcz = cz;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bv < -1) return fail(c, MHD_ECUDA, "autotune: no advance ran on this device");
+  c->use_fused[di] = bv >= 0;
+  c->fused_variant[di] = bv >= 0 ? bv : 0;
+  c->fused_chunk[di] = bv >= 0 ? bcz : 0;
+  if (variant_out) *variant_out = bv;
+  if (chunk_out) *chunk_out = bcz;
+  if (ms_out) *ms_out = best;
   return MHD_OK;
 }
 

@@ -21,7 +21,7 @@ struct DPatch {
   int32_t g;         // ghost layers
   int32_t k;         // update box = interior grown by k
   int32_t glo[3];    // global index of array index 0 (interior lo - g)
-  int32_t pad;
+  int32_t flags;     // bit 0: the fused advance also stores fluxes for captures
   double dx[3];
   double dt_scale;   // dt of this patch = (*d_dt) * dt_scale
   double cfl_scale;  // scale factor of the CFL candidate dt
@@ -57,6 +57,13 @@ struct BlockTask {
   int32_t start;
 };
 
+// One work item of the fused advance: an x-y tile of the update box with
+// lower corner (x0, y0) (array indices) and the planes [z0, z1).
+struct FusedItem {
+  int32_t patch, x0, y0, z0, z1;
+  int32_t pad[3];
+};
+
 // One ghost-fill copy, resolved to array indices of both patches.
 struct DCopy {
   int32_t src, dst;
@@ -82,7 +89,7 @@ constexpr int kThreads = 256;
 
 // Kernel ids of the per-kernel event timer (mhd_timing_*).
 enum KernelId : int {
-  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_AMR, K_COUNT
+  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_AMR, K_FUSED, K_COMMIT, K_COUNT
 };
 
 // Optional hook that records CUDA events around each launch on its stream.

@@ -19,7 +19,26 @@ struct AdvanceArgs {
   const double* d_dt;      // device
   int* d_status;           // device
   const KernelTimer* timer;  // nullable
+  // fused advance (one persistent kernel over the work items, then k_commit)
+  bool fused;
+  const FusedItem* items;    // device
+  int nitems;
+  int* counter;              // device, the work-queue head (zeroed by the launch)
+  const BlockTask* ctasks;   // device, k_commit blocks over each UB + 1
+  int nctasks;
+  int variant;               // index into the variant table of the element type
+  bool commit;               // false: leave the new state in the output copies
 };
+
+// Compiled shapes of the fused advance: x-y tile and threads per CTA (one CTA
+// per SM; FP64 fits smaller tiles, its intermediates being twice as large).
+struct FusedVariant {
+  int bx, by, nt;
+};
+constexpr FusedVariant kFusedVariants32[] = {{16, 16, 512}, {16, 16, 384}, {16, 12, 384}, {24, 8, 384}};
+constexpr FusedVariant kFusedVariants64[] = {{8, 8, 128}};
+constexpr int kNumFused32 = sizeof(kFusedVariants32) / sizeof(kFusedVariants32[0]);
+constexpr int kNumFused64 = sizeof(kFusedVariants64) / sizeof(kFusedVariants64[0]);
 
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);
 cudaError_t advance_f64c(const AdvanceArgs& a, cudaStream_t s);

@@ -32,7 +32,7 @@ def test_binding_struct_layouts_match_header():
     # mhd_patch_desc: 4 int32 + box (6 int32) + 8 pointers + 3 int64 + 3 double
     assert ctypes.sizeof(capi.mhd_box) == 24
     assert ctypes.sizeof(capi.mhd_patch_desc) == 16 + 24 + 64 + 24 + 24
-    assert ctypes.sizeof(capi.mhd_params) == 40
+    assert ctypes.sizeof(capi.mhd_params) == 48
     assert ctypes.sizeof(capi.mhd_copy) == 8 + 24 + 12
     assert ctypes.sizeof(capi.mhd_level_item) == ctypes.sizeof(capi.mhd_prolong_item) == 8 + 24
 

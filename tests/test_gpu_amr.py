@@ -78,18 +78,19 @@ def test_prolong_and_restrict_random_data(capi, orc):
         capi.mhd_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("split", [1, 2])
-def test_amr_coarse_steps_fp64_parity(capi, orc, split):
+@pytest.mark.parametrize("split,kernel", [(1, 1), (2, 1), (1, 2)])
+def test_amr_coarse_steps_fp64_parity(capi, orc, split, kernel):
     """Three subcycled coarse steps of a 3-level shell hierarchy (1 + 47 + 42
     patches of 4^3-8^3 cells, 4 ghost layers): every patch array equals the
-    oracle's."""
+    oracle's, with the staged advance (1) and with the fused one (2), whose
+    flux-register captures come from the fluxes it stores."""
     from oracle.amr import OHierarchy
     from paper_1112_1710_gb300.amr import Hierarchy
     n0 = 16
     H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8, level0_split=split)
     st = _states(H, n0)
     oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
-    ctx = capi.mhd_ctx_create(emf=1)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)
     try:
         ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
         oh.initialise()

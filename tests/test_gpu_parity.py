@@ -75,12 +75,15 @@ def test_cfl_dt_bitexact(capi, ctx, orc, problem):
 
 @pytest.mark.parametrize("emf,lim", [(0, 0), (1, 0), (0, 1), (0, 2)])
 @pytest.mark.parametrize("k", [0, 2])
-def test_one_step_random_state_ragged(capi, orc, emf, lim, k):
+@pytest.mark.parametrize("kernel,chunk", [(1, 0), (2, 0), (2, 4)])
+def test_one_step_random_state_ragged(capi, orc, emf, lim, k, kernel, chunk):
     """One step on a ragged patch (several blocks, partial tail) from random
-    data, including the extended update box (k = 2, g = 4)."""
+    data, including the extended update box (k = 2, g = 4), with the staged
+    kernels (1) and the fused kernel (2: 8 x 8 tiles in FP64, ragged in x and
+    y; z in one chunk or in chunks of 4 planes with a ragged last one)."""
     n, g, dx = (19, 13, 11), 4, (0.05, 0.07, 0.06)
     st = random_state(n, g, seed=5 + k)
-    ctx = capi.mhd_ctx_create(limiter=lim, emf=emf)
+    ctx = capi.mhd_ctx_create(limiter=lim, emf=emf, advance_kernel=kernel, fused_chunk=chunk)
     try:
         p = to_patch(st, n, g, dx)
         d = torch.full((1,), 1.3e-3, dtype=torch.float64, device="cuda")
@@ -211,10 +214,13 @@ def test_blast_fp32_error_report(capi, ctx_blast, orc, capsys):
     assert np.all(l1[[0, 4, 5, 6]] < 1e-4) and np.all(li[[0, 4]] < 1e-2)
 
 
-def test_batched_patches_equal_single_and_oracle(capi, ctx, orc):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_batched_patches_equal_single_and_oracle(capi, orc, kernel):
     """Independent periodic patches of uneven sizes advanced in one call give
-    the same bits as one call per patch, and match the oracle."""
+    the same bits as one call per patch, and match the oracle (staged and
+    fused advance; the fused work queue mixes the patches' tiles)."""
     from paper_1112_1710_gb300.patch import periodic_copies
+    ctx = capi.mhd_ctx_create(advance_kernel=kernel)
     sizes = [(8, 8, 8), (13, 9, 7), (24, 16, 12), (5, 5, 5)]
     probs = [random_state(n, 2, seed=20 + i) for i, n in enumerate(sizes)]
     dx = (0.05, 0.05, 0.05)
@@ -241,6 +247,47 @@ def test_batched_patches_equal_single_and_oracle(capi, ctx, orc):
         capi.mhd_ghost_fill(ctx, [batch[i].desc()], periodic_copies(n, 2))
         err = rel_linf(batch[i].state.cpu().numpy(), s, n, 2)
         assert np.all(err <= TOL), (i, err)
+    capi.mhd_ctx_destroy(ctx)
+
+
+def test_fused_fp64_blast_10_steps(capi, orc):
+    """The fused kernel in the FP64 parity build on the 3D blast (64^3, several
+    8 x 8 tiles, CFL dt every step) against the oracle after 10 steps."""
+    pr = synth.blast(64)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=2)
+    try:
+        got, want, gdts, odts = _run_both(capi, ctx, orc, pr, 10, emf=1)
+        assert gdts == odts
+        err = rel_linf(got, want, pr.n, pr.g)
+        assert np.all(err <= TOL), err
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+
+
+def test_fused_fp32_chunking_invariant_and_close_to_staged(capi, capsys):
+    """FP32: the fused kernel gives the same bits for any z-chunk length (every
+    element is computed by the same code whatever the work decomposition), and
+    stays within FP32 rounding of the staged kernels after 5 steps."""
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    pr = synth.blast(72)
+    outs = {}
+    for key, kernel, chunk in (("auto", 2, 0), ("c5", 2, 5), ("staged", 1, 0)):
+        ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel, fused_chunk=chunk)
+        try:
+            p = to_patch(pr.state.copy(), pr.n, pr.g, pr.dx, dtype="f32")
+            run = PeriodicRunner(p, ctx)
+            for _ in range(5):
+                run.step(2e-4)
+            assert capi.mhd_get_device_status(ctx) == 0
+            outs[key] = p.state.clone()
+        finally:
+            capi.mhd_ctx_destroy(ctx)
+    assert torch.equal(outs["auto"], outs["c5"])
+    err = rel_linf(outs["auto"].cpu().numpy(), outs["staged"].cpu().numpy().astype(np.float64), pr.n, pr.g)
+    with capsys.disabled():
+        print("\nfused vs staged FP32, blast 72^3, 5 steps: max rel Linf %.2e" % err.max())
+    assert err.max() <= 1e-5
 
 
 def test_conservation_sums_within_summation_bound(capi, ctx, orc):
@@ -298,3 +345,40 @@ def test_host_checks_reject_without_launch(capi, ctx):
     # an empty advance is valid and launches nothing
     capi.mhd_patch_advance(ctx, [], d.data_ptr())
     assert capi.mhd_launch_count(ctx) == before
+
+
+def test_autotune_keeps_state_and_stores_a_choice(capi):
+    """The autotuner times the staged kernels and every compiled fused shape
+    without touching the patch state, stores the fastest in the context, and
+    later advances agree with the staged kernels to FP32 rounding."""
+    from paper_1112_1710_gb300.patch import periodic_copies
+    pr = synth.blast(64)
+    ctx = capi.mhd_ctx_create(emf=1)
+    ref = capi.mhd_ctx_create(emf=1, advance_kernel=1)
+    try:
+        p = to_patch(pr.state, pr.n, pr.g, pr.dx, dtype="f32")
+        q = to_patch(pr.state, pr.n, pr.g, pr.dx, dtype="f32")
+        capi.mhd_ghost_fill(ctx, [p.desc()], periodic_copies(p.n, p.g))
+        capi.mhd_ghost_fill(ctx, [q.desc()], periodic_copies(q.n, q.g))
+        before = p.state.clone()
+        d = torch.full((1,), 2e-4, dtype=torch.float64, device="cuda")
+        v, cz, ms = capi.mhd_autotune_advance(ctx, [p.desc()], d.data_ptr(), reps=2)
+        torch.cuda.synchronize()
+        assert torch.equal(p.state, before)
+        assert -1 <= v < 4 and (cz == 0 if v < 0 else 1 <= cz <= 64) and ms > 0.0
+        capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr())
+        capi.mhd_patch_advance(ref, [q.desc()], d.data_ptr())
+        err = rel_linf(p.state.cpu().numpy(), q.state.cpu().numpy().astype(np.float64), pr.n, pr.g)
+        assert err.max() <= 1e-6, (v, cz, err)
+        if v < 0:
+            assert torch.equal(p.state, q.state)
+        p64 = to_patch(pr.state, pr.n, pr.g, pr.dx)
+        capi.mhd_ghost_fill(ctx, [p64.desc()], periodic_copies(p64.n, p64.g))
+        before64 = p64.state.clone()
+        v64, cz64, _ = capi.mhd_autotune_advance(ctx, [p64.desc()], d.data_ptr(), reps=1)
+        torch.cuda.synchronize()
+        assert v64 in (-1, 0) and torch.equal(p64.state, before64)
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+        capi.mhd_ctx_destroy(ref)
