@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
-    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve", "ot2d"])
+    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve", "ot2d", "deep"])
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests per offered load")
     ap.add_argument("--slots", type=int, default=3, help="serve: streams (one context each)")
     ap.add_argument("--batch-cells", type=int, default=4 << 20, help="serve: cell budget of one batch")
@@ -641,6 +641,76 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_deep(args):
+    """Deep AMR: base 32^3 + 7 refined levels (ratio 2, subcycled), about 108 M
+    cells in about 2,000 seeded patches of 8^3-64^3 placed where |curl v| +
+    |div v| of a k^-4 velocity field (256^3, Mach 5, seed 5) is largest,
+    plasma beta 1; FP32 state, FP64 flux registers and conservation sums; the
+    whole coarse step replayed as one CUDA graph; `--steps` coarse steps."""
+    import torch
+
+    import synth.turb as ST
+    from paper_1112_1710_gb300 import _build, capi
+    from paper_1112_1710_gb300.amr import Hierarchy
+    _build.build()
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    n0, G = 32, 4
+    t0 = time.time()
+    H, v, _ = ST.deep_hierarchy(n0=n0, levels=8, m=256)
+    states = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    stream = torch.cuda.Stream(device=local)
+    h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream,
+                  device="cuda:%d" % local)
+    del states
+    clk = ClockSampler(local)
+    try:
+        h.initialise()
+        out = torch.zeros(8, dtype=torch.float64, device="cuda:%d" % local)
+        capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        s0 = out.cpu().numpy().copy()
+        h.capture_graph()           # runs one eager coarse step first
+        h.replay()                  # warm-up replay
+        torch.cuda.synchronize()
+        setup_s = time.time() - t0
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            h.replay()
+        e1.record(stream)
+        e1.synchronize()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        s1 = out.cpu().numpy()
+        status = capi.mhd_get_device_status(ctx)
+        upd = h.cell_updates_per_coarse_step()
+    finally:
+        h.close()
+        capi.mhd_ctx_destroy(ctx)
+    if rank != 0:
+        return
+    cells = [sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in bl) for bl in H]
+    drift = [float(abs(s1[q] - s0[q]) / max(abs(s0[q]), 1e-300)) for q in (0, 1, 2, 3, 4, 5)]
+    line = {"metric": METRIC, "value": upd * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": 2, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "deep AMR: base 32^3 + 7 levels (ratio 2, subcycled), %d patches of 8^3-64^3 "
+                                   "on a k^-4 velocity field (256^3, Mach 5, beta 1, seed 5); FP32 state, FP64 "
+                                   "registers and sums; step = one coarse step (graph replay)" % sum(len(l) for l in H),
+                       "patches_per_level": [len(l) for l in H], "cells_per_level": cells,
+                       "cell_updates_per_coarse_step": upd, "setup_s": setup_s,
+                       "l2": "working set (tens of GB) far above L2", "parallelism": "replicas"},
+            "conservation_drift_rel": {"rho": drift[0], "Mx": drift[1], "My": drift[2], "Mz": drift[3],
+                                       "E": drift[4], "Bx": drift[5]},
+            "device_status": status, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -649,6 +719,8 @@ def main():
         run_serve(args)
     elif args.workload == "ot2d":
         run_ot2d(args)
+    elif args.workload == "deep":
+        run_deep(args)
     elif args.workload == "amr":
         run_amr(args)
     else:

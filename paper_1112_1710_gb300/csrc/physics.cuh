@@ -16,14 +16,21 @@
 
 namespace mhd {
 
+// degen: relative threshold of the HLLD single-star degeneracy test.  It must
+// sit well above the rounding of rho (S - u)(S - S_M) - Bn^2 in the arithmetic
+// type: 1e-12 in FP64 (about 4500 ulp), 1e-5 in FP32 (about 80 ulp); an FP32
+// test at 1e-12 never fires, and a denominator that is rounding noise then
+// divides the transverse velocity and field.
 template <typename R> struct Tr;
 template <> struct Tr<double> {
   __device__ static __forceinline__ double abs(double x) { return fabs(x); }
   __device__ static __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  __device__ static __forceinline__ double degen() { return 1e-12; }
 };
 template <> struct Tr<float> {
   __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
   __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  __device__ static __forceinline__ float degen() { return 1e-5f; }
 };
 
 template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return (a < b) ? a : b; }
@@ -124,7 +131,8 @@ template <typename R> __device__ __forceinline__ void flux_xyz(int d, const R* w
 // side) and R_ (upper side) with interface normal field bn.  Wave speeds
 // S_L = min(u_L,u_R) - max(cf), S_R = max(u_L,u_R) + max(cf); S_M, p_T* from
 // MK05 eqs. (38), (41); star states eqs. (43)-(48) with a degenerate branch
-// (|rho(S-u)(S-S_M) - Bn^2| <= 1e-12 max(rho(S-u)^2, Bn^2) keeps the outer
+// (|rho(S-u)(S-S_M) - Bn^2| <= degen max(rho(S-u)^2, Bn^2), degen 1e-12 in
+// FP64 and 1e-5 in FP32, keeps the outer
 // transverse v, B); Alfven speeds S* = S_M -/+ |Bn|/sqrt(rho*); double-star
 // states eqs. (59)-(63); left-closed region selection.  f gets the rotated
 // flux; *upw the upwind side of the contact (+1, -1, or 0 when
@@ -171,7 +179,7 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
   R bn2 = bn * bn;
   R vls, wls, byls, bzls;
   R denl = rsl * sml - bn2;
-  if (Tr<R>::abs(denl) <= R(1e-12) * rmax(rsl * sdl, bn2)) {
+  if (Tr<R>::abs(denl) <= Tr<R>::degen() * rmax(rsl * sdl, bn2)) {
     vls = vl; wls = wl_; byls = byl; bzls = bzl;
   } else {
     R fv = bn * (sm - ul) / denl;
@@ -181,7 +189,7 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
   }
   R vrs, wrs, byrs, bzrs;
   R denr = rsr * smr - bn2;
-  if (Tr<R>::abs(denr) <= R(1e-12) * rmax(rsr * sdr, bn2)) {
+  if (Tr<R>::abs(denr) <= Tr<R>::degen() * rmax(rsr * sdr, bn2)) {
     vrs = vr; wrs = wr_; byrs = byr; bzrs = bzr;
   } else {
     R fv = bn * (sm - ur) / denr;

@@ -187,3 +187,42 @@ def test_amr_graph_replay_and_per_patch_path_equal_eager_batched(capi):
     finally:
         capi.mhd_ctx_destroy(ctx)
         capi.mhd_ctx_destroy(ctx2)
+
+
+def test_turbulent_deep_hierarchy_fp64_parity(capi, orc):
+    """The deep-AMR workload's generator downscaled (base 16^3, 3 levels,
+    k^-4 velocity field at Mach 5, plasma beta 1): three subcycled coarse
+    steps of the FP64 parity build equal the oracle's on every patch."""
+    import synth.turb as ST
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H, v, _ = ST.deep_hierarchy(n0=n0, levels=3, m=32, size_min=4, size_max=8)
+    assert len(H) == 3 and all(len(l) > 0 for l in H)
+    st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        oh.initialise()
+        oh.fill(0)
+        ph.initialise()
+        for _ in range(3):
+            odt = oh.coarse_step()
+            ph.coarse_step()
+            assert ph.d_dt.item() == odt
+        assert capi.mhd_get_device_status(ctx) == 0
+        for l in range(3):
+            for P, Q in zip(oh.levels[l], ph.levels[l]):
+                got = Q.state.cpu().numpy()
+                n = P.n
+                for q in range(8):
+                    ext = list(n)
+                    if q >= 5:
+                        ext[q - 5] += 1
+                    a = got[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                    b = P.state[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                    assert np.abs(a - b).max() <= TOL * max(np.abs(b).max(), 1e-300), (l, q)
+        ph.close()
+    finally:
+        capi.mhd_ctx_destroy(ctx)
