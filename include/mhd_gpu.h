@@ -269,13 +269,17 @@ mhd_status mhd_restrict_prolong(mhd_ctx *ctx, int32_t mode, const mhd_patch_desc
                                 const mhd_level_item *items, int32_t n, void *stream);
 
 /* Refluxing (Sec. 2.2: fine fluxes restricted to the coarse level at the
- * coarse-fine boundary): zeroes the correction planes corr[p] (host array of
- * nc device pointers, NULL for coarse patches without children; 18 FP64
- * planes each, see mhd_deposit), executes the deposits, then corrects every
+ * coarse-fine boundary): executes the deposits into the correction planes
+ * corr[p] (host array of nc device pointers, NULL for coarse patches without
+ * children; 18 FP64 planes each, see mhd_deposit), then corrects every
  * interior cell and face of those coarse patches:
  *   U_q -= (dF_x(+x) - dF_x)/dx - (dF_y(+y) - dF_y)/dy - (dF_z(+z) - dF_z)/dz,
  *   B_a -= (dE_c(+b) - dE_c)/dx_b - (dE_b(+c) - dE_b)/dx_c   (b, c = a+1, a+2),
- * in FP64 (FP32 state is rounded once).  Call mhd_restrict afterwards: it
+ * in FP64 (FP32 state is rounded once).  The planes must be all zero on entry
+ * (zero them once after allocation); the call zeroes the elements its
+ * deposits wrote before returning, so they are zero again for the next call,
+ * and it touches only the cells and faces next to deposited elements (all
+ * others have a zero correction).  Call mhd_restrict afterwards: it
  * overwrites the covered cells and faces. */
 mhd_status mhd_reflux(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc,
                       double *const *corr, const mhd_deposit *deps, int32_t nd,
@@ -330,7 +334,7 @@ int64_t mhd_launch_count(const mhd_ctx *ctx);
 /* Per-kernel event timer (diagnostics, no counterpart in the paper).  While
  * enabled, every launch of the context is bracketed by two CUDA events
  * recorded on the launching stream.  mhd_timing_read synchronises on the
- * pending events and returns, for kernel id `kernel` (0 <= id < 10, names from
+ * pending events and returns, for kernel id `kernel` (0 <= id < 15, names from
  * mhd_kernel_name), the summed device time in ms and the number of launches
  * since the last reset; mhd_timing_reset clears the sums. */
 mhd_status mhd_timing_enable(mhd_ctx *ctx, int32_t on);

@@ -24,7 +24,7 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
            "mhd_restrict_prolong", "mhd_autotune_advance")
-N_KERNELS = 12
+N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
 

@@ -395,32 +395,43 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
   const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   const int id[3] = {c.i, c.j, c.k};
-  if (in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0)) {
+  // every load before the first store: the state and scratch pointers may
+  // alias as far as the compiler knows, so a store would order later loads
+  const bool cell = in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0);
+  R un[5];
+  if (cell) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const R* F0 = arr(scr, p, SC_F + 0 * 8 + q);
       const R* F1 = arr(scr, p, SC_F + 1 * 8 + q);
       const R* F2 = arr(scr, p, SC_F + 2 * 8 + q);
-      R* Uq = (R*)p.U[q];
-      R u = Uq[x];
-      u = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + p.s1] - F1[x]) -
-          st.dtdx[2] * (F2[x + p.s2] - F2[x]);
-      // without commit the new state goes to the (by now unused) primitive planes
-      (commit ? Uq : arr(scr, p, SC_W + q))[x] = u;
+      R u = ((const R*)p.U[q])[x];
+      un[q] = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + p.s1] - F1[x]) -
+              st.dtdx[2] * (F2[x + p.s2] - F2[x]);
     }
   }
+  bool face[3];
+  R bn[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int b = (a + 1) % 3, cc = (a + 2) % 3;
-    if (!in_ub(p, a, id[a], 0, 1) || !in_ub(p, b, id[b], 0, 0) || !in_ub(p, cc, id[cc], 0, 0)) continue;
+    face[a] = in_ub(p, a, id[a], 0, 1) && in_ub(p, b, id[b], 0, 0) && in_ub(p, cc, id[cc], 0, 0);
+    if (!face[a]) continue;
     const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
     const R* Ec = arr(scr, p, SC_ED + cc);
     const R* Eb = arr(scr, p, SC_ED + b);
     R dEc = Ec[x + sb] - Ec[x];
     R dEb = Eb[x + scc] - Eb[x];
-    R* Ba = (R*)p.B[a];
-    (commit ? Ba : arr(scr, p, SC_W + 5 + a))[x] = Ba[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
+    bn[a] = ((const R*)p.B[a])[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
   }
+  // without commit the new state goes to the (by now unused) primitive planes
+  if (cell) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) (commit ? (R*)p.U[q] : arr(scr, p, SC_W + q))[x] = un[q];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (face[a]) (commit ? (R*)p.B[a] : arr(scr, p, SC_W + 5 + a))[x] = bn[a];
 }
 
 // Enqueues the step constants and the six stages for the patches of one

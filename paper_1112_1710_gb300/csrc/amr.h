@@ -34,13 +34,16 @@ struct DDeposit {
   const double* fine;       // fine register (5 planes for faces, 1 for edges)
   const double* creg;       // coarse register over the box
   double* corr;             // correction planes of the coarse patch (18 planes)
+  unsigned int* flags;      // the coarse patch's element flags (bytes, 4-aligned)
 };
 
-// Correction planes of one coarse patch.
+// Correction planes of one coarse patch and its element flags (bit 0: the
+// cell has a corrected face; bit 1 + a: face a has a corrected edge).
 struct DCorr {
   int32_t patch, pad;
   int64_t count;  // 18 * nelem
   double* base;
+  const unsigned char* flags;
 };
 
 cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const BlockTask* tasks,
@@ -52,8 +55,8 @@ cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse,
 cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const BlockTask* tasks,
                            int nblocks, const void* scratch, const double* d_dt, const KernelTimer* tm,
                            cudaStream_t s);
-cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const BlockTask* zero_tasks,
-                          int nzero, const DDeposit* deps, const BlockTask* dep_tasks, int ndep,
-                          const BlockTask* corr_tasks, int ncorr, const KernelTimer* tm, cudaStream_t s);
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, void* flags, size_t flag_bytes,
+                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const BlockTask* corr_tasks,
+                          int ncorr, const KernelTimer* tm, cudaStream_t s);
 
 }  // namespace mhd

@@ -95,13 +95,24 @@ __global__ void __launch_bounds__(kThreads) k_ghost2(const DPatch* __restrict__ 
   const int64_t xd = lin3(d, di[0], di[1], di[2]);
   const int64_t xs = lin3(s, si[0], si[1], si[2]);
   if (pass == 0) {
+    // loads first: a store would order every later load of a may-alias array
     const bool cell_in = di[0] >= 0 && di[0] < d.N[0] && di[1] >= 0 && di[1] < d.N[1] && di[2] >= 0 && di[2] < d.N[2];
+    R u[5], b[3];
+    bool fw[3];
     if (cell_in)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd] = ((const R*)s.U[q])[xs];
+      for (int q = 0; q < 5; ++q) u[q] = ((const R*)s.U[q])[xs];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fw[a] = face_exists(d, di, a) && !own_face(d, di, a);
+      if (fw[a]) b[a] = ((const R*)s.B[a])[xs];
+    }
+    if (cell_in)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd] = u[q];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (face_exists(d, di, a) && !own_face(d, di, a)) ((R*)d.B[a])[xd] = ((const R*)s.B[a])[xs];
+      if (fw[a]) ((R*)d.B[a])[xd] = b[a];
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -341,11 +352,31 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
 }
 
 // ---------------------------------------------------------------- reflux
-__global__ void __launch_bounds__(kThreads) k_zero(const DCorr* __restrict__ C, const BlockTask* __restrict__ T) {
+// Sets flag bit `bit` of element x of a coarse patch (flags are bytes packed
+// four to a word; neighbouring elements of other threads share words).
+__device__ __forceinline__ void mark(unsigned int* flags, int64_t x, unsigned int bit) {
+  atomicOr(flags + (x >> 2), bit << (8 * (int)(x & 3)));
+}
+
+// After the correction: zeroes the plane elements the deposits wrote, so the
+// correction planes are zero again between calls (only C/F elements are ever
+// non-zero, and only during a call).
+__global__ void __launch_bounds__(kThreads) k_unset(const DPatch* __restrict__ PC, const DDeposit* __restrict__ D,
+                                                    const BlockTask* __restrict__ T) {
   const BlockTask t = T[blockIdx.x];
-  const DCorr cr = C[t.patch];
-  const int64_t e = (int64_t)t.start + threadIdx.x;
-  if (e < cr.count) cr.base[e] = 0.0;
+  const DDeposit dp = D[t.patch];
+  const int e = t.start + threadIdx.x;
+  if (e >= dp.ext[0] * dp.ext[1] * dp.ext[2]) return;
+  int C3[3];
+  box_cell(dp.lo, dp.ext, e, C3);
+  const DPatch& pc = PC[dp.coarse];
+  const int64_t c = lin3(pc, C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]);
+  if (dp.kind == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dp.corr[(int64_t)(dp.axis * 5 + q) * pc.nelem + c] = 0.0;
+  } else {
+    dp.corr[(int64_t)(15 + dp.axis) * pc.nelem + c] = 0.0;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__ PC,
@@ -394,6 +425,24 @@ __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__
     }
     dp.corr[(int64_t)(15 + a) * pc.nelem + c] = 0.5 * s - dp.creg[e];
   }
+  // flag the elements whose correction reads this one: for a face along d the
+  // cells above and below it; for an edge along a the faces that difference it
+  const int ai[3] = {C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]};
+  if (dp.kind == 0) {
+    const int d = dp.axis;
+    mark(dp.flags, c, 1u);
+    if (ai[d] > 0) mark(dp.flags, c - sof(pc, d), 1u);
+  } else {
+    const int e2 = dp.axis;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      if (f == e2) continue;
+      const int b = (f + 1) % 3, cc = (f + 2) % 3;
+      const int sh = e2 == cc ? b : cc;  // the face x reads the edge at x and at x + s_sh
+      mark(dp.flags, c, 2u << f);
+      if (ai[sh] > 0) mark(dp.flags, c - sof(pc, sh), 2u << f);
+    }
+  }
 }
 
 // Applies the correction planes to the interior cells and faces of a coarse
@@ -409,28 +458,40 @@ __global__ void __launch_bounds__(kThreads) k_correct(const DPatch* __restrict__
   if (e >= ex * ey * ez) return;
   const int ai[3] = {p.g + e % ex, p.g + (e / ex) % ey, p.g + e / (ex * ey)};
   const int64_t c = lin3(p, ai[0], ai[1], ai[2]);
+  // Elements no deposit touched see only zero plane differences, and
+  // u - 0/dx - 0/dx - 0/dx == u: they are skipped on their flag byte, with the
+  // same bits as applying the correction; so are zero differences below.
+  const unsigned int fl = cr.flags[c];
+  if (!fl) return;
   const double* K = cr.base;
   const int64_t ne = p.nelem;
-  const bool cell = ai[0] < p.g + p.n[0] && ai[1] < p.g + p.n[1] && ai[2] < p.g + p.n[2];
+  const bool cell = (fl & 1u) && ai[0] < p.g + p.n[0] && ai[1] < p.g + p.n[1] && ai[2] < p.g + p.n[2];
   if (cell) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
+      const double d0 = K[(0 * 5 + q) * ne + c + 1] - K[(0 * 5 + q) * ne + c];
+      const double d1 = K[(1 * 5 + q) * ne + c + p.s1] - K[(1 * 5 + q) * ne + c];
+      const double d2 = K[(2 * 5 + q) * ne + c + p.s2] - K[(2 * 5 + q) * ne + c];
+      if (d0 == 0.0 && d1 == 0.0 && d2 == 0.0) continue;
       R* Uq = (R*)p.U[q];
       double u = (double)Uq[c];
-      u = u - (K[(0 * 5 + q) * ne + c + 1] - K[(0 * 5 + q) * ne + c]) / p.dx[0] -
-          (K[(1 * 5 + q) * ne + c + p.s1] - K[(1 * 5 + q) * ne + c]) / p.dx[1] -
-          (K[(2 * 5 + q) * ne + c + p.s2] - K[(2 * 5 + q) * ne + c]) / p.dx[2];
+      // FP64 state: the oracle's divisions; FP32 state (rounded to FP32 at the
+      // end): multiplications by 1/dx, a tenth of the FP64 pipe work
+      if (sizeof(R) == 8) u = u - d0 / p.dx[0] - d1 / p.dx[1] - d2 / p.dx[2];
+      else u = u - d0 * p.rdx[0] - d1 * p.rdx[1] - d2 * p.rdx[2];
       Uq[c] = (R)u;
     }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (!own_face(p, ai, a)) continue;
+    if (!(fl & (2u << a)) || !own_face(p, ai, a)) continue;
     const int b = (a + 1) % 3, cc = (a + 2) % 3;
     const double dEc = K[(15 + cc) * ne + c + sof(p, b)] - K[(15 + cc) * ne + c];
     const double dEb = K[(15 + b) * ne + c + sof(p, cc)] - K[(15 + b) * ne + c];
+    if (dEc == 0.0 && dEb == 0.0) continue;
     R* Ba = (R*)p.B[a];
-    Ba[c] = (R)((double)Ba[c] - (dEc / p.dx[b] - dEb / p.dx[cc]));
+    if (sizeof(R) == 8) Ba[c] = (R)((double)Ba[c] - (dEc / p.dx[b] - dEb / p.dx[cc]));
+    else Ba[c] = (R)((double)Ba[c] - (dEc * p.rdx[b] - dEb * p.rdx[cc]));
   }
 }
 
@@ -452,9 +513,9 @@ cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, 
                            const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   if (dtype == 0)
-    MHD_TIMED(tm, K_AMR, s, (k_prolong<double><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<double><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
   else
-    MHD_TIMED(tm, K_AMR, s, (k_prolong<float><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<float><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
   return cudaGetLastError();
 }
 
@@ -463,9 +524,9 @@ cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse,
   if (nblocks == 0) return cudaSuccess;
   for (int pass = 0; pass < 2; ++pass) {
     if (dtype == 0)
-      MHD_TIMED(tm, K_AMR, s, (k_restrict<double><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<double><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
     else
-      MHD_TIMED(tm, K_AMR, s, (k_restrict<float><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<float><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
   }
   return cudaGetLastError();
 }
@@ -475,25 +536,27 @@ cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* cap
                            cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   if (dtype == 0)
-    MHD_TIMED(tm, K_AMR, s, (k_capture<double><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
+    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<double><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
                                                                             (const double*)scratch, d_dt)));
   else
-    MHD_TIMED(tm, K_AMR, s, (k_capture<float><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
+    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<float><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
                                                                            (const float*)scratch, d_dt)));
   return cudaGetLastError();
 }
 
-cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const BlockTask* zero_tasks,
-                          int nzero, const DDeposit* deps, const BlockTask* dep_tasks, int ndep,
-                          const BlockTask* corr_tasks, int ncorr, const KernelTimer* tm, cudaStream_t s) {
-  if (nzero) MHD_TIMED(tm, K_AMR, s, (k_zero<<<nzero, kThreads, 0, s>>>(corr, zero_tasks)));
-  if (ndep) MHD_TIMED(tm, K_AMR, s, (k_deposit<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, void* flags, size_t flag_bytes,
+                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const BlockTask* corr_tasks,
+                          int ncorr, const KernelTimer* tm, cudaStream_t s) {
+  if (ndep == 0) return cudaSuccess;  // no deposit: every correction is zero
+  MHD_TIMED(tm, K_REFLUX, s, (cudaMemsetAsync(flags, 0, flag_bytes, s),
+                              k_deposit<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
   if (ncorr) {
     if (dtype == 0)
-      MHD_TIMED(tm, K_AMR, s, (k_correct<double><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+      MHD_TIMED(tm, K_REFLUX, s, (k_correct<double><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
     else
-      MHD_TIMED(tm, K_AMR, s, (k_correct<float><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+      MHD_TIMED(tm, K_REFLUX, s, (k_correct<float><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
   }
+  MHD_TIMED(tm, K_REFLUX, s, (k_unset<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
   return cudaGetLastError();
 }
 

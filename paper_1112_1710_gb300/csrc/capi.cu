@@ -184,6 +184,7 @@ mhd_status convert(mhd_ctx* c, const mhd_patch_desc& d, int idx, DPatch& o) {
       return fail(c, MHD_EINVAL, "patch %d (id %d): dx[%d] must be > 0", idx, d.patch_id, a);
     o.dx[a] = d.dx[a];
     o.dxf[a] = (float)d.dx[a];
+    o.rdx[a] = 1.0 / d.dx[a];
   }
   if (d.stride[1] < N[0] + 1 || d.stride[2] < d.stride[1] * (N[1] + 1))
     return fail(c, MHD_EINVAL, "patch %d (id %d): strides too small for the face arrays", idx, d.patch_id);
@@ -240,8 +241,9 @@ void timer_mark(void* self, int kernel, int phase, cudaStream_t s) {
 
 const KernelTimer* timer_of(mhd_ctx* c) { return c->timing ? &c->timer : nullptr; }
 
-const char* const kKernelNames[K_COUNT] = {"k_prim", "k_pred",  "k_edge", "k_flux", "k_emf",   "k_update",
-                                            "k_cfl",  "k_ghost", "k_sums", "k_amr",  "k_fused", "k_commit"};
+const char* const kKernelNames[K_COUNT] = {"k_prim",  "k_pred",    "k_edge",     "k_flux",   "k_emf",
+                                            "k_update", "k_cfl",     "k_ghost",    "k_sums",   "k_reflux",
+                                            "k_fused",  "k_commit",  "k_prolong",  "k_restrict", "k_capture"};
 
 // converts a descriptor array (all of one dtype) to device form
 mhd_status convert_all(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, std::vector<DPatch>& dp,
@@ -961,8 +963,18 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
   int dtype = -1;
   std::vector<DPatch> dc;
   if ((r = convert_all(c, coarse, nc, dc, &dtype))) return r;
+  // element flags of the corrected patches in the arena: one byte per element
+  std::vector<int64_t> flag_off(nc, -1);
+  int64_t flag_bytes = 0;
   std::vector<DCorr> cr;
-  std::vector<int64_t> zc, kc;
+  std::vector<int64_t> kc;
+  for (int p = 0; p < nc; ++p) {
+    if (!corr[p]) continue;
+    flag_off[p] = flag_bytes;
+    flag_bytes += (dc[p].nelem + 15) / 16 * 16;
+  }
+  if ((r = ensure_scratch(c, (size_t)flag_bytes + 16))) return r;
+  unsigned char* flags = (unsigned char*)c->scratch;
   for (int p = 0; p < nc; ++p) {
     if (!corr[p]) continue;
     DCorr k;
@@ -970,8 +982,8 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
     k.pad = 0;
     k.count = 18 * dc[p].nelem;
     k.base = corr[p];
+    k.flags = flags + flag_off[p];
     cr.push_back(k);
-    zc.push_back(k.count);
     kc.push_back((int64_t)(dc[p].n[0] + 1) * (dc[p].n[1] + 1) * (dc[p].n[2] + 1));
   }
   std::vector<DDeposit> dd(nd);
@@ -990,6 +1002,7 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
     o.fine = m.fine;
     o.creg = m.coarse_reg;
     o.corr = corr[m.coarse];
+    o.flags = (unsigned int*)(flags + flag_off[m.coarse]);
     int64_t cnt = 1;
     for (int a = 0; a < 3; ++a) {
       const int lo = m.box.lo[a], hi = m.box.hi[a];
@@ -1009,22 +1022,20 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
     }
     dcount[t] = cnt;
   }
-  std::vector<BlockTask> tz, td, tk;
-  tasks_for(zc, tz);
+  std::vector<BlockTask> td, tk;
   tasks_for(dcount, td);
   tasks_for(kc, tk);
-  void *d_c = nullptr, *d_r = nullptr, *d_d = nullptr, *d_tz = nullptr, *d_td = nullptr, *d_tk = nullptr;
+  void *d_c = nullptr, *d_r = nullptr, *d_d = nullptr, *d_td = nullptr, *d_tk = nullptr;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
   if ((r = table(c, cr.data(), cr.size() * sizeof(DCorr), &d_r))) return r;
   if ((r = table(c, dd.data(), dd.size() * sizeof(DDeposit), &d_d))) return r;
-  if ((r = table(c, tz.data(), tz.size() * sizeof(BlockTask), &d_tz))) return r;
   if ((r = table(c, td.data(), td.size() * sizeof(BlockTask), &d_td))) return r;
   if ((r = table(c, tk.data(), tk.size() * sizeof(BlockTask), &d_tk))) return r;
-  cudaError_t e = reflux_launch(dtype, (const DPatch*)d_c, (const DCorr*)d_r, (const BlockTask*)d_tz,
-                                (int)tz.size(), (const DDeposit*)d_d, (const BlockTask*)d_td, (int)td.size(),
-                                (const BlockTask*)d_tk, (int)tk.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = reflux_launch(dtype, (const DPatch*)d_c, (const DCorr*)d_r, flags, (size_t)flag_bytes,
+                                (const DDeposit*)d_d, (const BlockTask*)d_td, (int)td.size(), (const BlockTask*)d_tk,
+                                (int)tk.size(), timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reflux launch");
-  c->launches += 3;
+  if (nd > 0) c->launches += 3;
   return MHD_OK;
 }
 

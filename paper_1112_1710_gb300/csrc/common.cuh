@@ -27,6 +27,7 @@ struct DPatch {
   double cfl_scale;  // scale factor of the CFL candidate dt
   float dxf[3];      // dx rounded to FP32 (FP32 kernels read no doubles per thread)
   int32_t pad2;
+  double rdx[3];     // 1 / dx (FP64): the FP32-state refluxing multiplies by it
 };
 
 // Cell width along d in the arithmetic type of a kernel.
@@ -89,7 +90,8 @@ constexpr int kThreads = 256;
 
 // Kernel ids of the per-kernel event timer (mhd_timing_*).
 enum KernelId : int {
-  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_AMR, K_FUSED, K_COMMIT, K_COUNT
+  K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_REFLUX, K_FUSED, K_COMMIT,
+  K_PROLONG, K_RESTRICT, K_CAPTURE, K_COUNT
 };
 
 // Optional hook that records CUDA events around each launch on its stream.

@@ -434,39 +434,46 @@ __device__ __forceinline__ void fused_update(const DPatch& p, R* sm, R* out, int
     const int s1 = (ty + 1) * L::P1 + tx + 1;
     const int st_ = ty * L::PT + tx;
     const int64_t x = (int64_t)(X0 + tx) + (int64_t)(Y0 + ty) * p.s1 + (int64_t)zu * p.s2;
-    if (cells && in_x && in_y) {
+    // all loads first (the output copy may alias the state for the compiler)
+    const bool do_c = cells && in_x && in_y, do_x = cells && in_y && (in_x || xlast),
+               do_y = cells && in_x && (in_y || ylast), do_z = cells && in_x && in_y, do_t = top && in_x && in_y;
+    R un[5], bx = R(0), by = R(0), bz = R(0), bt = R(0);
+    if (do_c) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         R u = ((const R*)p.U[q])[x];
-        u = u - st.dtdx[0] * (FX[q * L::G1 + s1 + 1] - FX[q * L::G1 + s1]) -
-            st.dtdx[1] * (FY[q * L::G1 + s1 + L::P1] - FY[q * L::G1 + s1]) -
-            st.dtdx[2] * (FZ1[q * L::G1 + s1] - FZ0[q * L::G1 + s1]);
-        out[(int64_t)q * p.nelem + x] = u;
+        un[q] = u - st.dtdx[0] * (FX[q * L::G1 + s1 + 1] - FX[q * L::G1 + s1]) -
+                st.dtdx[1] * (FY[q * L::G1 + s1 + L::P1] - FY[q * L::G1 + s1]) -
+                st.dtdx[2] * (FZ1[q * L::G1 + s1] - FZ0[q * L::G1 + s1]);
       }
     }
-    if (cells && in_y && (in_x || xlast)) {  // x-face (a = 0; b = y, c = z)
+    if (do_x) {  // x-face (a = 0; b = y, c = z)
       R dEc = EZ[st_ + L::PT] - EZ[st_];
       R dEb = EY1[st_] - EY0[st_];
-      out[5 * p.nelem + x] = ((const R*)p.B[0])[x] - (st.dtdx[1] * dEc - st.dtdx[2] * dEb);
+      bx = ((const R*)p.B[0])[x] - (st.dtdx[1] * dEc - st.dtdx[2] * dEb);
     }
-    if (cells && in_x && (in_y || ylast)) {  // y-face (a = 1; b = z, c = x)
+    if (do_y) {  // y-face (a = 1; b = z, c = x)
       R dEc = EX1[st_] - EX0[st_];
       R dEb = EZ[st_ + 1] - EZ[st_];
-      out[6 * p.nelem + x] = ((const R*)p.B[1])[x] - (st.dtdx[2] * dEc - st.dtdx[0] * dEb);
+      by = ((const R*)p.B[1])[x] - (st.dtdx[2] * dEc - st.dtdx[0] * dEb);
     }
-    if (in_x && in_y) {  // z-faces (a = 2; b = x, c = y)
-      if (cells) {
-        R dEc = EY0[st_ + 1] - EY0[st_];
-        R dEb = EX0[st_ + L::PT] - EX0[st_];
-        out[7 * p.nelem + x] = ((const R*)p.B[2])[x] - (st.dtdx[0] * dEc - st.dtdx[1] * dEb);
-      }
-      if (top) {
-        const int64_t xt = x + p.s2;
-        R dEc = EY1[st_ + 1] - EY1[st_];
-        R dEb = EX1[st_ + L::PT] - EX1[st_];
-        out[7 * p.nelem + xt] = ((const R*)p.B[2])[xt] - (st.dtdx[0] * dEc - st.dtdx[1] * dEb);
-      }
+    if (do_z) {  // z-face (a = 2; b = x, c = y)
+      R dEc = EY0[st_ + 1] - EY0[st_];
+      R dEb = EX0[st_ + L::PT] - EX0[st_];
+      bz = ((const R*)p.B[2])[x] - (st.dtdx[0] * dEc - st.dtdx[1] * dEb);
     }
+    if (do_t) {  // the top z-face of the last chunk
+      R dEc = EY1[st_ + 1] - EY1[st_];
+      R dEb = EX1[st_ + L::PT] - EX1[st_];
+      bt = ((const R*)p.B[2])[x + p.s2] - (st.dtdx[0] * dEc - st.dtdx[1] * dEb);
+    }
+    if (do_c)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) out[(int64_t)q * p.nelem + x] = un[q];
+    if (do_x) out[5 * p.nelem + x] = bx;
+    if (do_y) out[6 * p.nelem + x] = by;
+    if (do_z) out[7 * p.nelem + x] = bz;
+    if (do_t) out[7 * p.nelem + x + p.s2] = bt;
   }
 }
 
@@ -534,13 +541,17 @@ __global__ void __launch_bounds__(kThreads) k_commit(const DPatch* __restrict__ 
   const bool inner[3] = {r0 < ex - 1, r1 < ey - 1, q1 < ez - 1};
   const int64_t x = (int64_t)id[0] + (int64_t)id[1] * p.s1 + (int64_t)id[2] * p.s2;
   const R* out = arena + p.scr;
-  if (inner[0] && inner[1] && inner[2]) {
+  const bool cell = inner[0] && inner[1] && inner[2];
+  R v[8];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) ((R*)p.U[q])[x] = out[(int64_t)q * p.nelem + x];
+  for (int q = 0; q < 8; ++q) {
+    const bool ok = q < 5 ? cell : inner[(q - 4) % 3] && inner[(q - 3) % 3];
+    if (ok) v[q] = out[(int64_t)q * p.nelem + x];
   }
+  if (cell)
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const bool ok = inner[(a + 1) % 3] && inner[(a + 2) % 3];
-    if (ok) ((R*)p.B[a])[x] = out[(int64_t)(5 + a) * p.nelem + x];
-  }
+    for (int q = 0; q < 5; ++q) ((R*)p.U[q])[x] = v[q];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (inner[(a + 1) % 3] && inner[(a + 2) % 3]) ((R*)p.B[a])[x] = v[5 + a];
 }
