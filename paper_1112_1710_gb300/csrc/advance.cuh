@@ -8,9 +8,9 @@
 //   k_prim    UB+2 cells : primitives W, cell EMF E^n = -v x Bc
 //   k_pred    UB+1 cells : limited slopes, face values, positivity rule,
 //                          Hancock predictor, predicted face states, E_ref
-//   k_edge    edges      : E^n at cell edges (mean of the four cells)
+//   k_edge    UB+2 cells : E^n at the cell's three edges (mean of the four cells)
 //   k_flux    faces      : CT half-step normal field, HLLD flux, contact side
-//   k_emf     UB edges   : Gardiner-Stone (or arithmetic) edge EMF
+//   k_emf     UB+2 cells : Gardiner-Stone (or arithmetic) EMF of the cell's three edges
 //   k_update  UB         : conservative cell update and CT face update
 // Intermediates live in a per-patch scratch region with the patch's own
 // strides, so every stage addresses them like the state arrays.
@@ -251,11 +251,10 @@ __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  switch (blockIdx.y) {
-    case 0: edge_avg<R, 0>(p, c, scr); break;
-    case 1: edge_avg<R, 1>(p, c, scr); break;
-    default: edge_avg<R, 2>(p, c, scr); break;
-  }
+  // the three edges stored at this cell, one index decomposition
+  edge_avg<R, 0>(p, c, scr);
+  edge_avg<R, 1>(p, c, scr);
+  edge_avg<R, 2>(p, c, scr);
 }
 
 template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
@@ -330,11 +329,9 @@ __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  switch (blockIdx.y) {
-    case 0: edge_emf<R, 0>(p, c, scr, sc); break;
-    case 1: edge_emf<R, 1>(p, c, scr, sc); break;
-    default: edge_emf<R, 2>(p, c, scr, sc); break;
-  }
+  edge_emf<R, 0>(p, c, scr, sc);
+  edge_emf<R, 1>(p, c, scr, sc);
+  edge_emf<R, 2>(p, c, scr, sc);
 }
 
 template <typename R, int a>
@@ -446,9 +443,9 @@ cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask*
             (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
              k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
   MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
+  MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
   MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
+  MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
   MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, K, commit ? 1 : 0)));
   return cudaGetLastError();
 }

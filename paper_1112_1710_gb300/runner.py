@@ -1,6 +1,7 @@
 """Single-patch periodic driver: one step = ghost fill (periodic images) ->
 CFL dt (device scalar) -> patch advance of the interior.  Three library
-calls, nine kernels, no host synchronisation; the dt never leaves the device.
+calls, eleven kernels, no host synchronisation; the dt never leaves the
+device, so the step can be captured once as a CUDA graph and replayed.
 """
 from __future__ import annotations
 
@@ -34,6 +35,23 @@ class PeriodicRunner:
             with torch.cuda.stream(self.stream):
                 self.d_dt.fill_(float(dt))
         capi.mhd_patch_advance(self.ctx, self.descs, self.d_dt.data_ptr(), self.sp)
+
+    def capture_graph(self):
+        """Captures one step (fill, CFL dt, advance) as a CUDA graph; one eager
+        step first puts every descriptor table on the device and sizes the
+        scratch arena, so the capture uploads and allocates nothing."""
+        self.step()
+        torch.cuda.synchronize(self.patch.state.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.step()
+        self.graph = g
+        return g
+
+    def replay(self) -> None:
+        # CUDAGraph.replay launches on the current stream
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
 
     def run(self, steps: int, dt: float | None = None, record_dt: bool = False):
         dts = []
