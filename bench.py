@@ -627,8 +627,9 @@ def run_serve(args):
     clk = ClockSampler(local)
     launches0 = 0
 
-    def serve(reqs):
-        sch = Scheduler(be, n_slots=args.slots, budget_bytes=budget, max_batch_cells=args.batch_cells, g=G)
+    def serve(reqs, policy="greedy"):
+        sch = Scheduler(be, n_slots=args.slots, budget_bytes=budget, max_batch_cells=args.batch_cells, g=G,
+                        policy=policy)
         out = sch.run(reqs, t_limit=900.0)
         torch.cuda.synchronize()
         st = latency_stats(out)
@@ -645,6 +646,8 @@ def run_serve(args):
         loads = {}
         for f in (0.5, 0.8, 0.95):
             loads[str(f)] = serve(poisson_requests(args.requests, f * sat["requests_per_s"], seed=4242))
+        # the same 0.8 load with batches sized by the distribution equation of Sec. 5
+        balanced = serve(poisson_requests(args.requests, 0.8 * sat["requests_per_s"], seed=4242), "balanced")
         clocks = clk.stop()
         launches = sum(capi.mhd_launch_count(c) for c in be.ctxs) - launches0
         status = max(capi.mhd_get_device_status(c) for c in be.ctxs)
@@ -665,7 +668,7 @@ def run_serve(args):
                        "slots": args.slots, "batch_cells": args.batch_cells, "setup_s": setup_s,
                        "l2": "batches of up to %d cells: working set above L2" % args.batch_cells,
                        "parallelism": "replicas"},
-            "saturation": sat, "offered_load": loads,
+            "saturation": sat, "offered_load": loads, "offered_load_0.8_balanced_batches": balanced,
             "fp64_sample": {"served_batched": served64, "plain_per_patch": pp},
             "gpu_launches": launches, "device_status": status, "clocks": clocks}
     print(json.dumps(line))

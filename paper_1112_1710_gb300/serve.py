@@ -82,7 +82,16 @@ class Scheduler:
     """Finer-first, HBM-budgeted continuous batching over `n_slots` slots."""
 
     def __init__(self, backend, n_slots=2, budget_bytes=64 << 30, max_batch_cells=8 << 20, g=4,
-                 lookahead=64):
+                 lookahead=64, policy="greedy", min_batch_cells=1 << 16):
+        """policy "greedy": a free slot takes up to max_batch_cells of waiting
+        work; "balanced": its share from the distribution equation of Sec. 5
+        with the slots as workers (balance.desired_distribution), so that the
+        slots' predicted remaining work (in-flight cells plus the new batch)
+        evens out, clamped to [min_batch_cells, max_batch_cells]."""
+        if policy not in ("greedy", "balanced"):
+            raise ValueError("policy must be greedy or balanced")
+        self.policy = policy
+        self.min_batch_cells = min_batch_cells
         self.backend = backend
         self.n_slots = n_slots
         self.budget = budget_bytes
@@ -93,10 +102,22 @@ class Scheduler:
         self.peak_resident = 0
         self.batches = []            # (slot, [rid, ...]) in launch order
 
-    def _form_batch(self, waiting):
+    def _cell_budget(self, slot, slots, waiting):
+        """Cells the next batch of `slot` may take."""
+        if self.policy == "greedy":
+            return self.max_batch_cells
+        from .balance import desired_distribution
+        inflight = [sum(r.cells for r in f[1]) if f is not None else 0 for f in slots]
+        pending = sum(item[3].cells for item in waiting)
+        gbar = pending / self.n_slots
+        d = desired_distribution(gbar, [inflight], [[0] * self.n_slots], [1, 1], 1)
+        return int(min(self.max_batch_cells, max(self.min_batch_cells, d[slot])))
+
+    def _form_batch(self, waiting, budget=None):
         """Pops the next batch off the waiting heap: the head request fixes the
         precision; the rest join in priority order while the batch stays
         under the cell budget and the resident state under the HBM budget."""
+        budget = self.max_batch_cells if budget is None else budget
         dtype = waiting[0][3].dtype
         batch, cells, nbytes, skipped = [], 0, 0, []
         while waiting and len(skipped) <= self.lookahead:
@@ -104,7 +125,7 @@ class Scheduler:
             r = item[3]
             b = state_bytes(r.n, self.g, r.dtype)
             ok = r.dtype == dtype and self.resident + nbytes + b <= self.budget and (
-                not batch or cells + r.cells <= self.max_batch_cells)
+                not batch or cells + r.cells <= budget)
             if ok:
                 batch.append(r)
                 cells += r.cells
@@ -146,7 +167,7 @@ class Scheduler:
             for s in range(self.n_slots):
                 if slots[s] is not None or not waiting:
                     continue
-                batch, nbytes = self._form_batch(waiting)
+                batch, nbytes = self._form_batch(waiting, self._cell_budget(s, slots, waiting))
                 if not batch:
                     break                        # nothing fits until memory frees up
                 tstart = clock() - t0

@@ -141,3 +141,19 @@ def test_batch_copy_list_layout():
     got = [(arr[j].src, arr[j].dst, tuple(arr[j].box.lo), tuple(arr[j].box.hi), tuple(arr[j].offset))
            for j in range(total)]
     assert got == expect
+
+
+def test_balanced_policy_sizes_batches_by_the_distribution_equation():
+    """With one slot busy on a large batch, the balanced policy gives the free
+    slot a larger share of the waiting work (equal predicted remaining work),
+    never beyond the batch cap, and every request is still served once."""
+    from paper_1112_1710_gb300.balance import desired_distribution
+    reqs = [Request(i, 0.0, 32, 0, "f32") for i in range(64)]
+    out, sch, be = run(reqs, n_slots=2, max_batch_cells=1 << 20, policy="balanced", min_batch_cells=1 << 14)
+    assert sorted(r for _, rids in sch.batches for r in rids) == list(range(64))
+    assert all(sum(out[i].cells for i in rids) <= 1 << 20 for _, rids in sch.batches)
+    # the share of a free slot next to a busy one: gbar + (inflight busy) / 2
+    d = desired_distribution(1000.0, [[0, 600]], [[0, 0]], [1, 1], 1)
+    assert np.allclose(d, [1300, 700])
+    with pytest.raises(ValueError):
+        Scheduler(SimBackend(Clock()), policy="other")
