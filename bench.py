@@ -239,7 +239,8 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         if dtype == "f32" and not args.no_autotune:
             v, cz, tms = capi.mhd_autotune_advance(ctx, run.descs, run.d_dt.data_ptr(), reps=3,
                                                    stream=stream.cuda_stream)
-            tuned = {"choice": "staged" if v < 0 else "fused variant %d" % v, "chunk": cz, "ms_per_advance": tms}
+            tuned = {"choice": {-2: "staged, untiled predictor", -1: "staged, tiled predictor"}.get(
+                v, "fused variant %d" % v), "chunk": cz, "ms_per_advance": tms}
         status = capi.mhd_get_device_status(ctx)
         # headline: the step (fill, CFL dt, advance) replayed as one CUDA graph
         l0 = capi.mhd_launch_count(ctx)

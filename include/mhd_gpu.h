@@ -96,14 +96,16 @@ typedef struct {
                         the oracle's order), 1 the build with multiply-adds
                         fused (about 1.25x faster; differs from 0 by rounding) */
   int32_t advance_kernel; /* 0: the context's choice (the staged kernels until
-                        mhd_autotune_advance measured the fused kernel faster);
+                        mhd_autotune_advance measured something else faster);
                         1: the staged kernels (one launch per stage,
-                        intermediates in the scratch arena); 2: the fused
-                        kernel (one persistent launch over x-y tiles marching
-                        along z, intermediates in shared memory).  Both compute
-                        every element with the same expressions; a call whose
-                        captures need face fluxes outside the update box runs
-                        staged.                                              */
+                        intermediates in the scratch arena; the predictor
+                        tiled in shared memory if the autotuner chose it);
+                        2: the fused kernel (one persistent launch over x-y
+                        tiles marching along z, intermediates in shared
+                        memory); 3: the staged kernels with the predictor
+                        tiled in shared memory.  All compute every element with the same
+                        expressions; a call whose captures need face fluxes
+                        outside the update box runs staged.                  */
   int32_t fused_chunk; /* z-planes per work item of the fused kernel; 0 lets
                         each call choose from the device's SM count          */
   int32_t reserved;  /* must be 0                                           */
@@ -209,15 +211,17 @@ mhd_status mhd_patch_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_
 
 /* Autotuner of the advance (no counterpart in the paper; it picks how the
  * patches of a call are advanced).  Times, on these patches (update box grown
- * by grow[p], may be NULL for zeros; dt from *d_dt), the staged kernels and
- * every compiled x-y tile shape of the fused kernel of the patches' element
- * type, the latter each with a few z-chunk lengths: reps launches after one
+ * by grow[p], may be NULL for zeros; dt from *d_dt), the staged kernels with
+ * the untiled and with the shared-memory-tiled predictor, and every compiled
+ * x-y tile shape of the fused kernel of the patches' element type, the latter
+ * each with a few z-chunk lengths: reps launches after one
  * warm-up, with the new state written to the context's scratch only, so the
  * patch state is unchanged.  The fastest becomes this context's advance for
  * that element type (mhd_params.advance_kernel = 0; mhd_params.fused_chunk > 0
  * still fixes the chunk).  Synchronises `stream`.  Outputs (may be NULL): the
- * choice (-1 staged, else the fused variant index), the chunk length (0 for
- * staged) and the time per advance in milliseconds. */
+ * choice (-2 staged with the untiled predictor, the default before tuning;
+ * -1 staged with the tiled one; else the fused variant index), the chunk length
+ * (0 for staged) and the time per advance in milliseconds. */
 mhd_status mhd_autotune_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
                                 const int32_t *grow, const double *d_dt, int32_t reps,
                                 int32_t *choice_out, int32_t *chunk_out, float *ms_out,

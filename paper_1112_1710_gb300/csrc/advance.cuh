@@ -150,31 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
 }
 
 // ---------------------------------------------------------------- k_pred
+// The predictor of one cell from its primitives w and limited slopes dw:
+// first positivity rule, Hancock increment, the six predicted face states
+// (second positivity rule) and the reference cell EMF, stored at element x.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
-                                                   const BlockTask* __restrict__ T, R* scr,
-                                                   SolverConsts<R> sc, const R* __restrict__ K) {
-  const BlockTask t = T[blockIdx.x];
-  const DPatch& p = P[t.patch];
-  Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  if (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1)) return;
-  const StepDt<R> st(K, t.patch);
-  const int64_t x = lin(p, c);
-  R w[8], dw[3][8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) w[q] = arr(scr, p, SC_W + q)[x];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int64_t sd = stride_of(p, d);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const R* Wq = arr(scr, p, SC_W + q);
-      R a = w[q] - Wq[x - sd];
-      R b = Wq[x + sd] - w[q];
-      dw[d][q] = limiter(sc.limiter, a, b);
-    }
-  }
+__device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr, const SolverConsts<R>& sc,
+                                             const StepDt<R>& st, const R (&w)[8], const R (&dw)[3][8]) {
   // first positivity rule on the face values of rho and p
   bool bad = false;
 #pragma unroll
@@ -219,19 +200,22 @@ __global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
       for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + (d * 2 + sd) * 8 + q)[x] = pw[q];
     }
   }
+  R duk[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) duk[q] = du[q];
   if (bad2) {
 #pragma unroll
     for (int f = 0; f < 6; ++f)
 #pragma unroll
       for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + f * 8 + q)[x] = w[q];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) du[q] = R(0);
+    for (int q = 0; q < 8; ++q) duk[q] = R(0);
   }
   // reference cell EMF from U^{n+1/2}
   R uc[8], uh[8];
   prim2cons(w, sc.igm1, uc);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) uh[q] = uc[q] + du[q];
+  for (int q = 0; q < 8; ++q) uh[q] = uc[q] + duk[q];
   R ir = R(1) / uh[0];
   R v[3] = {uh[1] * ir, uh[2] * ir, uh[3] * ir};
 #pragma unroll
@@ -239,6 +223,99 @@ __global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
     const int b = (a + 1) % 3, cc = (a + 2) % 3;
     arr(scr, p, SC_ER + a)[x] = v[cc] * uh[5 + b] - v[b] * uh[5 + cc];
   }
+}
+
+// One thread per cell of UB+1; the stencil of W is read from the scratch
+// planes through the caches.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr,
+                                                   SolverConsts<R> sc, const R* __restrict__ K) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1)) return;
+  const StepDt<R> st(K, t.patch);
+  const int64_t x = lin(p, c);
+  R w[8], dw[3][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) w[q] = arr(scr, p, SC_W + q)[x];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int64_t sd = stride_of(p, d);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const R* Wq = arr(scr, p, SC_W + q);
+      R a = w[q] - Wq[x - sd];
+      R b = Wq[x + sd] - w[q];
+      dw[d][q] = limiter(sc.limiter, a, b);
+    }
+  }
+  predict_cell(p, x, scr, sc, st, w, dw);
+}
+
+// Tiled predictor: a block owns a TX x TY x TZ tile of UB+1 cells (its task's
+// `start` is the tile index within the patch), stages W on the tile grown by
+// one cell in shared memory with coalesced row loads, then runs the same
+// per-cell predictor from shared memory.
+template <typename R> struct PredTile;
+template <> struct PredTile<float> {
+  static constexpr int TX = kPredTile32[0], TY = kPredTile32[1], TZ = kPredTile32[2];
+};
+template <> struct PredTile<double> {
+  static constexpr int TX = kPredTile64[0], TY = kPredTile64[1], TZ = kPredTile64[2];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_pred_tiled(const DPatch* __restrict__ P,
+                                                         const BlockTask* __restrict__ T, R* scr,
+                                                         SolverConsts<R> sc, const R* __restrict__ K) {
+  constexpr int TX = PredTile<R>::TX, TY = PredTile<R>::TY, TZ = PredTile<R>::TZ;
+  constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
+  static_assert(TX * TY * TZ == kThreads, "one thread per tile cell");
+  __shared__ R sw[8][HN];
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  // the UB+1 region and this block's tile in it
+  const int lo = p.g - p.k - 1;
+  const int ex = p.n[0] + 2 * p.k + 2, ey = p.n[1] + 2 * p.k + 2, ez = p.n[2] + 2 * p.k + 2;
+  const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
+  int rx, ry;
+  const int q1 = divmod24(t.start, ntx, rx);
+  const int tz = divmod24(q1, nty, ry);
+  const int x0 = lo + rx * TX, y0 = lo + ry * TY, z0 = lo + tz * TZ;
+  // stage W on the tile grown by one (always inside UB+2, where W is valid)
+  const int hx_hi = min(HX, ex - rx * TX + 1), hy_hi = min(HY, ey - ry * TY + 1), hz_hi = min(HZ, ez - tz * TZ + 1);
+  for (int e = threadIdx.x; e < HN; e += kThreads) {
+    int hx, hy;
+    const int q2 = divmod24(e, HX, hx);
+    const int hz = divmod24(q2, HY, hy);
+    if (hx > hx_hi || hy > hy_hi || hz > hz_hi) continue;
+    const int64_t x = (int64_t)(x0 - 1 + hx) + (int64_t)(y0 - 1 + hy) * p.s1 + (int64_t)(z0 - 1 + hz) * p.s2;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sw[q][e] = arr(scr, p, SC_W + q)[x];
+  }
+  __syncthreads();
+  const int ix = threadIdx.x % TX, iy = (threadIdx.x / TX) % TY, iz = threadIdx.x / (TX * TY);
+  if (rx * TX + ix >= ex || ry * TY + iy >= ey || tz * TZ + iz >= ez) return;
+  const StepDt<R> st(K, t.patch);
+  const int s = (ix + 1) + HX * ((iy + 1) + HY * (iz + 1));
+  const int sd[3] = {1, HX, HX * HY};
+  R w[8], dw[3][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) w[q] = sw[q][s];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      R a = w[q] - sw[q][s - sd[d]];
+      R b = sw[q][s + sd[d]] - w[q];
+      dw[d][q] = limiter(sc.limiter, a, b);
+    }
+  }
+  const int64_t x = (int64_t)(x0 + ix) + (int64_t)(y0 + iy) * p.s1 + (int64_t)(z0 + iz) * p.s2;
+  predict_cell(p, x, scr, sc, st, w, dw);
 }
 
 // ---------------------------------------------------------------- k_edge
@@ -434,15 +511,18 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
 // Enqueues the step constants and the six stages for the patches of one
 // call; K (npatch x kStepConsts elements) is scratch.
 template <typename R>
-cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks, R* scr,
-                           R* K, const SolverConsts<R>& sc, const double* d_dt, int* d_status,
-                           const KernelTimer* tm, bool commit, cudaStream_t s) {
+cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks,
+                           const BlockTask* d_ptasks, int npblocks, R* scr, R* K, const SolverConsts<R>& sc,
+                           const double* d_dt, int* d_status, const KernelTimer* tm, bool commit, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   dim3 g1(nblocks), g3(nblocks, 3);
   MHD_TIMED(tm, K_PRIM, s,
             (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
              k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
-  MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
+  if (npblocks > 0)
+    MHD_TIMED(tm, K_PRED, s, (k_pred_tiled<R><<<npblocks, kThreads, 0, s>>>(d_patches, d_ptasks, scr, sc, K)));
+  else
+    MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
   MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
@@ -513,8 +593,8 @@ template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t
   sc.limiter = a.limiter;
   sc.emf = a.emf;
   if (a.fused) return launch_fused_variant<R>(a, sc, s);
-  return launch_advance<R>(a.patches, a.npatches, a.tasks, a.nblocks, (R*)a.scratch, (R*)a.stepc, sc, a.d_dt,
-                           a.d_status, a.timer, a.commit, s);
+  return launch_advance<R>(a.patches, a.npatches, a.tasks, a.nblocks, a.ptasks, a.npblocks, (R*)a.scratch,
+                           (R*)a.stepc, sc, a.d_dt, a.d_status, a.timer, a.commit, s);
 }
 
 }  // namespace MHD_ADVANCE_NS

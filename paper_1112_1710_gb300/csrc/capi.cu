@@ -57,6 +57,7 @@ struct mhd_ctx {
   // autotuner: staged or fused, the fused variant and its z-chunk length (0:
   // chosen per call); staged until the autotuner measured otherwise
   bool use_fused[2] = {false, false};
+  bool pred_tiled[2] = {false, false};  // staged path: the shared-memory-tiled predictor
   int fused_variant[2] = {0, 0};
   int fused_chunk[2] = {0, 0};
   // per-kernel event timer
@@ -273,7 +274,7 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
       params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1 ||
       params->fp64_contract < 0 || params->fp64_contract > 1 || params->advance_kernel < 0 ||
-      params->advance_kernel > 2 || params->fused_chunk < 0 || params->reserved != 0)
+      params->advance_kernel > 3 || params->fused_chunk < 0 || params->reserved != 0)
     return MHD_EINVAL;
   mhd_ctx* c = new mhd_ctx();
   c->prm = *params;
@@ -434,6 +435,18 @@ void fused_items(const std::vector<DPatch>& dp, int bx, int by, int cz, std::vec
   tasks_for(ccnt, ctasks);
 }
 
+// One block per tile of each patch's UB+1 for the tiled predictor.
+void pred_tiles(const std::vector<DPatch>& dp, int dtype, std::vector<BlockTask>& out) {
+  const int* T = dtype == MHD_F32 ? kPredTile32 : kPredTile64;
+  out.clear();
+  for (size_t p = 0; p < dp.size(); ++p) {
+    const DPatch& q = dp[p];
+    const int ex = q.n[0] + 2 * q.k + 2, ey = q.n[1] + 2 * q.k + 2, ez = q.n[2] + 2 * q.k + 2;
+    const int64_t nt = (int64_t)((ex + T[0] - 1) / T[0]) * ((ey + T[1] - 1) / T[1]) * ((ez + T[2] - 1) / T[2]);
+    for (int64_t t = 0; t < nt; ++t) out.push_back(BlockTask{(int32_t)p, (int32_t)t});
+  }
+}
+
 int sm_count(int dev) {
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
@@ -531,7 +544,7 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   const size_t es = elem_size(dtype);
   const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
   if ((r = ensure_scratch(c, counter_byte + 16))) return r;
-  std::vector<BlockTask> tasks;
+  std::vector<BlockTask> tasks, ptasks;
   std::vector<FusedItem> items;
   std::vector<BlockTask> ctasks;
   if (!fused) {
@@ -540,7 +553,8 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
       counts[p] = (int64_t)(dp[p].n[0] + 2 * dp[p].k + 4) * (dp[p].n[1] + 2 * dp[p].k + 4) *
                   (dp[p].n[2] + 2 * dp[p].k + 4);
     tasks_for(counts, tasks);
-    if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+    if (c->prm.advance_kernel == 3 || c->pred_tiled[dtype == MHD_F32 ? 1 : 0]) pred_tiles(dp, dtype, ptasks);
+    if (tasks.size() > 0x7fffffff || ptasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
   } else {
     const int di = dtype == MHD_F32 ? 1 : 0;
     const FusedVariant& v = fused_variant_of(dtype, c->fused_variant[di]);
@@ -550,16 +564,19 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     fused_items(dp, v.bx, v.by, cz, items, ctasks);
     if (items.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
   }
-  void *d_p = nullptr, *d_t = nullptr, *d_i = nullptr, *d_ct = nullptr;
+  void *d_p = nullptr, *d_t = nullptr, *d_i = nullptr, *d_ct = nullptr, *d_pt = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, ptasks.data(), ptasks.size() * sizeof(BlockTask), &d_pt))) return r;
   if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i))) return r;
   if ((r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) return r;
-  AdvanceArgs a;
+  AdvanceArgs a{};
   a.patches = (const DPatch*)d_p;
   a.npatches = n;
   a.tasks = (const BlockTask*)d_t;
   a.nblocks = (int)tasks.size();
+  a.ptasks = (const BlockTask*)d_pt;
+  a.npblocks = (int)ptasks.size();
   a.scratch = c->scratch;
   a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
   a.gamma = c->prm.gamma;
@@ -620,12 +637,14 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   const size_t es = elem_size(dtype);
   const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
   if ((r = ensure_scratch(c, counter_byte + 16))) return r;
-  std::vector<BlockTask> tasks;
+  std::vector<BlockTask> tasks, ptasks;
   tasks_for(counts, tasks);
-  if (tasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
-  void *d_p = nullptr, *d_t = nullptr;
+  pred_tiles(dp, dtype, ptasks);
+  if (tasks.size() > 0x7fffffff || ptasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  void *d_p = nullptr, *d_t = nullptr, *d_pt = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, ptasks.data(), ptasks.size() * sizeof(BlockTask), &d_pt))) return r;
   const int di = dtype == MHD_F32 ? 1 : 0;
   const int nv = dtype == MHD_F32 ? kNumFused32 : kNumFused64;
   const int nsm = sm_count(c->device);
@@ -638,11 +657,12 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
     return cuda_fail(c, e, "autotune events");
   }
   float best = 3.4e38f;
-  int bv = -2, bcz = 0;
+  int bv = -3, bcz = 0;
   std::vector<FusedItem> items;
   std::vector<BlockTask> ctasks;
-  // candidate -1: the staged kernels; then every fused variant x chunk length
-  for (int v = -1; v < nv; ++v) {
+  // candidates -2 / -1: the staged kernels with the untiled / tiled
+  // predictor; then every fused variant x chunk length
+  for (int v = -2; v < nv; ++v) {
     std::vector<int> chunks;
     if (v < 0) {
       chunks.push_back(0);
@@ -670,6 +690,10 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
       a.timer = nullptr;
       a.commit = false;  // both paths leave the patch state as it is
       a.fused = v >= 0;
+      if (v == -1) {
+        a.ptasks = (const BlockTask*)d_pt;
+        a.npblocks = (int)ptasks.size();
+      }
       if (a.fused) {
         const FusedVariant& fv = fused_variant_of(dtype, v);
         fused_items(dp, fv.bx, fv.by, cz, items, ctasks);
@@ -714,8 +738,9 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (bv < -1) return fail(c, MHD_ECUDA, "autotune: no advance ran on this device");
+  if (bv < -2) return fail(c, MHD_ECUDA, "autotune: no advance ran on this device");
   c->use_fused[di] = bv >= 0;
+  if (bv < 0) c->pred_tiled[di] = bv == -1;
   c->fused_variant[di] = bv >= 0 ? bv : 0;
   c->fused_chunk[di] = bv >= 0 ? bcz : 0;
   if (variant_out) *variant_out = bv;

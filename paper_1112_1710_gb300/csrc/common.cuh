@@ -58,6 +58,11 @@ struct BlockTask {
   int32_t start;
 };
 
+// Tile of the tiled predictor (cells, x fastest; one thread per cell) per
+// element type; the host builds one block per tile of each patch's UB+1.
+constexpr int kPredTile32[3] = {32, 4, 2};
+constexpr int kPredTile64[3] = {16, 4, 4};
+
 // One work item of the fused advance: an x-y tile of the update box with
 // lower corner (x0, y0) (array indices) and the planes [z0, z1).
 struct FusedItem {

@@ -12,6 +12,8 @@ struct AdvanceArgs {
   int npatches;
   const BlockTask* tasks;  // device
   int nblocks;
+  const BlockTask* ptasks;  // device, tiles of the tiled predictor (npblocks 0: untiled)
+  int npblocks;
   void* scratch;           // device arena of the call's element type
   void* stepc;             // device, npatches x 8 elements of that type (in the arena)
   double gamma, eps_up;

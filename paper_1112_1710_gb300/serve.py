@@ -18,7 +18,10 @@ was given.  The server
     patches (uneven sizes in one launch), each patch with its own dt passed
     as its dt scale (device dt = 1), so no patch's arithmetic depends on the
     mix;
-  * records arrival, start and completion times for p50/p99 latencies.
+  * records arrival, start and completion times for p50/p99 latencies;
+  * requeues the requests of a launch that raised (a host-side failure: a
+    rejected descriptor, an allocation that failed) up to max_retries times,
+    then reports them as failed instead of stopping the loop.
 
 The policy (`Scheduler`) is plain host code; the device side is a backend
 with `launch(slot, batch)` and `ready(handle)`, so the policy runs unchanged
@@ -82,7 +85,7 @@ class Scheduler:
     """Finer-first, HBM-budgeted continuous batching over `n_slots` slots."""
 
     def __init__(self, backend, n_slots=2, budget_bytes=64 << 30, max_batch_cells=8 << 20, g=4,
-                 lookahead=64, policy="greedy", min_batch_cells=1 << 16):
+                 lookahead=64, policy="greedy", min_batch_cells=1 << 16, max_retries=2):
         """policy "greedy": a free slot takes up to max_batch_cells of waiting
         work; "balanced": its share from the distribution equation of Sec. 5
         with the slots as workers (balance.desired_distribution), so that the
@@ -92,6 +95,8 @@ class Scheduler:
             raise ValueError("policy must be greedy or balanced")
         self.policy = policy
         self.min_batch_cells = min_batch_cells
+        self.max_retries = max_retries
+        self.failures = []           # (slot, [rid, ...], error text) of launches that raised
         self.backend = backend
         self.n_slots = n_slots
         self.budget = budget_bytes
@@ -173,10 +178,23 @@ class Scheduler:
                 tstart = clock() - t0
                 for r in batch:
                     r.start = tstart
+                try:
+                    handle = self.backend.launch(s, batch)
+                except Exception as exc:  # a failed launch: nothing of it is in flight
+                    self.failures.append((s, [r.rid for r in batch], str(exc)))
+                    for r in batch:
+                        r.retries = getattr(r, "retries", 0) + 1
+                        if r.retries > self.max_retries:
+                            r.error = "failed %d launches: %s" % (r.retries, exc)
+                            r.done = clock() - t0
+                            done += 1
+                        else:
+                            heapq.heappush(waiting, (-r.level, r.arrival, r.rid, r))
+                    continue
                 self.resident += nbytes
                 self.peak_resident = max(self.peak_resident, self.resident)
                 self.batches.append((s, [r.rid for r in batch]))
-                slots[s] = (self.backend.launch(s, batch), batch, nbytes)
+                slots[s] = (handle, batch, nbytes)
             if all(f is None for f in slots) and not waiting and nxt < len(reqs):
                 wait = reqs[nxt].arrival - (clock() - t0)
                 if wait > 0:

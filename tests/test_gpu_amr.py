@@ -226,3 +226,44 @@ def test_turbulent_deep_hierarchy_fp64_parity(capi, orc):
         ph.close()
     finally:
         capi.mhd_ctx_destroy(ctx)
+
+
+def test_blast_shell_full_size_fp64_properties(capi, capsys):
+    """The AMR workload at its full size (base 64^3 + 3 levels, 2,720 patches
+    of 8^3-48^3, 4 ghost layers; the oracle is too slow here): one subcycled
+    FP64 coarse step conserves the composite totals of rho, M, E to rounding
+    and keeps every patch's face divergence at rounding."""
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 64
+    H = SA.shell_hierarchy(n0=n0, levels=4, seed=1112, size_min=8, size_max=48)
+    assert [len(l) for l in H] == [1, 153, 594, 1972]
+    st = [[SA.blast_patch(lo, hi, l, n0, G)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    ctx = capi.mhd_ctx_create(emf=1)
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        del st
+        ph.initialise()
+        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s0 = out.cpu().numpy().copy()
+        ph.coarse_step()
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s1 = out.cpu().numpy()
+        assert capi.mhd_get_device_status(ctx) == 0
+        rel = np.abs(s1 - s0) / np.maximum(np.abs(s0), 1e-300)
+        divb = 0.0
+        for l, pats in enumerate(ph.levels):
+            for p in pats:
+                s = p.state
+                nx, ny, nz = p.n
+                d = ((s[5, G:G + nz, G:G + ny, G + 1:G + nx + 1] - s[5, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[6, G:G + nz, G + 1:G + ny + 1, G:G + nx] - s[6, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[7, G + 1:G + nz + 1, G:G + ny, G:G + nx] - s[7, G:G + nz, G:G + ny, G:G + nx]))
+                divb = max(divb, float(d.abs().max()))
+        with capsys.disabled():
+            print("\nFP64 AMR full size, one coarse step: relative drift (rho, E) %.1e %.1e, max |div B| dx %.1e"
+                  % (rel[0], rel[4], divb))
+        assert rel[0] < 1e-12 and rel[4] < 1e-12 and divb < 1e-12
+        ph.close()
+    finally:
+        capi.mhd_ctx_destroy(ctx)

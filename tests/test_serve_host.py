@@ -157,3 +157,38 @@ def test_balanced_policy_sizes_batches_by_the_distribution_equation():
     assert np.allclose(d, [1300, 700])
     with pytest.raises(ValueError):
         Scheduler(SimBackend(Clock()), policy="other")
+
+
+class FlakyBackend(SimBackend):
+    """Raises on the launches whose index is in `fail` (a host-side failure:
+    nothing of that batch reaches the device)."""
+
+    def __init__(self, clock, fail, **kw):
+        super().__init__(clock, **kw)
+        self.fail = set(fail)
+        self.calls = 0
+
+    def launch(self, slot, batch):
+        self.calls += 1
+        if self.calls in self.fail:
+            raise RuntimeError("launch %d rejected" % self.calls)
+        return super().launch(slot, batch)
+
+
+def test_failed_launch_is_requeued_then_reported():
+    clk = Clock()
+    be = FlakyBackend(clk, fail={1, 3})
+    sch = Scheduler(be, n_slots=2, max_batch_cells=1 << 15, max_retries=2)
+    reqs = [Request(i, 0.0, 16, i % 3, "f32") for i in range(20)]
+    out = sch.run(reqs, clock=clk, t_limit=1e6)
+    assert len(sch.failures) == 2
+    assert not any(r.error for r in out)                      # every request served after a retry
+    assert sorted(r for _, rids in sch.batches for r in rids) == list(range(20))
+    assert sch.resident == 0
+    # a backend that always fails: requests end as errors, the loop ends
+    clk = Clock()
+    bad = FlakyBackend(clk, fail=set(range(1, 100)))
+    sch = Scheduler(bad, n_slots=2, max_retries=1)
+    out = sch.run([Request(i, 0.0, 16, 0, "f64") for i in range(3)], clock=clk, t_limit=1e6)
+    assert all(r.error.startswith("failed 2 launches") for r in out)
+    assert sch.batches == [] and sch.resident == 0
