@@ -3,15 +3,21 @@
 //
 // One step of a patch updates the cells of its update box UB = interior grown
 // by k layers (Sec. 2.3 extended ghosts) and the faces of those cells; it reads
-// data on UB grown by 2.  Six kernels, each one thread per element, every
+// data on UB grown by 2.  The stages, each one thread per element, every
 // block working inside one patch (BlockTask):
 //   k_prim    UB+2 cells : primitives W, cell EMF E^n = -v x Bc
 //   k_pred    UB+1 cells : limited slopes, face values, positivity rule,
 //                          Hancock predictor, predicted face states, E_ref
 //   k_edge    UB+2 cells : E^n at the cell's three edges (mean of the four cells)
 //   k_flux    faces      : CT half-step normal field, HLLD flux, contact side
-//   k_emf     UB+2 cells : Gardiner-Stone (or arithmetic) EMF of the cell's three edges
-//   k_update  UB         : conservative cell update and CT face update
+//   k_emf     UB+2 cells : Gardiner-Stone (or arithmetic) EMF of the cell's
+//                          three edges (FP64 builds)
+//   k_update  UB         : conservative cell update and CT face update; the
+//                          FP32 build computes the EMFs of the faces' edges
+//                          here instead of in k_emf (measured on GB300: one
+//                          launch fewer pays in FP32, while in FP64 the
+//                          recomputation of shared edges costs more than the
+//                          launch)
 // Intermediates live in a per-patch scratch region with the patch's own
 // strides, so every stage addresses them like the state arrays.
 #pragma once
@@ -29,9 +35,20 @@
 #ifndef MHD_ADVANCE_NS
 #error "define MHD_ADVANCE_NS before including advance.cuh"
 #endif
+#ifndef MHD_FAST_RECIP
+#error "define MHD_FAST_RECIP (0: divide as the oracle does; 1: reciprocal form of HLLD)"
+#endif
 
 namespace mhd {
 namespace MHD_ADVANCE_NS {
+
+// HLLD in the reciprocal form (FP32 and contracted FP64 builds) or with the
+// oracle's divisions (parity build).
+constexpr bool kFastRecip = MHD_FAST_RECIP != 0;
+
+// Where the edge EMFs of the update are computed: inside k_update (FP32) or
+// by k_emf into scratch planes (FP64).
+template <typename R> constexpr bool kEmfInline = sizeof(R) == 4;
 
 template <typename R> struct SolverConsts {
   R gamma, gm1, igm1, eps_up;
@@ -149,10 +166,41 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
   if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
 }
 
+// ---------------------------------------------------------------- k_edge
+template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr);
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
+                                                   const BlockTask* __restrict__ T, R* scr) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  // the three edges stored at this cell, one index decomposition
+  edge_avg<R, 0>(p, c, scr);
+  edge_avg<R, 1>(p, c, scr);
+  edge_avg<R, 2>(p, c, scr);
+}
+
+template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
+  const int64_t x = lin(p, c);
+  const int64_t sb = stride_of(p, b), sc_ = stride_of(p, cc);
+  const R* En = arr(scr, p, SC_EN + a);
+  R e00 = En[x - sb - sc_];
+  R e10 = En[x - sc_];
+  R e01 = En[x - sb];
+  R e11 = En[x];
+  arr(scr, p, SC_EE + a)[x] = R(0.25) * (e00 + e10 + e01 + e11);
+}
+
 // ---------------------------------------------------------------- k_pred
 // The predictor of one cell from its primitives w and limited slopes dw:
 // first positivity rule, Hancock increment, the six predicted face states
-// (second positivity rule) and the reference cell EMF, stored at element x.
+// (second positivity rule) and, for the upwinded EMF average, the reference
+// cell EMF, stored at element x.
 template <typename R>
 __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr, const SolverConsts<R>& sc,
                                              const StepDt<R>& st, const R (&w)[8], const R (&dw)[3][8]) {
@@ -211,7 +259,8 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
 #pragma unroll
     for (int q = 0; q < 8; ++q) duk[q] = R(0);
   }
-  // reference cell EMF from U^{n+1/2}
+  // reference cell EMF from U^{n+1/2} (read only by the upwinded EMF average)
+  if (sc.emf == 1) return;
   R uc[8], uh[8];
   prim2cons(w, sc.igm1, uc);
 #pragma unroll
@@ -318,36 +367,6 @@ __global__ void __launch_bounds__(kThreads) k_pred_tiled(const DPatch* __restric
   predict_cell(p, x, scr, sc, st, w, dw);
 }
 
-// ---------------------------------------------------------------- k_edge
-template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr);
-
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
-                                                   const BlockTask* __restrict__ T, R* scr) {
-  const BlockTask t = T[blockIdx.x];
-  const DPatch& p = P[t.patch];
-  Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  // the three edges stored at this cell, one index decomposition
-  edge_avg<R, 0>(p, c, scr);
-  edge_avg<R, 1>(p, c, scr);
-  edge_avg<R, 2>(p, c, scr);
-}
-
-template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
-  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
-  const int id[3] = {c.i, c.j, c.k};
-  if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
-  const int64_t x = lin(p, c);
-  const int64_t sb = stride_of(p, b), sc_ = stride_of(p, cc);
-  const R* En = arr(scr, p, SC_EN + a);
-  R e00 = En[x - sb - sc_];
-  R e10 = En[x - sc_];
-  R e01 = En[x - sb];
-  R e11 = En[x];
-  arr(scr, p, SC_EE + a)[x] = R(0.25) * (e00 + e10 + e01 + e11);
-}
-
 // ---------------------------------------------------------------- k_flux
 // The face direction is a template parameter so that every array index below
 // is a compile-time constant (no local-memory arrays).
@@ -372,7 +391,7 @@ __device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell
   }
   rot_in(d, wl, L);
   rot_in(d, wr, Rr);
-  hlld(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
+  hlld<R, kFastRecip>(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
   rot_out(d, fr, f);
   f[5 + d] = upw;
 #pragma unroll
@@ -387,60 +406,21 @@ __global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
   const DPatch& p = P[t.patch];
   Cell c;
   if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  switch (blockIdx.y) {
-    case 0: flux_face<R, 0>(p, t.patch, c, scr, sc, K); break;
-    case 1: flux_face<R, 1>(p, t.patch, c, scr, sc, K); break;
-    default: flux_face<R, 2>(p, t.patch, c, scr, sc, K); break;
-  }
+  flux_face<R, 0>(p, t.patch, c, scr, sc, K);
+  flux_face<R, 1>(p, t.patch, c, scr, sc, K);
+  flux_face<R, 2>(p, t.patch, c, scr, sc, K);
 }
 
-// ---------------------------------------------------------------- k_emf
-template <typename R, int a>
-__device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc);
-
+// ---------------------------------------------------------------- edge EMFs
+// Gardiner-Stone (or arithmetic) EMF of one edge from the four face EMFs
+// around it (eb_lo, eb_hi, ec_lo, ec_hi), the contact sides of those faces
+// and the four reference cell EMFs, in one fixed expression order (the
+// staged and the fused advance both use it).
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
-                                                  const BlockTask* __restrict__ T, R* scr,
-                                                  SolverConsts<R> sc) {
-  const BlockTask t = T[blockIdx.x];
-  const DPatch& p = P[t.patch];
-  Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  edge_emf<R, 0>(p, c, scr, sc);
-  edge_emf<R, 1>(p, c, scr, sc);
-  edge_emf<R, 2>(p, c, scr, sc);
-}
-
-template <typename R, int a>
-__device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr, const SolverConsts<R>& sc) {
-  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
-  const int id[3] = {c.i, c.j, c.k};
-  if (!in_ub(p, a, id[a], 0, 0) || !in_ub(p, b, id[b], 0, 1) || !in_ub(p, cc, id[cc], 0, 1)) return;
-  const int64_t x = lin(p, c);
-  const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
-  const R* Fbc = arr(scr, p, SC_F + b * 8 + 5 + cc);
-  const R* Fcb = arr(scr, p, SC_F + cc * 8 + 5 + b);
-  R eb_lo = -Fbc[x - scc];
-  R eb_hi = -Fbc[x];
-  R ec_lo = Fcb[x - sb];
-  R ec_hi = Fcb[x];
+__device__ __forceinline__ R edge_emf_value(R eb_lo, R eb_hi, R ec_lo, R ec_hi, R r00, R r10, R r01, R r11,
+                                            R mb_lo, R mb_hi, R mc_lo, R mc_hi, int emf) {
   R avg = R(0.25) * (eb_lo + eb_hi + ec_lo + ec_hi);
-  R* Ed = arr(scr, p, SC_ED + a);
-  if (sc.emf == 1) {
-    Ed[x] = avg;
-    return;
-  }
-  const R* Er = arr(scr, p, SC_ER + a);
-  R r00 = Er[x - sb - scc];
-  R r10 = Er[x - scc];
-  R r01 = Er[x - sb];
-  R r11 = Er[x];
-  const R* Ub = arr(scr, p, SC_F + b * 8 + 5 + b);
-  const R* Uc = arr(scr, p, SC_F + cc * 8 + 5 + cc);
-  R mb_lo = Ub[x - scc];
-  R mb_hi = Ub[x];
-  R mc_lo = Uc[x - sb];
-  R mc_hi = Uc[x];
+  if (emf == 1) return avg;
   R dc14, dc34, db14, db34;
   if (mb_hi > R(0)) dc14 = r01 - ec_lo;
   else if (mb_hi < R(0)) dc14 = r11 - ec_hi;
@@ -454,14 +434,71 @@ __device__ __forceinline__ void edge_emf(const DPatch& p, const Cell& c, R* scr,
   if (mc_lo > R(0)) db34 = eb_lo - r00;
   else if (mc_lo < R(0)) db34 = eb_hi - r01;
   else db34 = R(0.5) * ((eb_lo - r00) + (eb_hi - r01));
-  Ed[x] = avg + R(0.25) * (dc34 - dc14 + db34 - db14);
+  return avg + R(0.25) * (dc34 - dc14 + db34 - db14);
+}
+
+// EMF of the axis-a edge stored at element x: the face EMFs -F_b[B_c] of the
+// two b-faces and F_c[B_b] of the two c-faces around it; with the upwinded
+// average also the contact sides of those faces and the reference EMFs of
+// the four cells around the edge.
+template <typename R, int a>
+__device__ __forceinline__ R emf_at(const DPatch& p, int64_t x, const R* scr, int emf) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
+  const R* Fbc = arr(scr, p, SC_F + b * 8 + 5 + cc);
+  const R* Fcb = arr(scr, p, SC_F + cc * 8 + 5 + b);
+  const R eb_lo = -Fbc[x - scc], eb_hi = -Fbc[x], ec_lo = Fcb[x - sb], ec_hi = Fcb[x];
+  if (emf == 1) return R(0.25) * (eb_lo + eb_hi + ec_lo + ec_hi);
+  const R* Er = arr(scr, p, SC_ER + a);
+  const R* Ub = arr(scr, p, SC_F + b * 8 + 5 + b);
+  const R* Uc = arr(scr, p, SC_F + cc * 8 + 5 + cc);
+  return edge_emf_value(eb_lo, eb_hi, ec_lo, ec_hi, Er[x - sb - scc], Er[x - scc], Er[x - sb], Er[x], Ub[x - scc],
+                        Ub[x], Uc[x - sb], Uc[x], emf);
+}
+
+// Is the axis-a edge stored at cell c one of the edges of the update box's
+// faces (the edges whose EMF the flux registers capture)?
+template <int a> __device__ __forceinline__ bool update_edge(const DPatch& p, const Cell& c) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  return in_ub(p, a, id[a], 0, 0) && in_ub(p, b, id[b], 0, 1) && in_ub(p, cc, id[cc], 0, 1);
+}
+
+// ---------------------------------------------------------------- k_emf
+// The EMFs of the three update-box edges stored at each cell of UB+2.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
+                                                  const BlockTask* __restrict__ T, R* scr,
+                                                  SolverConsts<R> sc) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  const int64_t x = lin(p, c);
+  const R* cs = scr;
+  const bool u0 = update_edge<0>(p, c), u1 = update_edge<1>(p, c), u2 = update_edge<2>(p, c);
+  R e0 = R(0), e1 = R(0), e2 = R(0);
+  if (u0) e0 = emf_at<R, 0>(p, x, cs, sc.emf);
+  if (u1) e1 = emf_at<R, 1>(p, x, cs, sc.emf);
+  if (u2) e2 = emf_at<R, 2>(p, x, cs, sc.emf);
+  if (u0) arr(scr, p, SC_ED + 0)[x] = e0;
+  if (u1) arr(scr, p, SC_ED + 1)[x] = e1;
+  if (u2) arr(scr, p, SC_ED + 2)[x] = e2;
 }
 
 // ---------------------------------------------------------------- k_update
-template <typename R>
+// One thread per cell of UB+2: the cell's conservative update and the CT
+// update of its three lower faces, each face from the EMFs of its four edges.
+// EmfInline: the nine distinct edge EMFs a cell's faces need are computed
+// here from the face fluxes (an edge is shared by four faces, so its EMF is
+// evaluated by up to three threads, always with the same expression), and
+// patches that feed flux registers also store the EMF of every update-box
+// edge at its element, where the capture kernel reads it; otherwise they are
+// read from k_emf's planes.
+template <typename R, bool EmfInline>
 __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ P,
                                                      const BlockTask* __restrict__ T, R* scr,
-                                                     const R* __restrict__ K, int commit) {
+                                                     SolverConsts<R> sc, const R* __restrict__ K, int commit) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
@@ -469,6 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
   const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   const int id[3] = {c.i, c.j, c.k};
+  const int64_t s1 = p.s1, s2 = p.s2;
   // every load before the first store: the state and scratch pointers may
   // alias as far as the compiler knows, so a store would order later loads
   const bool cell = in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0);
@@ -480,24 +518,56 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
       const R* F1 = arr(scr, p, SC_F + 1 * 8 + q);
       const R* F2 = arr(scr, p, SC_F + 2 * 8 + q);
       R u = ((const R*)p.U[q])[x];
-      un[q] = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + p.s1] - F1[x]) -
-              st.dtdx[2] * (F2[x + p.s2] - F2[x]);
+      un[q] = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + s1] - F1[x]) -
+              st.dtdx[2] * (F2[x + s2] - F2[x]);
     }
   }
   bool face[3];
-  R bn[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int b = (a + 1) % 3, cc = (a + 2) % 3;
     face[a] = in_ub(p, a, id[a], 0, 1) && in_ub(p, b, id[b], 0, 0) && in_ub(p, cc, id[cc], 0, 0);
-    if (!face[a]) continue;
-    const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
-    const R* Ec = arr(scr, p, SC_ED + cc);
-    const R* Eb = arr(scr, p, SC_ED + b);
-    R dEc = Ec[x + sb] - Ec[x];
-    R dEb = Eb[x + scc] - Eb[x];
-    bn[a] = ((const R*)p.B[a])[x] - (st.dtdx[b] * dEc - st.dtdx[cc] * dEb);
   }
+  // face 0 needs E2 at x, x+s1 and E1 at x, x+s2; face 1 E0 at x, x+s2 and
+  // E2 at x, x+1; face 2 E1 at x, x+1 and E0 at x, x+s1
+  const R* cs = scr;
+  R e0 = R(0), e0y = R(0), e0z = R(0), e1 = R(0), e1x = R(0), e1z = R(0), e2 = R(0), e2x = R(0), e2y = R(0);
+  if constexpr (EmfInline) {
+    if (face[1] || face[2]) e0 = emf_at<R, 0>(p, x, cs, sc.emf);
+    if (face[1]) e0z = emf_at<R, 0>(p, x + s2, cs, sc.emf);
+    if (face[2]) e0y = emf_at<R, 0>(p, x + s1, cs, sc.emf);
+    if (face[0] || face[2]) e1 = emf_at<R, 1>(p, x, cs, sc.emf);
+    if (face[0]) e1z = emf_at<R, 1>(p, x + s2, cs, sc.emf);
+    if (face[2]) e1x = emf_at<R, 1>(p, x + 1, cs, sc.emf);
+    if (face[0] || face[1]) e2 = emf_at<R, 2>(p, x, cs, sc.emf);
+    if (face[0]) e2y = emf_at<R, 2>(p, x + s1, cs, sc.emf);
+    if (face[1]) e2x = emf_at<R, 2>(p, x + 1, cs, sc.emf);
+  } else {
+    const R* E0 = arr(cs, p, SC_ED + 0);
+    const R* E1 = arr(cs, p, SC_ED + 1);
+    const R* E2 = arr(cs, p, SC_ED + 2);
+    if (face[1] || face[2]) e0 = E0[x];
+    if (face[1]) e0z = E0[x + s2];
+    if (face[2]) e0y = E0[x + s1];
+    if (face[0] || face[2]) e1 = E1[x];
+    if (face[0]) e1z = E1[x + s2];
+    if (face[2]) e1x = E1[x + 1];
+    if (face[0] || face[1]) e2 = E2[x];
+    if (face[0]) e2y = E2[x + s1];
+    if (face[1]) e2x = E2[x + 1];
+  }
+  // B_a^{n+1} = B_a^n - (dt/dx_b (E_c(x + s_b) - E_c(x)) - dt/dx_c (E_b(x + s_c) - E_b(x)))
+  R bn[3];
+  if (face[0]) bn[0] = ((const R*)p.B[0])[x] - (st.dtdx[1] * (e2y - e2) - st.dtdx[2] * (e1z - e1));
+  if (face[1]) bn[1] = ((const R*)p.B[1])[x] - (st.dtdx[2] * (e0z - e0) - st.dtdx[0] * (e2x - e2));
+  if (face[2]) bn[2] = ((const R*)p.B[2])[x] - (st.dtdx[0] * (e1x - e1) - st.dtdx[1] * (e0y - e0));
+  // edge EMFs for the flux registers
+  const bool cap = EmfInline && (p.flags & 1) != 0;
+  const bool ce0 = cap && update_edge<0>(p, c), ce1 = cap && update_edge<1>(p, c), ce2 = cap && update_edge<2>(p, c);
+  R ec0 = R(0), ec1 = R(0), ec2 = R(0);
+  if (ce0) ec0 = emf_at<R, 0>(p, x, cs, sc.emf);
+  if (ce1) ec1 = emf_at<R, 1>(p, x, cs, sc.emf);
+  if (ce2) ec2 = emf_at<R, 2>(p, x, cs, sc.emf);
   // without commit the new state goes to the (by now unused) primitive planes
   if (cell) {
 #pragma unroll
@@ -506,16 +576,19 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (face[a]) (commit ? (R*)p.B[a] : arr(scr, p, SC_W + 5 + a))[x] = bn[a];
+  if (ce0) arr(scr, p, SC_ED + 0)[x] = ec0;
+  if (ce1) arr(scr, p, SC_ED + 1)[x] = ec1;
+  if (ce2) arr(scr, p, SC_ED + 2)[x] = ec2;
 }
 
-// Enqueues the step constants and the six stages for the patches of one
-// call; K (npatch x kStepConsts elements) is scratch.
+// Enqueues the step constants and the stages for the patches of one call;
+// K (npatch x kStepConsts elements) is scratch.
 template <typename R>
 cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks,
                            const BlockTask* d_ptasks, int npblocks, R* scr, R* K, const SolverConsts<R>& sc,
                            const double* d_dt, int* d_status, const KernelTimer* tm, bool commit, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
-  dim3 g1(nblocks), g3(nblocks, 3);
+  dim3 g1(nblocks);
   MHD_TIMED(tm, K_PRIM, s,
             (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
              k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
@@ -524,9 +597,11 @@ cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask*
   else
     MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
   MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
-  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g3, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
-  MHD_TIMED(tm, K_UPDATE, s, (k_update<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, K, commit ? 1 : 0)));
+  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
+  constexpr bool inl = kEmfInline<R>;
+  if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
+  MHD_TIMED(tm, K_UPDATE, s,
+            (k_update<R, inl><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K, commit ? 1 : 0)));
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 // stay in FP64).  Built with multiply-add contraction and fast FP32 division,
 // reciprocal and square root.
 #define MHD_ADVANCE_NS fast32
+#define MHD_FAST_RECIP 1
 #include "advance.cuh"
 
 namespace mhd {

@@ -2,6 +2,7 @@
 // parity build: --fmad=false, so every result is the correctly rounded value
 // of the expression as written, in the oracle's order.
 #define MHD_ADVANCE_NS exact64
+#define MHD_FAST_RECIP 0
 #include "advance.cuh"
 
 namespace mhd {

@@ -3,6 +3,7 @@
 // fused into one rounding, which takes about a quarter fewer FP64 pipe
 // instructions.  Results differ from the parity build by rounding only.
 #define MHD_ADVANCE_NS contracted64
+#define MHD_FAST_RECIP 1
 #include "advance.cuh"
 
 namespace mhd {

@@ -237,7 +237,7 @@ __device__ __forceinline__ void face_flux(const R* wl, const R* wr, R bh, const 
   R L[8], Rr[8], fr[8], upw;
   rot_in(d, wl, L);
   rot_in(d, wr, Rr);
-  hlld(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
+  hlld<R, kFastRecip>(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
   rot_out(d, fr, f);
   f[5 + d] = upw;
 }
@@ -334,30 +334,6 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       }
     }
   }
-}
-
-// Gardiner-Stone (or arithmetic) EMF of one edge from the four face EMFs
-// around it (eb_lo, eb_hi, ec_lo, ec_hi), the contact sides of those faces
-// and the four reference cell EMFs; the staged kernel's expression order.
-template <typename R>
-__device__ __forceinline__ R edge_emf_value(R eb_lo, R eb_hi, R ec_lo, R ec_hi, R r00, R r10, R r01, R r11,
-                                            R mb_lo, R mb_hi, R mc_lo, R mc_hi, int emf) {
-  R avg = R(0.25) * (eb_lo + eb_hi + ec_lo + ec_hi);
-  if (emf == 1) return avg;
-  R dc14, dc34, db14, db34;
-  if (mb_hi > R(0)) dc14 = r01 - ec_lo;
-  else if (mb_hi < R(0)) dc14 = r11 - ec_hi;
-  else dc14 = R(0.5) * ((r01 - ec_lo) + (r11 - ec_hi));
-  if (mb_lo > R(0)) dc34 = ec_lo - r00;
-  else if (mb_lo < R(0)) dc34 = ec_hi - r10;
-  else dc34 = R(0.5) * ((ec_lo - r00) + (ec_hi - r10));
-  if (mc_hi > R(0)) db14 = r10 - eb_lo;
-  else if (mc_hi < R(0)) db14 = r11 - eb_hi;
-  else db14 = R(0.5) * ((r10 - eb_lo) + (r11 - eb_hi));
-  if (mc_lo > R(0)) db34 = eb_lo - r00;
-  else if (mc_lo < R(0)) db34 = eb_hi - r01;
-  else db34 = R(0.5) * ((eb_lo - r00) + (eb_hi - r01));
-  return avg + R(0.25) * (dc34 - dc14 + db34 - db14);
 }
 
 // Phase D: edge EMFs at z-index ze (x-, y-edges) and on plane ze (z-edges).

@@ -25,11 +25,13 @@ template <typename R> struct Tr;
 template <> struct Tr<double> {
   __device__ static __forceinline__ double abs(double x) { return fabs(x); }
   __device__ static __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  __device__ static __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
   __device__ static __forceinline__ double degen() { return 1e-12; }
 };
 template <> struct Tr<float> {
   __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
   __device__ static __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  __device__ static __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
   __device__ static __forceinline__ float degen() { return 1e-5f; }
 };
 
@@ -127,6 +129,18 @@ template <typename R> __device__ __forceinline__ void flux_xyz(int d, const R* w
   rot_out(d, fr, f);
 }
 
+// a / b, or a * ib with ib = 1 / b computed once for several quotients (the
+// reciprocal form of the FP32 and the contracted FP64 builds; the parity
+// build divides, as the oracle does)
+template <bool FR, typename R> __device__ __forceinline__ R qdiv(R a, R b, R ib) {
+  if constexpr (FR) return a * ib;
+  else return a / b;
+}
+template <bool FR, typename R> __device__ __forceinline__ R recip(R b) {
+  if constexpr (FR) return R(1) / b;
+  else return R(0);
+}
+
 // HLLD flux (Miyoshi & Kusano 2005) between rotated primitive states L (lower
 // side) and R_ (upper side) with interface normal field bn.  Wave speeds
 // S_L = min(u_L,u_R) - max(cf), S_R = max(u_L,u_R) + max(cf); S_M, p_T* from
@@ -136,8 +150,13 @@ template <typename R> __device__ __forceinline__ void flux_xyz(int d, const R* w
 // transverse v, B); Alfven speeds S* = S_M -/+ |Bn|/sqrt(rho*); double-star
 // states eqs. (59)-(63); left-closed region selection.  f gets the rotated
 // flux; *upw the upwind side of the contact (+1, -1, or 0 when
-// |S_M| <= eps_up (S_R - S_L)).
-template <typename R>
+// |S_M| <= eps_up (S_R - S_L)).  FR: quotients with a common denominator
+// multiply by its reciprocal, and |Bn|/sqrt(rho*) uses a reciprocal square
+// root (8 divisions per face instead of 18), and the single-star field factor
+// is written as 1 + rho (S - u)(S_M - u)/den, which is exactly 1 where
+// S_M = u (a plain reciprocal would turn x/x into x (1/x), off by an ulp,
+// and give a 2D problem a z-field of rounding noise).
+template <typename R, bool FR = false>
 __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R igm1, R eps_up,
                                      R* f, R* upw) {
   R rl = L[0], ul = L[1], vl = L[2], wl_ = L[3], pl = L[4], byl = L[6], bzl = L[7];
@@ -169,21 +188,32 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
   R sdl = sl - ul, sdr = sr - ur;
   R rsl = sdl * rl, rsr = sdr * rr;
   R dd = rsr - rsl;
-  R sm = ((rsr * ur - rsl * ul) - (ptr - ptl)) / dd;
-  R pts = ((rsr * ptl - rsl * ptr) + rsl * rsr * (ur - ul)) / dd;
+  const R idd = recip<FR>(dd);
+  R sm = qdiv<FR>((rsr * ur - rsl * ul) - (ptr - ptl), dd, idd);
+  R pts = qdiv<FR>((rsr * ptl - rsl * ptr) + rsl * rsr * (ur - ul), dd, idd);
   R tie = eps_up * (sr - sl);
   *upw = (sm > tie) ? R(1) : ((sm < -tie) ? R(-1) : R(0));
 
   R sml = sl - sm, smr = sr - sm;
-  R rls = rsl / sml, rrs = rsr / smr;
+  const R isml = recip<FR>(sml), ismr = recip<FR>(smr);
+  R rls = qdiv<FR>(rsl, sml, isml), rrs = qdiv<FR>(rsr, smr, ismr);
   R bn2 = bn * bn;
   R vls, wls, byls, bzls;
   R denl = rsl * sml - bn2;
   if (Tr<R>::abs(denl) <= Tr<R>::degen() * rmax(rsl * sdl, bn2)) {
     vls = vl; wls = wl_; byls = byl; bzls = bzl;
   } else {
-    R fv = bn * (sm - ul) / denl;
-    R fb = (rsl * sdl - bn2) / denl;
+    R fv, fb;
+    if constexpr (FR) {
+      // numerator of fb = den + rho (S - u)(S_M - u): fb = 1 + rho (S - u) t
+      // with t = (S_M - u) / den, exactly 1 where S_M = u
+      const R t = (sm - ul) * (R(1) / denl);
+      fv = bn * t;
+      fb = R(1) + rsl * t;
+    } else {
+      fv = bn * (sm - ul) / denl;
+      fb = (rsl * sdl - bn2) / denl;
+    }
     vls = vl - byl * fv; wls = wl_ - bzl * fv;
     byls = byl * fb; bzls = bzl * fb;
   }
@@ -192,8 +222,17 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
   if (Tr<R>::abs(denr) <= Tr<R>::degen() * rmax(rsr * sdr, bn2)) {
     vrs = vr; wrs = wr_; byrs = byr; bzrs = bzr;
   } else {
-    R fv = bn * (sm - ur) / denr;
-    R fb = (rsr * sdr - bn2) / denr;
+    R fv, fb;
+    if constexpr (FR) {
+      // numerator of fb = den + rho (S - u)(S_M - u): fb = 1 + rho (S - u) t
+      // with t = (S_M - u) / den, exactly 1 where S_M = u
+      const R t = (sm - ur) * (R(1) / denr);
+      fv = bn * t;
+      fb = R(1) + rsr * t;
+    } else {
+      fv = bn * (sm - ur) / denr;
+      fb = (rsr * sdr - bn2) / denr;
+    }
     vrs = vr - byr * fv; wrs = wr_ - bzr * fv;
     byrs = byr * fb; bzrs = bzr * fb;
   }
@@ -201,12 +240,22 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
   R vbr = ur * bn + vr * byr + wr_ * bzr;
   R vbls = sm * bn + vls * byls + wls * bzls;
   R vbrs = sm * bn + vrs * byrs + wrs * bzrs;
-  R els = (((sdl * el - ptl * ul) + pts * sm) + bn * (vbl - vbls)) / sml;
-  R ers = (((sdr * er - ptr * ur) + pts * sm) + bn * (vbr - vbrs)) / smr;
+  R els = qdiv<FR>(((sdl * el - ptl * ul) + pts * sm) + bn * (vbl - vbls), sml, isml);
+  R ers = qdiv<FR>(((sdr * er - ptr * ur) + pts * sm) + bn * (vbr - vbrs), smr, ismr);
 
-  R sqrl = Tr<R>::sqrt_(rls), sqrr = Tr<R>::sqrt_(rrs);
-  R sls = sm - Tr<R>::abs(bn) / sqrl;
-  R srs = sm + Tr<R>::abs(bn) / sqrr;
+  R sqrl, sqrr, sls, srs;
+  if constexpr (FR) {
+    const R isl = Tr<R>::rsqrt_(rls), isr = Tr<R>::rsqrt_(rrs);
+    sqrl = rls * isl;
+    sqrr = rrs * isr;
+    sls = sm - Tr<R>::abs(bn) * isl;
+    srs = sm + Tr<R>::abs(bn) * isr;
+  } else {
+    sqrl = Tr<R>::sqrt_(rls);
+    sqrr = Tr<R>::sqrt_(rrs);
+    sls = sm - Tr<R>::abs(bn) / sqrl;
+    srs = sm + Tr<R>::abs(bn) / sqrr;
+  }
 
   R fo[8];
   if (sls >= R(0) || srs < R(0)) {
@@ -227,10 +276,11 @@ __device__ __forceinline__ void hlld(const R* L, const R* Rr, R bn, R gamma, R i
 
   R sgn = (bn >= R(0)) ? R(1) : R(-1);
   R ssum = sqrl + sqrr;
-  R vss = ((sqrl * vls + sqrr * vrs) + sgn * (byrs - byls)) / ssum;
-  R wss = ((sqrl * wls + sqrr * wrs) + sgn * (bzrs - bzls)) / ssum;
-  R byss = ((sqrl * byrs + sqrr * byls) + sgn * (sqrl * sqrr) * (vrs - vls)) / ssum;
-  R bzss = ((sqrl * bzrs + sqrr * bzls) + sgn * (sqrl * sqrr) * (wrs - wls)) / ssum;
+  const R iss = recip<FR>(ssum);
+  R vss = qdiv<FR>((sqrl * vls + sqrr * vrs) + sgn * (byrs - byls), ssum, iss);
+  R wss = qdiv<FR>((sqrl * wls + sqrr * wrs) + sgn * (bzrs - bzls), ssum, iss);
+  R byss = qdiv<FR>((sqrl * byrs + sqrr * byls) + sgn * (sqrl * sqrr) * (vrs - vls), ssum, iss);
+  R bzss = qdiv<FR>((sqrl * bzrs + sqrr * bzls) + sgn * (sqrl * sqrr) * (wrs - wls), ssum, iss);
   R vbss = sm * bn + vss * byss + wss * bzss;
 
   const bool left = (sm >= R(0));
