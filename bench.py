@@ -218,10 +218,10 @@ def kernel_flops(name, n, launched=()):
     return f
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels on this
-# workload, from one ncu capture of the current kernels
-# (profiles/k_pred_k_flux_blast128_full.md).  Keys: bench pass, kernel.
-KERNEL_TRAFFIC = {("f64_exact", "k_flux"): 1358.4e6}
+# DRAM bytes (read + write) per step of the dominant kernels on this
+# workload (all of a kernel's launches in one step), from one ncu capture of
+# the current kernels (profiles/).  Keys: bench pass, kernel.
+KERNEL_TRAFFIC = {}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
@@ -396,13 +396,16 @@ def run_ours(args):
             if cnt:
                 kernels[nm] = {"ms_total": ms, "launches": cnt, "ms_per_launch": ms / cnt}
         dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
-        units = kernel_units(dom, args.n)
+        # launches of the kernel per step (one for every stage kernel)
+        lps = kernels[dom]["launches"] / args.steps
+        units = kernel_units(dom, args.n) / lps
         per_launch = kernels[dom]["ms_per_launch"] * 1e-3
         step_bytes = 8 * s * ((args.n + 4) ** 3 + args.n ** 3)
-        flops = kernel_flops(dom, args.n, kernels)
+        flops = kernel_flops(dom, args.n, kernels) / lps
         achieved = flops / per_launch / 1e12
         peak = alu_peak_tflops(dtype, sm_mhz)
         traffic = KERNEL_TRAFFIC.get((key, dom))
+        traffic = traffic / lps if traffic else None
         step_fl = sum(stage_flops(k, args.n) for k in STAGES + ("k_cfl",))
         out_dt[key] = {
             "value": value, "ms_per_step": ms_step,

@@ -245,7 +245,8 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
       cons2prim(u, sc.gm1, pw);
       if (!(pw[0] > R(0)) || !(pw[4] > R(0))) bad2 = true;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + (d * 2 + sd) * 8 + q)[x] = pw[q];
+      for (int q = 0; q < 8; ++q)
+        if (q != 5 + d) arr(scr, p, SC_WF + (d * 2 + sd) * 8 + q)[x] = pw[q];
     }
   }
   R duk[8];
@@ -255,7 +256,8 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
 #pragma unroll
     for (int f = 0; f < 6; ++f)
 #pragma unroll
-      for (int q = 0; q < 8; ++q) arr(scr, p, SC_WF + f * 8 + q)[x] = w[q];
+      for (int q = 0; q < 8; ++q)
+        if (q != 5 + f / 2) arr(scr, p, SC_WF + f * 8 + q)[x] = w[q];
 #pragma unroll
     for (int q = 0; q < 8; ++q) duk[q] = R(0);
   }
@@ -276,8 +278,12 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
 
 // One thread per cell of UB+1; the stencil of W is read from the scratch
 // planes through the caches.
+// Launch bounds: at most 128 registers per thread for the FP32 predictor and
+// 64 for the FP32 flux kernel (two and four blocks per SM); past those the
+// compiler's choice drops a block per SM and the kernels, bound by the
+// latency of their loads, slow down.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_pred(const DPatch* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
                                                    SolverConsts<R> sc, const R* __restrict__ K) {
   const BlockTask t = T[blockIdx.x];
@@ -384,22 +390,26 @@ __device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell
   R dEb = arr(scr, p, SC_EE + b)[x + scc] - arr(scr, p, SC_EE + b)[x];
   R bh = ((const R*)p.B[d])[x] - (st.hdtdx[b] * dEc - st.hdtdx[cc] * dEb);
   R wl[8], wr[8], L[8], Rr[8], fr[8], f[8], upw;
+  // the face-normal field of the predicted states is not stored: HLLD takes
+  // the CT half-step value bh instead
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    wl[q] = arr(scr, p, SC_WF + (d * 2 + 1) * 8 + q)[x - sd];
-    wr[q] = arr(scr, p, SC_WF + (d * 2 + 0) * 8 + q)[x];
+    wl[q] = q == 5 + d ? R(0) : arr(scr, p, SC_WF + (d * 2 + 1) * 8 + q)[x - sd];
+    wr[q] = q == 5 + d ? R(0) : arr(scr, p, SC_WF + (d * 2 + 0) * 8 + q)[x];
   }
   rot_in(d, wl, L);
   rot_in(d, wr, Rr);
   hlld<R, kFastRecip>(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
   rot_out(d, fr, f);
   f[5 + d] = upw;
+  // the contact side (slot 5+d) is read only by the upwinded EMF average
 #pragma unroll
-  for (int q = 0; q < 8; ++q) arr(scr, p, SC_F + d * 8 + q)[x] = f[q];
+  for (int q = 0; q < 8; ++q)
+    if (q != 5 + d || sc.emf != 1) arr(scr, p, SC_F + d * 8 + q)[x] = f[q];
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_flux(const DPatch* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_flux(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
                                                    SolverConsts<R> sc, const R* __restrict__ K) {
   const BlockTask t = T[blockIdx.x];

@@ -596,9 +596,8 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   a.commit = true;
   cudaError_t e = run_advance_args(c, dtype, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
-  // staged: step constants, k_prim, k_pred, k_edge, k_flux, k_update (+ k_emf
-  // in FP64); fused: step constants, k_fused, k_commit
-  c->launches += fused ? 3 : (dtype == MHD_F32 ? 6 : 7);
+  // fused: step constants, k_fused, k_commit
+  c->launches += fused ? 3 : staged_launches(elem_size(dtype));
   if (ncap > 0) {
     std::vector<BlockTask> cptasks;
     tasks_for(ccounts, cptasks);
@@ -729,7 +728,7 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
         cudaEventDestroy(e1);
         return cuda_fail(c, e, "autotune run");
       }
-      c->launches += (a.fused ? 2 : (dtype == MHD_F32 ? 6 : 7)) * (reps + 1);
+      c->launches += (a.fused ? 2 : staged_launches(es)) * (reps + 1);
       ms /= reps;
       if (ms < best) {
         best = ms;
