@@ -208,11 +208,14 @@ def stage_flops(name, n):
 
 def kernel_flops(name, n, launched=()):
     """Algorithmic flops of one launch.  The fused kernel does the work of all
-    six stages (its halo recomputation is not algorithmic work); k_update
-    also computes the edge EMFs where k_emf was not launched (FP32)."""
+    six stages (its halo recomputation is not algorithmic work); where k_edge
+    and k_emf were not launched (FP32), k_flux computes the edge averages of
+    E^n and k_update the edge EMFs."""
     if name == "k_fused":
         return sum(stage_flops(k, n) for k in STAGES)
     f = stage_flops(name, n)
+    if name == "k_flux" and "k_edge" not in launched:
+        f += stage_flops("k_edge", n)
     if name == "k_update" and "k_emf" not in launched:
         f += stage_flops("k_emf", n)
     return f

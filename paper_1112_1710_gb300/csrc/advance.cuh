@@ -8,16 +8,16 @@
 //   k_prim    UB+2 cells : primitives W, cell EMF E^n = -v x Bc
 //   k_pred    UB+1 cells : limited slopes, face values, positivity rule,
 //                          Hancock predictor, predicted face states, E_ref
-//   k_edge    UB+2 cells : E^n at the cell's three edges (mean of the four cells)
+//   k_edge    UB+2 cells : E^n at the cell's three edges (mean of the four
+//                          cells; FP64 builds)
 //   k_flux    faces      : CT half-step normal field, HLLD flux, contact side
 //   k_emf     UB+2 cells : Gardiner-Stone (or arithmetic) EMF of the cell's
 //                          three edges (FP64 builds)
-//   k_update  UB         : conservative cell update and CT face update; the
-//                          FP32 build computes the EMFs of the faces' edges
-//                          here instead of in k_emf (measured on GB300: one
-//                          launch fewer pays in FP32, while in FP64 the
-//                          recomputation of shared edges costs more than the
-//                          launch)
+//   k_update  UB         : conservative cell update and CT face update
+// The FP32 build computes the edge averages inside k_flux and the edge EMFs
+// inside k_update, from the cell and face values around each edge (measured
+// on GB300: a launch fewer pays in FP32, while in FP64 the recomputation of
+// edges shared by several faces costs more than the launch).
 // Intermediates live in a per-patch scratch region with the patch's own
 // strides, so every stage addresses them like the state arrays.
 #pragma once
@@ -46,9 +46,10 @@ namespace MHD_ADVANCE_NS {
 // oracle's divisions (parity build).
 constexpr bool kFastRecip = MHD_FAST_RECIP != 0;
 
-// Where the edge EMFs of the update are computed: inside k_update (FP32) or
-// by k_emf into scratch planes (FP64).
-template <typename R> constexpr bool kEmfInline = sizeof(R) == 4;
+// Where the edge averages of E^n and the edge EMFs are computed: inside the
+// kernels that use them (k_flux and k_update, FP32) or by k_edge and k_emf
+// into scratch planes (FP64).
+template <typename R> constexpr bool kInlineEdges = sizeof(R) == 4;
 
 template <typename R> struct SolverConsts {
   R gamma, gm1, igm1, eps_up;
@@ -182,18 +183,25 @@ __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
   edge_avg<R, 2>(p, c, scr);
 }
 
-template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
+// E^n at the axis-a edge stored at element x: the mean of the cell EMFs of
+// the four cells around it.
+template <typename R, int a> __device__ __forceinline__ R edge_avg_at(const DPatch& p, int64_t x, const R* scr) {
   constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
-  const int id[3] = {c.i, c.j, c.k};
-  if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
-  const int64_t x = lin(p, c);
   const int64_t sb = stride_of(p, b), sc_ = stride_of(p, cc);
   const R* En = arr(scr, p, SC_EN + a);
   R e00 = En[x - sb - sc_];
   R e10 = En[x - sc_];
   R e01 = En[x - sb];
   R e11 = En[x];
-  arr(scr, p, SC_EE + a)[x] = R(0.25) * (e00 + e10 + e01 + e11);
+  return R(0.25) * (e00 + e10 + e01 + e11);
+}
+
+template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int id[3] = {c.i, c.j, c.k};
+  if (!in_ub(p, a, id[a], -1, 1) || !in_ub(p, b, id[b], -1, 2) || !in_ub(p, cc, id[cc], -1, 2)) return;
+  const int64_t x = lin(p, c);
+  arr(scr, p, SC_EE + a)[x] = edge_avg_at<R, a>(p, x, scr);
 }
 
 // ---------------------------------------------------------------- k_pred
@@ -386,8 +394,14 @@ __device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell
   const int64_t x = lin(p, c);
   const int64_t sd = stride_of(p, d), sb = stride_of(p, b), scc = stride_of(p, cc);
   // CT half step of the face-normal field
-  R dEc = arr(scr, p, SC_EE + cc)[x + sb] - arr(scr, p, SC_EE + cc)[x];
-  R dEb = arr(scr, p, SC_EE + b)[x + scc] - arr(scr, p, SC_EE + b)[x];
+  R dEc, dEb;
+  if constexpr (kInlineEdges<R>) {
+    dEc = edge_avg_at<R, cc>(p, x + sb, scr) - edge_avg_at<R, cc>(p, x, scr);
+    dEb = edge_avg_at<R, b>(p, x + scc, scr) - edge_avg_at<R, b>(p, x, scr);
+  } else {
+    dEc = arr(scr, p, SC_EE + cc)[x + sb] - arr(scr, p, SC_EE + cc)[x];
+    dEb = arr(scr, p, SC_EE + b)[x + scc] - arr(scr, p, SC_EE + b)[x];
+  }
   R bh = ((const R*)p.B[d])[x] - (st.hdtdx[b] * dEc - st.hdtdx[cc] * dEb);
   R wl[8], wr[8], L[8], Rr[8], fr[8], f[8], upw;
   // the face-normal field of the predicted states is not stored: HLLD takes
@@ -606,9 +620,9 @@ cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask*
     MHD_TIMED(tm, K_PRED, s, (k_pred_tiled<R><<<npblocks, kThreads, 0, s>>>(d_patches, d_ptasks, scr, sc, K)));
   else
     MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
+  constexpr bool inl = kInlineEdges<R>;
+  if (!inl) MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
   MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  constexpr bool inl = kEmfInline<R>;
   if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
   MHD_TIMED(tm, K_UPDATE, s,
             (k_update<R, inl><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K, commit ? 1 : 0)));

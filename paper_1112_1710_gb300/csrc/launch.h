@@ -43,8 +43,8 @@ constexpr int kNumFused32 = sizeof(kFusedVariants32) / sizeof(kFusedVariants32[0
 constexpr int kNumFused64 = sizeof(kFusedVariants64) / sizeof(kFusedVariants64[0]);
 
 // Kernel launches of one staged advance: step constants, k_prim, k_pred,
-// k_edge, k_flux, k_update, and k_emf in FP64.
-inline int staged_launches(size_t elem) { return elem == 8 ? 7 : 6; }
+// k_flux, k_update, and k_edge and k_emf in FP64.
+inline int staged_launches(size_t elem) { return elem == 8 ? 7 : 5; }
 
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);
 cudaError_t advance_f64c(const AdvanceArgs& a, cudaStream_t s);
