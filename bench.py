@@ -224,7 +224,8 @@ def kernel_flops(name, n, launched=()):
 # DRAM bytes (read + write) per step of the dominant kernels on this
 # workload (all of a kernel's launches in one step), from one ncu capture of
 # the current kernels (profiles/).  Keys: bench pass, kernel.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {("f32", "k_pred"): 447.8e6, ("f32", "k_flux"): 627.9e6, ("f32", "k_update"): 310.6e6,
+                  ("f64", "k_pred"): 882.6e6, ("f64", "k_flux"): 1247.5e6}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
