@@ -183,37 +183,79 @@ def test_contracted_fp64_within_tolerance(capi, orc, case, capsys):
         capi.mhd_ctx_destroy(ctx)
 
 
-def test_blast_fp32_error_report(capi, ctx_blast, orc, capsys):
-    """FP32 bulk arithmetic against the FP64 oracle with the oracle's dt
-    sequence: the error is reported per variable (no parity bar), with loose
-    sanity bounds."""
-    pr = synth.blast(64)
+def _interior_totals(st, n, g):
+    """FP64 totals of rho, M, E over the interior cells and of each face
+    field over the faces of the interior (lower faces, plus the top face)."""
+    nx, ny, nz = n
+    a = st.astype(np.float64)
+    cells = a[:5, g:g + nz, g:g + ny, g:g + nx].reshape(5, -1).sum(axis=1)
+    bx = a[5, g:g + nz, g:g + ny, g:g + nx + 1].sum()
+    by = a[6, g:g + nz, g:g + ny + 1, g:g + nx].sum()
+    bz = a[7, g:g + nz + 1, g:g + ny, g:g + nx].sum()
+    return np.concatenate([cells, [bx, by, bz]])
+
+
+def _max_divb(st, n, g, dx):
+    """max over interior cells of |div B| dx / max|B| (the CT invariant)."""
+    nx, ny, nz = n
+    a = st.astype(np.float64)
+    bx = a[5, g:g + nz, g:g + ny, g:g + nx + 1]
+    by = a[6, g:g + nz, g:g + ny + 1, g:g + nx]
+    bz = a[7, g:g + nz + 1, g:g + ny, g:g + nx]
+    div = (bx[:, :, 1:] - bx[:, :, :-1]) / dx[0] + (by[:, 1:, :] - by[:, :-1, :]) / dx[1] + \
+        (bz[1:, :, :] - bz[:-1, :, :]) / dx[2]
+    bmax = max(np.abs(bx).max(), np.abs(by).max(), np.abs(bz).max())
+    return float(np.abs(div).max() * min(dx) / bmax)
+
+
+@pytest.mark.parametrize("case", ["orszag_tang", "blast"])
+def test_fp32_error_report(capi, orc, case, capsys):
+    """FP32 bulk arithmetic against the FP64 oracle on the two single-patch
+    workloads at full size (Orszag-Tang 128^2, blast 128^3), on the oracle's
+    dt sequence: the error is reported per variable at steps 10 and 50 (L1
+    and L-infinity, relative), with the FP32 run's relative drift of the
+    totals and its max |div B| dx / max|B|.  No parity bar: loose sanity
+    bounds only."""
     from paper_1112_1710_gb300.runner import PeriodicRunner
-    st0 = pr.state.copy()
-    p = to_patch(st0, pr.n, pr.g, pr.dx, dtype="f32")
-    run = PeriodicRunner(p, ctx_blast)
-    want = pr.state
-    P = orc.patch(want, pr.n, pr.g, pr.dx)
-    prm = orc.params(emf=1)
-    rows = []
-    for step in range(1, 11):
-        orc.fill_periodic(P)
-        dt = orc.cfl_dt(P, prm)
-        assert orc.advance(P, prm, dt, 0) == 0
-        run.step(dt)
-        if step in (1, 10):
-            run.fill()
+    emf = 1 if case == "blast" else 0
+    pr = synth.blast(128) if case == "blast" else synth.orszag_tang(128)
+    ctx = capi.mhd_ctx_create(emf=emf)
+    try:
+        p = to_patch(pr.state.copy(), pr.n, pr.g, pr.dx, dtype="f32")
+        run = PeriodicRunner(p, ctx)
+        want = pr.state
+        P = orc.patch(want, pr.n, pr.g, pr.dx)
+        prm = orc.params(emf=emf)
+        tot0 = _interior_totals(p.state.cpu().numpy(), pr.n, pr.g)
+        rows = []
+        for step in range(1, 51):
             orc.fill_periodic(P)
-            got = p.state.cpu().numpy()
-            rows.append((step, rel_linf(got, want, pr.n, pr.g), rel_l1(got, want, pr.n, pr.g)))
+            dt = orc.cfl_dt(P, prm)
+            assert orc.advance(P, prm, dt, 0) == 0
+            run.step(dt)
+            if step in (10, 50):
+                run.fill()
+                orc.fill_periodic(P)
+                got = p.state.cpu().numpy()
+                tot = _interior_totals(got, pr.n, pr.g)
+                scale = np.maximum(np.abs(tot0), np.abs(_interior_totals(np.abs(got), pr.n, pr.g)))
+                drift = np.abs(tot - tot0) / np.maximum(scale, 1e-300)
+                rows.append((step, rel_linf(got, want, pr.n, pr.g), rel_l1(got, want, pr.n, pr.g), drift,
+                             _max_divb(got, pr.n, pr.g, pr.dx)))
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        capi.mhd_ctx_destroy(ctx)
     with capsys.disabled():
-        for step, li, l1 in rows:
-            print("\nFP32 vs FP64 oracle, blast 64^3, step %d" % step)
-            print("  Linf rel:", " ".join("%.2e" % v for v in li))
-            print("  L1   rel:", " ".join("%.2e" % v for v in l1))
-    li = rows[-1][1]
-    l1 = rows[-1][2]
-    assert np.all(l1[[0, 4, 5, 6]] < 1e-4) and np.all(li[[0, 4]] < 1e-2)
+        for step, li, l1, drift, divb in rows:
+            print("\nFP32 vs FP64 oracle, %s %s, step %d (rho Mx My Mz E Bx By Bz)" %
+                  (case, "x".join(str(v) for v in pr.n if v > 1), step))
+            print("  Linf rel :", " ".join("%.2e" % v for v in li))
+            print("  L1   rel :", " ".join("%.2e" % v for v in l1))
+            print("  drift    :", " ".join("%.2e" % v for v in drift), " max|divB|dx/|B|: %.2e" % divb)
+    _, li, l1, drift, divb = rows[-1]
+    live = [0, 1, 2, 4, 5, 6] + ([3, 7] if case == "blast" else [])
+    assert np.all(l1[live] < 1e-3) and np.all(li[[0, 4]] < 5e-2)
+    assert np.all(drift[[0, 4]] < 1e-5) and divb < 1e-4
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
