@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -502,6 +504,127 @@ def time_amr(H, states, dtype, steps, mode, local):
             "device_status": status}
 
 
+def _box_vol(b):
+    return int(np.prod([b.hi[d] - b.lo[d] + 1 for d in range(3)]))
+
+
+def amr_level_work(h):
+    """Algorithmic work of one coarse step of a Hierarchy, per kernel: DRAM
+    bytes for the level operations (what each must read and write at least)
+    and flops for the advance stages.  Call counts per coarse step: level l
+    advances 2^l times (substeps 1 and 2 alternate); fill(l) runs 2^l times
+    (level 0 once); prolong(l), restrict(l) and reflux(l) once per step of
+    level l, i.e. 2^l times."""
+    import numpy as np  # noqa: F811
+    es = 4 if h.dtype == "f32" else 8
+    L = h.nlev
+    nfill = [1] + [2 ** l for l in range(1, L)]
+    ghost = sum(nfill[l] * sum(_box_vol(c.box) for c in h.copy_lists[l]) for l in range(L)) * 8 * 2 * es
+    # prolongation: per coarse cell of an item 8 coarse values read, 8 fine
+    # cells x 8 values written; restriction: the reverse
+    prol = sum(2 ** l * sum(_box_vol(it.box) for it in h.prolong_lists[l]) for l in range(L - 1)) * 8 * 9 * es
+    rest = sum(2 ** l * sum(_box_vol(it.box) for it in h.restrict_lists[l]) for l in range(L - 1)) * 8 * 9 * es
+
+    def nvals(kind, lo, hi):
+        return (5 if kind == 0 else 1) * int(np.prod(np.asarray(hi) - np.asarray(lo) + 1))
+    # captures: a fine patch captures on both of its substeps (set, then add:
+    # flux read + FP64 write, + FP64 read on the add); a coarse patch once
+    cap = 0
+    for l in range(L):
+        nadv = 2 ** l
+        for (_, kind, _, lo, hi, _) in h.fine_caps[l]:
+            v = nvals(kind, lo, hi)
+            cap += (nadv // 2) * v * ((es + 8) + (es + 16)) if l > 0 else 0
+        for (_, kind, _, lo, hi, _) in h.coarse_caps[l]:
+            cap += nadv * nvals(kind, lo, hi) * (es + 8)
+    # refluxing: each deposit reads the fine register (the coarse box's
+    # values x 4 fine faces or x 2 fine edge segments) and the coarse
+    # register, writes a correction; the correction reads it and updates the
+    # coarse state element (read + write)
+    ref = 0
+    for l in range(L - 1):
+        for (_, kind, _, lo, hi, _, _, _, _) in h.deposit_list[l]:
+            v = nvals(kind, lo, hi)
+            ref += 2 ** l * v * (8 * (4 if kind == 0 else 2) + 8 + 8 + 8 + 2 * es)
+    cells = sum(p.cells for pats in h.levels for p in pats)
+    cfl = cells * 8 * es
+    # advance: units per call as in kernel_units, on each patch's update box
+    flops = {k: 0.0 for k in STAGES}
+    for l, pats in enumerate(h.levels):
+        ks = [0] if l == 0 else [2, 0]
+        calls = 1 if l == 0 else 2 ** (l - 1)
+        for p in pats:
+            for k in ks:
+                nx, ny, nz = (v + 2 * k for v in p.n)
+                u = {"k_prim": (nx + 4) * (ny + 4) * (nz + 4), "k_pred": (nx + 2) * (ny + 2) * (nz + 2),
+                     "k_edge": (nx + 2) * (ny + 3) * (nz + 3) + (nx + 3) * (ny + 2) * (nz + 3) +
+                     (nx + 3) * (ny + 3) * (nz + 2),
+                     "k_flux": (nx + 1) * (ny + 2) * (nz + 2) + (nx + 2) * (ny + 1) * (nz + 2) +
+                     (nx + 2) * (ny + 2) * (nz + 1),
+                     "k_emf": nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz,
+                     "k_update": nx * ny * nz}
+                for st in STAGES:
+                    flops[st] += calls * u[st] * KERNEL_FLOPS[st]
+    return {"bytes": {"k_ghost": ghost, "k_prolong": prol, "k_restrict": rest, "k_capture": cap,
+                      "k_reflux": ref, "k_cfl": cfl}, "flops": flops}
+
+
+def amr_attribution(H, states, dtype, steps, local):
+    """Per-kernel device time of eager coarse steps (CUDA events around every
+    launch) against each kernel's roofline: HBM for the level operations
+    (algorithmic bytes / time vs the measured copy bandwidth), ALU for the
+    advance stages."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.amr import Hierarchy
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    stream = torch.cuda.Stream(device=local)
+    h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
+                  device="cuda:%d" % local)
+    try:
+        h.initialise()
+        h.coarse_step()
+        torch.cuda.synchronize()
+        capi.mhd_timing_enable(ctx, True)
+        capi.mhd_timing_reset(ctx)
+        for _ in range(steps):
+            h.coarse_step()
+        torch.cuda.synchronize()
+        kt = capi.mhd_timing_read(ctx)
+        capi.mhd_timing_enable(ctx, False)
+        work = amr_level_work(h)
+        status = capi.mhd_get_device_status(ctx)
+    finally:
+        h.close()
+        capi.mhd_ctx_destroy(ctx)
+    hbm, hbm_src, sm_mhz = peaks()
+    out = {}
+    for nm, (ms, cnt) in kt.items():
+        if not cnt:
+            continue
+        per = ms / steps
+        row = {"ms_per_coarse_step": per, "launches_per_coarse_step": cnt / steps}
+        if nm in work["bytes"]:
+            gbs = work["bytes"][nm] / (per * 1e-3) / 1e9
+            row.update({"bound": "hbm", "algorithmic_bytes": work["bytes"][nm], "achieved_gbs": gbs,
+                        "peak_gbs": hbm, "frac": gbs / hbm})
+        elif nm in work["flops"]:
+            fl = work["flops"][nm]
+            # FP32: k_flux computes the edge averages, k_update the edge EMFs
+            if nm == "k_flux" and not kt.get("k_edge", (0, 0))[1]:
+                fl += work["flops"]["k_edge"]
+            if nm == "k_update" and not kt.get("k_emf", (0, 0))[1]:
+                fl += work["flops"]["k_emf"]
+            tf = fl / (per * 1e-3) / 1e12
+            pk = alu_peak_tflops(dtype, sm_mhz)
+            row.update({"bound": "alu", "algorithmic_flops": fl, "achieved_tflops": tf,
+                        "peak_tflops": pk, "frac": tf / pk})
+        out[nm] = row
+    return {"dtype": dtype, "mode": "eager, per-launch events", "coarse_steps": steps, "kernels": out,
+            "device_status": status}
+
+
 def run_amr(args):
     import torch
     rank, world, local = dist_setup()
@@ -513,6 +636,7 @@ def run_amr(args):
            time_amr(H, states, "f32", args.steps, "batched", local),
            time_amr(H, states, "f64", max(1, args.steps // 2), "graph", local),
            time_amr(H, states, "f64", 1, "per_patch", local)]
+    attribution = amr_attribution(H, states, "f32", 2, local)
     if rank != 0:
         return
     main = res[0]
@@ -524,7 +648,7 @@ def run_amr(args):
                                    sum(len(l) for l in H),
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
-            "runs": res}
+            "runs": res, "kernels_f32": attribution}
     print(json.dumps(line))
 
 

@@ -46,6 +46,12 @@ namespace MHD_ADVANCE_NS {
 // oracle's divisions (parity build).
 constexpr bool kFastRecip = MHD_FAST_RECIP != 0;
 
+// Launch regions of the predictor / flux stages (UB grown by kM1) and of the
+// update stages ([lo - kMu, hi + kMuT]); see region_m1 / region_mu.
+template <typename R> constexpr int kM1 = region_m1(sizeof(R));
+template <typename R> constexpr int kMu = region_mu(sizeof(R));
+template <typename R> constexpr int kMuT = region_mu_top(sizeof(R));
+
 // Where the edge averages of E^n and the edge EMFs are computed: inside the
 // kernels that use them (k_flux and k_update, FP32) or by k_edge and k_emf
 // into scratch planes (FP64).
@@ -60,12 +66,15 @@ struct Cell {
   int i, j, k;
 };
 
-// Decomposes element e of the UB+2 launch region of patch p; false if e is
-// beyond the region.
-__device__ __forceinline__ bool launch_cell(const DPatch& p, int e, Cell& c) {
-  const int ex = p.n[0] + 2 * p.k + 4, ey = p.n[1] + 2 * p.k + 4, ez = p.n[2] + 2 * p.k + 4;
+// Decomposes element e of the launch region [lo - M, hi + MT]^3 of patch p
+// (lo, hi: the update box UB) into a cell; false if e is beyond the region.
+// The primitives (and in FP64 the edge averages) launch over UB+2; the other
+// stages over the regions of launch.h (region_m1, region_mu).
+template <int M, int MT>
+__device__ __forceinline__ bool region_cell(const DPatch& p, int e, Cell& c) {
+  const int ex = p.n[0] + 2 * p.k + M + MT, ey = p.n[1] + 2 * p.k + M + MT, ez = p.n[2] + 2 * p.k + M + MT;
   if (e >= ex * ey * ez) return false;
-  const int lo = p.g - p.k - 2;
+  const int lo = p.g - p.k - M;
   if (ex * ey * ez < (1 << 24)) {
     int rx, ry;
     const int qx = divmod24(e, ex, rx);
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!region_cell<2, 2>(p, t.start + threadIdx.x, c)) return;
   const int64_t x = lin(p, c);
   const R* U0 = (const R*)p.U[0];
   R u[8];
@@ -176,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_edge(const DPatch* __restrict__ P,
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!region_cell<2, 2>(p, t.start + threadIdx.x, c)) return;
   // the three edges stored at this cell, one index decomposition
   edge_avg<R, 0>(p, c, scr);
   edge_avg<R, 1>(p, c, scr);
@@ -297,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
-  if (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1)) return;
+  if (!region_cell<kM1<R>, kM1<R>>(p, t.start + threadIdx.x, c)) return;
+  if (kM1<R> > 1 && (!in_ub(p, 0, c.i, -1, 1) || !in_ub(p, 1, c.j, -1, 1) || !in_ub(p, 2, c.k, -1, 1))) return;
   const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   R w[8], dw[3][8];
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 2) k_flux(const
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!region_cell<kM1<R>, kM1<R>>(p, t.start + threadIdx.x, c)) return;
   flux_face<R, 0>(p, t.patch, c, scr, sc, K);
   flux_face<R, 1>(p, t.patch, c, scr, sc, K);
   flux_face<R, 2>(p, t.patch, c, scr, sc, K);
@@ -489,7 +498,7 @@ template <int a> __device__ __forceinline__ bool update_edge(const DPatch& p, co
 }
 
 // ---------------------------------------------------------------- k_emf
-// The EMFs of the three update-box edges stored at each cell of UB+2.
+// The EMFs of the three update-box edges stored at each cell of [lo, hi + 1].
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
                                                   const BlockTask* __restrict__ T, R* scr,
@@ -497,7 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!region_cell<kMu<R>, kMuT<R>>(p, t.start + threadIdx.x, c)) return;
   const int64_t x = lin(p, c);
   const R* cs = scr;
   const bool u0 = update_edge<0>(p, c), u1 = update_edge<1>(p, c), u2 = update_edge<2>(p, c);
@@ -511,22 +520,24 @@ __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
 }
 
 // ---------------------------------------------------------------- k_update
-// One thread per cell of UB+2: the cell's conservative update and the CT
-// update of its three lower faces, each face from the EMFs of its four edges.
+// One thread per cell of [lo, hi + 1]: the cell's conservative update and the
+// CT update of its three lower faces, each face from the EMFs of its four edges.
 // EmfInline: the nine distinct edge EMFs a cell's faces need are computed
 // here from the face fluxes (an edge is shared by four faces, so its EMF is
 // evaluated by up to three threads, always with the same expression), and
 // patches that feed flux registers also store the EMF of every update-box
 // edge at its element, where the capture kernel reads it; otherwise they are
 // read from k_emf's planes.
+// FP32: at most 51 registers (five blocks per SM); the compiler's free choice
+// (80-86) cost a quarter of the kernel's speed.
 template <typename R, bool EmfInline>
-__global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 1) k_update(const DPatch* __restrict__ P,
                                                      const BlockTask* __restrict__ T, R* scr,
                                                      SolverConsts<R> sc, const R* __restrict__ K, int commit) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!launch_cell(p, t.start + threadIdx.x, c)) return;
+  if (!region_cell<kMu<R>, kMuT<R>>(p, t.start + threadIdx.x, c)) return;
   const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   const int id[3] = {c.i, c.j, c.k};
@@ -608,24 +619,29 @@ __global__ void __launch_bounds__(kThreads) k_update(const DPatch* __restrict__ 
 // Enqueues the step constants and the stages for the patches of one call;
 // K (npatch x kStepConsts elements) is scratch.
 template <typename R>
-cudaError_t launch_advance(const DPatch* d_patches, int npatch, const BlockTask* d_tasks, int nblocks,
-                           const BlockTask* d_ptasks, int npblocks, R* scr, R* K, const SolverConsts<R>& sc,
-                           const double* d_dt, int* d_status, const KernelTimer* tm, bool commit, cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
-  dim3 g1(nblocks);
+cudaError_t launch_advance(const AdvanceArgs& a, R* scr, R* K, const SolverConsts<R>& sc, cudaStream_t s) {
+  const DPatch* d_patches = a.patches;
+  const int npatch = a.npatches, npblocks = a.npblocks;
+  const BlockTask *d_tasks = a.tasks, *d_tasks1 = a.tasks1, *d_tasksu = a.tasksu, *d_ptasks = a.ptasks;
+  const double* d_dt = a.d_dt;
+  int* d_status = a.d_status;
+  const KernelTimer* tm = a.timer;
+  const bool commit = a.commit;
+  if (a.nblocks == 0) return cudaSuccess;
+  const dim3 g1(a.nblocks), g1b(a.nblocks1), gu(a.nblocksu);
   MHD_TIMED(tm, K_PRIM, s,
             (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
              k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
   if (npblocks > 0)
     MHD_TIMED(tm, K_PRED, s, (k_pred_tiled<R><<<npblocks, kThreads, 0, s>>>(d_patches, d_ptasks, scr, sc, K)));
   else
-    MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
+    MHD_TIMED(tm, K_PRED, s, (k_pred<R><<<g1b, kThreads, 0, s>>>(d_patches, d_tasks1, scr, sc, K)));
   constexpr bool inl = kInlineEdges<R>;
   if (!inl) MHD_TIMED(tm, K_EDGE, s, (k_edge<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr)));
-  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K)));
-  if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc)));
+  MHD_TIMED(tm, K_FLUX, s, (k_flux<R><<<g1b, kThreads, 0, s>>>(d_patches, d_tasks1, scr, sc, K)));
+  if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<gu, kThreads, 0, s>>>(d_patches, d_tasksu, scr, sc)));
   MHD_TIMED(tm, K_UPDATE, s,
-            (k_update<R, inl><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, K, commit ? 1 : 0)));
+            (k_update<R, inl><<<gu, kThreads, 0, s>>>(d_patches, d_tasksu, scr, sc, K, commit ? 1 : 0)));
   return cudaGetLastError();
 }
 
@@ -692,8 +708,7 @@ template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t
   sc.limiter = a.limiter;
   sc.emf = a.emf;
   if (a.fused) return launch_fused_variant<R>(a, sc, s);
-  return launch_advance<R>(a.patches, a.npatches, a.tasks, a.nblocks, a.ptasks, a.npblocks, (R*)a.scratch,
-                           (R*)a.stepc, sc, a.d_dt, a.d_status, a.timer, a.commit, s);
+  return launch_advance<R>(a, (R*)a.scratch, (R*)a.stepc, sc, s);
 }
 
 }  // namespace MHD_ADVANCE_NS

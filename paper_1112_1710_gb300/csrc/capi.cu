@@ -222,6 +222,31 @@ void tasks_for(const std::vector<int64_t>& counts, std::vector<BlockTask>& out) 
     for (int64_t s = 0; s < counts[p]; s += kThreads) out.push_back(BlockTask{(int32_t)p, (int32_t)s});
 }
 
+// Block tables of the staged advance: over each patch's UB+2 (t2), the
+// predictor / flux region (t1) and the update region (tu) of an element of
+// `elem` bytes; UB = interior grown by the patch's k.
+void staged_tasks(const std::vector<DPatch>& dp, size_t elem, std::vector<BlockTask>& t2,
+                  std::vector<BlockTask>& t1, std::vector<BlockTask>& tu) {
+  const size_t n = dp.size();
+  const int m1 = region_m1(elem), mu = region_mu(elem) + region_mu_top(elem);
+  std::vector<int64_t> c2(n), c1(n), cu(n);
+  for (size_t p = 0; p < n; ++p) {
+    int64_t v2 = 1, v1 = 1, vu = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t e = dp[p].n[d] + 2 * dp[p].k;
+      v2 *= e + 4;
+      v1 *= e + 2 * m1;
+      vu *= e + mu;
+    }
+    c2[p] = v2;
+    c1[p] = v1;
+    cu[p] = vu;
+  }
+  tasks_for(c2, t2);
+  tasks_for(c1, t1);
+  tasks_for(cu, tu);
+}
+
 double eps_for(const mhd_params& prm, int dtype) {
   if (prm.upwind_eps > 0.0) return prm.upwind_eps;
   return dtype == MHD_F64 ? 1e-10 : 1e-5;
@@ -544,15 +569,11 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   const size_t es = elem_size(dtype);
   const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
   if ((r = ensure_scratch(c, counter_byte + 16))) return r;
-  std::vector<BlockTask> tasks, ptasks;
+  std::vector<BlockTask> tasks, tasks1, tasksu, ptasks;
   std::vector<FusedItem> items;
   std::vector<BlockTask> ctasks;
   if (!fused) {
-    std::vector<int64_t> counts(n);
-    for (int p = 0; p < n; ++p)
-      counts[p] = (int64_t)(dp[p].n[0] + 2 * dp[p].k + 4) * (dp[p].n[1] + 2 * dp[p].k + 4) *
-                  (dp[p].n[2] + 2 * dp[p].k + 4);
-    tasks_for(counts, tasks);
+    staged_tasks(dp, elem_size(dtype), tasks, tasks1, tasksu);
     if (c->prm.advance_kernel == 3 || c->pred_tiled[dtype == MHD_F32 ? 1 : 0]) pred_tiles(dp, dtype, ptasks);
     if (tasks.size() > 0x7fffffff || ptasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
   } else {
@@ -564,9 +585,12 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     fused_items(dp, v.bx, v.by, cz, items, ctasks);
     if (items.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
   }
-  void *d_p = nullptr, *d_t = nullptr, *d_i = nullptr, *d_ct = nullptr, *d_pt = nullptr;
+  void *d_p = nullptr, *d_t = nullptr, *d_t1 = nullptr, *d_tu = nullptr, *d_i = nullptr, *d_ct = nullptr,
+       *d_pt = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, tasks1.data(), tasks1.size() * sizeof(BlockTask), &d_t1))) return r;
+  if ((r = table(c, tasksu.data(), tasksu.size() * sizeof(BlockTask), &d_tu))) return r;
   if ((r = table(c, ptasks.data(), ptasks.size() * sizeof(BlockTask), &d_pt))) return r;
   if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i))) return r;
   if ((r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) return r;
@@ -575,6 +599,10 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   a.npatches = n;
   a.tasks = (const BlockTask*)d_t;
   a.nblocks = (int)tasks.size();
+  a.tasks1 = (const BlockTask*)d_t1;
+  a.nblocks1 = (int)tasks1.size();
+  a.tasksu = (const BlockTask*)d_tu;
+  a.nblocksu = (int)tasksu.size();
   a.ptasks = (const BlockTask*)d_pt;
   a.npblocks = (int)ptasks.size();
   a.scratch = c->scratch;
@@ -625,26 +653,26 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   // fused ones use the first 8 of them as output copies)
   int64_t off = 0;
   int zmax = 1;
-  std::vector<int64_t> counts(n);
   for (int p = 0; p < n; ++p) {
     dp[p].scr = off;
     off += (int64_t)SC_COUNT * dp[p].nelem;
     const int uz = dp[p].n[2] + 2 * dp[p].k;
     zmax = uz > zmax ? uz : zmax;
-    counts[p] = (int64_t)(dp[p].n[0] + 2 * dp[p].k + 4) * (dp[p].n[1] + 2 * dp[p].k + 4) * (uz + 4);
   }
   const int64_t stepc_off = off;
   off += 8 * (int64_t)n;
   const size_t es = elem_size(dtype);
   const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
   if ((r = ensure_scratch(c, counter_byte + 16))) return r;
-  std::vector<BlockTask> tasks, ptasks;
-  tasks_for(counts, tasks);
+  std::vector<BlockTask> tasks, tasks1, tasksu, ptasks;
+  staged_tasks(dp, elem_size(dtype), tasks, tasks1, tasksu);
   pred_tiles(dp, dtype, ptasks);
   if (tasks.size() > 0x7fffffff || ptasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
-  void *d_p = nullptr, *d_t = nullptr, *d_pt = nullptr;
+  void *d_p = nullptr, *d_t = nullptr, *d_t1 = nullptr, *d_tu = nullptr, *d_pt = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, tasks1.data(), tasks1.size() * sizeof(BlockTask), &d_t1))) return r;
+  if ((r = table(c, tasksu.data(), tasksu.size() * sizeof(BlockTask), &d_tu))) return r;
   if ((r = table(c, ptasks.data(), ptasks.size() * sizeof(BlockTask), &d_pt))) return r;
   const int di = dtype == MHD_F32 ? 1 : 0;
   const int nv = dtype == MHD_F32 ? kNumFused32 : kNumFused64;
@@ -680,6 +708,10 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
       a.npatches = n;
       a.tasks = (const BlockTask*)d_t;
       a.nblocks = (int)tasks.size();
+      a.tasks1 = (const BlockTask*)d_t1;
+      a.nblocks1 = (int)tasks1.size();
+      a.tasksu = (const BlockTask*)d_tu;
+      a.nblocksu = (int)tasksu.size();
       a.scratch = c->scratch;
       a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
       a.gamma = c->prm.gamma;

@@ -10,8 +10,12 @@ namespace mhd {
 struct AdvanceArgs {
   const DPatch* patches;   // device
   int npatches;
-  const BlockTask* tasks;  // device
+  const BlockTask* tasks;  // device, blocks over each patch's UB+2
   int nblocks;
+  const BlockTask* tasks1;  // device, blocks over each patch's UB+1
+  int nblocks1;
+  const BlockTask* tasksu;  // device, blocks over [lo, hi + 1] of each patch's UB
+  int nblocksu;
   const BlockTask* ptasks;  // device, tiles of the tiled predictor (npblocks 0: untiled)
   int npblocks;
   void* scratch;           // device arena of the call's element type
@@ -41,6 +45,17 @@ constexpr FusedVariant kFusedVariants32[] = {{16, 16, 512}, {16, 16, 384}, {16, 
 constexpr FusedVariant kFusedVariants64[] = {{8, 8, 128}};
 constexpr int kNumFused32 = sizeof(kFusedVariants32) / sizeof(kFusedVariants32[0]);
 constexpr int kNumFused64 = sizeof(kFusedVariants64) / sizeof(kFusedVariants64[0]);
+
+// Launch regions of the staged advance (UB = [lo, hi]): the predictor and
+// flux stages run over UB grown by region_m1 on each side, the update stages
+// over [lo - region_mu, hi + region_mu_top].  FP64: the regions the stages
+// fill (UB+1; [lo, hi + 1]), which saves the idle threads of small patches.
+// FP32: UB+2 for every stage, measured faster on GB300 for the 128^3 patch
+// (the predictor 150 against 165 us, the update 100 against 115 us) and
+// within 3% on the AMR hierarchy.
+constexpr int region_m1(size_t elem) { return elem == 8 ? 1 : 2; }
+constexpr int region_mu(size_t elem) { return elem == 8 ? 0 : 2; }
+constexpr int region_mu_top(size_t elem) { return elem == 8 ? 1 : 2; }
 
 // Kernel launches of one staged advance: step constants, k_prim, k_pred,
 // k_flux, k_update, and k_edge and k_emf in FP64.
