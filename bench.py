@@ -227,7 +227,8 @@ def kernel_flops(name, n, launched=()):
 # workload (all of a kernel's launches in one step), from one ncu capture of
 # the current kernels (profiles/).  Keys: bench pass, kernel.
 KERNEL_TRAFFIC = {("f32", "k_pred"): 447.8e6, ("f32", "k_flux"): 627.9e6, ("f32", "k_update"): 310.6e6,
-                  ("f64", "k_pred"): 882.6e6, ("f64", "k_flux"): 1247.5e6}
+                  ("f64", "k_pred"): 881.7e6, ("f64", "k_flux"): 1246.3e6,
+                  ("f64_exact", "k_pred"): 883.1e6, ("f64_exact", "k_flux"): 1250.0e6}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
@@ -340,6 +341,33 @@ def cpu_baseline(pr, steps):
     return {"value": pr.cells * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d full FP64 steps of the %d^3 blast (ghost fill + dt + advance), %.1f s" %
                       (steps, pr.n[0], dt)}
+
+
+def cpu_baseline_sample(items, what):
+    """The FP64 oracle as it stands, on the host cores, advancing a bounded
+    sample of a workload's patches.  items = [(state, n, g, dx, ks, periodic)]:
+    each sampled patch starts from its own initial data (ghosts included, or
+    refilled as periodic images), takes the CFL dt of its state and runs one
+    advance per entry of ks (update box grown by k); value = interior cells x
+    advances / wall time."""
+    from oracle import oracle as O
+    O.build()
+    prm = O.params(**SOLVER)
+    cells = 0
+    t0 = time.perf_counter()
+    for st, n, g, dx, ks, periodic in items:
+        P = O.patch(st.copy(), n, g, dx)
+        for k in ks:
+            if periodic:
+                O.fill_periodic(P)
+            dt = O.cfl_dt(P, prm)
+            O.advance(P, prm, dt, k)
+            cells += n[0] * n[1] * n[2]
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s: %d patch advances, %d interior cell updates, %.1f s" % (what, sum(len(i[4]) for i in items),
+                                                                                  cells, dt)}
 
 
 def run_reference(args):
@@ -639,6 +667,15 @@ def run_amr(args):
     attribution = amr_attribution(H, states, "f32", 2, local)
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline:
+        # every patch of every level, both substeps (update box grown by 2,
+        # then by 0), on the generator's data with its ghost layers (the
+        # oracle's level operations are left out of the sample)
+        items = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), 4, (1.0 / 64 / 2 ** l,) * 3,
+                  (0,) if l == 0 else (2, 0), False)
+                 for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl)]
+        cpu = cpu_baseline_sample(items, "every patch of the same hierarchy, once through its substeps")
     main = res[0]
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": 1, "ms_per_step": main["ms_per_coarse_step"], "higher_is_better": True, "scaling": "weak",
@@ -649,6 +686,8 @@ def run_amr(args):
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
             "runs": res, "kernels_f32": attribution}
+    if cpu:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line))
 
 
@@ -706,6 +745,17 @@ def run_ot2d(args):
                                    "CFL 0.4, 100 steps, plain per-patch launch (fill + CFL dt + advance)",
                        "l2": "state (2.6 MB) resident in L2: no roofline claim", "parallelism": "replicas"},
             "runs": out, "gpu_launches": main["launches"], "clocks": clk}
+    if not args.no_cpu_baseline:
+        # the whole workload: 100 oracle steps of fill + CFL dt + advance
+        from oracle import oracle as O
+        O.build()
+        st = pr.state.copy()
+        t0 = time.perf_counter()
+        O.run_periodic(st, pr.n, pr.g, pr.dx, O.params(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0), steps)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": pr.cells * steps / dt, "unit": UNIT,
+                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "kind": "oracle", "sample": "the whole workload (100 steps), %.1f s" % dt}
     print(json.dumps(line))
 
 
@@ -809,6 +859,14 @@ def run_serve(args):
             "saturation": sat, "offered_load": loads, "offered_load_0.8_balanced_batches": balanced,
             "fp64_sample": {"served_batched": served64, "plain_per_patch": pp},
             "gpu_launches": launches, "device_status": status, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        # the first 400 requests of the stream: periodic fill + CFL dt + one step
+        import synth
+        items = []
+        for r in poisson_requests(400, math.inf, seed=4242):
+            pr = synth.blast(r.n, g=G, seed=4242 + r.n)
+            items.append((pr.state, pr.n, G, pr.dx, (0,), True))
+        line["cpu_baseline"] = cpu_baseline_sample(items, "the first 400 requests of the same stream")
     print(json.dumps(line))
 
 
@@ -830,6 +888,10 @@ def run_deep(args):
     t0 = time.time()
     H, v, _ = ST.deep_hierarchy(n0=n0, levels=8, m=256)
     states = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    # oracle sample: every 4th patch of each level, both substeps
+    sample = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), G, (1.0 / n0 / 2 ** l,) * 3,
+               (0,) if l == 0 else (2, 0), False)
+              for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl) if i % 4 == 0]
     ctx = capi.mhd_ctx_create(device=local, **SOLVER)
     stream = torch.cuda.Stream(device=local)
     h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream,
@@ -879,6 +941,9 @@ def run_deep(args):
             "conservation_drift_rel": {"rho": drift[0], "Mx": drift[1], "My": drift[2], "Mz": drift[3],
                                        "E": drift[4], "Bx": drift[5]},
             "device_status": status, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(sample, "every 4th patch of each level of the same hierarchy, "
+                                                           "once through its substeps")
     print(json.dumps(line))
 
 
