@@ -597,6 +597,34 @@ def amr_level_work(h):
                       "k_reflux": ref, "k_cfl": cfl}, "flops": flops}
 
 
+def time_metadata(H, n0, local):
+    """Seconds to build the AMR metadata (ghost copies, prolongation and
+    restriction items, flux registers) by testing every pair of patches on the
+    host, and from the device AMR tree (Sec. 3.1: parents and inherited
+    interactions on the GPU, then the same list construction over each patch's
+    candidates); both give the same lists (tests/test_gpu_tree.py)."""
+    import torch
+
+    import synth
+    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300.tree import DeviceTree
+    fake = [[synth.empty_patch(tuple(hi[d] - lo[d] + 1 for d in range(3)), 4, dtype=np.float32) for lo, hi in bl]
+            for bl in H]
+    kw = dict(g=4, dtype="f32", device="cpu")
+    DeviceTree(H, n0, 5, device="cuda:%d" % local)  # warm-up (library, allocator)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree = DeviceTree(H, n0, 5, device="cuda:%d" % local)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    Hierarchy(H, n0, fake, (1.0 / n0,) * 3, tree=tree, **kw)
+    t2 = time.perf_counter()
+    Hierarchy(H, n0, fake, (1.0 / n0,) * 3, tree=False, **kw)
+    t3 = time.perf_counter()
+    return {"device_tree_s": t1 - t0, "lists_from_tree_s": t2 - t1, "tree_total_s": t2 - t0,
+            "all_pairs_s": t3 - t2, "patches": sum(len(b) for b in H)}
+
+
 def amr_attribution(H, states, dtype, steps, local):
     """Per-kernel device time of eager coarse steps (CUDA events around every
     launch) against each kernel's roofline: HBM for the level operations
@@ -665,6 +693,7 @@ def run_amr(args):
            time_amr(H, states, "f64", max(1, args.steps // 2), "graph", local),
            time_amr(H, states, "f64", 1, "per_patch", local)]
     attribution = amr_attribution(H, states, "f32", 2, local)
+    meta = time_metadata(H, 64, local)
     if rank != 0:
         return
     cpu = None
@@ -685,7 +714,7 @@ def run_amr(args):
                                    sum(len(l) for l in H),
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
-            "runs": res, "kernels_f32": attribution}
+            "runs": res, "kernels_f32": attribution, "metadata": meta}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))

@@ -332,6 +332,43 @@ mhd_status mhd_get_device_status(mhd_ctx *ctx, int32_t *out);
 /* Library version and build flags (for logs). */
 const char *mhd_version(void);
 
+/* ---- AMR tree on the device (Sec. 3.1: neighbour inheritance) ----------
+ * Boxes are int32 device arrays lo[3 n], hi[3 n] (inclusive, level index
+ * space, x first).  CSR offsets are int64 device arrays of length n + 1.
+ * Both calls are pure functions of their device inputs (no context, nothing
+ * allocated); each runs in two passes: with the output list NULL it writes
+ * one count per element into d_count, with it non-NULL it writes the entries
+ * of element i at positions d_off[i] ... (offsets from the counts).  They
+ * enqueue one kernel on `stream` and return MHD_EINVAL for bad arguments
+ * (nothing launched) or MHD_ECUDA if the launch fails. */
+
+/* Parents of nf fine boxes (level l+1) among nc coarse boxes (level l): the
+ * coarse boxes that meet the fine box coarsened by 2 ([floor(lo/2),
+ * floor(hi/2)]), listed in increasing index order.  A fine box of a properly
+ * nested hierarchy lies inside the union of its parents. */
+mhd_status mhd_tree_parents(const int32_t *d_flo, const int32_t *d_fhi, int32_t nf, const int32_t *d_clo,
+                            const int32_t *d_chi, int32_t nc, const int64_t *d_off, int32_t *d_count,
+                            int32_t *d_list, void *stream);
+
+/* Interactions of the n boxes of level l+1 inherited from level l (Sec. 3.1:
+ * the neighbours of a node's children are children of the node's
+ * neighbours).  For box c: every (c', s) such that c' is a child of P' (kid
+ * CSR of level l, the transpose of the parents lists), (P', s) is an
+ * interaction of a parent P of c (par CSR of the children; int CSR of level
+ * l with shifts s in {-1, 0, 1}^3 as three int8 per entry), and box(c') + s
+ * ndom meets box(c) grown by r cells (ndom: cells per side of the periodic
+ * level-(l+1) domain).  Entries come in loop order (parents, their
+ * interactions, their children) and may repeat; (c, 0) itself is included.
+ * If the level-l interactions hold every pair at range r, the output holds
+ * every such pair of level l+1 (nesting makes the inheritance complete).  A
+ * virtual root (one parent of every level-0 box, interacting with itself
+ * under all 27 shifts) gives the brute-force pairs of level 0. */
+mhd_status mhd_tree_inherit(const int32_t *d_lo, const int32_t *d_hi, int32_t n, int32_t ndom, int32_t r,
+                            const int64_t *d_par_off, const int32_t *d_par, const int64_t *d_int_off,
+                            const int32_t *d_int, const int8_t *d_int_shift, const int64_t *d_kid_off,
+                            const int32_t *d_kid, const int64_t *d_out_off, int32_t *d_count, int32_t *d_out,
+                            int8_t *d_out_shift, void *stream);
+
 /* Number of kernels this context has enqueued so far (for launch accounting). */
 int64_t mhd_launch_count(const mhd_ctx *ctx);
 

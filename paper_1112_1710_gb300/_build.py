@@ -26,6 +26,7 @@ UNITS = {
     "advance_f32.cu": ["--fmad=true", "--use_fast_math"],
     "noalloc.cu": ["--fmad=false"],
     "amr_ops.cu": ["--fmad=false"],
+    "tree.cu": [],
 }
 
 

@@ -36,12 +36,26 @@ def _isect(alo, ahi, blo, bhi):
 
 
 def _vol(lo, hi):
-    return int(np.prod(np.asarray(hi) - np.asarray(lo) + 1))
+    return (int(hi[0]) - int(lo[0]) + 1) * (int(hi[1]) - int(lo[1]) + 1) * (int(hi[2]) - int(lo[2]) + 1)
+
+
+# numpy layouts of mhd_capture and mhd_deposit (include/mhd_gpu.h), for
+# filling the ctypes arrays of long lists in one copy
+_CAP_DT = np.dtype([("patch", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("mode", "<i4"), ("lo", "<i4", 3),
+                    ("hi", "<i4", 3), ("dst", "<u8")])
+_DEP_DT = np.dtype([("coarse", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("pad", "<i4"), ("lo", "<i4", 3),
+                    ("hi", "<i4", 3), ("flo", "<i4", 3), ("fhi", "<i4", 3), ("fine", "<u8"), ("creg", "<u8")])
 
 
 class Hierarchy:
-    def __init__(self, boxes, n0, states, dx0, g=4, dtype="f32", ctx=None, stream=None, device="cuda"):
-        """boxes[l] = [(lo, hi)]; states[l][i] = float64 numpy array (synth layout)."""
+    def __init__(self, boxes, n0, states, dx0, g=4, dtype="f32", ctx=None, stream=None, device="cuda",
+                 tree=None):
+        """boxes[l] = [(lo, hi)]; states[l][i] = float64 numpy array (synth layout).
+
+        tree: build the metadata from the device AMR tree (neighbour
+        inheritance, Sec. 3.1; the default on a GPU; a tree.DeviceTree of the
+        same boxes may be passed) instead of testing every pair of patches;
+        both give the same lists in the same order."""
         self.n0, self.g, self.dtype = n0, g, dtype
         self.device = torch.device(device)
         self.gpu = self.device.type == "cuda"  # on the CPU only the metadata is built (tests)
@@ -61,6 +75,12 @@ class Hierarchy:
         self.lo = [np.array([p.lo for p in pats], dtype=np.int64) for pats in self.levels]
         self.hi = [np.array([p.hi for p in pats], dtype=np.int64) for pats in self.levels]
         self.d_dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.tree = None
+        if tree is not None and not isinstance(tree, bool):
+            self.tree = tree
+        elif tree if tree is not None else self.gpu:
+            from .tree import DeviceTree
+            self.tree = DeviceTree(boxes, n0, g + 1, device=self.device)
         self._build()
 
     @property
@@ -76,6 +96,8 @@ class Hierarchy:
         n = self.n0 * 2 ** l
         g = self.g
         lo, hi = self.lo[l], self.hi[l]
+        if self.tree is not None:
+            return self._copies_tree(l)
         near = np.any(lo <= g + 1, axis=1) | np.any(hi >= n - g - 2, axis=1)
         shifts = [(0, 0, 0)]
         if near.any():
@@ -101,11 +123,43 @@ class Hierarchy:
                     out.append(c)
         return out
 
+    def _copies_tree(self, l):
+        """The same copies from the tree's interactions of each destination,
+        already in (shift, source) order."""
+        n = self.n0 * 2 ** l
+        g = self.g
+        lo, hi = self.lo[l], self.hi[l]
+        out = []
+        for di in range(len(lo)):
+            idx, s = self.tree.interactions(l, di)
+            keep = (idx != di) | np.any(s != 0, axis=1)
+            idx, sh = idx[keep], s[keep].astype(np.int64) * n
+            blo = np.maximum(lo[idx] + sh, lo[di] - g - 1)
+            bhi = np.minimum(hi[idx] + sh, hi[di] + g + 1)
+            for k in range(len(idx)):
+                c = capi.mhd_copy()
+                c.src = int(idx[k])
+                c.dst = int(di)
+                c.box.lo[:] = [int(v) for v in blo[k]]
+                c.box.hi[:] = [int(v) for v in bhi[k]]
+                c.offset[:] = [int(-v) for v in sh[k]]
+                out.append(c)
+        return out
+
+    def _coarse(self, l, fi):
+        """Level-l patches that can touch fine patch fi of level l+1, ascending:
+        all of them, or the tree's candidates."""
+        if self.tree is None:
+            return np.arange(len(self.lo[l]))
+        return self.tree.coarse_candidates(l + 1, fi)
+
     def _prolongs(self, l):
         g = self.g
         clo, chi = self.lo[l], self.hi[l]
         out = []
         for fi, (flo, fhi) in enumerate(zip(self.lo[l + 1], self.hi[l + 1])):
+            cand = self._coarse(l, fi)
+            clo, chi = self.lo[l][cand], self.hi[l][cand]
             el, eh = flo - g, fhi + g
             slabs = [((el[0], el[1], el[2]), (eh[0], eh[1], flo[2] - 1)),
                      ((el[0], el[1], fhi[2] + 1), (eh[0], eh[1], eh[2])),
@@ -117,25 +171,26 @@ class Hierarchy:
                 cl = np.array(slo) // 2
                 ch = np.array(shi) // 2
                 blo, bhi, ok = _isect(clo, chi, cl, ch)
-                for ci in np.nonzero(ok)[0]:
+                for k in np.nonzero(ok)[0]:
                     it = capi.mhd_prolong_item()
-                    it.coarse = int(ci)
+                    it.coarse = int(cand[k])
                     it.fine = int(fi)
-                    it.box = capi.box(blo[ci], bhi[ci])
+                    it.box = capi.box(blo[k], bhi[k])
                     out.append(it)
         return out
 
     def _restricts(self, l):
-        clo, chi = self.lo[l], self.hi[l]
         out = []
         for fi, (flo, fhi) in enumerate(zip(self.lo[l + 1], self.hi[l + 1])):
+            cand = self._coarse(l, fi)
+            clo, chi = self.lo[l][cand], self.hi[l][cand]
             cl, ch = flo // 2, (fhi + 1) // 2 - 1
             blo, bhi, ok = _isect(clo - 1, chi + 1, cl, ch)
-            for ci in np.nonzero(ok)[0]:
+            for k in np.nonzero(ok)[0]:
                 it = capi.mhd_restrict_item()
                 it.fine = int(fi)
-                it.coarse = int(ci)
-                it.box = capi.box(blo[ci], bhi[ci])
+                it.coarse = int(cand[k])
+                it.box = capi.box(blo[k], bhi[k])
                 out.append(it)
         return out
 
@@ -155,8 +210,9 @@ class Hierarchy:
             return len(regs) - 1
 
         for l in range(1, L):
-            clo_all, chi_all = self.lo[l - 1], self.hi[l - 1]
             for fi, (flo, fhi) in enumerate(zip(self.lo[l], self.hi[l])):
+                cand = self._coarse(l - 1, fi)
+                clo_all, chi_all = self.lo[l - 1][cand], self.hi[l - 1][cand]
                 for d in range(3):
                     for side in (0, 1):
                         fidx = int(flo[d]) if side == 0 else int(fhi[d]) + 1
@@ -171,16 +227,17 @@ class Hierarchy:
                         cl = cl.copy()
                         ch = ch.copy()
                         cl[d] = ch[d] = cidx
-                        for ci in range(len(clo_all)):
-                            if not (clo_all[ci][d] <= outc <= chi_all[ci][d]):
+                        for k in range(len(clo_all)):
+                            ci = int(cand[k])
+                            if not (clo_all[k][d] <= outc <= chi_all[k][d]):
                                 continue
                             blo, bhi = cl.copy(), ch.copy()
                             ok = True
                             for e in range(3):
                                 if e == d:
                                     continue
-                                blo[e] = max(cl[e], clo_all[ci][e])
-                                bhi[e] = min(ch[e], chi_all[ci][e])
+                                blo[e] = max(cl[e], clo_all[k][e])
+                                bhi[e] = min(ch[e], chi_all[k][e])
                                 ok = ok and blo[e] <= bhi[e]
                             if not ok:
                                 continue
@@ -203,25 +260,27 @@ class Hierarchy:
                             top = chi_all + 1
                             top[:, a] -= 1
                             blo, bhi, ok = _isect(clo_all, top, cl, ch)
-                            for ci in np.nonzero(ok)[0]:
-                                rc = new_reg(_vol(blo[ci], bhi[ci]))
-                                coarse_caps[l - 1].append((int(ci), 1, a, blo[ci], bhi[ci], rc))
-                                deposits[l - 1].append((int(ci), 1, a, blo[ci], bhi[ci], re, elo, ehi, rc))
+                            for k in np.nonzero(ok)[0]:
+                                ci = int(cand[k])
+                                rc = new_reg(_vol(blo[k], bhi[k]))
+                                coarse_caps[l - 1].append((ci, 1, a, blo[k], bhi[k], rc))
+                                deposits[l - 1].append((ci, 1, a, blo[k], bhi[k], re, elo, ehi, rc))
         offs = np.concatenate([[0], np.cumsum(regs)]).astype(np.int64)
         self.regbuf = torch.zeros(max(1, int(offs[-1])), dtype=torch.float64, device=self.device)
         base = self.regbuf.data_ptr()
-        ptr = lambda r: base + 8 * int(offs[r])
 
         def cap_array(items, mode_fine):
-            arr = (capi.mhd_capture * max(1, len(items)))()
-            for t, (p, kind, ax, lo, hi, r, fine_side) in enumerate(items):
-                arr[t].patch = int(p)
-                arr[t].kind = kind
-                arr[t].axis = ax
-                arr[t].mode = mode_fine if fine_side else 0
-                arr[t].box = capi.box(lo, hi)
-                arr[t].dst = ptr(r)
-            return arr, len(items)
+            # the ctypes array is filled from a numpy record array of the same layout
+            rec = np.zeros(max(1, len(items)), dtype=_CAP_DT)
+            if items:
+                rec["patch"] = [it[0] for it in items]
+                rec["kind"] = [it[1] for it in items]
+                rec["axis"] = [it[2] for it in items]
+                rec["mode"] = [mode_fine if it[6] else 0 for it in items]
+                rec["lo"] = np.array([it[3] for it in items], dtype=np.int64)
+                rec["hi"] = np.array([it[4] for it in items], dtype=np.int64)
+                rec["dst"] = base + 8 * offs[np.array([it[5] for it in items], dtype=np.int64)]
+            return (capi.mhd_capture * len(rec)).from_buffer_copy(rec.tobytes()), len(items)
 
         self.caps = {}
         for l in range(L):
@@ -238,14 +297,18 @@ class Hierarchy:
             for ci in need:
                 nelem = int(np.prod(self.levels[l][ci].state.shape[1:]))
                 corr[ci] = torch.zeros(18 * nelem, dtype=torch.float64, device=self.device)
-            for t, (ci, kind, ax, lo, hi, rf, flo, fhi, rc) in enumerate(dl):
-                arr[t].coarse = int(ci)
-                arr[t].kind = kind
-                arr[t].axis = ax
-                arr[t].box = capi.box(lo, hi)
-                arr[t].fine_box = capi.box(flo, fhi)
-                arr[t].fine = ptr(rf)
-                arr[t].coarse_reg = ptr(rc)
+            if dl:
+                rec = np.zeros(len(dl), dtype=_DEP_DT)
+                rec["coarse"] = [x[0] for x in dl]
+                rec["kind"] = [x[1] for x in dl]
+                rec["axis"] = [x[2] for x in dl]
+                rec["lo"] = np.array([x[3] for x in dl], dtype=np.int64)
+                rec["hi"] = np.array([x[4] for x in dl], dtype=np.int64)
+                rec["flo"] = np.array([x[6] for x in dl], dtype=np.int64)
+                rec["fhi"] = np.array([x[7] for x in dl], dtype=np.int64)
+                rec["fine"] = base + 8 * offs[np.array([x[5] for x in dl], dtype=np.int64)]
+                rec["creg"] = base + 8 * offs[np.array([x[8] for x in dl], dtype=np.int64)]
+                arr = (capi.mhd_deposit * len(dl)).from_buffer_copy(rec.tobytes())
             self.deps[l] = (arr, len(dl))
             self.corr[l] = [corr[ci].data_ptr() if ci in corr else None for ci in range(len(self.levels[l]))]
             self._corr_keep = getattr(self, "_corr_keep", []) + list(corr.values())

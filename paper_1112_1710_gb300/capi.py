@@ -23,7 +23,7 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
-           "mhd_restrict_prolong", "mhd_autotune_advance")
+           "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit")
 N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
@@ -151,6 +151,10 @@ def load(build_if_missing: bool = False):
     L.mhd_kernel_name.argtypes = [i32]
     L.mhd_conservation_sums_static.restype = i32
     L.mhd_conservation_sums_static.argtypes = [C.POINTER(mhd_patch_desc), i32, P, P]
+    L.mhd_tree_parents.restype = i32
+    L.mhd_tree_parents.argtypes = [P, P, i32, P, P, i32, P, P, P, P]
+    L.mhd_tree_inherit.restype = i32
+    L.mhd_tree_inherit.argtypes = [P, P, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]
     _lib = L
     return L
 
@@ -310,3 +314,4 @@ def mhd_timing_read(ctx) -> dict:
         _check(ctx, load().mhd_timing_read(ctx, k, C.byref(ms), C.byref(n)))
         out[mhd_kernel_name(k)] = (float(ms.value), int(n.value))
     return out
+
