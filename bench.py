@@ -491,15 +491,16 @@ def amr_hierarchy():
     return H, states
 
 
-def time_amr(H, states, dtype, steps, mode, local):
+def time_amr(H, states, dtype, steps, mode, local, concurrent=False):
     import torch
 
     from paper_1112_1710_gb300 import capi
     from paper_1112_1710_gb300.amr import Hierarchy
     ctx = capi.mhd_ctx_create(device=local, **SOLVER)
-    stream = torch.cuda.Stream(device=local)
+    # the main stream carries every finer level: it gets the higher priority
+    stream = torch.cuda.Stream(device=local, priority=-1)
     h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
-                  device="cuda:%d" % local)
+                  device="cuda:%d" % local, concurrent=concurrent)
     try:
         h.initialise()
         if mode == "per_patch":
@@ -510,7 +511,7 @@ def time_amr(H, states, dtype, steps, mode, local):
             h.coarse_step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = capi.mhd_launch_count(ctx)
+        l0 = h.launch_count()
         e0.record(stream)
         for _ in range(steps):
             if mode == "graph":
@@ -520,13 +521,14 @@ def time_amr(H, states, dtype, steps, mode, local):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        status = capi.mhd_get_device_status(ctx)
+        status = h.device_status()
         upd = h.cell_updates_per_coarse_step()
-        launches = capi.mhd_launch_count(ctx) - l0
+        launches = h.launch_count() - l0
     finally:
         h.close()
         capi.mhd_ctx_destroy(ctx)
-    return {"dtype": dtype, "mode": mode, "coarse_steps": steps, "ms_per_coarse_step": ms / steps,
+    return {"dtype": dtype, "mode": mode, "levels_concurrent": h.concurrent, "coarse_steps": steps,
+            "ms_per_coarse_step": ms / steps,
             "cell_updates_per_coarse_step": upd, "value": upd * steps / (ms * 1e-3),
             "library_launches_per_step": (launches / steps) if mode != "graph" else None,
             "device_status": status}
@@ -636,8 +638,9 @@ def amr_attribution(H, states, dtype, steps, local):
     from paper_1112_1710_gb300.amr import Hierarchy
     ctx = capi.mhd_ctx_create(device=local, **SOLVER)
     stream = torch.cuda.Stream(device=local)
+    # one stream and one context, so that one timer sees every launch
     h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
-                  device="cuda:%d" % local)
+                  device="cuda:%d" % local, concurrent=False)
     try:
         h.initialise()
         h.coarse_step()
@@ -650,7 +653,7 @@ def amr_attribution(H, states, dtype, steps, local):
         kt = capi.mhd_timing_read(ctx)
         capi.mhd_timing_enable(ctx, False)
         work = amr_level_work(h)
-        status = capi.mhd_get_device_status(ctx)
+        status = h.device_status()
     finally:
         h.close()
         capi.mhd_ctx_destroy(ctx)
@@ -689,6 +692,7 @@ def run_amr(args):
     _build.build()
     H, states = amr_hierarchy()
     res = [time_amr(H, states, "f32", args.steps, "graph", local),
+           time_amr(H, states, "f32", args.steps, "graph", local, concurrent=True),
            time_amr(H, states, "f32", args.steps, "batched", local),
            time_amr(H, states, "f64", max(1, args.steps // 2), "graph", local),
            time_amr(H, states, "f64", 1, "per_patch", local)]
@@ -922,7 +926,7 @@ def run_deep(args):
                (0,) if l == 0 else (2, 0), False)
               for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl) if i % 4 == 0]
     ctx = capi.mhd_ctx_create(device=local, **SOLVER)
-    stream = torch.cuda.Stream(device=local)
+    stream = torch.cuda.Stream(device=local, priority=-1)
     h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream,
                   device="cuda:%d" % local)
     del states
@@ -949,7 +953,7 @@ def run_deep(args):
         capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         s1 = out.cpu().numpy()
-        status = capi.mhd_get_device_status(ctx)
+        status = h.device_status()
         upd = h.cell_updates_per_coarse_step()
     finally:
         h.close()

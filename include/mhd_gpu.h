@@ -183,6 +183,13 @@ typedef struct {
 /* Context: owns scratch memory and device copies of small host tables on
  * CUDA device `device`.  *out is NULL on failure. */
 mhd_status mhd_ctx_create(const mhd_params *params, int32_t device, mhd_ctx **out);
+/* A new context on the device of src with src's parameters and advance
+ * choices (those the autotuner stored included), and its own scratch arena,
+ * tables, status word and timer: the way to run calls of one solver
+ * configuration concurrently on several streams (each stream its own
+ * context), as the level-concurrent AMR step does (Sec. 4).  *out is NULL on
+ * failure; MHD_EINVAL for NULL arguments. */
+mhd_status mhd_ctx_clone(const mhd_ctx *src, mhd_ctx **out);
 void mhd_ctx_destroy(mhd_ctx *ctx);
 const char *mhd_last_error(const mhd_ctx *ctx);
 

@@ -23,7 +23,8 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_ghost_fill", "mhd_conservation_sums", "mhd_get_device_status", "mhd_version",
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
-           "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit")
+           "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit",
+           "mhd_ctx_clone")
 N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = False):
     dp = C.POINTER(C.c_double)
     L.mhd_ctx_create.restype = i32
     L.mhd_ctx_create.argtypes = [C.POINTER(mhd_params), i32, C.POINTER(P)]
+    L.mhd_ctx_clone.restype = i32
+    L.mhd_ctx_clone.argtypes = [P, C.POINTER(P)]
     L.mhd_ctx_destroy.restype = None
     L.mhd_ctx_destroy.argtypes = [P]
     L.mhd_last_error.restype = C.c_char_p
@@ -186,6 +189,12 @@ def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, d
     out = C.c_void_p()
     r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
     _check(None, r)
+    return out.value
+
+
+def mhd_ctx_clone(ctx):
+    out = C.c_void_p()
+    _check(ctx, load().mhd_ctx_clone(ctx, C.byref(out)))
     return out.value
 
 

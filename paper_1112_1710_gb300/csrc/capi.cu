@@ -317,6 +317,23 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   return MHD_OK;
 }
 
+mhd_status mhd_ctx_clone(const mhd_ctx* src, mhd_ctx** out) {
+  if (!out) return MHD_EINVAL;
+  *out = nullptr;
+  if (!src) return MHD_EINVAL;
+  mhd_ctx* c = nullptr;
+  mhd_status r = mhd_ctx_create(&src->prm, src->device, &c);
+  if (r) return r;
+  for (int i = 0; i < 2; ++i) {
+    c->use_fused[i] = src->use_fused[i];
+    c->pred_tiled[i] = src->pred_tiled[i];
+    c->fused_variant[i] = src->fused_variant[i];
+    c->fused_chunk[i] = src->fused_chunk[i];
+  }
+  *out = c;
+  return MHD_OK;
+}
+
 void mhd_ctx_destroy(mhd_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
