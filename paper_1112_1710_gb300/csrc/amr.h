@@ -46,15 +46,26 @@ struct DCorr {
   const unsigned char* flags;
 };
 
-cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const BlockTask* tasks,
-                               int nblocks, const KernelTimer* tm, cudaStream_t s);
+// A block table of an item list on the device (see list_elem): the blocks'
+// tasks, the items' first elements (nitems + 1 entries), and whether the
+// blocks are packed (small items share blocks) or aligned to the items.
+struct PackedTasks {
+  const BlockTask* tasks;
+  const int64_t* starts;
+  int nblocks, nitems;
+  int packed;
+};
+
+// Ghost fill: pass 0 packed over the copies, pass 1 over (copy, axis) top
+// layers (item 3 c + a).  Restriction: the same split over the items.
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const PackedTasks& p0,
+                               const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s);
 cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, const DBoxItem* items,
-                           const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s);
+                           const PackedTasks& p, const KernelTimer* tm, cudaStream_t s);
 cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse, const DBoxItem* items,
-                            const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s);
-cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const BlockTask* tasks,
-                           int nblocks, const void* scratch, const double* d_dt, const KernelTimer* tm,
-                           cudaStream_t s);
+                            const PackedTasks& p0, const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s);
+cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const PackedTasks& p,
+                           const void* scratch, const double* d_dt, const KernelTimer* tm, cudaStream_t s);
 cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, void* flags, size_t flag_bytes,
                           const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const BlockTask* corr_tasks,
                           int ncorr, const KernelTimer* tm, cudaStream_t s);

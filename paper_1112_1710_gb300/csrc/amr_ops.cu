@@ -13,6 +13,12 @@
 #include "common.cuh"
 #include "physics.cuh"
 
+// Blocks per SM the FP32 prolongation is compiled for (its registers per
+// thread: 80 at three blocks, with some spilling, the compiler's 112 at two).
+#ifndef MHD_PROLONG_MINB
+#define MHD_PROLONG_MINB 2
+#endif
+
 namespace mhd {
 
 namespace {
@@ -80,21 +86,39 @@ __device__ __forceinline__ void box_cell(const int32_t* lo, const int32_t* ext, 
 }
 
 // ---------------------------------------------------------------- ghost copy
-template <typename R>
+// Cell c of the top layer of a box along axis a (the item's element e runs
+// over the two transverse axes, lower one fastest).
+__device__ __forceinline__ void top_cell(const int32_t* lo, const int32_t* ext, int a, int e, int* c) {
+  const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  const int u = t1 < t2 ? t1 : t2, v = t1 < t2 ? t2 : t1;
+  c[a] = lo[a] + ext[a] - 1;
+  c[u] = lo[u] + e % ext[u];
+  c[v] = lo[v] + e / ext[u];
+}
+
+// Pass 0: one thread per destination cell of a copy box (packed over the
+// copies): the five cell values and the lower face along each axis unless it
+// is a face of the destination's interior.  Pass 1: one thread per cell of
+// the top layer of a box along one axis (packed over copy x axis): the upper
+// face of that cell along the axis.
+template <typename R, int pass>
 __global__ void __launch_bounds__(kThreads) k_ghost2(const DPatch* __restrict__ P, const DCopy* __restrict__ C,
-                                                     const BlockTask* __restrict__ T, int pass) {
-  const BlockTask t = T[blockIdx.x];
-  const DCopy cp = C[t.patch];
-  const int e = t.start + threadIdx.x;
-  if (e >= cp.ext[0] * cp.ext[1] * cp.ext[2]) return;
+                                                     const BlockTask* __restrict__ T,
+                                                     const int64_t* __restrict__ starts, int nitems, int packed) {
+  int item, e;
+  if (!list_elem(T[blockIdx.x], starts, nitems, packed, item, e)) return;
+  const int ci = pass == 0 ? item : item / 3;
+  const int ax = pass == 0 ? 0 : item - 3 * ci;
+  const DCopy cp = C[ci];
   int di[3];
-  box_cell(cp.lo, cp.ext, e, di);
+  if constexpr (pass == 0) box_cell(cp.lo, cp.ext, e, di);
+  else top_cell(cp.lo, cp.ext, ax, e, di);
   const DPatch& d = P[cp.dst];
   const DPatch& s = P[cp.src];
   const int si[3] = {di[0] + cp.off[0], di[1] + cp.off[1], di[2] + cp.off[2]};
   const int64_t xd = lin3(d, di[0], di[1], di[2]);
   const int64_t xs = lin3(s, si[0], si[1], si[2]);
-  if (pass == 0) {
+  if constexpr (pass == 0) {
     // loads first: a store would order every later load of a may-alias array
     const bool cell_in = di[0] >= 0 && di[0] < d.N[0] && di[1] >= 0 && di[1] < d.N[1] && di[2] >= 0 && di[2] < d.N[2];
     R u[5], b[3];
@@ -114,26 +138,24 @@ __global__ void __launch_bounds__(kThreads) k_ghost2(const DPatch* __restrict__ 
     for (int a = 0; a < 3; ++a)
       if (fw[a]) ((R*)d.B[a])[xd] = b[a];
   } else {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (di[a] != cp.lo[a] + cp.ext[a] - 1) continue;
-      int du[3] = {di[0], di[1], di[2]};
-      du[a] += 1;
-      if (!face_exists(d, du, a) || own_face(d, du, a)) continue;
-      ((R*)d.B[a])[xd + sof(d, a)] = ((const R*)s.B[a])[xs + sof(s, a)];
-    }
+    int du[3] = {di[0], di[1], di[2]};
+    du[ax] += 1;
+    if (!face_exists(d, du, ax) || own_face(d, du, ax)) return;
+    ((R*)d.B[ax])[xd + sof(d, ax)] = ((const R*)s.B[ax])[xs + sof(s, ax)];
   }
 }
 
 // ---------------------------------------------------------------- prolongation
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_prolong(const DPatch* __restrict__ PC, const DPatch* __restrict__ PF,
-                                                      const DBoxItem* __restrict__ items,
-                                                      const BlockTask* __restrict__ T) {
-  const BlockTask t = T[blockIdx.x];
-  const DBoxItem it = items[t.patch];
-  const int e = t.start + threadIdx.x;
-  if (e >= it.ext[0] * it.ext[1] * it.ext[2]) return;
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? MHD_PROLONG_MINB : 1) k_prolong(const DPatch* __restrict__ PC,
+                                                                        const DPatch* __restrict__ PF,
+                                                                        const DBoxItem* __restrict__ items,
+                                                                        const BlockTask* __restrict__ T,
+                                                                        const int64_t* __restrict__ starts,
+                                                                        int nitems, int packed) {
+  int ii, e;
+  if (!list_elem(T[blockIdx.x], starts, nitems, packed, ii, e)) return;
+  const DBoxItem it = items[ii];
   int C3[3];
   box_cell(it.lo, it.ext, e, C3);
   const DPatch& pc = PC[it.a];
@@ -263,13 +285,19 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const DPatch* __restrict__
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_restrict(const DPatch* __restrict__ PF, const DPatch* __restrict__ PC,
                                                        const DBoxItem* __restrict__ items,
-                                                       const BlockTask* __restrict__ T, int pass) {
-  const BlockTask t = T[blockIdx.x];
-  const DBoxItem it = items[t.patch];
-  const int e = t.start + threadIdx.x;
-  if (e >= it.ext[0] * it.ext[1] * it.ext[2]) return;
+                                                       const BlockTask* __restrict__ T,
+                                                       const int64_t* __restrict__ starts, int nitems, int packed,
+                                                       int pass) {
+  // pass 0: every cell of an item box; pass 1: the top layer of an item box
+  // along one axis (items: item x axis)
+  int ii, e;
+  if (!list_elem(T[blockIdx.x], starts, nitems, packed, ii, e)) return;
+  const int bi = pass == 0 ? ii : ii / 3;
+  const int ax = pass == 0 ? -1 : ii - 3 * bi;
+  const DBoxItem it = items[bi];
   int C3[3];
-  box_cell(it.lo, it.ext, e, C3);
+  if (pass == 0) box_cell(it.lo, it.ext, e, C3);
+  else top_cell(it.lo, it.ext, ax, e, C3);
   const DPatch& pf = PF[it.a];
   const DPatch& pc = PC[it.b];
   const int ca0[3] = {C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]};
@@ -298,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const DPatch* __restrict_
     const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
     const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
     const int up = pass;
-    if (up && C3[a] != chi[a]) continue;
+    if (up && (a != ax || C3[a] != chi[a])) continue;
     int cf[3] = {ca0[0], ca0[1], ca0[2]};
     cf[a] += up;
     if (!own_face(pc, cf, a)) continue;
@@ -323,13 +351,13 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const DPatch* __restrict_
 // dst = (or +=) dt * F_q on the axis faces (5 planes) / dt * E_axis on edges
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__ P, const DCapture* __restrict__ C,
-                                                      const BlockTask* __restrict__ T, const R* scr,
-                                                      const double* d_dt) {
-  const BlockTask t = T[blockIdx.x];
-  const DCapture cp = C[t.patch];
-  const int e = t.start + threadIdx.x;
+                                                      const BlockTask* __restrict__ T,
+                                                      const int64_t* __restrict__ starts, int nitems, int packed,
+                                                      const R* scr, const double* d_dt) {
+  int ii, e;
+  if (!list_elem(T[blockIdx.x], starts, nitems, packed, ii, e)) return;
+  const DCapture cp = C[ii];
   const int64_t nv = (int64_t)cp.ext[0] * cp.ext[1] * cp.ext[2];
-  if (e >= nv) return;
   int ai[3];
   box_cell(cp.lo, cp.ext, e, ai);
   const DPatch& p = P[cp.patch];
@@ -497,50 +525,67 @@ __global__ void __launch_bounds__(kThreads) k_correct(const DPatch* __restrict__
 
 }  // namespace
 
-cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const BlockTask* tasks,
-                               int nblocks, const KernelTimer* tm, cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
-  for (int pass = 0; pass < 2; ++pass) {
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const PackedTasks& p0,
+                               const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s) {
+  if (p0.nblocks) {
     if (dtype == 0)
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks, pass)));
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double, 0><<<p0.nblocks, kThreads, 0, s>>>(patches, copies, p0.tasks,
+                                                                                    p0.starts, p0.nitems, p0.packed)));
     else
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks, pass)));
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float, 0><<<p0.nblocks, kThreads, 0, s>>>(patches, copies, p0.tasks,
+                                                                                   p0.starts, p0.nitems, p0.packed)));
+  }
+  if (p1.nblocks) {
+    if (dtype == 0)
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double, 1><<<p1.nblocks, kThreads, 0, s>>>(patches, copies, p1.tasks,
+                                                                                    p1.starts, p1.nitems, p1.packed)));
+    else
+      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float, 1><<<p1.nblocks, kThreads, 0, s>>>(patches, copies, p1.tasks,
+                                                                                   p1.starts, p1.nitems, p1.packed)));
   }
   return cudaGetLastError();
 }
 
 cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, const DBoxItem* items,
-                           const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
+                           const PackedTasks& p, const KernelTimer* tm, cudaStream_t s) {
+  if (p.nblocks == 0) return cudaSuccess;
   if (dtype == 0)
-    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<double><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<double><<<p.nblocks, kThreads, 0, s>>>(coarse, fine, items, p.tasks,
+                                                                                  p.starts, p.nitems, p.packed)));
   else
-    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<float><<<nblocks, kThreads, 0, s>>>(coarse, fine, items, tasks)));
+    MHD_TIMED(tm, K_PROLONG, s, (k_prolong<float><<<p.nblocks, kThreads, 0, s>>>(coarse, fine, items, p.tasks,
+                                                                                 p.starts, p.nitems, p.packed)));
   return cudaGetLastError();
 }
 
 cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse, const DBoxItem* items,
-                            const BlockTask* tasks, int nblocks, const KernelTimer* tm, cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
+                            const PackedTasks& p0, const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s) {
   for (int pass = 0; pass < 2; ++pass) {
+    const PackedTasks& p = pass ? p1 : p0;
+    if (p.nblocks == 0) continue;
     if (dtype == 0)
-      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<double><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<double><<<p.nblocks, kThreads, 0, s>>>(fine, coarse, items, p.tasks,
+                                                                                      p.starts, p.nitems, p.packed, pass)));
     else
-      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<float><<<nblocks, kThreads, 0, s>>>(fine, coarse, items, tasks, pass)));
+      MHD_TIMED(tm, K_RESTRICT, s, (k_restrict<float><<<p.nblocks, kThreads, 0, s>>>(fine, coarse, items, p.tasks,
+                                                                                     p.starts, p.nitems, p.packed, pass)));
   }
   return cudaGetLastError();
 }
 
-cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const BlockTask* tasks,
-                           int nblocks, const void* scratch, const double* d_dt, const KernelTimer* tm,
-                           cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
+cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const PackedTasks& p,
+                           const void* scratch, const double* d_dt, const KernelTimer* tm, cudaStream_t s) {
+  if (p.nblocks == 0) return cudaSuccess;
   if (dtype == 0)
-    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<double><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
-                                                                            (const double*)scratch, d_dt)));
+    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<double><<<p.nblocks, kThreads, 0, s>>>(patches, caps, p.tasks, p.starts,
+                                                                                  p.nitems, p.packed,
+                                                                                  (const double*)scratch,
+                                                                                  d_dt)));
   else
-    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<float><<<nblocks, kThreads, 0, s>>>(patches, caps, tasks,
-                                                                           (const float*)scratch, d_dt)));
+    MHD_TIMED(tm, K_CAPTURE, s, (k_capture<float><<<p.nblocks, kThreads, 0, s>>>(patches, caps, p.tasks, p.starts,
+                                                                                 p.nitems, p.packed,
+                                                                                 (const float*)scratch,
+                                                                                 d_dt)));
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -220,6 +221,49 @@ void tasks_for(const std::vector<int64_t>& counts, std::vector<BlockTask>& out) 
   out.clear();
   for (size_t p = 0; p < counts.size(); ++p)
     for (int64_t s = 0; s < counts[p]; s += kThreads) out.push_back(BlockTask{(int32_t)p, (int32_t)s});
+}
+
+// Block table (list_elem) of items with counts[i] >= 1 elements each, packed
+// (small items share blocks) or aligned to the items, uploaded to the
+// context's table cache.  Measured on the AMR hierarchies: packing pays for
+// lists of many small boxes (prolongation, restriction, the top layers of
+// ghost copies) and costs for lists whose boxes fill their blocks (copies,
+// flux-register captures), where threads of one block then read different
+// items.
+mhd_status packed_table(mhd_ctx* c, const std::vector<int64_t>& counts, bool packed, PackedTasks& out) {
+  std::vector<int64_t> starts(counts.size() + 1, 0);
+  for (size_t i = 0; i < counts.size(); ++i) starts[i + 1] = starts[i] + counts[i];
+  std::vector<BlockTask> tasks;
+  if (packed) {
+    size_t item = 0;
+    for (int64_t b = 0; b < starts.back(); b += kThreads) {
+      while (starts[item + 1] <= b) ++item;
+      tasks.push_back(BlockTask{(int32_t)item, (int32_t)(b - starts[item])});
+    }
+  } else {
+    tasks_for(counts, tasks);
+  }
+  if (tasks.size() > 0x7fffffff || counts.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  void *d_t = nullptr, *d_s = nullptr;
+  mhd_status r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t);
+  if (!r) r = table(c, starts.data(), starts.size() * sizeof(int64_t), &d_s);
+  if (r) return r;
+  out.tasks = (const BlockTask*)d_t;
+  out.starts = (const int64_t*)d_s;
+  out.nblocks = (int)tasks.size();
+  out.nitems = (int)counts.size();
+  out.packed = packed ? 1 : 0;
+  return MHD_OK;
+}
+
+// Counts of the top-layer items (box i, axis a) -> item 3 i + a: the box's
+// extent over the two transverse axes.
+std::vector<int64_t> top_counts(const std::vector<std::array<int32_t, 3>>& ext) {
+  const size_t n = ext.size();
+  std::vector<int64_t> out(3 * n);
+  for (size_t i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = (int64_t)ext[i][(a + 1) % 3] * ext[i][(a + 2) % 3];
+  return out;
 }
 
 // Block tables of the staged advance: over each patch's UB+2 (t2), the
@@ -644,13 +688,12 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   // fused: step constants, k_fused, k_commit
   c->launches += fused ? 3 : staged_launches(elem_size(dtype));
   if (ncap > 0) {
-    std::vector<BlockTask> cptasks;
-    tasks_for(ccounts, cptasks);
-    void *d_c = nullptr, *d_cpt = nullptr;
+    PackedTasks pc{};
+    if ((r = packed_table(c, ccounts, false, pc))) return r;
+    void* d_c = nullptr;
     if ((r = table(c, dc.data(), dc.size() * sizeof(DCapture), &d_c))) return r;
-    if ((r = table(c, cptasks.data(), cptasks.size() * sizeof(BlockTask), &d_cpt))) return r;
-    e = capture_launch(dtype, (const DPatch*)d_p, (const DCapture*)d_c, (const BlockTask*)d_cpt,
-                       (int)cptasks.size(), c->scratch, d_dt, timer_of(c), (cudaStream_t)stream);
+    e = capture_launch(dtype, (const DPatch*)d_p, (const DCapture*)d_c, pc, c->scratch, d_dt, timer_of(c),
+                       (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "capture launch");
     c->launches += 1;
   }
@@ -869,14 +912,17 @@ mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, 
     o.start = 0;
     counts[t] = cnt;
   }
-  std::vector<BlockTask> tasks;
-  tasks_for(counts, tasks);
-  void *d_p = nullptr, *d_c = nullptr, *d_t = nullptr;
+  std::vector<std::array<int32_t, 3>> ext(nlist);
+  for (int t = 0; t < nlist; ++t)
+    for (int a = 0; a < 3; ++a) ext[t][a] = dc[t].ext[a];
+  PackedTasks p0{}, p1{};
+  if ((r = packed_table(c, counts, false, p0))) return r;
+  if ((r = packed_table(c, top_counts(ext), true, p1))) return r;
+  void *d_p = nullptr, *d_c = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DCopy), &d_c))) return r;
-  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
-  cudaError_t e = ghost_fill2_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, (const BlockTask*)d_t,
-                                     (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = ghost_fill2_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, p0, p1, timer_of(c),
+                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ghost fill launch");
   c->launches += 2;
   return MHD_OK;
@@ -943,15 +989,14 @@ mhd_status mhd_prolong(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, con
     di[t].b = m.fine;
     counts[t] = cnt;
   }
-  std::vector<BlockTask> tasks;
-  tasks_for(counts, tasks);
-  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr, *d_t = nullptr;
+  PackedTasks pk{};
+  if ((r = packed_table(c, counts, true, pk))) return r;
+  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
   if ((r = table(c, df.data(), df.size() * sizeof(DPatch), &d_f))) return r;
   if ((r = table(c, di.data(), di.size() * sizeof(DBoxItem), &d_i))) return r;
-  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
-  cudaError_t e = prolong_launch(dtype, (const DPatch*)d_c, (const DPatch*)d_f, (const DBoxItem*)d_i,
-                                 (const BlockTask*)d_t, (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = prolong_launch(dtype, (const DPatch*)d_c, (const DPatch*)d_f, (const DBoxItem*)d_i, pk,
+                                 timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "prolong launch");
   c->launches += 1;
   return MHD_OK;
@@ -991,15 +1036,18 @@ mhd_status mhd_restrict(mhd_ctx* c, const mhd_patch_desc* fine, int32_t nf, cons
     di[t].b = m.coarse;
     counts[t] = cnt;
   }
-  std::vector<BlockTask> tasks;
-  tasks_for(counts, tasks);
-  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr, *d_t = nullptr;
+  std::vector<std::array<int32_t, 3>> ext(n);
+  for (int t = 0; t < n; ++t)
+    for (int a = 0; a < 3; ++a) ext[t][a] = di[t].ext[a];
+  PackedTasks p0{}, p1{};
+  if ((r = packed_table(c, counts, true, p0))) return r;
+  if ((r = packed_table(c, top_counts(ext), true, p1))) return r;
+  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
   if ((r = table(c, df.data(), df.size() * sizeof(DPatch), &d_f))) return r;
   if ((r = table(c, di.data(), di.size() * sizeof(DBoxItem), &d_i))) return r;
-  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
-  cudaError_t e = restrict_launch(dtype, (const DPatch*)d_f, (const DPatch*)d_c, (const DBoxItem*)d_i,
-                                  (const BlockTask*)d_t, (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = restrict_launch(dtype, (const DPatch*)d_f, (const DPatch*)d_c, (const DBoxItem*)d_i, p0, p1,
+                                  timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "restrict launch");
   c->launches += 2;
   return MHD_OK;

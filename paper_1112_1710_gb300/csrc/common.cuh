@@ -58,6 +58,40 @@ struct BlockTask {
   int32_t start;
 };
 
+constexpr int kThreads = 256;
+
+// Packed block tables: the elements of consecutive items (boxes of a list)
+// laid end to end and cut into blocks of kThreads, so that small items share
+// blocks.  starts[i] is the first element of item i (starts[n] the total);
+// a block's task holds the item its first element lies in (patch) and that
+// element's offset in it (start).  Every item holds at least one element, so
+// a block spans at most kThreads items.  Returns false past the last element.
+__device__ __forceinline__ bool packed_elem(const BlockTask& t, const int64_t* __restrict__ starts, int nitems,
+                                            int& item, int& e) {
+  const int64_t G = starts[t.patch] + t.start + threadIdx.x;
+  if (G >= starts[nitems]) return false;
+  int lo = t.patch, hi = nitems - 1 < t.patch + kThreads ? nitems - 1 : t.patch + kThreads;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= G) lo = mid;
+    else hi = mid - 1;
+  }
+  item = lo;
+  e = (int)(G - starts[lo]);
+  return true;
+}
+
+// Element of an item list under either block table: aligned (packed == 0:
+// every block inside one item, the task's item and offset as given, threads
+// past the item's end idle) or packed (packed_elem).
+__device__ __forceinline__ bool list_elem(const BlockTask& t, const int64_t* __restrict__ starts, int nitems,
+                                          int packed, int& item, int& e) {
+  if (packed) return packed_elem(t, starts, nitems, item, e);
+  item = t.patch;
+  e = t.start + threadIdx.x;
+  return e < starts[item + 1] - starts[item];
+}
+
 // Tile of the tiled predictor (cells, x fastest; one thread per cell) per
 // element type; the host builds one block per tile of each patch's UB+1.
 constexpr int kPredTile32[3] = {32, 4, 2};
@@ -91,7 +125,6 @@ enum : int {
   SC_COUNT = 92
 };
 
-constexpr int kThreads = 256;
 
 // Kernel ids of the per-kernel event timer (mhd_timing_*).
 enum KernelId : int {
