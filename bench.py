@@ -226,9 +226,7 @@ def kernel_flops(name, n, launched=()):
 # DRAM bytes (read + write) per step of the dominant kernels on this
 # workload (all of a kernel's launches in one step), from one ncu capture of
 # the current kernels (profiles/).  Keys: bench pass, kernel.
-KERNEL_TRAFFIC = {("f32", "k_pred"): 447.8e6, ("f32", "k_flux"): 627.9e6, ("f32", "k_update"): 310.6e6,
-                  ("f64", "k_pred"): 881.7e6, ("f64", "k_flux"): 1246.3e6,
-                  ("f64_exact", "k_pred"): 883.1e6, ("f64_exact", "k_flux"): 1250.0e6}
+KERNEL_TRAFFIC = {("f32", "k_update"): 310.6e6}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):

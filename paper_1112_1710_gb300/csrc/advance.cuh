@@ -105,7 +105,79 @@ __device__ __forceinline__ int64_t stride_of(const DPatch& p, int d) {
 }
 
 template <typename R> __device__ __forceinline__ R* arr(R* scr, const DPatch& p, int a) {
-  return scr + p.scr + (int64_t)a * p.nelem;
+  return scr + p.scr + (int64_t)a * p.snelem;
+}
+
+// Vector groups of scratch slots: the 8 slots from slot a on hold 8 values
+// per element as vectors, FP32 in two float4 planes (values 0-3 in slots
+// a..a+3 as one plane of float4, values 4-7 in slots a+4..a+7), FP64 in four
+// double2 planes; one vector access moves 16 bytes per thread.  The primitives
+// W and the predicted face states use them.  The planes are aligned: arena
+// offsets and the plane stride (snelem) are multiples of 8 elements.  A face
+// state is stored in its face's rotated frame (rho, v_n, v_t1, v_t2, p, B_t1,
+// B_t2) as 7 values; the eighth slot of its group is never read.
+template <typename R> struct VecIO;
+template <> struct VecIO<float> {
+  static __device__ __forceinline__ void load8(const float* g, int64_t sn, int64_t x, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(g)[x];
+    const float4 b = reinterpret_cast<const float4*>(g + 4 * sn)[x];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  static __device__ __forceinline__ void store8(float* g, int64_t sn, int64_t x, const float (&v)[8]) {
+    reinterpret_cast<float4*>(g)[x] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(g + 4 * sn)[x] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+  static __device__ __forceinline__ void load7(const float* g, int64_t sn, int64_t x, float (&v)[7]) {
+    const float4 a = reinterpret_cast<const float4*>(g)[x];
+    const float* h = g + 4 * sn + 4 * x;
+    const float2 b = *reinterpret_cast<const float2*>(h);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = h[2];
+  }
+  static __device__ __forceinline__ void store7(float* g, int64_t sn, int64_t x, const float (&v)[7]) {
+    reinterpret_cast<float4*>(g)[x] = make_float4(v[0], v[1], v[2], v[3]);
+    float* h = g + 4 * sn + 4 * x;
+    *reinterpret_cast<float2*>(h) = make_float2(v[4], v[5]);
+    h[2] = v[6];
+  }
+};
+template <> struct VecIO<double> {
+  static __device__ __forceinline__ void load8(const double* g, int64_t sn, int64_t x, double (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(g + 2 * k * sn)[x];
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+  }
+  static __device__ __forceinline__ void store8(double* g, int64_t sn, int64_t x, const double (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) reinterpret_cast<double2*>(g + 2 * k * sn)[x] = make_double2(v[2 * k], v[2 * k + 1]);
+  }
+  static __device__ __forceinline__ void load7(const double* g, int64_t sn, int64_t x, double (&v)[7]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(g + 2 * k * sn)[x];
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+    v[6] = (g + 6 * sn)[2 * x];
+  }
+  static __device__ __forceinline__ void store7(double* g, int64_t sn, int64_t x, const double (&v)[7]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) reinterpret_cast<double2*>(g + 2 * k * sn)[x] = make_double2(v[2 * k], v[2 * k + 1]);
+    (g + 6 * sn)[2 * x] = v[6];
+  }
+};
+
+// Stores the face state pw (primitives, xyz order) of the axis-d face in its
+// rotated frame.
+template <typename R>
+__device__ __forceinline__ void store_face_state(R* g, int64_t sn, int64_t x, int d, const R (&pw)[8]) {
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  const R v[7] = {pw[0], pw[1 + d], pw[1 + t1], pw[1 + t2], pw[4], pw[5 + t1], pw[5 + t2]};
+  VecIO<R>::store7(g, sn, x, v);
 }
 
 __device__ __forceinline__ void raise_status(int* status, int code) {
@@ -166,8 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
   (void)U0;
   R w[8];
   cons2prim(u, sc.gm1, w);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) arr(scr, p, SC_W + q)[x] = w[q];
+  VecIO<R>::store8(arr(scr, p, SC_W), p.snelem, x, w);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int b = (a + 1) % 3, cc = (a + 2) % 3;
@@ -261,9 +332,7 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
       for (int q = 0; q < 8; ++q) u[q] = u[q] + du[q];
       cons2prim(u, sc.gm1, pw);
       if (!(pw[0] > R(0)) || !(pw[4] > R(0))) bad2 = true;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q != 5 + d) arr(scr, p, SC_WF + (d * 2 + sd) * 8 + q)[x] = pw[q];
+      store_face_state(arr(scr, p, SC_WF + (d * 2 + sd) * 8), p.snelem, x, d, pw);
     }
   }
   R duk[8];
@@ -271,10 +340,7 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
   for (int q = 0; q < 8; ++q) duk[q] = du[q];
   if (bad2) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f)
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q != 5 + f / 2) arr(scr, p, SC_WF + f * 8 + q)[x] = w[q];
+    for (int f = 0; f < 6; ++f) store_face_state(arr(scr, p, SC_WF + f * 8), p.snelem, x, f / 2, w);
 #pragma unroll
     for (int q = 0; q < 8; ++q) duk[q] = R(0);
   }
@@ -311,16 +377,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const
   const StepDt<R> st(K, t.patch);
   const int64_t x = lin(p, c);
   R w[8], dw[3][8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) w[q] = arr(scr, p, SC_W + q)[x];
+  const R* Wg = arr(scr, p, SC_W);
+  VecIO<R>::load8(Wg, p.snelem, x, w);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int64_t sd = stride_of(p, d);
+    R wm[8], wp[8];
+    VecIO<R>::load8(Wg, p.snelem, x - sd, wm);
+    VecIO<R>::load8(Wg, p.snelem, x + sd, wp);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const R* Wq = arr(scr, p, SC_W + q);
-      R a = w[q] - Wq[x - sd];
-      R b = Wq[x + sd] - w[q];
+      R a = w[q] - wm[q];
+      R b = wp[q] - w[q];
       dw[d][q] = limiter(sc.limiter, a, b);
     }
   }
@@ -365,8 +433,10 @@ __global__ void __launch_bounds__(kThreads) k_pred_tiled(const DPatch* __restric
     const int hz = divmod24(q2, HY, hy);
     if (hx > hx_hi || hy > hy_hi || hz > hz_hi) continue;
     const int64_t x = (int64_t)(x0 - 1 + hx) + (int64_t)(y0 - 1 + hy) * p.s1 + (int64_t)(z0 - 1 + hz) * p.s2;
+    R v[8];
+    VecIO<R>::load8(arr(scr, p, SC_W), p.snelem, x, v);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sw[q][e] = arr(scr, p, SC_W + q)[x];
+    for (int q = 0; q < 8; ++q) sw[q][e] = v[q];
   }
   __syncthreads();
   const int ix = threadIdx.x % TX, iy = (threadIdx.x / TX) % TY, iz = threadIdx.x / (TX * TY);
@@ -412,16 +482,13 @@ __device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell
     dEb = arr(scr, p, SC_EE + b)[x + scc] - arr(scr, p, SC_EE + b)[x];
   }
   R bh = ((const R*)p.B[d])[x] - (st.hdtdx[b] * dEc - st.hdtdx[cc] * dEb);
-  R wl[8], wr[8], L[8], Rr[8], fr[8], f[8], upw;
-  // the face-normal field of the predicted states is not stored: HLLD takes
-  // the CT half-step value bh instead
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    wl[q] = q == 5 + d ? R(0) : arr(scr, p, SC_WF + (d * 2 + 1) * 8 + q)[x - sd];
-    wr[q] = q == 5 + d ? R(0) : arr(scr, p, SC_WF + (d * 2 + 0) * 8 + q)[x];
-  }
-  rot_in(d, wl, L);
-  rot_in(d, wr, Rr);
+  R vl[7], vr[7], fr[8], f[8], upw;
+  // the face states are stored in the face's rotated frame without their
+  // normal field: HLLD takes the CT half-step value bh instead
+  VecIO<R>::load7(arr(scr, p, SC_WF + (d * 2 + 1) * 8), p.snelem, x - sd, vl);
+  VecIO<R>::load7(arr(scr, p, SC_WF + (d * 2 + 0) * 8), p.snelem, x, vr);
+  const R L[8] = {vl[0], vl[1], vl[2], vl[3], vl[4], R(0), vl[5], vl[6]};
+  const R Rr[8] = {vr[0], vr[1], vr[2], vr[3], vr[4], R(0), vr[5], vr[6]};
   hlld<R, kFastRecip>(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
   rot_out(d, fr, f);
   f[5 + d] = upw;

@@ -366,13 +366,13 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
   if (cp.kind == 0) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8 + q) * p.nelem;
+      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8 + q) * p.snelem;
       const double v = dt * (double)F[x];
       double* o = cp.dst + (int64_t)q * nv + e;
       *o = cp.mode ? *o + v : v;
     }
   } else {
-    const R* Ed = scr + p.scr + (int64_t)(SC_ED + cp.axis) * p.nelem;
+    const R* Ed = scr + p.scr + (int64_t)(SC_ED + cp.axis) * p.snelem;
     const double v = dt * (double)Ed[x];
     double* o = cp.dst + e;
     *o = cp.mode ? *o + v : v;

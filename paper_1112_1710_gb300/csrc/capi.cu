@@ -203,6 +203,7 @@ mhd_status convert(mhd_ctx* c, const mhd_patch_desc& d, int idx, DPatch& o) {
   o.s1 = d.stride[1];
   o.s2 = d.stride[2];
   o.nelem = d.stride[2] * (N[2] + 1);
+  o.snelem = (o.nelem + 7) / 8 * 8;
   o.g = d.nghost;
   o.dt_scale = 1.0;
   o.cfl_scale = 1.0;
@@ -623,7 +624,7 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   int64_t off = 0;
   for (int p = 0; p < n; ++p) {
     dp[p].scr = off;
-    off += (int64_t)((!fused || (dp[p].flags & 1)) ? SC_COUNT : 8) * dp[p].nelem;
+    off += (int64_t)((!fused || (dp[p].flags & 1)) ? SC_COUNT : 8) * dp[p].snelem;
   }
   const int64_t stepc_off = off;
   off += 8 * (int64_t)n;
@@ -715,7 +716,7 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   int zmax = 1;
   for (int p = 0; p < n; ++p) {
     dp[p].scr = off;
-    off += (int64_t)SC_COUNT * dp[p].nelem;
+    off += (int64_t)SC_COUNT * dp[p].snelem;
     const int uz = dp[p].n[2] + 2 * dp[p].k;
     zmax = uz > zmax ? uz : zmax;
   }

@@ -15,6 +15,8 @@ struct DPatch {
   void* B[3];
   int64_t s1, s2;
   int64_t nelem;     // elements of one array (s2 * (N_2 + 1))
+  int64_t snelem;    // stride of the library's scratch planes: nelem rounded
+                     // up to 8, so that vector groups of planes stay aligned
   int64_t scr;       // offset of this patch's scratch in the arena (elements)
   int32_t n[3];      // interior cells
   int32_t N[3];      // cells including ghosts

@@ -297,7 +297,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FX[q * L::G1 + s1] = f[q];
       if (fst && own_z && hy >= 1 && hy <= TY && (hx <= TX || xlast)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 0 * 8 + q) * p.nelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 0 * 8 + q) * p.snelem + x] = f[q];
       }
     } else if (dir == 1) {  // y-face: cells j-1 | j
       if (hy == 0) continue;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FY[q * L::G1 + s1] = f[q];
       if (fst && own_z && hx >= 1 && hx <= TX && (hy <= TY || ylast)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 1 * 8 + q) * p.nelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 1 * 8 + q) * p.snelem + x] = f[q];
       }
     } else {  // z-face at z-index zc: cells zc-1 | zc
       R dEc = EY0[se + 1] - EY0[se];
@@ -330,7 +330,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FZ[q * L::G1 + s1] = f[q];
       if (fst && (own_z || own_ztop) && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 2 * 8 + q) * p.nelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 2 * 8 + q) * p.snelem + x] = f[q];
       }
     }
   }
@@ -365,7 +365,7 @@ __device__ __forceinline__ void fused_emf(const DPatch& p, R* sm, int X0, int Y0
                            ER0[0 * L::G1 + s - L::P1], ER0[0 * L::G1 + s], FYm[6 * L::G1 + s],
                            FY0[6 * L::G1 + s], FZ0[7 * L::G1 + s - L::P1], FZ0[7 * L::G1 + s], sc.emf);
       EDXY[0 * L::GT + st_] = v;
-      if (fst && own_xy && oy) fst[(int64_t)(SC_ED + 0) * p.nelem + x] = v;
+      if (fst && own_xy && oy) fst[(int64_t)(SC_ED + 0) * p.snelem + x] = v;
     }
     if (do_xy && ty < TY) {  // y-edge (a = 1; b = z, c = x)
       R v = edge_emf_value(-FZ0[5 * L::G1 + s - 1], -FZ0[5 * L::G1 + s], FXm[7 * L::G1 + s],
@@ -373,7 +373,7 @@ __device__ __forceinline__ void fused_emf(const DPatch& p, R* sm, int X0, int Y0
                            ERm[1 * L::G1 + s], ER0[1 * L::G1 + s], FZ0[7 * L::G1 + s - 1], FZ0[7 * L::G1 + s],
                            FXm[5 * L::G1 + s], FX0[5 * L::G1 + s], sc.emf);
       EDXY[1 * L::GT + st_] = v;
-      if (fst && own_xy && ox) fst[(int64_t)(SC_ED + 1) * p.nelem + x] = v;
+      if (fst && own_xy && ox) fst[(int64_t)(SC_ED + 1) * p.snelem + x] = v;
     }
     if (do_z) {  // z-edge (a = 2; b = x, c = y)
       R v = edge_emf_value(-FX0[6 * L::G1 + s - L::P1], -FX0[6 * L::G1 + s], FY0[5 * L::G1 + s - 1],
@@ -381,7 +381,7 @@ __device__ __forceinline__ void fused_emf(const DPatch& p, R* sm, int X0, int Y0
                            ER0[2 * L::G1 + s - 1], ER0[2 * L::G1 + s], FX0[5 * L::G1 + s - L::P1],
                            FX0[5 * L::G1 + s], FY0[6 * L::G1 + s - 1], FY0[6 * L::G1 + s], sc.emf);
       EDZ[st_] = v;
-      if (fst && ox && oy) fst[(int64_t)(SC_ED + 2) * p.nelem + x] = v;
+      if (fst && ox && oy) fst[(int64_t)(SC_ED + 2) * p.snelem + x] = v;
     }
   }
 }
@@ -445,11 +445,11 @@ __device__ __forceinline__ void fused_update(const DPatch& p, R* sm, R* out, int
     }
     if (do_c)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) out[(int64_t)q * p.nelem + x] = un[q];
-    if (do_x) out[5 * p.nelem + x] = bx;
-    if (do_y) out[6 * p.nelem + x] = by;
-    if (do_z) out[7 * p.nelem + x] = bz;
-    if (do_t) out[7 * p.nelem + x + p.s2] = bt;
+      for (int q = 0; q < 5; ++q) out[(int64_t)q * p.snelem + x] = un[q];
+    if (do_x) out[5 * p.snelem + x] = bx;
+    if (do_y) out[6 * p.snelem + x] = by;
+    if (do_z) out[7 * p.snelem + x] = bz;
+    if (do_t) out[7 * p.snelem + x + p.s2] = bt;
   }
 }
 
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(kThreads) k_commit(const DPatch* __restrict__ 
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const bool ok = q < 5 ? cell : inner[(q - 4) % 3] && inner[(q - 3) % 3];
-    if (ok) v[q] = out[(int64_t)q * p.nelem + x];
+    if (ok) v[q] = out[(int64_t)q * p.snelem + x];
   }
   if (cell)
 #pragma unroll
