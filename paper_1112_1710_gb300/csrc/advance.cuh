@@ -115,7 +115,9 @@ template <typename R> __device__ __forceinline__ R* arr(R* scr, const DPatch& p,
 // W and the predicted face states use them.  The planes are aligned: arena
 // offsets and the plane stride (snelem) are multiples of 8 elements.  A face
 // state is stored in its face's rotated frame (rho, v_n, v_t1, v_t2, p, B_t1,
-// B_t2) as 7 values; the eighth slot of its group is never read.
+// B_t2) as 7 values; the eighth slot of its group is never read.  The face
+// fluxes of each axis form one group too (the 8 components in the order of
+// the state, slot 5 + d carrying the contact side).
 template <typename R> struct VecIO;
 template <> struct VecIO<float> {
   static __device__ __forceinline__ void load8(const float* g, int64_t sn, int64_t x, float (&v)[8]) {
@@ -140,6 +142,11 @@ template <> struct VecIO<float> {
     float* h = g + 4 * sn + 4 * x;
     *reinterpret_cast<float2*>(h) = make_float2(v[4], v[5]);
     h[2] = v[6];
+  }
+  static __device__ __forceinline__ void load5(const float* g, int64_t sn, int64_t x, float (&v)[5]) {
+    const float4 a = reinterpret_cast<const float4*>(g)[x];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = (g + 4 * sn)[4 * x];
   }
 };
 template <> struct VecIO<double> {
@@ -168,6 +175,15 @@ template <> struct VecIO<double> {
 #pragma unroll
     for (int k = 0; k < 3; ++k) reinterpret_cast<double2*>(g + 2 * k * sn)[x] = make_double2(v[2 * k], v[2 * k + 1]);
     (g + 6 * sn)[2 * x] = v[6];
+  }
+  static __device__ __forceinline__ void load5(const double* g, int64_t sn, int64_t x, double (&v)[5]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double2 a = reinterpret_cast<const double2*>(g + 2 * k * sn)[x];
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+    v[4] = (g + 4 * sn)[2 * x];
   }
 };
 
@@ -492,10 +508,7 @@ __device__ __forceinline__ void flux_face(const DPatch& p, int patch, const Cell
   hlld<R, kFastRecip>(L, Rr, bh, sc.gamma, sc.igm1, sc.eps_up, fr, &upw);
   rot_out(d, fr, f);
   f[5 + d] = upw;
-  // the contact side (slot 5+d) is read only by the upwinded EMF average
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (q != 5 + d || sc.emf != 1) arr(scr, p, SC_F + d * 8 + q)[x] = f[q];
+  VecIO<R>::store8(arr(scr, p, SC_F + d * 8), p.snelem, x, f);
 }
 
 template <typename R>
@@ -545,15 +558,16 @@ template <typename R, int a>
 __device__ __forceinline__ R emf_at(const DPatch& p, int64_t x, const R* scr, int emf) {
   constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
   const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
-  const R* Fbc = arr(scr, p, SC_F + b * 8 + 5 + cc);
-  const R* Fcb = arr(scr, p, SC_F + cc * 8 + 5 + b);
-  const R eb_lo = -Fbc[x - scc], eb_hi = -Fbc[x], ec_lo = Fcb[x - sb], ec_hi = Fcb[x];
+  const int64_t sn = p.snelem;
+  const R* Fb = arr(scr, p, SC_F + b * 8);
+  const R* Fc = arr(scr, p, SC_F + cc * 8);
+  const R eb_lo = -*vgroup_at(Fb, sn, x - scc, 5 + cc), eb_hi = -*vgroup_at(Fb, sn, x, 5 + cc);
+  const R ec_lo = *vgroup_at(Fc, sn, x - sb, 5 + b), ec_hi = *vgroup_at(Fc, sn, x, 5 + b);
   if (emf == 1) return R(0.25) * (eb_lo + eb_hi + ec_lo + ec_hi);
   const R* Er = arr(scr, p, SC_ER + a);
-  const R* Ub = arr(scr, p, SC_F + b * 8 + 5 + b);
-  const R* Uc = arr(scr, p, SC_F + cc * 8 + 5 + cc);
-  return edge_emf_value(eb_lo, eb_hi, ec_lo, ec_hi, Er[x - sb - scc], Er[x - scc], Er[x - sb], Er[x], Ub[x - scc],
-                        Ub[x], Uc[x - sb], Uc[x], emf);
+  return edge_emf_value(eb_lo, eb_hi, ec_lo, ec_hi, Er[x - sb - scc], Er[x - scc], Er[x - sb], Er[x],
+                        *vgroup_at(Fb, sn, x - scc, 5 + b), *vgroup_at(Fb, sn, x, 5 + b),
+                        *vgroup_at(Fc, sn, x - sb, 5 + cc), *vgroup_at(Fc, sn, x, 5 + cc), emf);
 }
 
 // Is the axis-a edge stored at cell c one of the edges of the update box's
@@ -595,10 +609,10 @@ __global__ void __launch_bounds__(kThreads) k_emf(const DPatch* __restrict__ P,
 // patches that feed flux registers also store the EMF of every update-box
 // edge at its element, where the capture kernel reads it; otherwise they are
 // read from k_emf's planes.
-// FP32: at most 51 registers (five blocks per SM); the compiler's free choice
-// (80-86) cost a quarter of the kernel's speed.
+// At most 51 registers in FP32 (five blocks per SM) and 85 in FP64 (three); the compiler's free choice
+// (80-86 in FP32) cost a quarter of the kernel's speed.
 template <typename R, bool EmfInline>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 1) k_update(const DPatch* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(const DPatch* __restrict__ P,
                                                      const BlockTask* __restrict__ T, R* scr,
                                                      SolverConsts<R> sc, const R* __restrict__ K, int commit) {
   const BlockTask t = T[blockIdx.x];
@@ -614,14 +628,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 1) k_update(con
   const bool cell = in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0);
   R un[5];
   if (cell) {
+    R f0a[5], f0b[5], f1a[5], f1b[5], f2a[5], f2b[5];
+    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x, f0a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x + 1, f0b);
+    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x, f1a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x + s1, f1b);
+    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x, f2a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x + s2, f2b);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const R* F0 = arr(scr, p, SC_F + 0 * 8 + q);
-      const R* F1 = arr(scr, p, SC_F + 1 * 8 + q);
-      const R* F2 = arr(scr, p, SC_F + 2 * 8 + q);
       R u = ((const R*)p.U[q])[x];
-      un[q] = u - st.dtdx[0] * (F0[x + 1] - F0[x]) - st.dtdx[1] * (F1[x + s1] - F1[x]) -
-              st.dtdx[2] * (F2[x + s2] - F2[x]);
+      un[q] = u - st.dtdx[0] * (f0b[q] - f0a[q]) - st.dtdx[1] * (f1b[q] - f1a[q]) - st.dtdx[2] * (f2b[q] - f2a[q]);
     }
   }
   bool face[3];

@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
   if (cp.kind == 0) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8 + q) * p.snelem;
-      const double v = dt * (double)F[x];
+      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8) * p.snelem;
+      const double v = dt * (double)*vgroup_at(F, p.snelem, x, q);
       double* o = cp.dst + (int64_t)q * nv + e;
       *o = cp.mode ? *o + v : v;
     }

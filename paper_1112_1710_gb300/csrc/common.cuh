@@ -94,6 +94,14 @@ __device__ __forceinline__ bool list_elem(const BlockTask& t, const int64_t* __r
   return e < starts[item + 1] - starts[item];
 }
 
+// Component q of element x in a vector group of scratch planes (the 8 slots
+// from g on, plane stride sn): FP32 groups are two planes of float4 (values
+// 0-3, 4-7), FP64 four planes of double2.
+template <typename R> __device__ __forceinline__ R* vgroup_at(R* g, int64_t sn, int64_t x, int q) {
+  constexpr int W = 16 / (int)sizeof(R);
+  return g + (int64_t)(q / W) * W * sn + W * x + (q % W);
+}
+
 // Tile of the tiled predictor (cells, x fastest; one thread per cell) per
 // element type; the host builds one block per tile of each patch's UB+1.
 constexpr int kPredTile32[3] = {32, 4, 2};

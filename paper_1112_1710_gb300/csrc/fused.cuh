@@ -297,7 +297,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FX[q * L::G1 + s1] = f[q];
       if (fst && own_z && hy >= 1 && hy <= TY && (hx <= TX || xlast)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 0 * 8 + q) * p.snelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) *vgroup_at(fst + (int64_t)(SC_F + 0 * 8) * p.snelem, p.snelem, x, q) = f[q];
       }
     } else if (dir == 1) {  // y-face: cells j-1 | j
       if (hy == 0) continue;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FY[q * L::G1 + s1] = f[q];
       if (fst && own_z && hx >= 1 && hx <= TX && (hy <= TY || ylast)) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 1 * 8 + q) * p.snelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) *vgroup_at(fst + (int64_t)(SC_F + 1 * 8) * p.snelem, p.snelem, x, q) = f[q];
       }
     } else {  // z-face at z-index zc: cells zc-1 | zc
       R dEc = EY0[se + 1] - EY0[se];
@@ -330,7 +330,7 @@ __device__ __forceinline__ void fused_flux(const DPatch& p, R* sm, int X0, int Y
       for (int q = 0; q < 8; ++q) FZ[q * L::G1 + s1] = f[q];
       if (fst && (own_z || own_ztop) && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) fst[(int64_t)(SC_F + 2 * 8 + q) * p.snelem + x] = f[q];
+        for (int q = 0; q < 5; ++q) *vgroup_at(fst + (int64_t)(SC_F + 2 * 8) * p.snelem, p.snelem, x, q) = f[q];
       }
     }
   }
