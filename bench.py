@@ -226,7 +226,7 @@ def kernel_flops(name, n, launched=()):
 # DRAM bytes (read + write) per step of the dominant kernels on this
 # workload (all of a kernel's launches in one step), from one ncu capture of
 # the current kernels (profiles/).  Keys: bench pass, kernel.
-KERNEL_TRAFFIC = {("f32", "k_update"): 310.6e6}
+KERNEL_TRAFFIC = {("f32", "k_pred"): 455.7e6, ("f32", "k_flux"): 686.3e6, ("f32", "k_update"): 341.1e6}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):

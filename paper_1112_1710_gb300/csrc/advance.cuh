@@ -115,7 +115,7 @@ template <typename R> __device__ __forceinline__ R* arr(R* scr, const DPatch& p,
 // W and the predicted face states use them.  The planes are aligned: arena
 // offsets and the plane stride (snelem) are multiples of 8 elements.  A face
 // state is stored in its face's rotated frame (rho, v_n, v_t1, v_t2, p, B_t1,
-// B_t2) as 7 values; the eighth slot of its group is never read.  The face
+// B_t2) as 7 values and a zero; the eighth slot of its group is never read.  The face
 // fluxes of each axis form one group too (the 8 components in the order of
 // the state, slot 5 + d carrying the contact side).
 template <typename R> struct VecIO;
@@ -132,16 +132,15 @@ template <> struct VecIO<float> {
   }
   static __device__ __forceinline__ void load7(const float* g, int64_t sn, int64_t x, float (&v)[7]) {
     const float4 a = reinterpret_cast<const float4*>(g)[x];
-    const float* h = g + 4 * sn + 4 * x;
-    const float2 b = *reinterpret_cast<const float2*>(h);
+    const float4 b = reinterpret_cast<const float4*>(g + 4 * sn)[x];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = h[2];
+    v[4] = b.x; v[5] = b.y; v[6] = b.z;
   }
+  // whole vectors (the eighth value 0): a partly written sector would be
+  // filled from DRAM first
   static __device__ __forceinline__ void store7(float* g, int64_t sn, int64_t x, const float (&v)[7]) {
     reinterpret_cast<float4*>(g)[x] = make_float4(v[0], v[1], v[2], v[3]);
-    float* h = g + 4 * sn + 4 * x;
-    *reinterpret_cast<float2*>(h) = make_float2(v[4], v[5]);
-    h[2] = v[6];
+    reinterpret_cast<float4*>(g + 4 * sn)[x] = make_float4(v[4], v[5], v[6], 0.0f);
   }
   static __device__ __forceinline__ void load5(const float* g, int64_t sn, int64_t x, float (&v)[5]) {
     const float4 a = reinterpret_cast<const float4*>(g)[x];
@@ -169,12 +168,12 @@ template <> struct VecIO<double> {
       v[2 * k] = a.x;
       v[2 * k + 1] = a.y;
     }
-    v[6] = (g + 6 * sn)[2 * x];
+    v[6] = reinterpret_cast<const double2*>(g + 6 * sn)[x].x;
   }
   static __device__ __forceinline__ void store7(double* g, int64_t sn, int64_t x, const double (&v)[7]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) reinterpret_cast<double2*>(g + 2 * k * sn)[x] = make_double2(v[2 * k], v[2 * k + 1]);
-    (g + 6 * sn)[2 * x] = v[6];
+    reinterpret_cast<double2*>(g + 6 * sn)[x] = make_double2(v[6], 0.0);
   }
   static __device__ __forceinline__ void load5(const double* g, int64_t sn, int64_t x, double (&v)[5]) {
 #pragma unroll
