@@ -239,6 +239,7 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
     from paper_1112_1710_gb300.runner import PeriodicRunner
 
     ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER)
+    ctx2 = None
     try:
         p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
         run = PeriodicRunner(p, ctx, stream)
@@ -279,7 +280,6 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         torch.cuda.synchronize()
         barrier(world)
         launches = per_graph * args.steps
-        run.graph = None
         # per-kernel attribution: the same steps launched eagerly, each launch
         # bracketed by CUDA events on the launching stream
         capi.mhd_timing_enable(ctx, True)
@@ -300,28 +300,50 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         capi.mhd_timing_enable(ctx, False)
         status = status or capi.mhd_get_device_status(ctx)
 
-        # end to end through the public API with host buffers: per step the state
-        # goes host -> device from pinned memory and the new state comes back
-        ne = args.e2e_steps or max(3, args.steps // 2)
-        host = torch.empty_like(p.state, device="cpu").pin_memory()
-        host.copy_(p.state)
-        nbytes = host.numel() * host.element_size()
+        # end to end through the public API with host buffers: every step moves
+        # its input state host -> device from pinned memory into a runner's
+        # patch, advances it with the runner's captured step, and reads the new
+        # state back into pinned memory.  Two runners (one cloned context, so
+        # one scratch arena, each) alternate on two streams, so that one
+        # step's copies overlap the other's compute and both directions of the
+        # host link are busy at once.
+        ne = args.e2e_steps or max(4, args.steps // 2)
+        ne += ne % 2
+        ctx2 = capi.mhd_ctx_clone(ctx)
+        stream2 = torch.cuda.Stream(device=local)
+        p2 = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
+        run2 = PeriodicRunner(p2, ctx2, stream2)
+        run2.capture_graph()
+        host_in = torch.empty_like(p.state, device="cpu").pin_memory()
+        host_in.copy_(p.state)
+        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+        nbytes = host_in.numel() * host_in.element_size()
+        runs = [(run, p, stream), (run2, p2, stream2)]
         torch.cuda.synchronize()
         barrier(world)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for _ in range(ne):
-            with torch.cuda.stream(stream):
-                p.state.copy_(host, non_blocking=True)
-            run.step()
-            with torch.cuda.stream(stream):
-                host.copy_(p.state, non_blocking=True)
+        stream2.wait_event(t0)
+        for k in range(ne):
+            r, pk, sk = runs[k % 2]
+            with torch.cuda.stream(sk):
+                pk.state.copy_(host_in, non_blocking=True)
+            r.replay()
+            with torch.cuda.stream(sk):
+                host_out[k % 2].copy_(pk.state, non_blocking=True)
+        j = torch.cuda.Event()
+        j.record(stream2)
+        stream.wait_event(j)
         t1.record(stream)
         t1.synchronize()
         e2e_ms = t0.elapsed_time(t1)
+        run.graph = None
+        run2.graph = None
         barrier(world)
     finally:
+        if ctx2 is not None:
+            capi.mhd_ctx_destroy(ctx2)
         capi.mhd_ctx_destroy(ctx)
     return {"total_ms": total_ms, "per_step_ms": per_step, "launches": launches, "kernels": kt,
             "status": status, "e2e_ms": e2e_ms, "e2e_steps": ne, "state_bytes": nbytes, "autotune": tuned,

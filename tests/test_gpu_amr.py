@@ -277,3 +277,50 @@ def test_blast_shell_full_size_fp64_properties(capi, capsys):
         ph.close()
     finally:
         capi.mhd_ctx_destroy(ctx)
+
+
+def test_deep_hierarchy_full_size_fp32_properties(capi, capsys):
+    """The deep-AMR workload at its full size (base 32^3 + 7 levels, 1,800
+    patches, 108 M cells on the k^-4 Mach-5 field, beta 1; the oracle runs it
+    only downscaled): one subcycled FP32 coarse step with FP64 flux registers
+    and sums keeps the composite totals of rho and E to the FP32 budget,
+    every face divergence at FP32 rounding, and the device status clean (no
+    non-positive density or pressure)."""
+    import synth.turb as ST
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 32
+    H, v, _ = ST.deep_hierarchy(n0=n0, levels=8, m=256)
+    assert len(H) == 8 and sum(len(l) for l in H) == 1800
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = None
+    try:
+        st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
+        del st
+        ph.initialise()
+        out = torch.zeros(8, dtype=torch.float64, device="cuda")
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s0 = out.cpu().numpy().copy()
+        ph.coarse_step()
+        capi.mhd_conservation_sums(ctx, ph.descs[0], out.data_ptr())
+        s1 = out.cpu().numpy()
+        assert ph.device_status() == 0
+        rel = np.abs(s1 - s0) / np.maximum(np.abs(s0), 1e-300)
+        divb = 0.0
+        for l, pats in enumerate(ph.levels):
+            for p in pats:
+                s = p.state
+                nx, ny, nz = p.n
+                d = ((s[5, G:G + nz, G:G + ny, G + 1:G + nx + 1] - s[5, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[6, G:G + nz, G + 1:G + ny + 1, G:G + nx] - s[6, G:G + nz, G:G + ny, G:G + nx])
+                     + (s[7, G + 1:G + nz + 1, G:G + ny, G:G + nx] - s[7, G:G + nz, G:G + ny, G:G + nx]))
+                bmax = max(float(s[5].abs().max()), float(s[6].abs().max()), float(s[7].abs().max()))
+                divb = max(divb, float(d.abs().max()) / bmax)
+        with capsys.disabled():
+            print("\nFP32 deep AMR full size, one coarse step: relative drift (rho, E) %.1e %.1e, "
+                  "max |div B| dx / max|B| %.1e" % (rel[0], rel[4], divb))
+        assert rel[0] < 1e-6 and rel[4] < 1e-6 and divb < 1e-4
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)
