@@ -48,14 +48,16 @@ constexpr int kNumFused64 = sizeof(kFusedVariants64) / sizeof(kFusedVariants64[0
 
 // Launch regions of the staged advance (UB = [lo, hi]): the predictor and
 // flux stages run over UB grown by region_m1 on each side, the update stages
-// over [lo - region_mu, hi + region_mu_top].  FP64: the regions the stages
-// fill (UB+1; [lo, hi + 1]), which saves the idle threads of small patches.
-// FP32: UB+2 for every stage, measured faster on GB300 for the 128^3 patch
-// (the predictor 150 against 165 us, the update 100 against 115 us) and
-// within 3% on the AMR hierarchy.
-constexpr int region_m1(size_t elem) { return elem == 8 ? 1 : 2; }
-constexpr int region_mu(size_t elem) { return elem == 8 ? 0 : 2; }
-constexpr int region_mu_top(size_t elem) { return elem == 8 ? 1 : 2; }
+// over [lo - region_mu, hi + region_mu_top]: the regions the stages fill
+// (UB+1; [lo, hi + 1]), which saves the idle threads of small patches.  The
+// alternative, UB+2 for every stage (a thread's element is then its storage
+// element), measured on GB300 in FP32: a 128^3 patch 0.432 against 0.428 ms
+// per step, a 64^3 patch 0.084 against 0.085 ms, and the AMR hierarchy of
+// 8-48 cell patches 65.9 against 63.1 ms per coarse step; FP64 is faster
+// over the tight regions at every size.
+constexpr int region_m1(size_t) { return 1; }
+constexpr int region_mu(size_t) { return 0; }
+constexpr int region_mu_top(size_t) { return 1; }
 
 // Kernel launches of one staged advance: step constants, k_prim, k_pred,
 // k_flux, k_update, and k_edge and k_emf in FP64.
