@@ -35,6 +35,10 @@
 #ifndef MHD_ADVANCE_NS
 #error "define MHD_ADVANCE_NS before including advance.cuh"
 #endif
+// Resident blocks per SM the FP32 predictor is compiled for.
+#ifndef MHD_PRED_MINB
+#define MHD_PRED_MINB 3
+#endif
 #ifndef MHD_FAST_RECIP
 #error "define MHD_FAST_RECIP (0: divide as the oracle does; 1: reciprocal form of HLLD)"
 #endif
@@ -300,32 +304,70 @@ template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPat
 }
 
 // ---------------------------------------------------------------- k_pred
-// The predictor of one cell from its primitives w and limited slopes dw:
-// first positivity rule, Hancock increment, the six predicted face states
-// (second positivity rule) and, for the upwinded EMF average, the reference
-// cell EMF, stored at element x.
-template <typename R>
-__device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr, const SolverConsts<R>& sc,
-                                             const StepDt<R>& st, const R (&w)[8], const R (&dw)[3][8]) {
-  // first positivity rule on the face values of rho and p
-  bool bad = false;
+// Limited slopes of one cell held in registers (dw[axis][component]).
+template <typename R> struct RegSlopes {
+  const R (&dw)[3][8];
+  __device__ __forceinline__ void get(int d, R (&out)[8]) const {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    R rm = w[0] - R(0.5) * dw[d][0], rp = w[0] + R(0.5) * dw[d][0];
-    R pm = w[4] - R(0.5) * dw[d][4], pp = w[4] + R(0.5) * dw[d][4];
-    if (!(rm > R(0)) || !(rp > R(0)) || !(pm > R(0)) || !(pp > R(0))) bad = true;
+    for (int q = 0; q < 8; ++q) out[q] = dw[d][q];
   }
+};
+
+// Limited slopes of one cell parked in shared memory: six float4 rows of
+// kThreads entries (axis d: rows 2d and 2d + 1), each thread its own column.
+// The stores and loads are volatile asm, so that the compiler neither
+// forwards the stored values in registers nor moves a load above its store;
+// the slopes then do not stay live across the Hancock increment, which is
+// what holds the FP32 predictor's registers down.
+__device__ __forceinline__ void sts4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w));
+}
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+struct SmemSlopes {
+  uint32_t base;  // shared address of row 0, this thread's column
+  __device__ __forceinline__ void put(int d, const float (&v)[8]) const {
+    sts4(base + (2 * d) * kThreads * 16, v[0], v[1], v[2], v[3]);
+    sts4(base + (2 * d + 1) * kThreads * 16, v[4], v[5], v[6], v[7]);
+  }
+  __device__ __forceinline__ void get(int d, float (&out)[8]) const {
+    const float4 a = lds4(base + (2 * d) * kThreads * 16), b = lds4(base + (2 * d + 1) * kThreads * 16);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+  }
+};
+
+// First positivity rule on the face values of rho and p along one axis:
+// true if a face value is not positive.
+template <typename R> __device__ __forceinline__ bool face_rule1(const R (&w)[8], const R (&dw)[8]) {
+  const R rm = w[0] - R(0.5) * dw[0], rp = w[0] + R(0.5) * dw[0];
+  const R pm = w[4] - R(0.5) * dw[4], pp = w[4] + R(0.5) * dw[4];
+  return !(rm > R(0)) || !(rp > R(0)) || !(pm > R(0)) || !(pp > R(0));
+}
+
+// The predictor of one cell from its primitives w and limited slopes (S),
+// given the first positivity rule's verdict `bad` over the three axes:
+// Hancock increment, the six predicted face states (second positivity rule)
+// and, for the upwinded EMF average, the reference cell EMF, stored at
+// element x.
+template <typename R, typename S>
+__device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr, const SolverConsts<R>& sc,
+                                             const StepDt<R>& st, const R (&w)[8], const S& slopes, bool bad) {
   // Hancock increment
   R du[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) du[q] = R(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    R fwm[8], fwp[8], fm[8], fp[8];
+    R dw[8], fwm[8], fwp[8], fm[8], fp[8];
+    slopes.get(d, dw);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      fwm[q] = bad ? w[q] : w[q] - R(0.5) * dw[d][q];
-      fwp[q] = bad ? w[q] : w[q] + R(0.5) * dw[d][q];
+      fwm[q] = bad ? w[q] : w[q] - R(0.5) * dw[q];
+      fwp[q] = bad ? w[q] : w[q] + R(0.5) * dw[q];
     }
     flux_xyz(d, fwp, sc.igm1, fp);
     flux_xyz(d, fwm, sc.igm1, fm);
@@ -336,12 +378,13 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
   bool bad2 = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
+    R dw[8];
+    slopes.get(d, dw);
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
       R fw[8], u[8], pw[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        fw[q] = bad ? w[q] : (sd ? w[q] + R(0.5) * dw[d][q] : w[q] - R(0.5) * dw[d][q]);
+      for (int q = 0; q < 8; ++q) fw[q] = bad ? w[q] : (sd ? w[q] + R(0.5) * dw[q] : w[q] - R(0.5) * dw[q]);
       prim2cons(fw, sc.igm1, u);
 #pragma unroll
       for (int q = 0; q < 8; ++q) u[q] = u[q] + du[q];
@@ -375,15 +418,19 @@ __device__ __forceinline__ void predict_cell(const DPatch& p, int64_t x, R* scr,
 }
 
 // One thread per cell of UB+1; the stencil of W is read from the scratch
-// planes through the caches.
-// Launch bounds: at most 128 registers per thread for the FP32 predictor and
-// 64 for the FP32 flux kernel (two and four blocks per SM); past those the
-// compiler's choice drops a block per SM and the kernels, bound by the
-// latency of their loads, slow down.
+// planes through the caches.  FP32 parks the slopes in shared memory
+// (SmemSlopes) and is held at 80 registers, three blocks per SM (measured on
+// GB300: 132 us against 136 us with the slopes in registers at 117 registers
+// and two blocks); FP64 keeps them in registers at one block per SM, its
+// time being set by the FP64 pipe.  The FP32 flux kernel is held at 64
+// registers (four blocks per SM): past that the compiler's choice drops a
+// block per SM and the kernel, bound by the latency of its loads, slows down.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const DPatch* __restrict__ P,
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? MHD_PRED_MINB : 1) k_pred(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
                                                    SolverConsts<R> sc, const R* __restrict__ K) {
+  constexpr bool smem = sizeof(R) == 4;
+  __shared__ float4 sdw[smem ? 6 : 1][smem ? kThreads : 1];
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
@@ -394,6 +441,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const
   R w[8], dw[3][8];
   const R* Wg = arr(scr, p, SC_W);
   VecIO<R>::load8(Wg, p.snelem, x, w);
+  SmemSlopes ss{(uint32_t)__cvta_generic_to_shared(&sdw[0][smem ? threadIdx.x : 0])};
+  bool bad = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int64_t sd = stride_of(p, d);
@@ -401,13 +450,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_pred(const
     VecIO<R>::load8(Wg, p.snelem, x - sd, wm);
     VecIO<R>::load8(Wg, p.snelem, x + sd, wp);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      R a = w[q] - wm[q];
-      R b = wp[q] - w[q];
-      dw[d][q] = limiter(sc.limiter, a, b);
-    }
+    for (int q = 0; q < 8; ++q) dw[d][q] = limiter(sc.limiter, w[q] - wm[q], wp[q] - w[q]);
+    if (face_rule1(w, dw[d])) bad = true;
+    if constexpr (smem) ss.put(d, dw[d]);
   }
-  predict_cell(p, x, scr, sc, st, w, dw);
+  if constexpr (smem) predict_cell(p, x, scr, sc, st, w, ss, bad);
+  else predict_cell(p, x, scr, sc, st, w, RegSlopes<R>{dw}, bad);
 }
 
 // Tiled predictor: a block owns a TX x TY x TZ tile of UB+1 cells (its task's
@@ -471,8 +519,12 @@ __global__ void __launch_bounds__(kThreads) k_pred_tiled(const DPatch* __restric
       dw[d][q] = limiter(sc.limiter, a, b);
     }
   }
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (face_rule1(w, dw[d])) bad = true;
   const int64_t x = (int64_t)(x0 + ix) + (int64_t)(y0 + iy) * p.s1 + (int64_t)(z0 + iz) * p.s2;
-  predict_cell(p, x, scr, sc, st, w, dw);
+  predict_cell(p, x, scr, sc, st, w, RegSlopes<R>{dw}, bad);
 }
 
 // ---------------------------------------------------------------- k_flux
