@@ -149,7 +149,7 @@ template <> struct VecIO<float> {
   static __device__ __forceinline__ void load5(const float* g, int64_t sn, int64_t x, float (&v)[5]) {
     const float4 a = reinterpret_cast<const float4*>(g)[x];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = (g + 4 * sn)[4 * x];
+    v[4] = reinterpret_cast<const float4*>(g + 4 * sn)[x].x;
   }
 };
 template <> struct VecIO<double> {
@@ -621,6 +621,24 @@ __device__ __forceinline__ R emf_at(const DPatch& p, int64_t x, const R* scr, in
                         *vgroup_at(Fc, sn, x - sb, 5 + cc), *vgroup_at(Fc, sn, x, 5 + cc), emf);
 }
 
+// FP32 arithmetic-average edge EMF (the same value as emf_at with emf == 1)
+// with the induction fluxes read as whole float4 vectors, slots 4-7 of the
+// flux groups: one thread's nine edges and its cell update read 24 such
+// vectors at repeated positions, which the compiler then loads once each,
+// instead of 36 scalars at a 16-byte stride.
+template <int i> __device__ __forceinline__ float slot4(const float4& v) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+template <int a> __device__ __forceinline__ float emf_avg4(const DPatch& p, int64_t y, const float* scr) {
+  constexpr int b = (a + 1) % 3, cc = (a + 2) % 3;
+  const int64_t sb = stride_of(p, b), scc = stride_of(p, cc);
+  const float4* Fb = reinterpret_cast<const float4*>(arr(scr, p, SC_F + b * 8) + 4 * p.snelem);
+  const float4* Fc = reinterpret_cast<const float4*>(arr(scr, p, SC_F + cc * 8) + 4 * p.snelem);
+  const float eb_lo = -slot4<1 + cc>(Fb[y - scc]), eb_hi = -slot4<1 + cc>(Fb[y]);
+  const float ec_lo = slot4<1 + b>(Fc[y - sb]), ec_hi = slot4<1 + b>(Fc[y]);
+  return 0.25f * (eb_lo + eb_hi + ec_lo + ec_hi);
+}
+
 // Is the axis-a edge stored at cell c one of the edges of the update box's
 // faces (the edges whose EMF the flux registers capture)?
 template <int a> __device__ __forceinline__ bool update_edge(const DPatch& p, const Cell& c) {
@@ -677,21 +695,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(con
   // every load before the first store: the state and scratch pointers may
   // alias as far as the compiler knows, so a store would order later loads
   const bool cell = in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0);
-  R un[5];
-  if (cell) {
-    R f0a[5], f0b[5], f1a[5], f1b[5], f2a[5], f2b[5];
-    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x, f0a);
-    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x + 1, f0b);
-    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x, f1a);
-    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x + s1, f1b);
-    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x, f2a);
-    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x + s2, f2b);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      R u = ((const R*)p.U[q])[x];
-      un[q] = u - st.dtdx[0] * (f0b[q] - f0a[q]) - st.dtdx[1] * (f1b[q] - f1a[q]) - st.dtdx[2] * (f2b[q] - f2a[q]);
-    }
-  }
   bool face[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -702,7 +705,31 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(con
   // E2 at x, x+1; face 2 E1 at x, x+1 and E0 at x, x+s1
   const R* cs = scr;
   R e0 = R(0), e0y = R(0), e0z = R(0), e1 = R(0), e1x = R(0), e1z = R(0), e2 = R(0), e2x = R(0), e2y = R(0);
-  if constexpr (EmfInline) {
+  if constexpr (EmfInline && sizeof(R) == 4) {
+    if (sc.emf == 1) {
+      // every position these read lies in UB+2, inside the planes, so the
+      // reads are unconditional and repeated positions are loaded once
+      e0 = emf_avg4<0>(p, x, cs);
+      e0z = emf_avg4<0>(p, x + s2, cs);
+      e0y = emf_avg4<0>(p, x + s1, cs);
+      e1 = emf_avg4<1>(p, x, cs);
+      e1z = emf_avg4<1>(p, x + s2, cs);
+      e1x = emf_avg4<1>(p, x + 1, cs);
+      e2 = emf_avg4<2>(p, x, cs);
+      e2y = emf_avg4<2>(p, x + s1, cs);
+      e2x = emf_avg4<2>(p, x + 1, cs);
+    } else {
+      if (face[1] || face[2]) e0 = emf_at<R, 0>(p, x, cs, sc.emf);
+      if (face[1]) e0z = emf_at<R, 0>(p, x + s2, cs, sc.emf);
+      if (face[2]) e0y = emf_at<R, 0>(p, x + s1, cs, sc.emf);
+      if (face[0] || face[2]) e1 = emf_at<R, 1>(p, x, cs, sc.emf);
+      if (face[0]) e1z = emf_at<R, 1>(p, x + s2, cs, sc.emf);
+      if (face[2]) e1x = emf_at<R, 1>(p, x + 1, cs, sc.emf);
+      if (face[0] || face[1]) e2 = emf_at<R, 2>(p, x, cs, sc.emf);
+      if (face[0]) e2y = emf_at<R, 2>(p, x + s1, cs, sc.emf);
+      if (face[1]) e2x = emf_at<R, 2>(p, x + 1, cs, sc.emf);
+    }
+  } else if constexpr (EmfInline) {
     if (face[1] || face[2]) e0 = emf_at<R, 0>(p, x, cs, sc.emf);
     if (face[1]) e0z = emf_at<R, 0>(p, x + s2, cs, sc.emf);
     if (face[2]) e0y = emf_at<R, 0>(p, x + s1, cs, sc.emf);
@@ -726,6 +753,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(con
     if (face[0]) e2y = E2[x + s1];
     if (face[1]) e2x = E2[x + 1];
   }
+  R un[5];
+  if (cell) {
+    R f0a[5], f0b[5], f1a[5], f1b[5], f2a[5], f2b[5];
+    // (FP32: VecIO::load5 reads slot 4 as the x of the plane-2 float4, the
+    // vector the inline edge EMFs read too)
+    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x, f0a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 0 * 8), p.snelem, x + 1, f0b);
+    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x, f1a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 1 * 8), p.snelem, x + s1, f1b);
+    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x, f2a);
+    VecIO<R>::load5(arr(scr, p, SC_F + 2 * 8), p.snelem, x + s2, f2b);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      R u = ((const R*)p.U[q])[x];
+      un[q] = u - st.dtdx[0] * (f0b[q] - f0a[q]) - st.dtdx[1] * (f1b[q] - f1a[q]) - st.dtdx[2] * (f2b[q] - f2a[q]);
+    }
+  }
   // B_a^{n+1} = B_a^n - (dt/dx_b (E_c(x + s_b) - E_c(x)) - dt/dx_c (E_b(x + s_c) - E_b(x)))
   R bn[3];
   if (face[0]) bn[0] = ((const R*)p.B[0])[x] - (st.dtdx[1] * (e2y - e2) - st.dtdx[2] * (e1z - e1));
@@ -735,9 +779,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(con
   const bool cap = EmfInline && (p.flags & 1) != 0;
   const bool ce0 = cap && update_edge<0>(p, c), ce1 = cap && update_edge<1>(p, c), ce2 = cap && update_edge<2>(p, c);
   R ec0 = R(0), ec1 = R(0), ec2 = R(0);
-  if (ce0) ec0 = emf_at<R, 0>(p, x, cs, sc.emf);
-  if (ce1) ec1 = emf_at<R, 1>(p, x, cs, sc.emf);
-  if (ce2) ec2 = emf_at<R, 2>(p, x, cs, sc.emf);
+  if constexpr (sizeof(R) == 4) {
+    if (sc.emf == 1) {  // the values the face updates used
+      ec0 = e0;
+      ec1 = e1;
+      ec2 = e2;
+    }
+  }
+  if (ce0 && !(sizeof(R) == 4 && sc.emf == 1)) ec0 = emf_at<R, 0>(p, x, cs, sc.emf);
+  if (ce1 && !(sizeof(R) == 4 && sc.emf == 1)) ec1 = emf_at<R, 1>(p, x, cs, sc.emf);
+  if (ce2 && !(sizeof(R) == 4 && sc.emf == 1)) ec2 = emf_at<R, 2>(p, x, cs, sc.emf);
   // without commit the new state goes to the (by now unused) primitive planes
   if (cell) {
 #pragma unroll
