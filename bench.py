@@ -36,6 +36,7 @@ METRIC = "MHD cell-updates/s (FP64 vs FP32-mixed, % HBM roofline); patch p50/p99
 # perpendicular shock front within a few steps)
 SOLVER = {"gamma": 5.0 / 3.0, "cfl": 0.4, "limiter": 0, "emf": 1}
 UNIT = "cell-updates/s"
+E2E_RUNNERS = 3  # runners taking the end-to-end steps in turn
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -239,7 +240,7 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
     from paper_1112_1710_gb300.runner import PeriodicRunner
 
     ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER)
-    ctx2 = None
+    clones = []
     try:
         p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
         run = PeriodicRunner(p, ctx, stream)
@@ -303,47 +304,53 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         # end to end through the public API with host buffers: every step moves
         # its input state host -> device from pinned memory into a runner's
         # patch, advances it with the runner's captured step, and reads the new
-        # state back into pinned memory.  Two runners (one cloned context, so
-        # one scratch arena, each) alternate on two streams, so that one
-        # step's copies overlap the other's compute and both directions of the
-        # host link are busy at once.
-        ne = args.e2e_steps or max(4, args.steps // 2)
-        ne += ne % 2
-        ctx2 = capi.mhd_ctx_clone(ctx)
-        stream2 = torch.cuda.Stream(device=local)
-        p2 = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
-        run2 = PeriodicRunner(p2, ctx2, stream2)
-        run2.capture_graph()
+        # state back into pinned memory.  E2E_RUNNERS runners (cloned
+        # contexts, so one scratch arena each) take the steps in turn on their
+        # own streams, so that the copies of some steps overlap the compute of
+        # another and both directions of the host link stay busy (the link
+        # moves a step's state in and out in about the time of one step).
+        ne = args.e2e_steps or max(8 * E2E_RUNNERS, args.steps)
+        ne += (-ne) % E2E_RUNNERS
+        runs = [(run, p, stream)]
+        for _ in range(E2E_RUNNERS - 1):
+            cx = capi.mhd_ctx_clone(ctx)
+            clones.append(cx)
+            sx = torch.cuda.Stream(device=local)
+            px = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
+            rx = PeriodicRunner(px, cx, sx)
+            rx.capture_graph()
+            runs.append((rx, px, sx))
         host_in = torch.empty_like(p.state, device="cpu").pin_memory()
         host_in.copy_(p.state)
-        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(E2E_RUNNERS)]
         nbytes = host_in.numel() * host_in.element_size()
-        runs = [(run, p, stream), (run2, p2, stream2)]
         torch.cuda.synchronize()
         barrier(world)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        stream2.wait_event(t0)
+        for _, _, sx in runs[1:]:
+            sx.wait_event(t0)
         for k in range(ne):
-            r, pk, sk = runs[k % 2]
+            r, pk, sk = runs[k % E2E_RUNNERS]
             with torch.cuda.stream(sk):
                 pk.state.copy_(host_in, non_blocking=True)
             r.replay()
             with torch.cuda.stream(sk):
-                host_out[k % 2].copy_(pk.state, non_blocking=True)
-        j = torch.cuda.Event()
-        j.record(stream2)
-        stream.wait_event(j)
+                host_out[k % E2E_RUNNERS].copy_(pk.state, non_blocking=True)
+        for _, _, sx in runs[1:]:
+            j = torch.cuda.Event()
+            j.record(sx)
+            stream.wait_event(j)
         t1.record(stream)
         t1.synchronize()
         e2e_ms = t0.elapsed_time(t1)
-        run.graph = None
-        run2.graph = None
+        for r, _, _ in runs:
+            r.graph = None
         barrier(world)
     finally:
-        if ctx2 is not None:
-            capi.mhd_ctx_destroy(ctx2)
+        for cx in clones:
+            capi.mhd_ctx_destroy(cx)
         capi.mhd_ctx_destroy(ctx)
     return {"total_ms": total_ms, "per_step_ms": per_step, "launches": launches, "kernels": kt,
             "status": status, "e2e_ms": e2e_ms, "e2e_steps": ne, "state_bytes": nbytes, "autotune": tuned,
