@@ -24,8 +24,8 @@ differences and order are used).
 
 Hilbert splitting (Sec. 5.2), readings where the text leaves the detail
 open (each also listed with the design notes):
-  1. the weight list is cut into a prefix and a suffix whose sums differ
-     least; ties go to the shorter prefix;
+  1. the weight list is cut into a prefix and a suffix whose sums (added
+     in list order) differ least; ties go to the shorter prefix;
   2. a candidate split cuts one axis of extent >= 2 at an integer position
      next to the proportional point (floor and ceiling of share * extent,
      kept inside [1, extent - 1]), with the prefix's piece on the low side or
@@ -128,13 +128,22 @@ def global_index(local_counts):
     return out
 
 
+def wsum(ws):
+    """Sum of a weight list added in list order, one rounding per addition
+    (Python's built-in sum() compensates the rounding of float sums)."""
+    s = 0.0
+    for v in ws:
+        s = s + v
+    return s
+
+
 def split_weights(weights):
     """Step 1: (prefix, suffix) of the weight list with the least difference
     of sums, ties to the shorter prefix."""
     best, cut = None, 1
     for k in range(1, len(weights)):
-        a = sum(weights[:k])
-        b = sum(weights[k:])
+        a = wsum(weights[:k])
+        b = wsum(weights[k:])
         dif = abs(a - b)
         if best is None or dif < best:
             best, cut = dif, k
@@ -152,14 +161,14 @@ def advance_cost(lo, hi, g):
 def split_candidates(lo, hi, wa, wb):
     """Step 2: (axis, prefix piece on the high side?, cut) in enumeration
     order; the cut is the extent of the low piece along the axis."""
-    tot = sum(wa) + sum(wb)
+    tot = wsum(wa) + wsum(wb)
     out = []
     for d in range(len(lo)):
         L = hi[d] - lo[d] + 1
         if L < 2:
             continue
         for high in (False, True):
-            share_low = (sum(wb) if high else sum(wa)) / tot
+            share_low = (wsum(wb) if high else wsum(wa)) / tot
             pos = share_low * L
             cuts = sorted({min(max(int(pos // 1), 1), L - 1), min(max(-int((-pos) // 1), 1), L - 1)})
             for c in cuts:
@@ -182,8 +191,8 @@ def hilbert_split(lo, hi, weights, bits, g=2):
     if len(weights) == 1:
         return [(lo, hi)]
     wa, wb = split_weights(weights)
-    tot = sum(wa) + sum(wb)
-    sa, sb = sum(wa) / tot, sum(wb) / tot
+    tot = wsum(wa) + wsum(wb)
+    sa, sb = wsum(wa) / tot, wsum(wb) / tot
     cands = []
     for d, high, c in split_candidates(lo, hi, wa, wb):
         low_box, high_box = cut_box(lo, hi, d, c)
