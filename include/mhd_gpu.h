@@ -376,6 +376,46 @@ mhd_status mhd_tree_inherit(const int32_t *d_lo, const int32_t *d_hi, int32_t n,
                             const int32_t *d_kid, const int64_t *d_out_off, int32_t *d_count, int32_t *d_out,
                             int8_t *d_out_shift, void *stream);
 
+/* ---- Space-filling-curve ordering and Hilbert splitting (Sec. 5.1, 5.2) ----
+ * Hilbert index: Skilling's transposed-axes construction of the Hilbert
+ * curve through [0, 2^bits)^dim (dim 2 or 3; bits <= 30 in 2-D, <= 20 in
+ * 3-D).  The curve starts at the origin, steps between face neighbours, and
+ * gives the 2^dim children of a cell (coordinates 2x .. 2x+1) one contiguous
+ * block of indices, so that child order follows parent order (Sec. 5.1).
+ * The distance of a grid along the curve is the sum of the indices of its
+ * 2^dim corner cells (Sec. 5.1 samples a grid by its corners). */
+
+/* Keys of n_pts points: d_pts int32 device array [n_pts][dim] (coordinates
+ * of one point together), d_keys uint64 device array of n_pts; a point
+ * outside [0, 2^bits)^dim gets the key UINT64_MAX.  Enqueues one kernel on
+ * `stream`; MHD_EINVAL for bad arguments (nothing launched), MHD_ECUDA if the
+ * launch fails. */
+mhd_status mhd_hilbert_keys(const int32_t *d_pts, int64_t n_pts, int32_t dim, int32_t bits, uint64_t *d_keys,
+                            void *stream);
+
+/* Distances of n_boxes inclusive boxes (d_lo, d_hi int32 device arrays
+ * [n_boxes][dim]) into d_dist (int64 device array); a box that is empty or
+ * leaves [0, 2^bits)^dim gets INT64_MAX.  Same launch and errors as
+ * mhd_hilbert_keys. */
+mhd_status mhd_box_distances(const int32_t *d_lo, const int32_t *d_hi, int64_t n_boxes, int32_t dim,
+                             int32_t bits, int64_t *d_dist, void *stream);
+
+/* Hilbert splitting of the inclusive box [lo, hi] (host arrays of dim
+ * values, inside [0, 2^bits)^dim) into one piece per weight (host array of
+ * n_weights positive finite values), by the recursive bisection of Sec. 5.2:
+ * the weight list is cut where the two sums differ least (ties to the
+ * shorter prefix); each axis of extent >= 2 is cut next to the proportional
+ * point (floor and ceiling), with the prefix's piece on the low or on the
+ * high side; the candidate whose slower piece has the least cells-with-ghosts
+ * (extent + 2 ghost per axis) per unit of weight wins, and among candidates
+ * within 1% of that cost the one whose suffix piece leads the prefix piece
+ * furthest along the curve; both pieces are split again with their weights.
+ * Writes the pieces, in weight order, to the host arrays out_lo, out_hi
+ * [n_weights][dim].  Host code only (no device work).  MHD_EINVAL for bad
+ * arguments or when a piece of one cell would have to be split. */
+mhd_status mhd_hilbert_split(const int32_t *lo, const int32_t *hi, int32_t dim, const double *weights,
+                             int32_t n_weights, int32_t bits, int32_t ghost, int32_t *out_lo, int32_t *out_hi);
+
 /* Number of kernels this context has enqueued so far (for launch accounting). */
 int64_t mhd_launch_count(const mhd_ctx *ctx);
 

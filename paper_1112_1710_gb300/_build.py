@@ -27,6 +27,7 @@ UNITS = {
     "noalloc.cu": ["--fmad=false"],
     "amr_ops.cu": ["--fmad=false"],
     "tree.cu": [],
+    "hilbert.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
 }
 
 
