@@ -713,6 +713,43 @@ def amr_attribution(H, states, dtype, steps, local):
             "device_status": status}
 
 
+def time_hilbert(H, states, steps, local):
+    """Sec. 5.1-5.2 on one GPU: the device key kernel on 2^26 3-D points
+    (20-bit coordinates), the host splitting of a 512^3 base grid over 152
+    equal shares, and the FP32 AMR coarse step with every level's patches in
+    curve order instead of the generator's order."""
+    import torch
+
+    from paper_1112_1710_gb300 import hilbert as PH
+    n = 1 << 26
+    g = torch.Generator(device="cuda:%d" % local).manual_seed(1112)
+    pts = torch.randint(0, 1 << 20, (n, 3), dtype=torch.int32, device="cuda:%d" % local, generator=g)
+    PH.keys(pts, 20)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        PH.keys(pts, 20)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    hbm, hbm_src, _ = peaks()
+    gbs = n * (12 + 8) / (ms * 1e-3) / 1e9
+    t0 = time.perf_counter()
+    PH.split((0, 0, 0), (511, 511, 511), [1.0] * 152, 9)
+    split_ms = (time.perf_counter() - t0) * 1e3
+    perms = PH.hilbert_order_hierarchy(H, 64, device="cuda:%d" % local)
+    H2 = [[bl[i] for i in perms[l]] for l, bl in enumerate(H)]
+    S2 = [[states[l][i] for i in perms[l]] for l in range(len(H))]
+    run = time_amr(H2, S2, "f32", steps, "graph", local)
+    run["order"] = "hilbert"
+    return {"keys": {"points": n, "bits": 20, "ms": ms, "points_per_s": n / (ms * 1e-3),
+                     "bytes_per_point": 20, "achieved_gbs": gbs, "peak_gbs": hbm, "frac_of_hbm": gbs / hbm,
+                     "peak_source": hbm_src},
+            "split_512cube_152_ms": split_ms, "amr_f32_graph_hilbert_order": run}
+
+
 def run_amr(args):
     import torch
     rank, world, local = dist_setup()
@@ -727,6 +764,7 @@ def run_amr(args):
            time_amr(H, states, "f64", 1, "per_patch", local)]
     attribution = amr_attribution(H, states, "f32", 2, local)
     meta = time_metadata(H, 64, local)
+    hil = time_hilbert(H, states, args.steps, local)
     if rank != 0:
         return
     cpu = None
@@ -747,7 +785,7 @@ def run_amr(args):
                                    sum(len(l) for l in H),
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
-            "runs": res, "kernels_f32": attribution, "metadata": meta}
+            "runs": res, "kernels_f32": attribution, "metadata": meta, "hilbert": hil}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))

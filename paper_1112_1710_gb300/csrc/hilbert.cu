@@ -35,8 +35,33 @@ constexpr int64_t kBadDist = INT64_MAX;
 // 3-D keys 3; a corner sum of 2^dim keys must stay below 2^63.
 __host__ __device__ inline int max_bits(int dim) { return dim == 2 ? 30 : 20; }
 
+// Spreads the low 21 bits of v to every third bit (bit j -> bit 3 j).
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+// Spreads the low 32 bits of v to every second bit (bit j -> bit 2 j).
+__host__ __device__ inline uint64_t spread2(uint32_t v) {
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
 // Hilbert index of the cell x[0..dim) at resolution `bits` (every coordinate
-// in [0, 2^bits) is the caller's precondition).
+// in [0, 2^bits) is the caller's precondition).  The exchange step is
+// written without branches (a mask selects inversion or exchange), and the
+// transposed bits are read off as a bit interleave: bit j of coordinate i
+// becomes bit dim j + (dim - 1 - i) of the index.
 __host__ __device__ inline uint64_t hilbert_key(const int32_t* x, int dim, int bits) {
   uint32_t X[3] = {0, 0, 0};
   for (int i = 0; i < dim; ++i) X[i] = (uint32_t)x[i];
@@ -44,25 +69,21 @@ __host__ __device__ inline uint64_t hilbert_key(const int32_t* x, int dim, int b
   const uint32_t top = 1u << (bits - 1);
   for (uint32_t Q = top; Q > 1; Q >>= 1) {
     const uint32_t P = Q - 1;
-    for (int i = 0; i < dim; ++i) {
-      if (X[i] & Q) {
-        X[0] ^= P;
-      } else {
-        const uint32_t t = (X[0] ^ X[i]) & P;
-        X[0] ^= t;
-        X[i] ^= t;
-      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (i >= dim) break;
+      const uint32_t inv = (X[i] & Q) ? P : 0u;          // bit set: invert
+      const uint32_t t = (X[0] ^ X[i]) & (P & ~inv);     // bit clear: exchange
+      X[0] ^= inv | t;
+      X[i] ^= t;
     }
   }
   for (int i = 1; i < dim; ++i) X[i] ^= X[i - 1];
   uint32_t t = 0;
-  for (uint32_t Q = top; Q > 1; Q >>= 1)
-    if (X[dim - 1] & Q) t ^= Q - 1;
+  for (uint32_t Q = top; Q > 1; Q >>= 1) t ^= (X[dim - 1] & Q) ? Q - 1 : 0u;
   for (int i = 0; i < dim; ++i) X[i] ^= t;
-  uint64_t h = 0;
-  for (int j = bits - 1; j >= 0; --j)
-    for (int i = 0; i < dim; ++i) h = (h << 1) | ((X[i] >> j) & 1u);
-  return h;
+  return dim == 3 ? (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2])
+                  : (spread2(X[0]) << 1) | spread2(X[1]);
 }
 
 __host__ __device__ inline bool in_curve(const int32_t* x, int dim, int bits) {
