@@ -227,7 +227,7 @@ def kernel_flops(name, n, launched=()):
 # DRAM bytes (read + write) per step of the dominant kernels on this
 # workload (all of a kernel's launches in one step), from one ncu capture of
 # the current kernels (profiles/).  Keys: bench pass, kernel.
-KERNEL_TRAFFIC = {("f32", "k_pred"): 471.1e6, ("f32", "k_flux"): 685.6e6, ("f32", "k_update"): None,
+KERNEL_TRAFFIC = {("f32", "k_pred"): 471.1e6, ("f32", "k_flux"): 685.6e6, ("f32", "k_update"): 342.7e6,
                   ("f64", "k_pred"): 969.3e6, ("f64", "k_flux"): 1395.4e6,
                   ("f64_exact", "k_pred"): 969.2e6, ("f64_exact", "k_flux"): 1398.0e6}
 
