@@ -216,6 +216,18 @@ mhd_status mhd_patch_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_
                              const double *dt_scale, const mhd_capture *caps,
                              int32_t ncap, void *stream);
 
+/* One single-level step whose dt is the CFL time step of the state it starts
+ * from: writes to the device double *d_dt_out what mhd_cfl_dt (scale NULL)
+ * would, then advances the n patches (update box = interior, no captures) by
+ * that dt as mhd_patch_advance does.  The staged kernels compute the CFL
+ * reduction inside the primitive pass (the same expressions, so the same dt
+ * in the FP64 parity build), which saves reading the state a second time;
+ * the fused kernel runs the separate reduction first.  For a hierarchy, whose
+ * dt is a minimum over all levels (Sec. 2.2), use mhd_cfl_dt and
+ * mhd_patch_advance.  Errors as mhd_patch_advance. */
+mhd_status mhd_patch_step_cfl(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n, double *d_dt_out,
+                              void *stream);
+
 /* Autotuner of the advance (no counterpart in the paper; it picks how the
  * patches of a call are advanced).  Times, on these patches (update box grown
  * by grow[p], may be NULL for zeros; dt from *d_dt), the staged kernels with

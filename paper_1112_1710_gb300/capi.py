@@ -24,7 +24,8 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_launch_count", "mhd_timing_enable", "mhd_timing_read", "mhd_timing_reset",
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
            "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit",
-           "mhd_ctx_clone", "mhd_hilbert_keys", "mhd_box_distances", "mhd_hilbert_split")
+           "mhd_ctx_clone", "mhd_hilbert_keys", "mhd_box_distances", "mhd_hilbert_split",
+           "mhd_patch_step_cfl")
 N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
@@ -158,6 +159,8 @@ def load(build_if_missing: bool = False):
     L.mhd_tree_parents.argtypes = [P, P, i32, P, P, i32, P, P, P, P]
     L.mhd_tree_inherit.restype = i32
     L.mhd_tree_inherit.argtypes = [P, P, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]
+    L.mhd_patch_step_cfl.restype = i32
+    L.mhd_patch_step_cfl.argtypes = [P, C.POINTER(mhd_patch_desc), i32, P, P]
     L.mhd_hilbert_keys.restype = i32
     L.mhd_hilbert_keys.argtypes = [P, i64, i32, i32, P, P]
     L.mhd_box_distances.restype = i32
@@ -242,6 +245,11 @@ def mhd_patch_advance(ctx, patches, d_dt: int, stream: int = 0, grow=None, dt_sc
     else:
         ca, nca = _structs(mhd_capture, caps)
     _check(ctx, load().mhd_patch_advance(ctx, arr, n, gr, d_dt, sc, ca, nca, stream))
+
+
+def mhd_patch_step_cfl(ctx, patches, d_dt_out: int, stream: int = 0) -> None:
+    arr, n = _descs(patches)
+    _check(ctx, load().mhd_patch_step_cfl(ctx, arr, n, d_dt_out, stream))
 
 
 def mhd_prolong(ctx, coarse, fine, items, stream: int = 0) -> None:

@@ -238,33 +238,80 @@ template <typename R> struct StepDt {
 };
 
 // ---------------------------------------------------------------- k_prim
-template <typename R>
+// Primitives and cell EMFs on UB+2.  With Cfl, also the CFL time step of the
+// step (the quantity mhd_cfl_dt computes, with the same expressions): each
+// interior cell's candidate min_d dx_d / (|v_d| + c_f,d) from the same
+// primitives, the block minimum (warp shuffles, then shared memory), and one
+// atomicMin per block on the IEEE bits of (cfl * min) * cfl_scale in FP64
+// (positive doubles order as their bits), into *dt_bits, which must hold
+// +infinity before the launch.
+template <typename R, bool Cfl>
 __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
                                                    const BlockTask* __restrict__ T, R* scr,
-                                                   SolverConsts<R> sc, int* status) {
+                                                   SolverConsts<R> sc, int* status, double cfl,
+                                                   unsigned long long* dt_bits) {
   const BlockTask t = T[blockIdx.x];
   const DPatch& p = P[t.patch];
   Cell c;
-  if (!region_cell<2, 2>(p, t.start + threadIdx.x, c)) return;
-  const int64_t x = lin(p, c);
-  const R* U0 = (const R*)p.U[0];
-  R u[8];
+  const bool act = region_cell<2, 2>(p, t.start + threadIdx.x, c);
+  if (!Cfl && !act) return;
+  const R inf = R(1) / R(0);
+  R m = inf;
+  if (act) {
+    const int64_t x = lin(p, c);
+    R u[8];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) u[q] = ((const R*)p.U[q])[x];
-  u[5] = R(0.5) * (((const R*)p.B[0])[x] + ((const R*)p.B[0])[x + 1]);
-  u[6] = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
-  u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
-  (void)U0;
-  R w[8];
-  cons2prim(u, sc.gm1, w);
-  VecIO<R>::store8(arr(scr, p, SC_W), p.snelem, x, w);
+    for (int q = 0; q < 5; ++q) u[q] = ((const R*)p.U[q])[x];
+    u[5] = R(0.5) * (((const R*)p.B[0])[x] + ((const R*)p.B[0])[x + 1]);
+    u[6] = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
+    u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
+    R w[8];
+    cons2prim(u, sc.gm1, w);
+    VecIO<R>::store8(arr(scr, p, SC_W), p.snelem, x, w);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int b = (a + 1) % 3, cc = (a + 2) % 3;
-    arr(scr, p, SC_EN + a)[x] = w[1 + cc] * w[5 + b] - w[1 + b] * w[5 + cc];
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, cc = (a + 2) % 3;
+      arr(scr, p, SC_EN + a)[x] = w[1 + cc] * w[5 + b] - w[1 + b] * w[5 + cc];
+    }
+    if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
+    if constexpr (Cfl) {
+      const bool interior = c.i >= p.g && c.i < p.g + p.n[0] && c.j >= p.g && c.j < p.g + p.n[1] &&
+                            c.k >= p.g && c.k < p.g + p.n[2];
+      if (interior) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          R cf = fast_speed(w[0], w[4], w[5 + d], w[5 + t1], w[5 + t2], sc.gamma);
+          R tt = dx_of<R>(p, d) / (Tr<R>::abs(w[1 + d]) + cf);
+          m = rmin(m, tt);
+        }
+      }
+    }
   }
-  if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
+  if constexpr (Cfl) {
+    for (int o = 16; o > 0; o >>= 1) {
+      R u2 = __shfl_down_sync(0xffffffffu, m, o);
+      m = (u2 < m) ? u2 : m;
+    }
+    __shared__ R red[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      m = (threadIdx.x < kThreads / 32) ? red[threadIdx.x] : inf;
+      for (int o = 16; o > 0; o >>= 1) {
+        R u2 = __shfl_down_sync(0xffffffffu, m, o);
+        m = (u2 < m) ? u2 : m;
+      }
+      if (threadIdx.x == 0) {
+        const double v = (cfl * (double)m) * p.cfl_scale;
+        if (v == v) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
 }
+
+// Sets the FP64 time step the CFL reduction of k_prim lowers to +infinity.
+__global__ void k_dt_reset(unsigned long long* dt_bits) { *dt_bits = 0x7FF0000000000000ull; }
 
 // ---------------------------------------------------------------- k_edge
 template <typename R, int a> __device__ __forceinline__ void edge_avg(const DPatch& p, const Cell& c, R* scr);
@@ -815,9 +862,17 @@ cudaError_t launch_advance(const AdvanceArgs& a, R* scr, R* K, const SolverConst
   const bool commit = a.commit;
   if (a.nblocks == 0) return cudaSuccess;
   const dim3 g1(a.nblocks), g1b(a.nblocks1), gu(a.nblocksu);
-  MHD_TIMED(tm, K_PRIM, s,
-            (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
-             k_prim<R><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status)));
+  if (a.cfl_out) {
+    // the step's own CFL dt first (k_prim), then the step constants from it
+    MHD_TIMED(tm, K_PRIM, s,
+              (k_dt_reset<<<1, 1, 0, s>>>(a.cfl_out),
+               k_prim<R, true><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status, a.cfl, a.cfl_out),
+               k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K)));
+  } else {
+    MHD_TIMED(tm, K_PRIM, s,
+              (k_stepc<R><<<(npatch + 127) / 128, 128, 0, s>>>(d_patches, npatch, d_dt, K),
+               k_prim<R, false><<<g1, kThreads, 0, s>>>(d_patches, d_tasks, scr, sc, d_status, 0.0, nullptr)));
+  }
   if (npblocks > 0)
     MHD_TIMED(tm, K_PRED, s, (k_pred_tiled<R><<<npblocks, kThreads, 0, s>>>(d_patches, d_ptasks, scr, sc, K)));
   else

@@ -566,9 +566,12 @@ cudaError_t run_advance_args(mhd_ctx* c, int dtype, const AdvanceArgs& a, cudaSt
                                 : advance_f64(a, s);
 }
 
-mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n,
-                             const int32_t* grow, const double* d_dt, const double* dt_scale,
-                             const mhd_capture* caps, int32_t ncap, void* stream) {
+// The advance of mhd_patch_advance; with cfl_dt set (single-level steps, no
+// captures), the step first computes its own CFL dt into *d_dt: inside k_prim
+// for the staged kernels, by the separate reduction before the fused one.
+static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
+                        const double* d_dt, const double* dt_scale, const mhd_capture* caps, int32_t ncap,
+                        void* stream, bool cfl_dt) {
   mhd_status r = begin(c);
   if (r) return r;
   if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
@@ -580,6 +583,11 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   if ((r = advance_patches(c, patches, n, grow, dt_scale, dp))) return r;
   // which advance: the context's (autotuned) choice, or forced staged / fused
   bool fused = c->prm.advance_kernel == 2 || (c->prm.advance_kernel == 0 && c->use_fused[dtype == MHD_F32 ? 1 : 0]);
+  if (cfl_dt && fused) {
+    // the fused kernel has no primitive pass: the CFL reduction runs first
+    if ((r = mhd_cfl_dt(c, patches, n, nullptr, const_cast<double*>(d_dt), stream))) return r;
+    cfl_dt = false;
+  }
   // flux-register captures: checked against the faces / edges this call computes
   std::vector<DCapture> dc(ncap);
   std::vector<int64_t> ccounts(ncap);
@@ -684,10 +692,12 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
   a.nctasks = (int)ctasks.size();
   a.variant = c->fused_variant[dtype == MHD_F32 ? 1 : 0];
   a.commit = true;
+  a.cfl_out = cfl_dt ? (unsigned long long*)const_cast<double*>(d_dt) : nullptr;
+  a.cfl = c->prm.cfl;
   cudaError_t e = run_advance_args(c, dtype, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
-  // fused: step constants, k_fused, k_commit
-  c->launches += fused ? 3 : staged_launches(elem_size(dtype));
+  // fused: step constants, k_fused, k_commit; staged with the CFL dt: + reset
+  c->launches += fused ? 3 : staged_launches(elem_size(dtype)) + (cfl_dt ? 1 : 0);
   if (ncap > 0) {
     PackedTasks pc{};
     if ((r = packed_table(c, ccounts, false, pc))) return r;
@@ -699,6 +709,20 @@ mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t 
     c->launches += 1;
   }
   return MHD_OK;
+}
+
+mhd_status mhd_patch_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
+                             const double* d_dt, const double* dt_scale, const mhd_capture* caps, int32_t ncap,
+                             void* stream) {
+  return advance_impl(c, patches, n, grow, d_dt, dt_scale, caps, ncap, stream, false);
+}
+
+mhd_status mhd_patch_step_cfl(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, double* d_dt_out,
+                              void* stream) {
+  if (!c) return MHD_EINVAL;
+  if (n < 1 || !patches) return fail(c, MHD_EINVAL, "patch_step_cfl needs at least one patch");
+  if (!d_dt_out) return fail(c, MHD_EINVAL, "d_dt_out is NULL");
+  return advance_impl(c, patches, n, nullptr, d_dt_out, nullptr, nullptr, 0, stream, true);
 }
 
 mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,

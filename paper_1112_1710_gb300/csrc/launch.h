@@ -34,6 +34,10 @@ struct AdvanceArgs {
   int nctasks;
   int variant;               // index into the variant table of the element type
   bool commit;               // false: leave the new state in the output copies
+  // staged only: non-null makes k_prim compute the step's CFL dt into this
+  // device double (the same one as d_dt) before the step constants read it
+  unsigned long long* cfl_out;
+  double cfl;
 };
 
 // Compiled shapes of the fused advance: x-y tile and threads per CTA (one CTA
@@ -60,7 +64,8 @@ constexpr int region_mu(size_t) { return 0; }
 constexpr int region_mu_top(size_t) { return 1; }
 
 // Kernel launches of one staged advance: step constants, k_prim, k_pred,
-// k_flux, k_update, and k_edge and k_emf in FP64.
+// k_flux, k_update, and k_edge and k_emf in FP64 (one more, the dt reset,
+// when k_prim computes the CFL dt).
 inline int staged_launches(size_t elem) { return elem == 8 ? 7 : 5; }
 
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);

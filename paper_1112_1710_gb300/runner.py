@@ -1,7 +1,9 @@
 """Single-patch periodic driver: one step = ghost fill (periodic images) ->
-CFL dt (device scalar) -> patch advance of the interior.  Three library
-calls, eleven kernels, no host synchronisation; the dt never leaves the
-device, so the step can be captured once as a CUDA graph and replayed.
+CFL dt (device scalar) -> patch advance of the interior.  Two library calls
+(the fill, then mhd_patch_step_cfl, whose primitive pass also reduces the
+CFL dt), or three with the separate mhd_cfl_dt (cfl_in_step = False); no
+host synchronisation: the dt never leaves the device, so the step can be
+captured once as a CUDA graph and replayed.
 """
 from __future__ import annotations
 
@@ -12,8 +14,9 @@ from .patch import Patch, periodic_copies
 
 
 class PeriodicRunner:
-    def __init__(self, patch: Patch, ctx, stream: torch.cuda.Stream | None = None):
+    def __init__(self, patch: Patch, ctx, stream: torch.cuda.Stream | None = None, cfl_in_step: bool = True):
         self.patch = patch
+        self.cfl_in_step = cfl_in_step
         self.ctx = ctx
         self.stream = stream or torch.cuda.current_stream(patch.state.device)
         self.descs = [patch.desc()]
@@ -29,6 +32,9 @@ class PeriodicRunner:
 
     def step(self, dt: float | None = None) -> None:
         self.fill()
+        if dt is None and self.cfl_in_step:
+            capi.mhd_patch_step_cfl(self.ctx, self.descs, self.d_dt.data_ptr(), self.sp)
+            return
         if dt is None:
             capi.mhd_cfl_dt(self.ctx, self.descs, self.d_dt.data_ptr(), self.sp)
         else:

@@ -447,3 +447,39 @@ def test_tiled_predictor_fp64_bitexact(capi, orc, k):
     P = orc.patch(st, n, g, dx)
     assert orc.advance(P, orc.params(limiter=0, emf=0), 1.1e-3, k) == 0
     assert np.array_equal(got, st)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["ragged", "blast64"])
+def test_cfl_in_primitive_pass_equals_separate_cfl(capi, dtype, case):
+    """mhd_patch_step_cfl (the CFL reduction inside k_prim) against
+    mhd_cfl_dt + mhd_patch_advance on the same states: the same dt and state
+    bit for bit in the FP64 parity build; in FP32 (fast math in k_prim, not in
+    the separate reduction) the dt within 1e-6 and the state within 1e-5."""
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    if case == "ragged":
+        n, g, dx = (37, 29, 23), 2, (1.0 / 37, 1.3 / 29, 0.9 / 23)
+        st = random_state(n, g, seed=77)
+        ctx = capi.mhd_ctx_create()
+    else:
+        pr = synth.blast(64)
+        n, g, dx, st = pr.n, pr.g, pr.dx, pr.state
+        ctx = capi.mhd_ctx_create(emf=1)
+    try:
+        out = []
+        for fused in (True, False):
+            p = to_patch(st.copy(), n, g, dx, dtype=dtype)
+            run = PeriodicRunner(p, ctx, cfl_in_step=fused)
+            dts = run.run(3, record_dt=True)
+            out.append((dts, p.state.cpu().numpy()))
+        assert capi.mhd_get_device_status(ctx) == 0
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    (d1, s1), (d2, s2) = out
+    if dtype == "f64":
+        assert d1 == d2
+        assert np.array_equal(s1, s2)
+    else:
+        assert np.allclose(d1, d2, rtol=1e-6, atol=0)
+        err = rel_linf(s1.astype(np.float64), s2.astype(np.float64), n, g)
+        assert np.all(err <= 1e-5), err
