@@ -428,6 +428,25 @@ mhd_status mhd_box_distances(const int32_t *d_lo, const int32_t *d_hi, int64_t n
 mhd_status mhd_hilbert_split(const int32_t *lo, const int32_t *hi, int32_t dim, const double *weights,
                              int32_t n_weights, int32_t bits, int32_t ghost, int32_t *out_lo, int32_t *out_hi);
 
+/* ---- Grid generation for regridding (Sec. 2.1) ----
+ * Boxes covering the flagged cells of a level: the paper leaves the rule
+ * open; this is the point clustering of Berger & Rigoutsos (IEEE Trans. SMC
+ * 21, 1278 (1991)).  flags: host uint8 array of shape[0] x ... x shape[dim-1]
+ * cells (dim 2 or 3, C order: the last index fastest), nonzero = flagged.  A
+ * box is shrunk to its flags' bounding box and accepted when flagged cells /
+ * cells >= eff (0 < eff <= 1) or when no axis is at least 2 min_size long;
+ * otherwise it is cut, both pieces at least min_size long, at the signature
+ * hole nearest its centre (axes in order), else at the largest sign change of
+ * the signature's second difference, else at the middle of its longest axis,
+ * and both pieces are clustered again (low piece first).  Writes the boxes
+ * (inclusive, in the flag array's index space and axis order) to the host
+ * arrays out_lo, out_hi [max_boxes][dim] and their number to *n_out.  Host
+ * code only.  MHD_EINVAL for bad arguments; MHD_ETOOBIG (with *n_out set)
+ * when more than max_boxes boxes result. */
+mhd_status mhd_cluster_flags(const uint8_t *flags, int32_t dim, const int32_t *shape, double eff,
+                             int32_t min_size, int32_t max_boxes, int32_t *out_lo, int32_t *out_hi,
+                             int32_t *n_out);
+
 /* Number of kernels this context has enqueued so far (for launch accounting). */
 int64_t mhd_launch_count(const mhd_ctx *ctx);
 

@@ -28,6 +28,7 @@ UNITS = {
     "amr_ops.cu": ["--fmad=false"],
     "tree.cu": [],
     "hilbert.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
+    "cluster.cu": ["-Xcompiler", "-ffp-contract=off"],
 }
 
 

@@ -25,7 +25,7 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
            "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit",
            "mhd_ctx_clone", "mhd_hilbert_keys", "mhd_box_distances", "mhd_hilbert_split",
-           "mhd_patch_step_cfl")
+           "mhd_patch_step_cfl", "mhd_cluster_flags")
 N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
@@ -161,6 +161,8 @@ def load(build_if_missing: bool = False):
     L.mhd_tree_inherit.argtypes = [P, P, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P]
     L.mhd_patch_step_cfl.restype = i32
     L.mhd_patch_step_cfl.argtypes = [P, C.POINTER(mhd_patch_desc), i32, P, P]
+    L.mhd_cluster_flags.restype = i32
+    L.mhd_cluster_flags.argtypes = [P, i32, P, C.c_double, i32, i32, P, P, P]
     L.mhd_hilbert_keys.restype = i32
     L.mhd_hilbert_keys.argtypes = [P, i64, i32, i32, P, P]
     L.mhd_box_distances.restype = i32

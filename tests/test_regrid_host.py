@@ -1,0 +1,66 @@
+"""The library's grid generation for regridding (mhd_cluster_flags, Sec.
+2.1) and the overlap lists against the oracle, box for box -- host code
+only, no GPU."""
+import numpy as np
+import pytest
+
+from oracle import cluster as K
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1112_1710_gb300 import _build
+    _build.build()
+    from paper_1112_1710_gb300 import regrid
+    return regrid
+
+
+def _flags(rng, nd):
+    shape = tuple(int(v) for v in rng.integers(1, 16 if nd == 3 else 30, nd))
+    f = np.zeros(shape, bool)
+    for _ in range(rng.integers(0, 5)):
+        c = [rng.integers(0, s) for s in shape]
+        r = [rng.integers(1, 6) for _ in shape]
+        f[tuple(slice(max(0, c[d] - r[d]), min(shape[d], c[d] + r[d])) for d in range(nd))] = True
+    return f | (rng.random(shape) < rng.choice([0.0, 0.02, 0.2]))
+
+
+def test_clustering_equals_oracle(R):
+    rng = np.random.default_rng(1112)
+    for t in range(300):
+        f = _flags(rng, 2 + t % 2)
+        eff = float(rng.choice([0.5, 0.7, 0.9, 1.0]))
+        ms = int(rng.integers(1, 4))
+        assert R.cluster(f, eff, ms) == K.cluster(f, eff, ms)
+
+
+def test_overlaps_equal_oracle(R):
+    rng = np.random.default_rng(5)
+    for t in range(60):
+        f = _flags(rng, 2 + t % 2)
+        new = K.cluster(f)
+        old = K.cluster(np.roll(f, int(rng.integers(1, 4)), axis=0))
+        for g in (0, 2, 4):
+            assert R.overlaps(new, old, g) == K.overlaps(new, old, g)
+
+
+def test_pins_through_the_library(R):
+    f = np.zeros((12, 12), bool)
+    f[0:12, 0:4] = True
+    f[0:4, 4:12] = True
+    assert R.cluster(f) == [((0, 0), (3, 11)), ((4, 0), (11, 3))]
+    g = np.zeros((20, 8), bool)
+    g[1:5, 2:6] = True
+    g[12:18, 1:7] = True
+    assert R.cluster(g) == [((1, 2), (4, 5)), ((12, 1), (17, 6))]
+    assert R.cluster(np.zeros((4, 4, 4), bool)) == []
+
+
+def test_cluster_rejects_bad_arguments(R):
+    from paper_1112_1710_gb300 import capi
+    with pytest.raises(capi.MHDError):
+        R.cluster(np.ones((4, 4)), eff=0.0)
+    with pytest.raises(capi.MHDError):
+        R.cluster(np.ones((4, 4)), min_size=0)
+    with pytest.raises(capi.MHDError):
+        R.cluster(np.ones(4))
