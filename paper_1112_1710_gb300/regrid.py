@@ -45,3 +45,19 @@ def overlaps(new_boxes, old_boxes, grow: int = 0):
         for j in np.nonzero(np.all(lo <= hi, axis=1))[0]:
             out.append((i, int(j), (tuple(int(v) for v in lo[j]), tuple(int(v) for v in hi[j]))))
     return out
+
+
+def children(cluster_boxes, coarse_boxes, ratio: int = 2):
+    """Level-(l+1) boxes from level-l cluster boxes: each cluster box cut by
+    every level-l grid it meets, so that each child lies inside one parent
+    grid (Sec. 2: grids are nested in a coarser parent), then refined by
+    `ratio`.  With disjoint cluster boxes and disjoint level-l grids the
+    children are disjoint; they come in (cluster box, grid) order."""
+    out = []
+    for clo, chi in cluster_boxes:
+        for plo, phi in coarse_boxes:
+            lo = [max(clo[d], plo[d]) for d in range(len(clo))]
+            hi = [min(chi[d], phi[d]) for d in range(len(clo))]
+            if all(lo[d] <= hi[d] for d in range(len(lo))):
+                out.append((tuple(ratio * v for v in lo), tuple(ratio * v + ratio - 1 for v in hi)))
+    return out

@@ -64,3 +64,28 @@ def test_cluster_rejects_bad_arguments(R):
         R.cluster(np.ones((4, 4)), min_size=0)
     with pytest.raises(capi.MHDError):
         R.cluster(np.ones(4))
+
+
+def test_children_are_the_refined_flagged_parent_cells(R):
+    # the fine cells are exactly {R c + r : c in (cluster boxes) and in (grids)},
+    # each covered once, each child inside one parent grid
+    import itertools
+    rng = np.random.default_rng(9)
+    for t in range(40):
+        nd = 2 + t % 2
+        shape = (16, 14) if nd == 2 else (10, 9, 8)
+        f = rng.random(shape) < 0.15
+        clusters = K.cluster(f)
+        grids = K.cluster(rng.random(shape) < 0.6, eff=0.6)
+        kids = R.children(clusters, grids, 2)
+        cells = lambda b: set(itertools.product(*[range(b[0][d], b[1][d] + 1) for d in range(nd)]))
+        parents = set().union(*[cells(b) for b in clusters]) & set().union(*[cells(b) for b in grids]) \
+            if clusters and grids else set()
+        want = {tuple(2 * c[d] + r[d] for d in range(nd)) for c in parents for r in itertools.product((0, 1), repeat=nd)}
+        got = set()
+        for k in kids:
+            ck = cells(k)
+            assert not (got & ck)
+            got |= ck
+            assert any(all(2 * g[0][d] <= k[0][d] and k[1][d] <= 2 * g[1][d] + 1 for d in range(nd)) for g in grids)
+        assert got == want
