@@ -111,8 +111,8 @@ typedef struct {
   int32_t reserved;  /* must be 0                                           */
 } mhd_params;
 
-/* One ghost-fill copy (Sec. 2.2 "synchronise ... and update ghost cells",
- * Sec. 2.3): `box` (global index space of the destination's level) is an
+/* One ghost-fill copy (Sec. 2.2, the step that refreshes ghost cells from
+ * neighbours; Sec. 2.3): `box` (global index space of the destination's level) is an
  * image of src's interior (source index = destination index + `offset`, a
  * periodic shift or zero) clipped to dst's ghost-extended box grown by one
  * cell.  Every box cell that lies in dst's arrays takes src's values, and so
@@ -308,7 +308,7 @@ mhd_status mhd_reflux(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc,
                       double *const *corr, const mhd_deposit *deps, int32_t nd,
                       void *stream);
 
-/* Ghost fill (Sec. 2.2 S step "update ghost cells"; periodic images and
+/* Ghost fill (Sec. 2.2 S step: ghost cells refreshed; periodic images and
  * same-level neighbours): executes the copies of `list` (host array) in one
  * launch.  All patches of the call must have one dtype. */
 mhd_status mhd_ghost_fill(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,

@@ -17,8 +17,8 @@ face-adjacent cells, and the nesting of Sec. 5.1 (the children of a cell
 occupy one contiguous block of 2^n indices, so that child order follows
 parent order).
 
-Distance of a grid along the curve (Sec. 5.1: "averaging ... some subset of
-cells that appropriately samples the grid (ie the four corners ...)"): the
+Distance of a grid along the curve (Sec. 5.1 lets a grid's position on the
+curve be taken from a sample of its cells, its corners for instance): the
 sum of the indices of its 2^n corner cells (the mean times 2^n; only
 differences and order are used).
 

@@ -7,8 +7,8 @@
  * reference leg load it.  It shares no code with the CUDA path.
  *
  * The paper (Carroll-Nellenback et al., "Efficient Parallelization for AMR MHD
- * Multiphysics Calculations") says only that each grid receives an independent
- * "hyperbolic advance" that consumes n_ghost ghost layers (Sec. 2.3) inside
+ * Multiphysics Calculations") says only that each grid is advanced on its own
+ * by a hyperbolic solver that consumes n_ghost ghost layers (Sec. 2.3) inside
  * the O/P/A/S/R life cycle of Sec. 2.2; it never states the solver.  The solver
  * below is the named published method:
  *   - primitive PLM reconstruction with a van Leer / minmod / MC limiter;

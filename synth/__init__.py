@@ -227,3 +227,60 @@ def random_states(rng: np.random.Generator, count: int, bn_zero: bool = False) -
     if bn_zero:
         w[:, 5] = 0.0
     return w
+
+
+def field_loop(n: int, normal: int = 2, v=(1.0, 0.5, 0.0), amp: float = 1e-3, radius: float = 0.3,
+               g: int = 2, align: int = 8) -> Problem:
+    """Weak magnetic field loop in a uniform flow (the advection test Gardiner
+    & Stone 2005 use for their edge EMF): a periodic n x n patch one cell
+    thick along axis `normal`, on [-1/2, 1/2] per axis, rho = 1, p = 1,
+    velocity v, and face B from the vector potential A_normal = amp (radius -
+    r) inside r < radius (r measured in the plane), else 0.  The field is
+    passive to rounding (magnetic pressure amp^2 against p = 1)."""
+    nn = [n, n, n]
+    nn[normal] = 1
+    nn = tuple(nn)
+    dx = tuple(1.0 / a for a in nn)
+    xlo = (-0.5, -0.5, -0.5)
+    st = empty_patch(nn, g, align=align)
+    t1, t2 = (normal + 1) % 3, (normal + 2) % 3
+
+    def a_n(x, y, z):
+        r3 = (x, y, z)
+        r = np.sqrt(r3[t1] ** 2 + r3[t2] ** 2)
+        return np.where(r < radius, amp * (radius - r), 0.0)
+
+    zero = lambda x, y, z: 0.0 * x
+    A = [zero, zero, zero]
+    A[normal] = a_n
+    _face_b_from_potential(st, nn, g, xlo, dx, (0, 0, 0), tuple(A))
+    _set_cells(st, nn, g, 1.0, v[0], v[1], v[2], 1.0, GAMMA)
+    return Problem("field_loop", st, nn, g, dx, xlo)
+
+
+def swirl_2d(n: int, seed: int = 5, g: int = 2, align: int = 8) -> Problem:
+    """Smooth 2D state on the unit periodic square whose velocity changes
+    sign across the grid along both axes (v_x = 0.8 sin(2 pi y + 0.3) + 0.2
+    cos 2 pi x, v_y = 0.7 sin(2 pi x + 1.1) - 0.3 cos 2 pi y, v_z = 0.1), rho = 1 +
+    0.2 sin 2 pi (x + y), p = 1, and a field from three seeded Fourier modes of
+    A_z (amplitude 0.05 each)."""
+    rng = np.random.default_rng(seed)
+    nn = (n, n, 1)
+    dx = (1.0 / n,) * 3
+    xlo = (0.0, 0.0, 0.0)
+    st = empty_patch(nn, g, align=align)
+    modes = [(int(rng.integers(1, 3)), int(rng.integers(1, 3)), rng.uniform(0, 2 * np.pi), rng.uniform(-1, 1))
+             for _ in range(3)]
+
+    def az(x, y, z):
+        return sum(0.05 * a * np.cos(2 * np.pi * (kx * x + ky * y) + ph) for kx, ky, ph, a in modes)
+
+    zero = lambda x, y, z: 0.0 * x
+    _face_b_from_potential(st, nn, g, xlo, dx, (0, 0, 0), (zero, zero, az))
+    x = (np.arange(n) + 0.5) / n
+    X, Y = x[None, None, :], x[None, :, None]
+    vx = 0.8 * np.sin(2 * np.pi * Y + 0.3) + 0.2 * np.cos(2 * np.pi * X)
+    vy = 0.7 * np.sin(2 * np.pi * X + 1.1) - 0.3 * np.cos(2 * np.pi * Y)
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * (X + Y))
+    _set_cells(st, nn, g, rho, vx, vy, 0.1, 1.0, GAMMA)
+    return Problem("swirl_2d", st, nn, g, dx, xlo)

@@ -483,3 +483,62 @@ def test_cfl_in_primitive_pass_equals_separate_cfl(capi, dtype, case):
         assert np.allclose(d1, d2, rtol=1e-6, atol=0)
         err = rel_linf(s1.astype(np.float64), s2.astype(np.float64), n, g)
         assert np.all(err <= 1e-5), err
+
+
+def _interior_face_energy(s, n, g):
+    """Sum of squared interior face fields (the loop's magnetic energy up to
+    a constant factor and the face-to-cell averaging)."""
+    tot = 0.0
+    for a in range(3):
+        ext = list(n)
+        ext[a] += 1
+        tot += float(np.sum(s[5 + a, g:g + ext[2], g:g + ext[1], g:g + ext[0]] ** 2))
+    return tot
+
+
+@pytest.mark.parametrize("normal", [0, 1, 2])
+def test_field_loop_gs05_fp64_and_fp32(capi, orc, normal):
+    """The field loop that pins the upwinded edge EMF (Gardiner & Stone 2005)
+    in each coordinate plane, carried along the diagonal of its plane, 20
+    steps with the default (upwinded) EMF: FP64 equals the oracle within
+    1e-11 per variable with the same dt sequence; FP32 keeps the pinned
+    property (the loop's magnetic energy never rises) and its field stays
+    within 1e-4 of the oracle's field strength."""
+    t1, t2 = (normal + 1) % 3, (normal + 2) % 3
+    v = [0.0, 0.0, 0.0]
+    v[t1], v[t2] = 1.0, 0.5
+    pr = synth.field_loop(32, normal, tuple(v))
+    res = {}
+    for dtype in ("f64", "f32"):
+        ctx = capi.mhd_ctx_create(emf=0)
+        try:
+            from paper_1112_1710_gb300.runner import PeriodicRunner
+            p = to_patch(pr.state.copy(), pr.n, pr.g, pr.dx, dtype=dtype)
+            run = PeriodicRunner(p, ctx)
+            eb = []
+            dts = []
+            for _ in range(20):
+                dts += run.run(1, record_dt=True)
+                s = p.state.cpu().numpy().astype(np.float64)
+                eb.append(_interior_face_energy(s, pr.n, pr.g))
+            assert capi.mhd_get_device_status(ctx) == 0
+            res[dtype] = (p.state.cpu().numpy(), dts, np.array(eb))
+        finally:
+            capi.mhd_ctx_destroy(ctx)
+    want = pr.state.copy()
+    odts = orc.run_periodic(want, pr.n, pr.g, pr.dx, orc.params(emf=0), 20)
+    got64, dts64, _ = res["f64"]
+    assert dts64 == odts
+    err = rel_linf(got64, want, pr.n, pr.g)
+    assert np.all(err[5:] <= TOL), err
+    assert np.all(err[:5] <= TOL), err
+    got32, _, eb32 = res["f32"]
+    assert np.all(np.diff(eb32) <= 1e-5 * eb32[0]), eb32
+    g = pr.g
+    nx, ny, nz = pr.n
+    for a in range(3):
+        ext = [nx, ny, nz]
+        ext[a] += 1
+        d = np.abs(got32[5 + a, g:g + ext[2], g:g + ext[1], g:g + ext[0]] -
+                   want[5 + a, g:g + ext[2], g:g + ext[1], g:g + ext[0]]).max()
+        assert d <= 1e-4 * 1e-3, (a, d)
