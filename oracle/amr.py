@@ -268,6 +268,11 @@ class OHierarchy:
             self.step(l + 1, 0, 0.5 * dt, False)
             self.reflux(l)
             self.restrict(l)
+            if self.prm.p_floor > 0.0 or self.prm.rho_floor > 0.0:
+                # refluxing changes cells outside any advance: the floors
+                # again (reading R33)
+                for P in self.levels[l]:
+                    O.floor(P.P, self.prm)
 
     def initialise(self):
         for l in range(len(self.levels) - 2, -1, -1):

@@ -63,7 +63,13 @@ typedef struct {
   int32_t limiter;  /* 0 van Leer (harmonic), 1 minmod, 2 monotonised central */
   int32_t emf;      /* 0 Gardiner-Stone upwinded, 1 arithmetic mean          */
   double upwind_eps;/* |S_M| <= upwind_eps (S_R - S_L) counts as no upwind side */
+  double p_floor;   /* > 0: pressure floor after the update (R33); 0: none    */
+  double rho_floor; /* > 0: density floor after the update (R33); 0: none     */
 } orc_params;
+
+/* Cells raised to the pressure floor by the last orc_advance. */
+static int64_t orc_floored = 0;
+ORC_EXPORT int64_t orc_floor_count(void) { return orc_floored; }
 
 /* ------------------------------------------------------------------ */
 /* small helpers                                                        */
@@ -445,6 +451,47 @@ typedef struct {
 } orc_ecapture;
 
 /* ------------------------------------------------------------------ */
+/* floors (reading R33)                                                  */
+/* ------------------------------------------------------------------ */
+/* One cell (i, j, k) under the floors of prm: a density below rho_floor is
+ * set to rho_floor with M kept and the pressure reset to p_floor (E =
+ * p_floor / (gamma - 1) + |M|^2 / (2 rho_floor) + |Bc|^2 / 2); otherwise a
+ * pressure below p_floor gets E += (p_floor - p) / (gamma - 1).  Bc is the
+ * mean of the cell's two faces.  Returns 1 if the cell was changed. */
+static int floor_cell(const orc_patch *P, int i, int j, int k, const orc_params *prm) {
+  const double gm1 = prm->gamma - 1.0;
+  int64_t c = ix(P, i, j, k);
+  double w[8];
+  cell_prim(P, i, j, k, gm1, w);
+  if (prm->rho_floor > 0.0 && !(w[0] >= prm->rho_floor)) {
+    double mx = P->U[1][c], my = P->U[2][c], mz = P->U[3][c];
+    double ke = 0.5 * (mx * mx + my * my + mz * mz) / prm->rho_floor;
+    double me = 0.5 * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    P->U[0][c] = prm->rho_floor;
+    P->U[4][c] = (prm->p_floor / gm1 + ke) + me;
+    return 1;
+  }
+  if (prm->p_floor > 0.0 && w[4] < prm->p_floor) {
+    double add = (prm->p_floor - w[4]) / gm1;
+    P->U[4][c] = P->U[4][c] + add;
+    return 1;
+  }
+  return 0;
+}
+
+/* The floors applied to every interior cell of P (after refluxing, which
+ * changes cells outside any advance).  Returns the number of changed cells. */
+ORC_EXPORT int64_t orc_floor(const orc_patch *P, const orc_params *prm) {
+  const int g = P->g;
+  int64_t n = 0;
+  if (!(prm->p_floor > 0.0 || prm->rho_floor > 0.0)) return 0;
+  for (int k = g; k < g + P->n[2]; ++k)
+    for (int j = g; j < g + P->n[1]; ++j)
+      for (int i = g; i < g + P->n[0]; ++i) n += floor_cell(P, i, j, k, prm);
+  return n;
+}
+
+/* ------------------------------------------------------------------ */
 /* the patch advance                                                    */
 /* ------------------------------------------------------------------ */
 /* One step of length dt of the cells in the update box = interior grown by k
@@ -758,7 +805,16 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
           P->B[a][c] = P->B[a][c] - (dtdx[b] * dEc - dtdx[cc] * dEb);
         }
   }
-  /* positivity of the new state (status only; no floor is applied) */
+  /* floors (reading R33; off when p_floor and rho_floor are 0) */
+  int64_t nfl = 0;
+  if (prm->p_floor > 0.0 || prm->rho_floor > 0.0) {
+#pragma omp parallel for collapse(2) reduction(+ : nfl)
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i) nfl += floor_cell(P, i, j, k, prm);
+  }
+  orc_floored = nfl;
+  /* positivity of the new state (status only) */
 #pragma omp parallel for collapse(2) reduction(+ : nneg)
   for (int k = lo[2]; k <= hi[2]; ++k)
     for (int j = lo[1]; j <= hi[1]; ++j)
@@ -778,6 +834,45 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
     free(Up[d]);
   }
   return nneg;
+}
+
+/* ------------------------------------------------------------------ */
+/* error flagging for regridding (Sec. 2.1)                             */
+/* ------------------------------------------------------------------ */
+/* The paper leaves the refinement criterion to the application.  Reading:
+ * an interior cell is flagged when the normalised central difference of the
+ * density or of the pressure along some axis exceeds theta,
+ *   eta = |q(+d) - q(-d)| / (|q(+d)| + 2 |q| + |q(-d)|) > theta,
+ * q in {rho, p} (p from the cell-centred field), d in {x, y, z}; eta lies in
+ * [0, 1].  flags: one byte per interior cell, x fastest (1 = flagged).
+ * Needs one valid ghost layer.  Returns the number of flagged cells. */
+ORC_EXPORT int64_t orc_flag(const orc_patch *P, const orc_params *prm, double theta, uint8_t *flags) {
+  const int g = P->g;
+  const double gm1 = prm->gamma - 1.0;
+  int64_t count = 0;
+  for (int k = g; k < g + P->n[2]; ++k)
+    for (int j = g; j < g + P->n[1]; ++j)
+      for (int i = g; i < g + P->n[0]; ++i) {
+        double w[8], wm[8], wp[8];
+        cell_prim(P, i, j, k, gm1, w);
+        int f = 0;
+        for (int d = 0; d < 3; ++d) {
+          int im = i - (d == 0), jm = j - (d == 1), km = k - (d == 2);
+          int ip = i + (d == 0), jp = j + (d == 1), kp = k + (d == 2);
+          cell_prim(P, im, jm, km, gm1, wm);
+          cell_prim(P, ip, jp, kp, gm1, wp);
+          for (int t = 0; t < 2; ++t) {
+            int q = t ? 4 : 0;
+            double num = fabs(wp[q] - wm[q]);
+            double den = fabs(wp[q]) + 2.0 * fabs(w[q]) + fabs(wm[q]);
+            if (num > theta * den) f = 1;
+          }
+        }
+        int64_t o = (int64_t)(i - g) + (int64_t)P->n[0] * ((j - g) + (int64_t)P->n[1] * (k - g));
+        flags[o] = (uint8_t)f;
+        count += f;
+      }
+  return count;
 }
 
 /* ------------------------------------------------------------------ */
@@ -996,6 +1091,262 @@ ORC_EXPORT void orc_prolong(const orc_patch *Pc, const int32_t *cglo, const orc_
       }
 }
 
+/* ================================================================== */
+/* Data transfer into a new iteration of a level (regridding, Sec. 2.1; */
+/* the O step of Sec. 2.2): a new fine patch takes the previous         */
+/* iteration's data where the two meet and is prolonged from its        */
+/* parent level elsewhere.                                              */
+/* ================================================================== */
+
+/* Copy of one box from an old patch Ps to a new patch Pd of the same level
+ * (global indices, both patches' own arrays): kind -1 copies the five cell
+ * arrays over the cells of [lo, hi]; kind a (0..2) copies the axis-a face
+ * array over the faces of [lo, hi] (index along a = face index). */
+ORC_EXPORT void orc_transfer_copy(const orc_patch *Ps, const int32_t *sglo, const orc_patch *Pd,
+                                  const int32_t *dglo, int32_t kind, const int32_t *lo, const int32_t *hi) {
+  for (int k = lo[2]; k <= hi[2]; ++k)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int i = lo[0]; i <= hi[0]; ++i) {
+        int64_t xs = ix(Ps, gidx(i, sglo[0], Ps->g), gidx(j, sglo[1], Ps->g), gidx(k, sglo[2], Ps->g));
+        int64_t xd = ix(Pd, gidx(i, dglo[0], Pd->g), gidx(j, dglo[1], Pd->g), gidx(k, dglo[2], Pd->g));
+        if (kind < 0)
+          for (int q = 0; q < 5; ++q) Pd->U[q][xd] = Ps->U[q][xs];
+        else
+          Pd->B[kind][xd] = Ps->B[kind][xs];
+      }
+}
+
+/* The potential phi = L^+ r on the eight fine cells of a coarse cell (cell c
+ * = fa + 2 fb + 4 fc), L the graph Laplacian of the cube (two cells joined by
+ * each inner face): through the cube's Walsh functions chi_S(c) = (-1)^|S & c|,
+ * eigenvalue 2 |S| for S != 0; the S = 0 part (the coarse cell's net flux,
+ * zero up to rounding) is dropped. */
+static void cube_potential(const double *r, double *phi) {
+  double coef[8];
+  coef[0] = 0.0;
+  for (int S = 1; S < 8; ++S) {
+    double t = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      int par = __builtin_popcount(S & c) & 1;
+      t = par ? t - r[c] : t + r[c];
+    }
+    int w = __builtin_popcount(S);
+    coef[S] = (t * 0.125) / (2.0 * w);
+  }
+  for (int c = 0; c < 8; ++c) {
+    double v = 0.0;
+    for (int S = 1; S < 8; ++S) {
+      int par = __builtin_popcount(S & c) & 1;
+      v = par ? v - coef[S] : v + coef[S];
+    }
+    phi[c] = v;
+  }
+}
+
+/* Prolongation of the coarse cells of box [clo, chi] (coarse global index)
+ * of Pc into the interior of a new fine patch Pf (cells and every face of
+ * the fine cells, the fine patch's own boundary faces included), cell by
+ * cell under mask[] (one byte per coarse cell of the box [mlo, mlo + mext),
+ * x fastest):
+ *   bit 0: the coarse cell's children already hold the previous iteration's
+ *          data (copied): nothing is written;
+ *   bit 1 + 2 a + s: the four fine sub-faces on side s of axis a already hold
+ *          the previous iteration's values: they are kept and read, not
+ *          written.
+ * Cells: density and momentum limited-linear as orc_prolong; energy with
+ * energy_mode 0 as orc_prolong (thermal energy limited-linear, R22), with
+ * energy_mode 1 conservatively: the thermal part of the eight children is
+ * scaled by (1 + delta / ebar), delta = E_c - mean of the children's total
+ * energies, ebar = mean thermal energy, so that the children's energies
+ * average to E_c while every thermal energy keeps its sign (unchanged when
+ * ebar + delta <= 0; such cells are counted).  Faces: the divergence-free
+ * reconstruction of orc_prolong (Balsara 2001) on the coarse faces that are
+ * not kept and inside the coarse cell; where some sub-faces are kept, the
+ * twelve inner faces are then changed by the least-squares correction that
+ * makes every child's divergence zero again (Toth & Roe 2002 fix the inner
+ * faces of a refined cell from its boundary sub-faces; here the smallest
+ * change of Balsara's values does): delta_f = phi(upper child) - phi(lower
+ * child), phi = L^+ r, r the children's divergences (cube_potential).
+ * Equal cell widths along the three axes.  Returns the count of energy
+ * fallbacks. */
+ORC_EXPORT int64_t orc_prolong_new(const orc_patch *Pc, const int32_t *cglo, const orc_patch *Pf,
+                                   const int32_t *fglo, const int32_t *clo, const int32_t *chi,
+                                   const uint8_t *mask, const int32_t *mlo, const int32_t *mext,
+                                   int32_t energy_mode) {
+  const int gc = Pc->g, gf = Pf->g;
+  const int64_t *sc = Pc->s;
+  int64_t nfall = 0;
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int C3[3] = {I, J, K};
+        int mk = mask[(I - mlo[0]) + mext[0] * ((J - mlo[1]) + mext[1] * (K - mlo[2]))];
+        if (mk & 1) continue;
+        int ci[3] = {gidx(I, cglo[0], gc), gidx(J, cglo[1], gc), gidx(K, cglo[2], gc)};
+        int64_t c = ix(Pc, ci[0], ci[1], ci[2]);
+        double uc[4], h[4][3], ec, he[3];
+        for (int q = 0; q < 4; ++q) {
+          uc[q] = Pc->U[q][c];
+          for (int d = 0; d < 3; ++d) {
+            double a = uc[q] - Pc->U[q][c - sc[d]];
+            double b = Pc->U[q][c + sc[d]] - uc[q];
+            h[q][d] = 0.25 * minmod2(a, b);
+          }
+        }
+        ec = thermal(Pc, c);
+        for (int d = 0; d < 3; ++d) {
+          double a = ec - thermal(Pc, c - sc[d]);
+          double b = thermal(Pc, c + sc[d]) - ec;
+          he[d] = 0.25 * minmod2(a, b);
+        }
+        double m[3][2], qs[3][2][3];
+        for (int a = 0; a < 3; ++a)
+          for (int sd = 0; sd < 2; ++sd) {
+            int64_t f = c + (sd ? sc[a] : 0);
+            m[a][sd] = Pc->B[a][f];
+            for (int t = 0; t < 3; ++t) {
+              if (t == a) { qs[a][sd][t] = 0.0; continue; }
+              double lo = m[a][sd] - Pc->B[a][f - sc[t]];
+              double hi = Pc->B[a][f + sc[t]] - m[a][sd];
+              qs[a][sd][t] = 0.25 * minmod2(lo, hi);
+            }
+          }
+        double lin[3][3], crs[3][3], sq[3], c0[3];
+        for (int a = 0; a < 3; ++a)
+          for (int t = 0; t < 3; ++t) {
+            if (t == a) { lin[a][t] = 0.0; crs[a][t] = 0.0; continue; }
+            lin[a][t] = qs[a][1][t] + qs[a][0][t];
+            crs[a][t] = qs[a][1][t] - qs[a][0][t];
+          }
+        for (int a = 0; a < 3; ++a) {
+          int b = (a + 1) % 3, cc = (a + 2) % 3;
+          sq[a] = -0.5 * (crs[b][a] + crs[cc][a]);
+          c0[a] = 0.5 * (m[a][0] + m[a][1]) - sq[a];
+        }
+        /* fine faces of this coarse cell: fb_[a][pos][s2][s1] with pos 0
+         * lower coarse face, 1 inner, 2 upper; s1 / s2 the sub-index along
+         * the lower / higher transverse axis */
+        double fv[3][3][2][2];
+        int64_t fx[3][3][2][2];
+        for (int a = 0; a < 3; ++a) {
+          int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+          int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+          for (int pos = 0; pos < 3; ++pos)
+            for (int s2 = 0; s2 < 2; ++s2)
+              for (int s1 = 0; s1 < 2; ++s1) {
+                int g3[3];
+                g3[a] = 2 * C3[a] + pos;
+                g3[lo_t] = 2 * C3[lo_t] + s1;
+                g3[hi_t] = 2 * C3[hi_t] + s2;
+                int64_t x = ix(Pf, gidx(g3[0], fglo[0], gf), gidx(g3[1], fglo[1], gf), gidx(g3[2], fglo[2], gf));
+                fx[a][pos][s2][s1] = x;
+                int keep = pos != 1 && ((mk >> (1 + 2 * a + (pos == 2))) & 1);
+                double v;
+                if (keep) {
+                  v = Pf->B[a][x];
+                } else if (pos == 1) {
+                  double sl = s1 ? 0.5 * lin[a][lo_t] : -0.5 * lin[a][lo_t];
+                  double sh = s2 ? 0.5 * lin[a][hi_t] : -0.5 * lin[a][hi_t];
+                  v = c0[a] + sl + sh;
+                } else {
+                  int sd = pos == 2;
+                  double sl = s1 ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
+                  double sh = s2 ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
+                  v = m[a][sd] + sl + sh;
+                }
+                fv[a][pos][s2][s1] = v;
+              }
+        }
+        if (mk >> 1) {
+          /* the children's divergences with the kept sub-faces, then the
+           * smallest change of the inner faces that zeroes them */
+          double r[8], phi[8];
+          for (int cc8 = 0; cc8 < 8; ++cc8) {
+            int sub[3] = {cc8 & 1, (cc8 >> 1) & 1, (cc8 >> 2) & 1};
+            double dv = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+              int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+              double up = fv[a][sub[a] + 1][sub[hi_t]][sub[lo_t]];
+              double dn = fv[a][sub[a]][sub[hi_t]][sub[lo_t]];
+              dv = dv + (up - dn);
+            }
+            r[cc8] = dv;
+          }
+          cube_potential(r, phi);
+          for (int a = 0; a < 3; ++a) {
+            int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+            int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+            for (int s2 = 0; s2 < 2; ++s2)
+              for (int s1 = 0; s1 < 2; ++s1) {
+                int lo8 = 0, hi8;
+                lo8 |= (s1 << lo_t) | (s2 << hi_t);
+                hi8 = lo8 | (1 << a);
+                fv[a][1][s2][s1] = fv[a][1][s2][s1] + (phi[hi8] - phi[lo8]);
+              }
+          }
+        }
+        /* write the faces that are not kept */
+        for (int a = 0; a < 3; ++a)
+          for (int pos = 0; pos < 3; ++pos) {
+            int keep = pos != 1 && ((mk >> (1 + 2 * a + (pos == 2))) & 1);
+            if (keep) continue;
+            for (int s2 = 0; s2 < 2; ++s2)
+              for (int s1 = 0; s1 < 2; ++s1) Pf->B[a][fx[a][pos][s2][s1]] = fv[a][pos][s2][s1];
+          }
+        /* the eight children */
+        double uf[8][4], ef[8], kef[8], mef[8];
+        int64_t xf[8];
+        for (int cc8 = 0; cc8 < 8; ++cc8) {
+          int fa = cc8 & 1, fb = (cc8 >> 1) & 1, fc = (cc8 >> 2) & 1;
+          int sub[3] = {fa, fb, fc};
+          xf[cc8] = ix(Pf, gidx(2 * I + fa, fglo[0], gf), gidx(2 * J + fb, fglo[1], gf), gidx(2 * K + fc, fglo[2], gf));
+          for (int q = 0; q < 4; ++q) {
+            double u = uc[q];
+            u = u + (fa ? h[q][0] : -h[q][0]);
+            u = u + (fb ? h[q][1] : -h[q][1]);
+            u = u + (fc ? h[q][2] : -h[q][2]);
+            uf[cc8][q] = u;
+          }
+          double bc[3];
+          for (int a = 0; a < 3; ++a) {
+            int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+            int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
+            bc[a] = 0.5 * (fv[a][sub[a]][sub[hi_t]][sub[lo_t]] + fv[a][sub[a] + 1][sub[hi_t]][sub[lo_t]]);
+          }
+          double e = ec;
+          e = e + (fa ? he[0] : -he[0]);
+          e = e + (fb ? he[1] : -he[1]);
+          e = e + (fc ? he[2] : -he[2]);
+          ef[cc8] = e;
+          kef[cc8] = 0.5 * (uf[cc8][1] * uf[cc8][1] + uf[cc8][2] * uf[cc8][2] + uf[cc8][3] * uf[cc8][3]) / uf[cc8][0];
+          mef[cc8] = 0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        }
+        double scale = 0.0;
+        int cons = 0;
+        if (energy_mode == 1) {
+          double sE = 0.0, se = 0.0;
+          for (int cc8 = 0; cc8 < 8; ++cc8) {
+            sE = sE + ((ef[cc8] + kef[cc8]) + mef[cc8]);
+            se = se + ef[cc8];
+          }
+          double delta = Pc->U[4][c] - 0.125 * sE, ebar = 0.125 * se;
+          if (ebar + delta > 0.0) {
+            cons = 1;
+            scale = delta / ebar;
+          } else {
+            nfall += 1;
+          }
+        }
+        for (int cc8 = 0; cc8 < 8; ++cc8) {
+          for (int q = 0; q < 4; ++q) Pf->U[q][xf[cc8]] = uf[cc8][q];
+          double e = cons ? ef[cc8] + ef[cc8] * scale : ef[cc8];
+          Pf->U[4][xf[cc8]] = (e + kef[cc8]) + mef[cc8];
+        }
+      }
+  return nfall;
+}
+
 /* Restriction of fine patch Pf onto coarse patch Pc for the coarse cells of
  * box [clo, chi] (the coarsened fine interior clipped to Pc's interior grown
  * by one cell): every box cell inside Pc's interior = 0.125 * (sum of its 8
@@ -1133,6 +1484,48 @@ ORC_EXPORT void orc_deposit_edges(const orc_patch *Pc, const int32_t *cglo, doub
           s = seg ? s + fine[fo] : fine[fo];
         }
         corr[15 + a][c] = 0.5 * s - coarse[co];
+      }
+}
+
+/* Synchronisation of fluxes on faces shared by two patches of one level
+ * (Sec. 2.2 S step; R14): each of the two patches registered dt * F on the
+ * shared faces of box [clo, chi] (its level's global index, x fastest, 5
+ * planes) during its advance.  When the two registers differ (the patches
+ * computed the face from different data), both are corrected to their mean:
+ * the patch with register `own` gets dF_q = 0.5 * (other - own) in corr[5 d
+ * + q] at those faces, so that orc_correct leaves its cells as if it had
+ * used the mean flux.  Called once for each of the two patches (own and
+ * other swapped); where the registers agree the correction is exactly 0. */
+ORC_EXPORT void orc_sync_faces(const orc_patch *P, const int32_t *glo, double *const *corr, int32_t d,
+                               const int32_t *clo, const int32_t *chi, const double *other,
+                               const double *own) {
+  const int g = P->g;
+  int ce[3];
+  for (int e = 0; e < 3; ++e) ce[e] = chi[e] - clo[e] + 1;
+  int64_t cn = (int64_t)ce[0] * ce[1] * ce[2];
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int64_t o = (int64_t)(I - clo[0]) + (int64_t)ce[0] * ((J - clo[1]) + (int64_t)ce[1] * (K - clo[2]));
+        int64_t c = ix(P, gidx(I, glo[0], g), gidx(J, glo[1], g), gidx(K, glo[2], g));
+        for (int q = 0; q < 5; ++q) corr[d * 5 + q][c] = 0.5 * (other[q * cn + o] - own[q * cn + o]);
+      }
+}
+
+/* The same for the EMFs dt * E_a registered on shared axis-a edges of box
+ * [clo, chi]: dE = 0.5 * (other - own) into corr[15 + a]. */
+ORC_EXPORT void orc_sync_edges(const orc_patch *P, const int32_t *glo, double *const *corr, int32_t a,
+                               const int32_t *clo, const int32_t *chi, const double *other,
+                               const double *own) {
+  const int g = P->g;
+  int ce[3];
+  for (int e = 0; e < 3; ++e) ce[e] = chi[e] - clo[e] + 1;
+  for (int K = clo[2]; K <= chi[2]; ++K)
+    for (int J = clo[1]; J <= chi[1]; ++J)
+      for (int I = clo[0]; I <= chi[0]; ++I) {
+        int64_t o = (int64_t)(I - clo[0]) + (int64_t)ce[0] * ((J - clo[1]) + (int64_t)ce[1] * (K - clo[2]));
+        int64_t c = ix(P, gidx(I, glo[0], g), gidx(J, glo[1], g), gidx(K, glo[2], g));
+        corr[15 + a][c] = 0.5 * (other[o] - own[o]);
       }
 }
 

@@ -44,7 +44,8 @@ class _Patch(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
-                ("emf", C.c_int32), ("upwind_eps", C.c_double)]
+                ("emf", C.c_int32), ("upwind_eps", C.c_double), ("p_floor", C.c_double),
+                ("rho_floor", C.c_double)]
 
 
 class _Capture(C.Structure):
@@ -87,6 +88,21 @@ def bind(L):
         f = getattr(L, nm)
         f.restype = None
         f.argtypes = [C.POINTER(_Patch), i3, pp, C.c_int32, i3, i3, dp, i3, i3, dp]
+    for nm in ("orc_sync_faces", "orc_sync_edges"):
+        f = getattr(L, nm)
+        f.restype = None
+        f.argtypes = [C.POINTER(_Patch), i3, pp, C.c_int32, i3, i3, dp, dp]
+    L.orc_floor.restype = C.c_int64
+    L.orc_floor.argtypes = [C.POINTER(_Patch), C.POINTER(_Params)]
+    L.orc_floor_count.restype = C.c_int64
+    L.orc_floor_count.argtypes = []
+    L.orc_transfer_copy.restype = None
+    L.orc_transfer_copy.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, C.c_int32, i3, i3]
+    L.orc_prolong_new.restype = C.c_int64
+    L.orc_prolong_new.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, i3, i3, C.c_void_p, i3, i3,
+                                  C.c_int32]
+    L.orc_flag.restype = C.c_int64
+    L.orc_flag.argtypes = [C.POINTER(_Patch), C.POINTER(_Params), C.c_double, C.c_void_p]
     L.orc_correct.restype = None
     L.orc_correct.argtypes = [C.POINTER(_Patch), pp]
     L.orc_copy.restype = None
@@ -111,8 +127,19 @@ def _dp(a: np.ndarray):
 UPWIND_EPS = 1e-10
 
 
-def params(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=UPWIND_EPS) -> _Params:
-    return _Params(gamma, cfl, limiter, emf, upwind_eps)
+def params(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=UPWIND_EPS, p_floor=0.0,
+           rho_floor=0.0) -> _Params:
+    return _Params(gamma, cfl, limiter, emf, upwind_eps, p_floor, rho_floor)
+
+
+def floor(P: _Patch, prm: _Params) -> int:
+    """The floors applied to P's interior cells; the number changed."""
+    return int(lib().orc_floor(C.byref(P), C.byref(prm)))
+
+
+def floor_count() -> int:
+    """Cells the last advance raised to the pressure floor."""
+    return int(lib().orc_floor_count())
 
 
 def patch(state: np.ndarray, n, g: int, dx) -> _Patch:
@@ -242,6 +269,34 @@ def deposit_faces(Pc, cglo, corr, d, clo, chi, fine, flo, fhi, coarse) -> None:
 def deposit_edges(Pc, cglo, corr, a, clo, chi, fine, flo, fhi, coarse) -> None:
     lib().orc_deposit_edges(C.byref(Pc), _i3(cglo), _planes(corr), int(a), _i3(clo), _i3(chi),
                             _dp(fine), _i3(flo), _i3(fhi), _dp(coarse))
+
+
+def sync_faces(P, glo, corr, d, lo, hi, other, own) -> None:
+    lib().orc_sync_faces(C.byref(P), _i3(glo), _planes(corr), int(d), _i3(lo), _i3(hi), _dp(other), _dp(own))
+
+
+def sync_edges(P, glo, corr, a, lo, hi, other, own) -> None:
+    lib().orc_sync_edges(C.byref(P), _i3(glo), _planes(corr), int(a), _i3(lo), _i3(hi), _dp(other), _dp(own))
+
+
+def transfer_copy(Ps, sglo, Pd, dglo, kind, lo, hi) -> None:
+    lib().orc_transfer_copy(C.byref(Ps), _i3(sglo), C.byref(Pd), _i3(dglo), int(kind), _i3(lo), _i3(hi))
+
+
+def prolong_new(Pc, cglo, Pf, fglo, clo, chi, mask: np.ndarray, mlo, energy_mode: int = 1) -> int:
+    """mask: uint8 array shaped (mext_z, mext_y, mext_x) over coarse cells from mlo."""
+    assert mask.dtype == np.uint8 and mask.flags.c_contiguous
+    mext = (mask.shape[2], mask.shape[1], mask.shape[0])
+    return int(lib().orc_prolong_new(C.byref(Pc), _i3(cglo), C.byref(Pf), _i3(fglo), _i3(clo), _i3(chi),
+                                     mask.ctypes.data, _i3(mlo), _i3(mext), int(energy_mode)))
+
+
+def flag(P: _Patch, prm: _Params, theta: float) -> np.ndarray:
+    """Refinement flags of the interior cells, shape (nz, ny, nx), uint8."""
+    nx, ny, nz = P.n
+    out = np.zeros((nz, ny, nx), dtype=np.uint8)
+    lib().orc_flag(C.byref(P), C.byref(prm), float(theta), out.ctypes.data)
+    return out
 
 
 def correct(P, corr) -> None:

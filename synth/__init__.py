@@ -284,3 +284,20 @@ def swirl_2d(n: int, seed: int = 5, g: int = 2, align: int = 8) -> Problem:
     rho = 1.0 + 0.2 * np.sin(2 * np.pi * (X + Y))
     _set_cells(st, nn, g, rho, vx, vy, 0.1, 1.0, GAMMA)
     return Problem("swirl_2d", st, nn, g, dx, xlo)
+
+
+def split_x(pr: Problem, at: int, g: int = None):
+    """Two patches cut from a single-patch problem whose ghosts are already
+    filled (periodic images): A holds interior cells x < at, B the rest, both
+    with g ghost layers taken from the filled array (so each one's ghosts hold
+    the other's cells and the periodic images).  Returns (A, B) states and
+    their interior sizes."""
+    g = pr.g if g is None else g
+    assert g == pr.g
+    nx, ny, nz = pr.n
+    na, nb = (at, ny, nz), (nx - at, ny, nz)
+    A = empty_patch(na, g)
+    B = empty_patch(nb, g)
+    A[:, :, :, :at + 2 * g + 1] = pr.state[:, :, :, :at + 2 * g + 1]
+    B[:, :, :, :nx - at + 2 * g + 1] = pr.state[:, :, :, at:nx + 2 * g + 1]
+    return A, na, B, nb

@@ -160,3 +160,72 @@ def test_cyclic_axis_permutation(orc):
     ra = interior(a, pr.n, g)[0]
     rb = interior(b, pr.n, g)[0]
     assert np.abs(np.transpose(ra, (1, 2, 0)) - rb).max() <= 1e-13
+
+
+def test_pressure_floor_closed_form(orc):
+    """The optional pressure floor (reading R33): after the update, every
+    cell whose pressure lies below p_floor has its energy raised by exactly
+    (p_floor - p) / (gamma - 1), computed from the unfloored update; every
+    other value is the unfloored one bit for bit, and p_floor = 0 changes
+    nothing."""
+    pr = synth.blast(12, noise=0.01, seed=4)
+    g, n = pr.g, pr.n
+    a, b = pr.state.copy(), pr.state.copy()
+    Pa, Pb = orc.patch(a, n, g, pr.dx), orc.patch(b, n, g, pr.dx)
+    for P in (Pa, Pb):
+        orc.fill_periodic(P)
+    dt = orc.cfl_dt(Pa, orc.params(emf=1))
+    assert orc.advance(Pa, orc.params(emf=1), dt, 0) == 0
+    assert orc.floor_count() == 0
+    assert orc.advance(Pb, orc.params(emf=1, p_floor=0.15), dt, 0) == 0
+    nfl = orc.floor_count()
+    st = interior(a, n, g)
+    bx = 0.5 * (a[5, g:g + n[2], g:g + n[1], g:g + n[0]] + a[5, g:g + n[2], g:g + n[1], g + 1:g + n[0] + 1])
+    by = 0.5 * (a[6, g:g + n[2], g:g + n[1], g:g + n[0]] + a[6, g:g + n[2], g + 1:g + n[1] + 1, g:g + n[0]])
+    bz = 0.5 * (a[7, g:g + n[2], g:g + n[1], g:g + n[0]] + a[7, g + 1:g + n[2] + 1, g:g + n[1], g:g + n[0]])
+    ir = 1.0 / st[0]
+    v = [st[1 + c] * ir for c in range(3)]
+    p = (G - 1.0) * (st[4] - 0.5 * st[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - 0.5 * (bx * bx + by * by + bz * bz))
+    low = p < 0.15
+    assert nfl == int(low.sum()) and 0 < nfl < low.size
+    want = st[4] + np.where(low, (0.15 - p) / (G - 1.0), 0.0)
+    got = interior(b, n, g)
+    assert np.array_equal(got[4][~low], st[4][~low])
+    assert np.abs(got[4][low] - want[low]).max() <= 1e-15 * np.abs(want).max()
+    assert np.array_equal(np.delete(got, 4, axis=0), np.delete(st, 4, axis=0))
+
+
+def test_density_and_pressure_floor_closed_form(orc):
+    """orc_floor on a state with planted low-density and low-pressure cells:
+    a density below rho_floor becomes rho_floor with M and B kept and the
+    pressure reset to p_floor; a pressure below p_floor (density above) is
+    raised to p_floor; every other cell is left bit for bit."""
+    pr = synth.blast(8, noise=0.01, seed=5)
+    g, n = pr.g, pr.n
+    st = pr.state.copy()
+    P = orc.patch(st, n, g, pr.dx)
+    orc.fill_periodic(P)
+    lowrho = (g + 1, g + 2, g + 3)       # (i, j, k)
+    st[0, lowrho[2], lowrho[1], lowrho[0]] = 1e-6
+    before = st.copy()
+    prm = orc.params(p_floor=0.2, rho_floor=1e-3)
+    nch = orc.floor(P, prm)
+    it = interior(st, n, g)
+    ib = interior(before, n, g)
+    bx = 0.5 * (ib[5] + before[5, g:g + n[2], g:g + n[1], g + 1:g + n[0] + 1])
+    by = 0.5 * (ib[6] + before[6, g:g + n[2], g + 1:g + n[1] + 1, g:g + n[0]])
+    bz = 0.5 * (ib[7] + before[7, g + 1:g + n[2] + 1, g:g + n[1], g:g + n[0]])
+    me = 0.5 * (bx * bx + by * by + bz * bz)
+    rho, m2 = ib[0], ib[1] ** 2 + ib[2] ** 2 + ib[3] ** 2
+    p = (G - 1.0) * (ib[4] - 0.5 * rho * (m2 / rho ** 2) - me)
+    dens = rho < 1e-3
+    pres = ~dens & (p < 0.2)
+    assert dens.sum() == 1 and pres.sum() > 0 and nch == dens.sum() + pres.sum()
+    k, j, i = lowrho[2] - g, lowrho[1] - g, lowrho[0] - g
+    assert it[0, k, j, i] == 1e-3
+    e_want = 0.2 / (G - 1.0) + 0.5 * m2[k, j, i] / 1e-3 + me[k, j, i]
+    assert abs(it[4, k, j, i] - e_want) <= 1e-14 * e_want
+    assert np.all(np.abs(it[4][pres] - (ib[4][pres] + (0.2 - p[pres]) / (G - 1.0))) <= 1e-14 * np.abs(ib[4]).max())
+    keep = ~dens & ~pres
+    assert np.array_equal(it[:, keep], ib[:, keep])
+    assert np.array_equal(it[1:4], ib[1:4]) and np.array_equal(st[5:8], before[5:8])
