@@ -534,6 +534,11 @@ ORC_EXPORT int64_t orc_advance(const orc_patch *P, const orc_params *prm, double
         double w[8];
         int64_t c = ix(P, i, j, k);
         cell_prim(P, i, j, k, gm1, w);
+        /* the floors (R33) also bound the primitives the step reads, ghost
+         * cells included (a prolonged ghost next to a copied face can have
+         * a pressure below them) */
+        if (prm->rho_floor > 0.0 && !(w[0] >= prm->rho_floor)) w[0] = prm->rho_floor;
+        if (prm->p_floor > 0.0 && !(w[4] >= prm->p_floor)) w[4] = prm->p_floor;
         for (int q = 0; q < 8; ++q) W[q][c] = w[q];
         for (int a = 0; a < 3; ++a) {
           int b = (a + 1) % 3, cc = (a + 2) % 3;
