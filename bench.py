@@ -35,6 +35,11 @@ METRIC = "MHD cell-updates/s (FP64 vs FP32-mixed, % HBM roofline); patch p50/p99
 # upwinded Gardiner-Stone average loses positivity at this blast's
 # perpendicular shock front within a few steps)
 SOLVER = {"gamma": 5.0 / 3.0, "cfl": 0.4, "limiter": 0, "emf": 1}
+# deep AMR (Mach-5 turbulence): the same solver with floors at 1e-3 of the
+# initial pressure 1/gamma and density 1 (without them the method itself, FP64
+# oracle included, reaches non-positive pressure within 6-13 coarse steps)
+DEEP_P_FLOOR = 1e-3 * 3.0 / 5.0
+DEEP_RHO_FLOOR = 1e-3
 UNIT = "cell-updates/s"
 E2E_RUNNERS = 3  # runners taking the end-to-end steps in turn
 FALLBACK_HBM_GBS = 6800.0
@@ -57,6 +62,12 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests per offered load")
     ap.add_argument("--slots", type=int, default=3, help="serve: streams (one context each)")
     ap.add_argument("--batch-cells", type=int, default=4 << 20, help="serve: cell budget of one batch")
+    ap.add_argument("--patch-only", action="store_true",
+                    help="default workload: time the single 128^3 patch only (not the deep-AMR, AMR and serving "
+                         "configs)")
+    ap.add_argument("--deep-steps", type=int, default=20, help="deep AMR: coarse steps through the served path")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="default run: requests per offered load of the serving config")
     return ap.parse_args()
 
 
@@ -78,11 +89,43 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback", 2070.0
 
 
-def alu_peak_tflops(dtype, sm_mhz):
-    """Plain-ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x
-    2 flop (FMA) per clock; FP64: 152 SMs x 2 FP64 FMA per clock x 2 flop."""
+_ALU = {}
+
+
+def measure_alu_peaks(local):
+    """FP32 and FP64 multiply-add rates measured on this device by the
+    library's probe (mhd_alu_probe: independent FMA chains over SM count x 8
+    blocks, timed with CUDA events), and the SM count read from the device."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    props = torch.cuda.get_device_properties(local)
+    out = {"sms": int(props.multi_processor_count)}
+    for dt, iters in (("f32", 65536), ("f64", 1024)):
+        best = 0.0
+        for _ in range(3):
+            tf, ms = capi.mhd_alu_probe(dt, iters)
+            best = max(best, tf)
+        out[dt] = best
+    _ALU.update(out)
+    return out
+
+
+def alu_peak_tflops(dtype, sm_mhz=2070.0):
+    """The plain-ALU roofline denominator: the measured FMA rate of the probe
+    (measure_alu_peaks) when it ran, else unit counts x clock: SMs x 128 FP32
+    lanes x 2 flop per clock; FP64: SMs x 2 FP64 FMA per clock x 2 flop."""
+    if dtype in _ALU:
+        return _ALU[dtype]
     lanes = 128 if dtype == "f32" else 2
-    return 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+    return _ALU.get("sms", 152) * lanes * 2 * sm_mhz * 1e6 / 1e12
+
+
+def alu_peak_source(dtype, sm_mhz=2070.0):
+    if dtype in _ALU:
+        return "measured: FMA-chain probe (mhd_alu_probe) on %d SMs, best of 3" % _ALU["sms"]
+    return "derived: %d SMs x %s x 2 flop x %.0f MHz" % (_ALU.get("sms", 152), "128 FP32 lanes" if dtype == "f32"
+                                                         else "2 FP64 FMA/clk", sm_mhz)
 
 
 class ClockSampler:
@@ -437,6 +480,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=local)
     flush = torch.empty(max(1, args.flush_mb) * 256 * 1024, dtype=torch.float32, device="cuda:%d" % local)
     hbm, hbm_src, sm_mhz = peaks()
+    alu = measure_alu_peaks(local)
     clocks = ClockSampler(local)
     clocks.start()
     res = {}
@@ -483,8 +527,7 @@ def run_ours(args):
                          "algorithmic_flops_per_launch": flops, "units_per_launch": units,
                          "flops_per_unit": flops / units,
                          "dram_gbs": (traffic / per_launch / 1e9) if traffic else None,
-                         "peak_source": "derived: 152 SMs x %s x 2 flop x %.0f MHz" %
-                                        ("128 FP32 lanes" if dtype == "f32" else "2 FP64 FMA/clk", sm_mhz)},
+                         "peak_source": alu_peak_source(dtype, sm_mhz)},
             "step_flops": {"flops_per_cell_update": step_fl / cells,
                            "achieved_tflops": step_fl / (ms_step * 1e-3) / 1e12, "peak_tflops": peak},
             "kernels": kernels,
@@ -505,8 +548,21 @@ def run_ours(args):
             "e2e": main["e2e"], "gpu_launches": main["gpu_launches"], "clocks": clk,
             "fp64": out_dt["f64"], "fp64_exact": out_dt["f64_exact"],
             "fp32": {k: v for k, v in main.items() if k not in ("roofline", "e2e")}}
+    line["alu_peaks"] = {"f32_tflops": alu["f32"], "f64_tflops": alu["f64"], "sms": alu["sms"],
+                         "how": "mhd_alu_probe: 16 independent FMA chains per thread, SMs x 8 blocks of 256 "
+                                "threads, one launch timed with CUDA events, best of 3"}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pr, args.cpu_steps)
+    # the other workloads of the metric, measured on one GPU in the same run
+    # (single-GPU figures; a multi-rank run reports the single-patch replicas)
+    if world == 1 and not args.patch_only:
+        del flush
+        torch.cuda.empty_cache()
+        line["deep_amr"] = measure_deep(args, local)
+        torch.cuda.empty_cache()
+        line["amr"] = measure_amr(args, local)
+        torch.cuda.empty_cache()
+        line["serving"] = measure_serve(args, local)
     print(json.dumps(line))
 
 
@@ -686,6 +742,14 @@ def amr_attribution(H, states, dtype, steps, local):
     finally:
         h.close()
         capi.mhd_ctx_destroy(ctx)
+    out = attribute_kernels(kt, work, dtype, steps)
+    return {"dtype": dtype, "mode": "eager, per-launch events", "coarse_steps": steps, "kernels": out,
+            "device_status": status}
+
+
+def attribute_kernels(kt, work, dtype, steps):
+    """Rows {kernel: time per coarse step, bound, achieved, peak, frac} from
+    the timers' (ms, launches) and a hierarchy's algorithmic work."""
     hbm, hbm_src, sm_mhz = peaks()
     out = {}
     for nm, (ms, cnt) in kt.items():
@@ -709,8 +773,20 @@ def amr_attribution(H, states, dtype, steps, local):
             row.update({"bound": "alu", "algorithmic_flops": fl, "achieved_tflops": tf,
                         "peak_tflops": pk, "frac": tf / pk})
         out[nm] = row
-    return {"dtype": dtype, "mode": "eager, per-launch events", "coarse_steps": steps, "kernels": out,
-            "device_status": status}
+    return out
+
+
+def roofline_of(rows, dtype, what):
+    """The roofline object of the dominant kernel of attribution rows."""
+    hbm, hbm_src, sm_mhz = peaks()
+    dom = max((k for k in rows if "bound" in rows[k]), key=lambda k: rows[k]["ms_per_coarse_step"])
+    r = rows[dom]
+    if r["bound"] == "hbm":
+        return {"kernel": dom, "bound": "hbm", "achieved": r["achieved_gbs"], "peak": r["peak_gbs"], "unit": "GB/s",
+                "frac": r["frac"], "traffic": None, "peak_source": hbm_src, "per": what}
+    return {"kernel": dom, "bound": "alu", "achieved": r["achieved_tflops"], "peak": r["peak_tflops"],
+            "unit": "TFLOP/s", "frac": r["frac"], "traffic": None, "peak_source": alu_peak_source(dtype, sm_mhz),
+            "algorithmic_flops_per_coarse_step": r["algorithmic_flops"], "per": what}
 
 
 def time_hilbert(H, states, steps, local):
@@ -859,14 +935,14 @@ def run_ot2d(args):
     print(json.dumps(line))
 
 
-def per_patch_f64(tpl, reqs, local):
+def per_patch_f64(tpl, reqs, local, contract=0):
     """The plain per-patch FP64 launch path over the same requests (each as
     FP64): one patch per ghost fill and per advance, one stream, no batching."""
     import torch
 
     from paper_1112_1710_gb300 import capi
     from paper_1112_1710_gb300.patch import Patch, periodic_copies
-    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER)
     stream = torch.cuda.Stream(device=local)
     one = torch.ones(1, dtype=torch.float64, device="cuda:%d" % local)
     copies = {}
@@ -971,80 +1047,279 @@ def run_serve(args):
 
 
 def run_deep(args):
-    """Deep AMR: base 32^3 + 7 refined levels (ratio 2, subcycled), about 108 M
-    cells in about 2,000 seeded patches of 8^3-64^3 placed where |curl v| +
-    |div v| of a k^-4 velocity field (256^3, Mach 5, seed 5) is largest,
-    plasma beta 1; FP32 state, FP64 flux registers and conservation sums; the
-    whole coarse step replayed as one CUDA graph; `--steps` coarse steps."""
+    """Config 5 alone (`--workload deep`): the deep-AMR hierarchy through the
+    served level-step path for `--deep-steps` coarse steps, as one JSON line
+    (the same measurement the default run reports under "deep_amr")."""
     import torch
 
-    import synth.turb as ST
-    from paper_1112_1710_gb300 import _build, capi
-    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300 import _build
     _build.build()
     rank, world, local = dist_setup()
     torch.cuda.set_device(local)
-    n0, G = 32, 4
-    t0 = time.time()
+    measure_alu_peaks(local)
+    res = measure_deep(args, local)
+    if rank != 0:
+        return
+    line = dict(res)
+    line.update({"metric": METRIC, "n_gpus": world, "steps": args.deep_steps, "warmup": 2,
+                 "ms_per_step": res["ms_per_coarse_step"], "higher_is_better": True, "scaling": "weak",
+                 "vs_baseline": None, "data": "synthetic"})
+    print(json.dumps(line))
+
+
+def deep_setup(n0=32, G=4, sample_every=8):
+    """The deep-AMR hierarchy (base 32^3 + 7 levels on the k^-4 Mach-5 field)
+    with every patch's initial state, and the oracle sample: every
+    `sample_every`-th patch of each level, once through its substeps."""
+    import synth.turb as ST
     H, v, _ = ST.deep_hierarchy(n0=n0, levels=8, m=256)
     states = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
-    # oracle sample: every 4th patch of each level, both substeps
     sample = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), G, (1.0 / n0 / 2 ** l,) * 3,
                (0,) if l == 0 else (2, 0), False)
-              for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl) if i % 4 == 0]
-    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+              for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl) if i % sample_every == 0]
+    return H, states, sample
+
+
+def hierarchy_step_bytes(h):
+    """Algorithmic HBM bytes of one coarse step of a hierarchy's advances: per
+    patch-step 8 arrays read on the update box grown by 2 and written on the
+    update box (level l steps 2^l times, the substeps with k = 2 and 0)."""
+    es = 4 if h.dtype == "f32" else 8
+    tot = 0
+    for l, pats in enumerate(h.levels):
+        ks = [0] if l == 0 else [2, 0]
+        calls = 1 if l == 0 else 2 ** (l - 1)
+        for p in pats:
+            for k in ks:
+                a = [v + 2 * k for v in p.n]
+                tot += calls * 8 * es * ((a[0] + 4) * (a[1] + 4) * (a[2] + 4) + a[0] * a[1] * a[2])
+    return tot
+
+
+def measure_deep(args, local):
+    """Config 5: deep AMR (base 32^3 + 7 levels, ~1.1e8 cells, k^-4 Mach-5
+    field, beta 1), FP32 state with FP64 flux registers and conservation sums,
+    `--deep-steps` coarse steps through the served path (serve.AmrLevelServer:
+    the level-step requests of the resident hierarchy issued finer level first,
+    each a captured graph of one batched launch sequence, the advance of every
+    level with children on a slot of its own)."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300.serve import AmrLevelServer
+    n0, G = 32, 4
+    t0 = time.time()
+    H, states, sample = deep_setup(n0, G)
+    dev = "cuda:%d" % local
+    ctx = capi.mhd_ctx_create(device=local, p_floor=DEEP_P_FLOOR, rho_floor=DEEP_RHO_FLOOR, **SOLVER)
     stream = torch.cuda.Stream(device=local, priority=-1)
-    h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream,
-                  device="cuda:%d" % local)
+    h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream, device=dev,
+                  concurrent=True, floors=True)
     del states
     clk = ClockSampler(local)
+    srv = None
+    total_mem = torch.cuda.get_device_properties(local).total_memory
     try:
         h.initialise()
-        out = torch.zeros(8, dtype=torch.float64, device="cuda:%d" % local)
+        out = torch.zeros(8, dtype=torch.float64, device=dev)
         capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         s0 = out.cpu().numpy().copy()
-        h.capture_graph()           # runs one eager coarse step first
-        h.replay()                  # warm-up replay
+        srv = AmrLevelServer(h, budget_bytes=int(0.9 * total_mem))
+        srv.run(1, timing=False)                       # warm-up coarse step through the server
         torch.cuda.synchronize()
         setup_s = time.time() - t0
+        for c in [h.ctx] + [c for c, _ in h.side]:
+            capi.mhd_floor_count(c)                    # reset
         clk.start()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            h.replay()
-        e1.record(stream)
-        e1.synchronize()
+        served = srv.run(args.deep_steps)
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
+        floored = sum(capi.mhd_floor_count(c) for c in [h.ctx] + [c for c, _ in h.side])
         capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         s1 = out.cpu().numpy()
         status = h.device_status()
+        # per-kernel attribution: one eager coarse step on one stream and
+        # context (no overlap between levels, so that every launch's events
+        # bracket that launch alone), CUDA events around every launch
+        ctxs = [h.ctx]
+        for c in ctxs:
+            capi.mhd_timing_enable(c, True)
+            capi.mhd_timing_reset(c)
+        h.concurrent = False
+        h.coarse_step()
+        torch.cuda.synchronize()
+        h.concurrent = True
+        kt = {}
+        for c in ctxs:
+            for nm, (ms, cnt) in capi.mhd_timing_read(c).items():
+                a = kt.get(nm, (0.0, 0))
+                kt[nm] = (a[0] + ms, a[1] + cnt)
+            capi.mhd_timing_enable(c, False)
+        status = status or h.device_status()
         upd = h.cell_updates_per_coarse_step()
+        work = amr_level_work(h)
+        step_bytes = hierarchy_step_bytes(h)
+        resident = srv.resident_bytes
     finally:
+        srv = None
         h.close()
         capi.mhd_ctx_destroy(ctx)
-    if rank != 0:
-        return
-    cells = [sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in bl) for bl in H]
-    drift = [float(abs(s1[q] - s0[q]) / max(abs(s0[q]), 1e-300)) for q in (0, 1, 2, 3, 4, 5)]
-    line = {"metric": METRIC, "value": upd * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": 2, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "deep AMR: base 32^3 + 7 levels (ratio 2, subcycled), %d patches of 8^3-64^3 "
-                                   "on a k^-4 velocity field (256^3, Mach 5, beta 1, seed 5); FP32 state, FP64 "
-                                   "registers and sums; step = one coarse step (graph replay)" % sum(len(l) for l in H),
-                       "patches_per_level": [len(l) for l in H], "cells_per_level": cells,
-                       "cell_updates_per_coarse_step": upd, "setup_s": setup_s,
-                       "l2": "working set (tens of GB) far above L2", "parallelism": "replicas"},
-            "conservation_drift_rel": {"rho": drift[0], "Mx": drift[1], "My": drift[2], "Mz": drift[3],
-                                       "E": drift[4], "Bx": drift[5]},
-            "device_status": status, "clocks": clocks}
+    rows = attribute_kernels(kt, work, "f32", 1)
+    ncells = sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for bl in H for lo, hi in bl)
+    ms = served["ms"] / args.deep_steps
+    hbm, hbm_src, _ = peaks()
+    # change of each FP64 total over the timed steps, relative to the size of
+    # its quantity's initial total (the vector's length for M and B, whose
+    # components may start at zero)
+    ref = [abs(s0[0])] + [float(np.linalg.norm(s0[1:4]))] * 3 + [abs(s0[4])] + [float(np.linalg.norm(s0[5:8]))] * 3
+    drift = {nm: float(abs(s1[q] - s0[q]) / max(ref[q], 1e-300))
+             for q, nm in enumerate(("rho", "Mx", "My", "Mz", "E", "Bx", "By", "Bz"))}
+    res = {"metric": UNIT, "value": upd * args.deep_steps / (served["ms"] * 1e-3), "unit": UNIT,
+           "coarse_steps": args.deep_steps, "ms_per_coarse_step": ms, "dtype": "f32 (FP64 registers and sums)",
+           "config": {"workload": "deep AMR: base 32^3 + 7 levels (ratio 2, subcycled), %d patches of 8^3-64^3, "
+                                  "%d cells, on a k^-4 velocity field (256^3, Mach 5, beta 1, seed 5); FP32 state, "
+                                  "FP64 flux registers and conservation sums; step = one coarse step through the "
+                                  "served level-step path" % (sum(len(l) for l in H), ncells),
+                      "patches_per_level": [len(l) for l in H], "cell_updates_per_coarse_step": upd,
+                      "setup_s": setup_s, "resident_gb": resident / 2 ** 30,
+                      "l2": "working set (tens of GB) far above L2"},
+           "served": {"level_step_requests_per_coarse_step": served["requests"] // args.deep_steps,
+                      "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"], "max_ms": served["max_ms"],
+                      "by_level": served["by_level"],
+                      "latency": "per request: device time from its last input request done to its own end"},
+           "roofline": roofline_of(rows, "f32", "one eager coarse step, per-launch CUDA events"),
+           "hbm_step": {"bytes_per_coarse_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                        "peak_gbs": hbm, "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm, "peak_source": hbm_src,
+                        "definition": "per patch-step 8 arrays x 4 B x ((update box + 2)^3 read + update box^3 "
+                                      "written)"},
+           "step_flops": {"achieved_tflops": sum(r.get("algorithmic_flops", 0.0) for r in rows.values()) /
+                          (ms * 1e-3) / 1e12, "peak_tflops": alu_peak_tflops("f32")},
+           "kernels": rows, "conservation_drift_rel": drift,
+           "conservation_note": "E drifts by what the floors add; rho by the density floor", "device_status": status, "clocks": clocks,
+           "floors": {"p_floor": DEEP_P_FLOOR, "rho_floor": DEEP_RHO_FLOOR, "cells_changed": floored,
+                              "cell_updates": upd * args.deep_steps,
+                       "note": "after every update and every refluxing: rho below rho_floor set to it (M kept, "
+                               "p reset to p_floor), else E raised to p = p_floor where p fell below it (not "
+                               "conservative); cells changed over the timed coarse steps"}}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(sample, "every 4th patch of each level of the same hierarchy, "
-                                                           "once through its substeps")
-    print(json.dumps(line))
+        res["cpu_baseline"] = cpu_baseline_sample(sample, "every 8th patch of each level of the same hierarchy, "
+                                                          "once through its substeps")
+    return res
+
+
+def measure_amr(args, local):
+    """Config 3: the AMR blast-shell hierarchy (base 64^3 + 3 levels), one
+    coarse step as a CUDA graph in FP32 and in FP64, against the plain
+    per-patch FP64 launch path."""
+    H, states = amr_hierarchy()
+    runs = {"f32_graph": time_amr(H, states, "f32", 3, "graph", local),
+            "f64_graph": time_amr(H, states, "f64", 1, "graph", local),
+            "f64_per_patch": time_amr(H, states, "f64", 1, "per_patch", local)}
+    att = amr_attribution(H, states, "f32", 1, local)
+    main = runs["f32_graph"]
+    res = {"metric": UNIT, "value": main["value"], "unit": UNIT, "ms_per_coarse_step": main["ms_per_coarse_step"],
+           "dtype": "f32 (FP64 registers)",
+           "config": {"workload": "AMR blast-shell hierarchy: base 64^3 + 3 levels (ratio 2, subcycled), %d patches "
+                                  "of 8^3-48^3, 4 ghost layers; step = one coarse step as a CUDA graph" %
+                                  sum(len(l) for l in H), "patches_per_level": [len(l) for l in H],
+                      "l2": "working set (GBs) larger than L2"},
+           "runs": runs,
+           "speedup_vs_per_patch_f64": {"f32_graph": main["value"] / runs["f64_per_patch"]["value"],
+                                        "f64_graph": runs["f64_graph"]["value"] / runs["f64_per_patch"]["value"]},
+           "roofline": roofline_of(att["kernels"], "f32", "one eager FP32 coarse step, per-launch CUDA events"),
+           "kernels": att["kernels"]}
+    if not args.no_cpu_baseline:
+        items = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), 4, (1.0 / 64 / 2 ** l,) * 3,
+                  (0,) if l == 0 else (2, 0), False)
+                 for l, bl in enumerate(H) for i, (lo, hi) in enumerate(bl) if i % 8 == 0]
+        res["cpu_baseline"] = cpu_baseline_sample(items, "every 8th patch of each level of the same hierarchy, "
+                                                         "once through its substeps")
+    return res
+
+
+def measure_serve(args, local):
+    """Config 4: the serving stream (Poisson arrivals, edges 16-128, levels 0-7
+    finer first, FP32/FP64 50/50, 64 GB budget): saturation throughput, then
+    p50/p99 at offered loads 0.5, 0.8 and 0.95 of it; FP64 requests on the
+    contracted FP64 build."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.serve import GpuBackend, Scheduler, latency_stats, make_templates, poisson_requests
+    G, budget, nreq = 4, 64 << 30, args.serve_requests
+    solver = dict(SOLVER, fp64_contract=1)
+    t_setup = time.time()
+    tpl = make_templates(range(16, 129, 2), g=G, solver=SOLVER, device="cuda:%d" % local)
+    be = GpuBackend(tpl, n_slots=args.slots, g=G, solver=solver, device="cuda:%d" % local)
+    clk = ClockSampler(local)
+
+    def serve(reqs, policy="greedy"):
+        sch = Scheduler(be, n_slots=args.slots, budget_bytes=budget, max_batch_cells=args.batch_cells, g=G,
+                        policy=policy)
+        out = sch.run(reqs, t_limit=600.0)
+        torch.cuda.synchronize()
+        st = latency_stats(out)
+        st["batches"] = len(sch.batches)
+        st["peak_resident_gb"] = sch.peak_resident / 2 ** 30
+        return st
+
+    try:
+        serve(poisson_requests(max(200, nreq // 10), math.inf, seed=1))     # warm-up: arenas sized
+        setup_s = time.time() - t_setup
+        l0 = sum(capi.mhd_launch_count(c) for c in be.ctxs)
+        clk.start()
+        sat = serve(poisson_requests(nreq, math.inf, seed=4242))
+        loads = {str(f): serve(poisson_requests(nreq, f * sat["requests_per_s"], seed=4242)) for f in (0.5, 0.8, 0.95)}
+        clocks = clk.stop()
+        launches = sum(capi.mhd_launch_count(c) for c in be.ctxs) - l0
+        # roofline of the FP32 requests: their kernels timed with per-launch
+        # events over a saturation pass of the stream's FP32 requests
+        f32reqs = [r for r in poisson_requests(nreq, math.inf, seed=4242) if r.dtype == "f32"][:500]
+        for c in be.ctxs:
+            capi.mhd_timing_enable(c, True)
+            capi.mhd_timing_reset(c)
+        serve(f32reqs)
+        kt = {}
+        for c in be.ctxs:
+            for nm, (ms, cnt) in capi.mhd_timing_read(c).items():
+                a = kt.get(nm, (0.0, 0))
+                kt[nm] = (a[0] + ms, a[1] + cnt)
+            capi.mhd_timing_enable(c, False)
+        status = max(capi.mhd_get_device_status(c) for c in be.ctxs)
+        sample = poisson_requests(nreq, math.inf, seed=4242)[:200]
+        pp = per_patch_f64(tpl, sample, local, contract=1)
+        served64 = serve([type(r)(r.rid, 0.0, r.n, r.level, "f64") for r in sample])
+    finally:
+        be.close()
+    flops = {k: 0.0 for k in STAGES}
+    for r in f32reqs:
+        for k in STAGES:
+            flops[k] += KERNEL_FLOPS[k] * kernel_units(k, r.n)
+    rows = attribute_kernels(kt, {"bytes": {}, "flops": flops}, "f32", 1)
+    res = {"metric": UNIT, "value": sat["cell_updates_per_s"], "unit": UNIT, "requests": nreq,
+           "dtype": "f32+f64 (FP64 contracted build)",
+           "config": {"workload": "serving stream: single-step requests on periodic blast-wave cubes, edges "
+                                  "log-uniform 16-128 (even) + 4 ghost layers, levels 0-7 finer first, FP32/FP64 "
+                                  "50/50, 64 GB HBM budget, seed 4242; Poisson arrivals at 0.5/0.8/0.95 of the "
+                                  "saturation rate", "slots": args.slots, "batch_cells": args.batch_cells,
+                      "setup_s": setup_s},
+           "saturation": sat, "offered_load": loads,
+           "p50_ms": {k: v["p50_ms"] for k, v in loads.items()}, "p99_ms": {k: v["p99_ms"] for k, v in loads.items()},
+           "fp64_sample": {"served_batched": served64, "plain_per_patch": pp,
+                           "build": "FP64 contracted (fp64_contract = 1) on both paths"},
+           "roofline": roofline_of(rows, "f32", "the stream's first 500 FP32 requests at saturation, per-launch "
+                                               "CUDA events"),
+           "gpu_launches": launches, "device_status": status, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        import synth
+        items = []
+        for r in poisson_requests(100, math.inf, seed=4242):
+            pr = synth.blast(r.n, g=G, seed=4242 + r.n)
+            items.append((pr.state, pr.n, G, pr.dx, (0,), True))
+        res["cpu_baseline"] = cpu_baseline_sample(items, "the first 100 requests of the same stream")
+    return res
 
 
 def main():

@@ -109,6 +109,15 @@ typedef struct {
   int32_t fused_chunk; /* z-planes per work item of the fused kernel; 0 lets
                         each call choose from the device's SM count          */
   int32_t reserved;  /* must be 0                                           */
+  double p_floor;    /* floors, applied after every update to the cells of
+                        the update box (and by mhd_floor): a density below
+                        rho_floor becomes rho_floor with M kept and the
+                        pressure reset to p_floor; otherwise a pressure (from
+                        the new face field) below p_floor gets E raised by
+                        (p_floor - p) / (gamma - 1).  Not conservative; the
+                        changed cells are counted (mhd_floor_count).  0: no
+                        floor (the paper names none).                       */
+  double rho_floor;  /* see p_floor; 0: no density floor                    */
 } mhd_params;
 
 /* One ghost-fill copy (Sec. 2.2, the step that refreshes ghost cells from
@@ -162,19 +171,33 @@ typedef struct {
   double *dst;          /* device                                            */
 } mhd_capture;
 
+#define MHD_REFLUX 0
+#define MHD_SYNC 1
+
 /* One flux-register deposit (Sec. 2.2: restriction of fluxes from the fine
- * level and synchronisation at coarse-fine faces): for each coarse face of
- * `box` (kind MHD_CAP_FACE, normal `axis`) the correction
+ * level and synchronisation of fluxes).
+ * mode MHD_REFLUX (coarse-fine faces): for each coarse face of `box` (kind
+ * MHD_CAP_FACE, normal `axis`) the correction
  *   dF_q = 0.25 * (sum of the 4 fine sub-face registers) - coarse register,
  * for each coarse edge (kind MHD_CAP_EDGE, along `axis`)
- *   dE = 0.5 * (sum of the 2 fine segment registers) - coarse register,
- * is written into the coarse patch's correction planes (18 FP64 planes with
- * the patch's strides: plane 5 d + q holds dF_q of axis-d faces, plane 15 + a
- * the axis-a dE).  fine: register over fine_box (fine global index, x
- * fastest); coarse_reg: register over box. */
+ *   dE = 0.5 * (sum of the 2 fine segment registers) - coarse register;
+ * fine: register over fine_box (fine global index, x fastest); coarse_reg:
+ * register over box.
+ * mode MHD_SYNC (faces or edges shared by two patches of one level, whose two
+ * registers differ when the patches computed them from different data): the
+ * patch `coarse` is corrected to the mean of the two registers,
+ *   dF_q = 0.5 * (other - own),  dE = 0.5 * (other - own),
+ * with `coarse_reg` its own register over box and `fine` the other patch's
+ * register over fine_box, which must equal box (one level, one index
+ * space); give one deposit per patch of the pair.  Where the two registers
+ * agree (R14: the usual case after a ghost fill from identical data) the
+ * correction is exactly zero and nothing changes.
+ * Either way the correction goes into the patch's correction planes (18
+ * FP64 planes with the patch's strides: plane 5 d + q holds dF_q of axis-d
+ * faces, plane 15 + a the axis-a dE). */
 typedef struct {
-  int32_t coarse, kind, axis, pad;
-  mhd_box box;          /* coarse global index                               */
+  int32_t coarse, kind, axis, mode;   /* mode: MHD_REFLUX or MHD_SYNC         */
+  mhd_box box;          /* global index of the corrected patch's level       */
   mhd_box fine_box;
   const double *fine;   /* device                                            */
   const double *coarse_reg;
@@ -308,6 +331,34 @@ mhd_status mhd_reflux(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc,
                       double *const *corr, const mhd_deposit *deps, int32_t nd,
                       void *stream);
 
+/* Library-owned FP64 flux registers (Sec. 2.2: the fluxes of a patch's
+ * boundary kept for the synchronisation and refluxing steps).  For each of the
+ * n patches (host array of descriptors; only the interiors are read) the
+ * library allocates on the context's device
+ *   - six boundary-face registers: side s of axis d covers the axis-d faces
+ *     with normal index lo_d (s = 0) or hi_d + 1 (s = 1) and transverse
+ *     indices over the interior: 5 planes (dt F of rho, Mx, My, Mz, E), x
+ *     fastest, the layout of a face capture over that box;
+ *   - twelve boundary-edge registers, two per boundary face: the axis-a
+ *     edges (a one of the face's two transverse axes) that lie in side s of
+ *     axis d, i.e. normal index lo_d (s = 0) or hi_d + 1 (s = 1), index
+ *     lo_a .. hi_a along a and lo_t .. hi_t + 1 along the remaining axis t:
+ *     1 plane (dt E_a), the layout of an edge capture over that box.
+ * All are zero after creation.  mhd_fluxreg_face / mhd_fluxreg_edge return
+ * the device pointer of one register (NULL for a bad index) and its box, to
+ * be named as mhd_capture.dst and as mhd_deposit.fine / coarse_reg; the
+ * library frees them in mhd_fluxreg_destroy (after synchronising the
+ * device).  MHD_EINVAL for bad arguments, MHD_ENOMEM if the allocation
+ * fails. */
+typedef struct mhd_fluxreg mhd_fluxreg;
+mhd_status mhd_fluxreg_create(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n, mhd_fluxreg **out);
+void mhd_fluxreg_destroy(mhd_fluxreg *reg);
+double *mhd_fluxreg_face(const mhd_fluxreg *reg, int32_t patch, int32_t axis, int32_t side, mhd_box *box);
+double *mhd_fluxreg_edge(const mhd_fluxreg *reg, int32_t patch, int32_t face_axis, int32_t side,
+                         int32_t edge_axis, mhd_box *box);
+/* Zeroes every register of `reg` on `stream` (asynchronous). */
+mhd_status mhd_fluxreg_zero(mhd_fluxreg *reg, void *stream);
+
 /* Ghost fill (Sec. 2.2 S step: ghost cells refreshed; periodic images and
  * same-level neighbours): executes the copies of `list` (host array) in one
  * launch.  All patches of the call must have one dtype. */
@@ -337,7 +388,8 @@ mhd_status mhd_conservation_sums(mhd_ctx *ctx, const mhd_patch_desc *patches, in
  * blocks of 256 cells); larger requests return MHD_ETOOBIG and launch
  * nothing; bad descriptors return MHD_EINVAL.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture.  All calls on a
+ * current), and so does the first call after the device's context changed
+ * (cudaDeviceReset); make such a first call before any stream capture.  All calls on a
  * device share the array: calls that overlap on the GPU (different streams
  * without ordering between them) race and may return wrong sums. */
 mhd_status mhd_conservation_sums_static(const mhd_patch_desc *patches, int32_t n,
@@ -446,6 +498,95 @@ mhd_status mhd_hilbert_split(const int32_t *lo, const int32_t *hi, int32_t dim, 
 mhd_status mhd_cluster_flags(const uint8_t *flags, int32_t dim, const int32_t *shape, double eff,
                              int32_t min_size, int32_t max_boxes, int32_t *out_lo, int32_t *out_hi,
                              int32_t *n_out);
+
+/* Measured ALU peak of the current device (diagnostics for the roofline of
+ * the advance; no counterpart in the paper): times, with CUDA events, one
+ * launch of a kernel in which every thread of (SM count x 8) blocks of 256
+ * threads runs 16 independent multiply-add chains for `iters` iterations, in
+ * FP32 (dtype MHD_F32) or FP64 (MHD_F64), after one shorter warm-up launch.
+ * Writes the rate in TFLOP/s (2 flops per multiply-add) to *tflops and the
+ * timed launch's duration to *ms.  Synchronous: it allocates a small device
+ * buffer, a stream and two events of its own, waits for the kernel and frees
+ * them.  MHD_EINVAL for bad arguments, MHD_ECUDA if a CUDA call fails. */
+mhd_status mhd_alu_probe(int32_t dtype, int32_t iters, double *tflops, double *ms);
+
+/* Error flags for regridding (Sec. 2.1: each iteration of a level flags the
+ * cells that need refinement; the paper leaves the criterion to the
+ * application).  An interior cell is flagged when the normalised central
+ * difference of the density or of the pressure along some axis exceeds theta:
+ *   |q(+d) - q(-d)| > theta (|q(+d)| + 2 |q| + |q(-d)|),  q in {rho, p},
+ * evaluated in FP64 (an FP32 state is converted first; p from the
+ * cell-centred field, the mean of the two faces).  d_flags (device) receives
+ * one byte per interior cell (1 flagged, 0 not), patch after patch, each
+ * patch's interior x fastest.  Needs one valid ghost layer.  Asynchronous on
+ * `stream`; MHD_EINVAL for bad arguments.  mhd_cluster_flags turns the flags
+ * of a level into grids. */
+mhd_status mhd_flag_cells(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n, double theta,
+                          uint8_t *d_flags, void *stream);
+
+/* Data transfer into a new iteration of a level (regridding, Sec. 2.1: a
+ * new grid takes the previous iteration's data where the two meet, and is
+ * prolonged from the parent level elsewhere; the O step of Sec. 2.2).
+ *
+ * mhd_transfer_copy: for every item, copies from old patch `src` (index into
+ * `old`) to new patch `dst` (index into `fresh`), both of one level and one
+ * dtype: kind -1 the five cell arrays over the cells of `box`, kind a (0..2)
+ * the axis-a face array over the faces of `box` (index along a = face index).
+ * Give the cells of the intersection of the two interiors and, per axis, the
+ * faces common to both patches' face sets (normal index in [lo, hi + 1] of
+ * both, the others in both interiors), so that a new patch that only touches
+ * an old one still takes the old value of the face they share.
+ * MHD_EINVAL for an index or a box outside the arrays (nothing launched). */
+typedef struct {
+  int32_t src, dst, kind, pad;
+  mhd_box box;          /* global index of the level                          */
+} mhd_transfer_item;
+mhd_status mhd_transfer_copy(mhd_ctx *ctx, const mhd_patch_desc *old, int32_t no, const mhd_patch_desc *fresh,
+                             int32_t nn, const mhd_transfer_item *items, int32_t ni, void *stream);
+
+/* mhd_prolong_new: prolongation of the coarse cells of each item's `box`
+ * (coarse global index; coarse patch `coarse`, new fine patch `fine`) into
+ * the fine patch's interior: the eight children and every face of them, the
+ * fine patch's own boundary faces included.  Each coarse cell is governed by
+ * its byte of the item's mask (device, one byte per coarse cell of
+ * mask_box, x fastest):
+ *   bit 0          the children already hold the previous iteration's data
+ *                  (mhd_transfer_copy): nothing is written;
+ *   bit 1 + 2a + s the four sub-faces on side s of axis a already hold the
+ *                  previous iteration's values: they are kept and read.
+ * Cells: density and momentum limited-linear (minmod quarter slopes, as
+ * mhd_prolong); energy_mode 0: the thermal energy prolonged the same way
+ * (as mhd_prolong), energy_mode 1: the children's thermal energies then
+ * scaled by (1 + delta / ebar) so that their total energies average to the
+ * coarse cell's (delta = E_c - mean child energy, ebar = mean child thermal
+ * energy; left unscaled, and counted in *d_fallbacks (device, nullable), where
+ * ebar + delta <= 0).  Faces: Balsara's divergence-free reconstruction (as
+ * mhd_prolong) on the faces not kept; where a coarse cell keeps sub-faces, its
+ * twelve inner fine faces are changed by the least-squares correction that
+ * zeroes every child's divergence given the kept values (the gradient of the
+ * cube-Laplacian potential of the children's divergences).  Equal cell
+ * widths along the three axes; old patches aligned to the coarse grid.
+ * MHD_EINVAL for bad indices or boxes (nothing launched). */
+typedef struct {
+  int32_t coarse, fine;
+  mhd_box box;          /* coarse cells, coarse global index                  */
+  const uint8_t *mask;  /* device                                             */
+  mhd_box mask_box;     /* coarse global index, contains box                  */
+} mhd_prolong_new_item;
+mhd_status mhd_prolong_new(mhd_ctx *ctx, const mhd_patch_desc *coarse, int32_t nc, const mhd_patch_desc *fine,
+                           int32_t nf, const mhd_prolong_new_item *items, int32_t ni, int32_t energy_mode,
+                           unsigned long long *d_fallbacks, void *stream);
+
+/* Synchronises the context's device, then returns in *out the number of
+ * cells that the floors (mhd_params.p_floor, rho_floor) changed since the
+ * last call, and resets the count. */
+mhd_status mhd_floor_count(mhd_ctx *ctx, int64_t *out);
+
+/* The context's floors (mhd_params.p_floor, rho_floor) applied to every
+ * interior cell of the patches, e.g. after refluxing, which changes cells
+ * outside any advance.  Asynchronous; nothing is launched when both floors are
+ * 0.  MHD_EINVAL for bad arguments. */
+mhd_status mhd_floor(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n, void *stream);
 
 /* Number of kernels this context has enqueued so far (for launch accounting). */
 int64_t mhd_launch_count(const mhd_ctx *ctx);

@@ -29,6 +29,8 @@ UNITS = {
     "tree.cu": [],
     "hilbert.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
     "cluster.cu": ["-Xcompiler", "-ffp-contract=off"],
+    "probe.cu": ["--fmad=true"],
+    "regrid.cu": ["--fmad=false"],
 }
 
 

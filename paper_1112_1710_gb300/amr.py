@@ -53,13 +53,13 @@ def _vol(lo, hi):
 # filling the ctypes arrays of long lists in one copy
 _CAP_DT = np.dtype([("patch", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("mode", "<i4"), ("lo", "<i4", 3),
                     ("hi", "<i4", 3), ("dst", "<u8")])
-_DEP_DT = np.dtype([("coarse", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("pad", "<i4"), ("lo", "<i4", 3),
+_DEP_DT = np.dtype([("coarse", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("mode", "<i4"), ("lo", "<i4", 3),
                     ("hi", "<i4", 3), ("flo", "<i4", 3), ("fhi", "<i4", 3), ("fine", "<u8"), ("creg", "<u8")])
 
 
 class Hierarchy:
     def __init__(self, boxes, n0, states, dx0, g=4, dtype="f32", ctx=None, stream=None, device="cuda",
-                 tree=None, concurrent=None):
+                 tree=None, concurrent=None, floors=False):
         """boxes[l] = [(lo, hi)]; states[l][i] = float64 numpy array (synth layout).
 
         tree: build the metadata from the device AMR tree (neighbour
@@ -69,7 +69,12 @@ class Hierarchy:
         concurrent: advance each level that has children on a stream of its
         own alongside the finer substeps (off by default: on one GB300 the
         finer levels' launches already fill the GPU, and the measured coarse
-        step is the same within 1%, for a scratch arena per level)."""
+        step is the same within 1%, for a scratch arena per level).
+        floors: the context was created with floors (mhd_params.p_floor /
+        rho_floor); they are then applied again to a level's interiors after
+        its refluxing and restriction, which change cells outside any
+        advance (reading R33)."""
+        self.floors = bool(floors)
         self.n0, self.g, self.dtype = n0, g, dtype
         self.device = torch.device(device)
         self.gpu = self.device.type == "cuda"  # on the CPU only the metadata is built (tests)
@@ -425,6 +430,11 @@ class Hierarchy:
                 self.stream.wait_event(join)
             self.reflux(l)
             self.restrict(l)
+            if self.floors:
+                self.floor(l)
+
+    def floor(self, l):
+        capi.mhd_floor(self.ctx, self.descs[l], self.sp)
 
     def launch_count(self) -> int:
         """Kernel launches of all the hierarchy's contexts so far."""

@@ -25,10 +25,13 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_kernel_name", "mhd_conservation_sums_static", "mhd_prolong", "mhd_restrict", "mhd_reflux",
            "mhd_restrict_prolong", "mhd_autotune_advance", "mhd_tree_parents", "mhd_tree_inherit",
            "mhd_ctx_clone", "mhd_hilbert_keys", "mhd_box_distances", "mhd_hilbert_split",
-           "mhd_patch_step_cfl", "mhd_cluster_flags")
+           "mhd_patch_step_cfl", "mhd_cluster_flags", "mhd_alu_probe", "mhd_fluxreg_create",
+           "mhd_fluxreg_destroy", "mhd_fluxreg_face", "mhd_fluxreg_edge", "mhd_fluxreg_zero", "mhd_flag_cells",
+           "mhd_transfer_copy", "mhd_prolong_new", "mhd_floor_count", "mhd_floor")
 N_KERNELS = 15
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
+MHD_REFLUX, MHD_SYNC = 0, 1
 
 
 class MHDError(RuntimeError):
@@ -50,7 +53,8 @@ class mhd_patch_desc(C.Structure):
 class mhd_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
                 ("emf", C.c_int32), ("upwind_eps", C.c_double), ("fp64_contract", C.c_int32),
-                ("advance_kernel", C.c_int32), ("fused_chunk", C.c_int32), ("reserved", C.c_int32)]
+                ("advance_kernel", C.c_int32), ("fused_chunk", C.c_int32), ("reserved", C.c_int32),
+                ("p_floor", C.c_double), ("rho_floor", C.c_double)]
 
 
 class mhd_copy(C.Structure):
@@ -74,8 +78,17 @@ class mhd_capture(C.Structure):
                 ("box", mhd_box), ("dst", C.c_void_p)]
 
 
+class mhd_transfer_item(C.Structure):
+    _fields_ = [("src", C.c_int32), ("dst", C.c_int32), ("kind", C.c_int32), ("pad", C.c_int32), ("box", mhd_box)]
+
+
+class mhd_prolong_new_item(C.Structure):
+    _fields_ = [("coarse", C.c_int32), ("fine", C.c_int32), ("box", mhd_box), ("mask", C.c_void_p),
+                ("mask_box", mhd_box)]
+
+
 class mhd_deposit(C.Structure):
-    _fields_ = [("coarse", C.c_int32), ("kind", C.c_int32), ("axis", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("coarse", C.c_int32), ("kind", C.c_int32), ("axis", C.c_int32), ("mode", C.c_int32),
                 ("box", mhd_box), ("fine_box", mhd_box), ("fine", C.c_void_p), ("coarse_reg", C.c_void_p)]
 
 
@@ -169,6 +182,30 @@ def load(build_if_missing: bool = False):
     L.mhd_box_distances.argtypes = [P, P, i64, i32, i32, P, P]
     L.mhd_hilbert_split.restype = i32
     L.mhd_hilbert_split.argtypes = [P, P, i32, P, i32, i32, i32, P, P]
+    L.mhd_alu_probe.restype = i32
+    L.mhd_alu_probe.argtypes = [i32, i32, dp, dp]
+    L.mhd_fluxreg_create.restype = i32
+    L.mhd_fluxreg_create.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(P)]
+    L.mhd_fluxreg_destroy.restype = None
+    L.mhd_fluxreg_destroy.argtypes = [P]
+    L.mhd_fluxreg_face.restype = P
+    L.mhd_fluxreg_face.argtypes = [P, i32, i32, i32, C.POINTER(mhd_box)]
+    L.mhd_fluxreg_edge.restype = P
+    L.mhd_fluxreg_edge.argtypes = [P, i32, i32, i32, i32, C.POINTER(mhd_box)]
+    L.mhd_floor.restype = i32
+    L.mhd_floor.argtypes = [P, C.POINTER(mhd_patch_desc), i32, P]
+    L.mhd_floor_count.restype = i32
+    L.mhd_floor_count.argtypes = [P, C.POINTER(i64)]
+    L.mhd_transfer_copy.restype = i32
+    L.mhd_transfer_copy.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
+                                    C.POINTER(mhd_transfer_item), i32, P]
+    L.mhd_prolong_new.restype = i32
+    L.mhd_prolong_new.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
+                                  C.POINTER(mhd_prolong_new_item), i32, i32, P, P]
+    L.mhd_flag_cells.restype = i32
+    L.mhd_flag_cells.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.c_double, P, P]
+    L.mhd_fluxreg_zero.restype = i32
+    L.mhd_fluxreg_zero.argtypes = [P, P]
     _lib = L
     return L
 
@@ -195,8 +232,9 @@ def _descs(patches):
 
 # ------------------------------------------------------------------ C names
 def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0, fp64_contract=0,
-                   advance_kernel=0, fused_chunk=0):
-    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, advance_kernel, fused_chunk, 0)
+                   advance_kernel=0, fused_chunk=0, p_floor=0.0, rho_floor=0.0):
+    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, advance_kernel, fused_chunk, 0,
+                     float(p_floor), float(rho_floor))
     out = C.c_void_p()
     r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
     _check(None, r)
@@ -293,6 +331,74 @@ def mhd_reflux(ctx, coarse, corr_ptrs, deposits, stream: int = 0) -> None:
     _check(ctx, load().mhd_reflux(ctx, ca, nc, cp, dp_, nd, stream))
 
 
+def mhd_flag_cells(ctx, patches, theta: float, d_flags: int, stream: int = 0) -> None:
+    arr, n = _descs(patches)
+    _check(ctx, load().mhd_flag_cells(ctx, arr, n, float(theta), d_flags, stream))
+
+
+def mhd_floor(ctx, patches, stream: int = 0) -> None:
+    arr, n = _descs(patches)
+    _check(ctx, load().mhd_floor(ctx, arr, n, stream))
+
+
+def mhd_floor_count(ctx) -> int:
+    """Cells the pressure floor raised since the last call (synchronises)."""
+    v = C.c_int64()
+    _check(ctx, load().mhd_floor_count(ctx, C.byref(v)))
+    return int(v.value)
+
+
+def mhd_transfer_copy(ctx, old, fresh, items, stream: int = 0) -> None:
+    oa, no = _descs(old)
+    na, nn = _descs(fresh)
+    ia, ni = _structs(mhd_transfer_item, items)
+    _check(ctx, load().mhd_transfer_copy(ctx, oa, no, na, nn, ia, ni, stream))
+
+
+def mhd_prolong_new(ctx, coarse, fine, items, energy_mode: int = 1, d_fallbacks: int = 0, stream: int = 0) -> None:
+    ca, nc = _descs(coarse)
+    fa, nf = _descs(fine)
+    ia, ni = _structs(mhd_prolong_new_item, items)
+    _check(ctx, load().mhd_prolong_new(ctx, ca, nc, fa, nf, ia, ni, int(energy_mode), d_fallbacks or None, stream))
+
+
+def mhd_fluxreg_create(ctx, patches):
+    """Library-owned FP64 boundary registers of `patches` (opaque handle)."""
+    arr, n = _descs(patches)
+    out = C.c_void_p()
+    _check(ctx, load().mhd_fluxreg_create(ctx, arr, n, C.byref(out)))
+    return out.value
+
+
+def mhd_fluxreg_destroy(reg) -> None:
+    load().mhd_fluxreg_destroy(reg)
+
+
+def mhd_fluxreg_face(reg, patch: int, axis: int, side: int):
+    """(device pointer, (lo, hi)) of a patch's boundary-face register."""
+    b = mhd_box()
+    ptr = load().mhd_fluxreg_face(reg, patch, axis, side, C.byref(b))
+    if not ptr:
+        raise MHDError(-1, "mhd_fluxreg_face: bad index")
+    return ptr, (tuple(b.lo), tuple(b.hi))
+
+
+def mhd_fluxreg_edge(reg, patch: int, face_axis: int, side: int, edge_axis: int):
+    """(device pointer, (lo, hi)) of the register of a patch's axis-edge_axis
+    edges in its boundary face (face_axis, side)."""
+    b = mhd_box()
+    ptr = load().mhd_fluxreg_edge(reg, patch, face_axis, side, edge_axis, C.byref(b))
+    if not ptr:
+        raise MHDError(-1, "mhd_fluxreg_edge: bad index")
+    return ptr, (tuple(b.lo), tuple(b.hi))
+
+
+def mhd_fluxreg_zero(reg, stream: int = 0) -> None:
+    r = load().mhd_fluxreg_zero(reg, stream)
+    if r != 0:
+        raise MHDError(r, "mhd_fluxreg_zero failed")
+
+
 def mhd_ghost_fill(ctx, patches, copies, stream: int = 0) -> None:
     arr, n = _descs(patches)
     carr, nc = copies if isinstance(copies, tuple) else _structs(mhd_copy, copies)
@@ -316,6 +422,15 @@ def mhd_get_device_status(ctx) -> int:
     v = C.c_int32(0)
     _check(ctx, load().mhd_get_device_status(ctx, C.byref(v)))
     return int(v.value)
+
+
+def mhd_alu_probe(dtype: str = "f32", iters: int = 4096) -> tuple:
+    """Measured FMA rate of the current device: (TFLOP/s, ms of the timed launch)."""
+    t, ms = C.c_double(), C.c_double()
+    r = load().mhd_alu_probe(0 if dtype == "f64" else 1, int(iters), C.byref(t), C.byref(ms))
+    if r != 0:
+        raise MHDError(r, "mhd_alu_probe failed")
+    return t.value, ms.value
 
 
 def mhd_timing_enable(ctx, on: bool = True) -> None:

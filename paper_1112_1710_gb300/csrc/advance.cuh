@@ -64,6 +64,7 @@ template <typename R> constexpr bool kInlineEdges = sizeof(R) == 4;
 template <typename R> struct SolverConsts {
   R gamma, gm1, igm1, eps_up;
   int limiter, emf;
+  R p_floor, rho_floor;
 };
 
 struct Cell {
@@ -267,14 +268,8 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
     u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
     R w[8];
     cons2prim(u, sc.gm1, w);
-    VecIO<R>::store8(arr(scr, p, SC_W), p.snelem, x, w);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int b = (a + 1) % 3, cc = (a + 2) % 3;
-      arr(scr, p, SC_EN + a)[x] = w[1 + cc] * w[5 + b] - w[1 + b] * w[5 + cc];
-    }
-    if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
     if constexpr (Cfl) {
+      // the CFL candidate from the unfloored primitives (as mhd_cfl_dt)
       const bool interior = c.i >= p.g && c.i < p.g + p.n[0] && c.j >= p.g && c.j < p.g + p.n[1] &&
                             c.k >= p.g && c.k < p.g + p.n[2];
       if (interior) {
@@ -287,6 +282,17 @@ __global__ void __launch_bounds__(kThreads) k_prim(const DPatch* __restrict__ P,
         }
       }
     }
+    // the floors (when set) bound the primitives the step reads, ghost cells
+    // included
+    if (sc.rho_floor > R(0) && !(w[0] >= sc.rho_floor)) w[0] = sc.rho_floor;
+    if (sc.p_floor > R(0) && !(w[4] >= sc.p_floor)) w[4] = sc.p_floor;
+    VecIO<R>::store8(arr(scr, p, SC_W), p.snelem, x, w);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, cc = (a + 2) % 3;
+      arr(scr, p, SC_EN + a)[x] = w[1 + cc] * w[5 + b] - w[1 + b] * w[5 + cc];
+    }
+    if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
   }
   if constexpr (Cfl) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -849,6 +855,47 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 5 : 3) k_update(con
   if (ce2) arr(scr, p, SC_ED + 2)[x] = ec2;
 }
 
+// ---------------------------------------------------------------- k_floor
+// The floors after the update (enabled by p_floor > 0 or rho_floor > 0): one
+// thread per cell of the update box.  A density below rho_floor becomes
+// rho_floor with M kept and E = p_floor / (gamma - 1) + |M|^2 / (2 rho_floor)
+// + |Bc|^2 / 2; otherwise a pressure below p_floor, from the new face field,
+// gets E += (p_floor - p) / (gamma - 1).  The oracle's expressions and order.
+template <typename R>
+__device__ __forceinline__ bool floor_cell(const DPatch& p, int64_t x, const SolverConsts<R>& sc) {
+  R u[8], w[8];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = ((const R*)p.U[q])[x];
+  u[5] = R(0.5) * (((const R*)p.B[0])[x] + ((const R*)p.B[0])[x + 1]);
+  u[6] = R(0.5) * (((const R*)p.B[1])[x] + ((const R*)p.B[1])[x + p.s1]);
+  u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
+  cons2prim(u, sc.gm1, w);
+  if (sc.rho_floor > R(0) && !(w[0] >= sc.rho_floor)) {
+    const R ke = R(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / sc.rho_floor;
+    const R me = R(0.5) * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    ((R*)p.U[0])[x] = sc.rho_floor;
+    ((R*)p.U[4])[x] = (sc.p_floor / sc.gm1 + ke) + me;
+    return true;
+  }
+  if (sc.p_floor > R(0) && w[4] < sc.p_floor) {
+    const R add = (sc.p_floor - w[4]) / sc.gm1;
+    ((R*)p.U[4])[x] = u[4] + add;
+    return true;
+  }
+  return false;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_floor(const DPatch* __restrict__ P, const BlockTask* __restrict__ T,
+                                                    SolverConsts<R> sc, unsigned long long* count) {
+  const BlockTask t = T[blockIdx.x];
+  const DPatch& p = P[t.patch];
+  Cell c;
+  if (!region_cell<kMu<R>, kMuT<R>>(p, t.start + threadIdx.x, c)) return;
+  if (!in_ub(p, 0, c.i, 0, 0) || !in_ub(p, 1, c.j, 0, 0) || !in_ub(p, 2, c.k, 0, 0)) return;
+  if (floor_cell<R>(p, lin(p, c), sc)) atomicAdd(count, 1ull);
+}
+
 // Enqueues the step constants and the stages for the patches of one call;
 // K (npatch x kStepConsts elements) is scratch.
 template <typename R>
@@ -883,6 +930,8 @@ cudaError_t launch_advance(const AdvanceArgs& a, R* scr, R* K, const SolverConst
   if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<gu, kThreads, 0, s>>>(d_patches, d_tasksu, scr, sc)));
   MHD_TIMED(tm, K_UPDATE, s,
             (k_update<R, inl><<<gu, kThreads, 0, s>>>(d_patches, d_tasksu, scr, sc, K, commit ? 1 : 0)));
+  if (commit && (a.p_floor > 0.0 || a.rho_floor > 0.0))
+    MHD_TIMED(tm, K_UPDATE, s, (k_floor<R><<<gu, kThreads, 0, s>>>(d_patches, d_tasksu, sc, a.d_floors)));
   return cudaGetLastError();
 }
 
@@ -919,6 +968,9 @@ cudaError_t launch_fused(const AdvanceArgs& a, const SolverConsts<R>& sc, cudaSt
   if (a.commit)
     MHD_TIMED(a.timer, K_COMMIT, s,
               (k_commit<R><<<a.nctasks, kThreads, 0, s>>>(a.patches, a.ctasks, (const R*)a.scratch)));
+  if (a.commit && (a.p_floor > 0.0 || a.rho_floor > 0.0))
+    MHD_TIMED(a.timer, K_COMMIT, s,
+              (k_floor<R><<<a.nctasks, kThreads, 0, s>>>(a.patches, a.ctasks, sc, a.d_floors)));
   return cudaGetLastError();
 }
 
@@ -939,6 +991,19 @@ template <typename R> cudaError_t launch_fused_variant(const AdvanceArgs& a, con
   }
 }
 
+// The floors over the interiors of a call's patches (k = 0, tasks over
+// [lo, hi + 1] as the update's).
+template <typename R> cudaError_t run_floor(const AdvanceArgs& a, cudaStream_t s) {
+  SolverConsts<R> sc{};
+  sc.gamma = (R)a.gamma;
+  sc.gm1 = sc.gamma - R(1);
+  sc.p_floor = (R)a.p_floor;
+  sc.rho_floor = (R)a.rho_floor;
+  if (a.nblocksu == 0) return cudaSuccess;
+  k_floor<R><<<a.nblocksu, kThreads, 0, s>>>(a.patches, a.tasksu, sc, a.d_floors);
+  return cudaGetLastError();
+}
+
 // Solver constants in the arithmetic type, then the launches.
 template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t s) {
   SolverConsts<R> sc;
@@ -948,6 +1013,8 @@ template <typename R> cudaError_t run_advance(const AdvanceArgs& a, cudaStream_t
   sc.eps_up = (R)a.eps_up;
   sc.limiter = a.limiter;
   sc.emf = a.emf;
+  sc.p_floor = (R)a.p_floor;
+  sc.rho_floor = (R)a.rho_floor;
   if (a.fused) return launch_fused_variant<R>(a, sc, s);
   return launch_advance<R>(a, (R*)a.scratch, (R*)a.stepc, sc, s);
 }

@@ -9,5 +9,6 @@
 namespace mhd {
 
 cudaError_t advance_f32(const AdvanceArgs& a, cudaStream_t s) { return fast32::run_advance<float>(a, s); }
+cudaError_t floor_f32(const AdvanceArgs& a, cudaStream_t s) { return fast32::run_floor<float>(a, s); }
 
 }  // namespace mhd

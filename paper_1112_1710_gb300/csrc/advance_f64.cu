@@ -8,5 +8,6 @@
 namespace mhd {
 
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s) { return exact64::run_advance<double>(a, s); }
+cudaError_t floor_f64(const AdvanceArgs& a, cudaStream_t s) { return exact64::run_floor<double>(a, s); }
 
 }  // namespace mhd

@@ -28,13 +28,14 @@ struct DCapture {
 // One deposit into a coarse patch's correction planes: box in coarse global
 // index (faces: face index = index of the upper cell; edges: storing cell).
 struct DDeposit {
-  int32_t coarse, kind, axis, pad;
+  int32_t coarse, kind, axis, mode;  // mode 0: refluxing (ratio 2), 1: same-level synchronisation
   int32_t lo[3], ext[3];
   int32_t flo[3], fext[3];  // fine register box (fine global index)
   const double* fine;       // fine register (5 planes for faces, 1 for edges)
   const double* creg;       // coarse register over the box
   double* corr;             // correction planes of the coarse patch (18 planes)
   unsigned int* flags;      // the coarse patch's element flags (bytes, 4-aligned)
+  int32_t corr_idx, pad2;   // index of the coarse patch's DCorr
 };
 
 // Correction planes of one coarse patch and its element flags (bit 0: the
@@ -43,7 +44,15 @@ struct DCorr {
   int32_t patch, pad;
   int64_t count;  // 18 * nelem
   double* base;
-  const unsigned char* flags;
+  unsigned char* flags;  // zero outside a call: each call resets what it set
+};
+
+// The elements a refluxing call flags, one entry per element: (index into
+// the call's DCorr array) << 40 | element index.
+struct RefluxList {
+  unsigned long long* entries;
+  unsigned long long* count;
+  unsigned long long capacity;
 };
 
 // A block table of an item list on the device (see list_elem): the blocks'
@@ -66,8 +75,11 @@ cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse,
                             const PackedTasks& p0, const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s);
 cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* caps, const PackedTasks& p,
                            const void* scratch, const double* d_dt, const KernelTimer* tm, cudaStream_t s);
-cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, void* flags, size_t flag_bytes,
-                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const BlockTask* corr_tasks,
-                          int ncorr, const KernelTimer* tm, cudaStream_t s);
+// Refluxing: deposits (flagging the elements they affect into `list`), the
+// correction of the listed elements (which also clears their flags), and the
+// zeroing of the deposited plane elements.
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const RefluxList& list,
+                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const KernelTimer* tm,
+                          cudaStream_t s);
 
 }  // namespace mhd

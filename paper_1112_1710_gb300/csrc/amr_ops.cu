@@ -381,9 +381,16 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
 
 // ---------------------------------------------------------------- reflux
 // Sets flag bit `bit` of element x of a coarse patch (flags are bytes packed
-// four to a word; neighbouring elements of other threads share words).
-__device__ __forceinline__ void mark(unsigned int* flags, int64_t x, unsigned int bit) {
-  atomicOr(flags + (x >> 2), bit << (8 * (int)(x & 3)));
+// four to a word; neighbouring elements of other threads share words); the
+// thread that sets the element's first bit appends it to the call's list.
+__device__ __forceinline__ void mark(unsigned int* flags, int64_t x, unsigned int bit, const RefluxList& L,
+                                     int corr_idx) {
+  const int sh = 8 * (int)(x & 3);
+  const unsigned int old = atomicOr(flags + (x >> 2), bit << sh);
+  if (((old >> sh) & 0xFFu) == 0u) {
+    const unsigned long long i = atomicAdd(L.count, 1ull);
+    if (i < L.capacity) L.entries[i] = ((unsigned long long)corr_idx << 40) | (unsigned long long)x;
+  }
 }
 
 // After the correction: zeroes the plane elements the deposits wrote, so the
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(kThreads) k_unset(const DPatch* __restrict__ P
 
 __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__ PC,
                                                       const DDeposit* __restrict__ D,
-                                                      const BlockTask* __restrict__ T) {
+                                                      const BlockTask* __restrict__ T, RefluxList L) {
   const BlockTask t = T[blockIdx.x];
   const DDeposit dp = D[t.patch];
   const int e = t.start + threadIdx.x;
@@ -420,7 +427,19 @@ __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__
   const DPatch& pc = PC[dp.coarse];
   const int64_t c = lin3(pc, C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]);
   const int64_t fn = (int64_t)dp.fext[0] * dp.fext[1] * dp.fext[2];
-  if (dp.kind == 0) {
+  if (dp.mode == 1) {
+    // synchronisation of a face / edge shared by two patches of one level:
+    // the other patch's register over the same box; dF = 0.5 (other - own)
+    const int64_t fo = (int64_t)(C3[0] - dp.flo[0]) +
+                       (int64_t)dp.fext[0] * ((C3[1] - dp.flo[1]) + (int64_t)dp.fext[1] * (C3[2] - dp.flo[2]));
+    if (dp.kind == 0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        dp.corr[(int64_t)(dp.axis * 5 + q) * pc.nelem + c] = 0.5 * (dp.fine[q * fn + fo] - dp.creg[q * cn + e]);
+    } else {
+      dp.corr[(int64_t)(15 + dp.axis) * pc.nelem + c] = 0.5 * (dp.fine[fo] - dp.creg[e]);
+    }
+  } else if (dp.kind == 0) {
     const int d = dp.axis;
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
@@ -458,8 +477,8 @@ __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__
   const int ai[3] = {C3[0] - pc.glo[0], C3[1] - pc.glo[1], C3[2] - pc.glo[2]};
   if (dp.kind == 0) {
     const int d = dp.axis;
-    mark(dp.flags, c, 1u);
-    if (ai[d] > 0) mark(dp.flags, c - sof(pc, d), 1u);
+    mark(dp.flags, c, 1u, L, dp.corr_idx);
+    if (ai[d] > 0) mark(dp.flags, c - sof(pc, d), 1u, L, dp.corr_idx);
   } else {
     const int e2 = dp.axis;
 #pragma unroll
@@ -467,29 +486,35 @@ __global__ void __launch_bounds__(kThreads) k_deposit(const DPatch* __restrict__
       if (f == e2) continue;
       const int b = (f + 1) % 3, cc = (f + 2) % 3;
       const int sh = e2 == cc ? b : cc;  // the face x reads the edge at x and at x + s_sh
-      mark(dp.flags, c, 2u << f);
-      if (ai[sh] > 0) mark(dp.flags, c - sof(pc, sh), 2u << f);
+      mark(dp.flags, c, 2u << f, L, dp.corr_idx);
+      if (ai[sh] > 0) mark(dp.flags, c - sof(pc, sh), 2u << f, L, dp.corr_idx);
     }
   }
 }
 
-// Applies the correction planes to the interior cells and faces of a coarse
-// patch: launch region = interior grown by one on the upper side.
+// Applies the correction planes to the flagged elements of the coarse
+// patches, one thread per entry of the call's list (the elements the deposits
+// flagged, each once): the cell if it is an interior cell, the faces that are
+// interior faces (region: interior grown by one on the upper side; flagged
+// ghost elements are only cleared).  Each thread clears its element's flags.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_correct(const DPatch* __restrict__ PC, const DCorr* __restrict__ C,
-                                                      const BlockTask* __restrict__ T) {
-  const BlockTask t = T[blockIdx.x];
-  const DCorr cr = C[t.patch];
+                                                      RefluxList L) {
+  const unsigned long long li = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
+  if (li >= *L.count || li >= L.capacity) return;
+  const unsigned long long ent = L.entries[li];
+  const DCorr cr = C[(int)(ent >> 40)];
   const DPatch& p = PC[cr.patch];
-  const int e = t.start + threadIdx.x;
-  const int ex = p.n[0] + 1, ey = p.n[1] + 1, ez = p.n[2] + 1;
-  if (e >= ex * ey * ez) return;
-  const int ai[3] = {p.g + e % ex, p.g + (e / ex) % ey, p.g + e / (ex * ey)};
-  const int64_t c = lin3(p, ai[0], ai[1], ai[2]);
-  // Elements no deposit touched see only zero plane differences, and
-  // u - 0/dx - 0/dx - 0/dx == u: they are skipped on their flag byte, with the
-  // same bits as applying the correction; so are zero differences below.
+  const int64_t c = (int64_t)(ent & ((1ull << 40) - 1));
   const unsigned int fl = cr.flags[c];
+  cr.flags[c] = 0;
+  const int ai[3] = {(int)(c % p.s1), (int)((c / p.s1) % (p.s2 / p.s1)), (int)(c / p.s2)};
+  if (ai[0] < p.g || ai[0] > p.g + p.n[0] || ai[1] < p.g || ai[1] > p.g + p.n[1] || ai[2] < p.g ||
+      ai[2] > p.g + p.n[2])
+    return;
+  // Elements no deposit touched see only zero plane differences, and
+  // u - 0/dx - 0/dx - 0/dx == u: they are not in the list, with the same
+  // bits as applying the correction; so are zero differences below.
   if (!fl) return;
   const double* K = cr.base;
   const int64_t ne = p.nelem;
@@ -589,17 +614,18 @@ cudaError_t capture_launch(int dtype, const DPatch* patches, const DCapture* cap
   return cudaGetLastError();
 }
 
-cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, void* flags, size_t flag_bytes,
-                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const BlockTask* corr_tasks,
-                          int ncorr, const KernelTimer* tm, cudaStream_t s) {
+cudaError_t reflux_launch(int dtype, const DPatch* coarse, const DCorr* corr, const RefluxList& list,
+                          const DDeposit* deps, const BlockTask* dep_tasks, int ndep, const KernelTimer* tm,
+                          cudaStream_t s) {
   if (ndep == 0) return cudaSuccess;  // no deposit: every correction is zero
-  MHD_TIMED(tm, K_REFLUX, s, (cudaMemsetAsync(flags, 0, flag_bytes, s),
-                              k_deposit<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
+  const int ncorr = (int)((list.capacity + kThreads - 1) / kThreads);
+  MHD_TIMED(tm, K_REFLUX, s, (cudaMemsetAsync(list.count, 0, sizeof(unsigned long long), s),
+                              k_deposit<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks, list)));
   if (ncorr) {
     if (dtype == 0)
-      MHD_TIMED(tm, K_REFLUX, s, (k_correct<double><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+      MHD_TIMED(tm, K_REFLUX, s, (k_correct<double><<<ncorr, kThreads, 0, s>>>(coarse, corr, list)));
     else
-      MHD_TIMED(tm, K_REFLUX, s, (k_correct<float><<<ncorr, kThreads, 0, s>>>(coarse, corr, corr_tasks)));
+      MHD_TIMED(tm, K_REFLUX, s, (k_correct<float><<<ncorr, kThreads, 0, s>>>(coarse, corr, list)));
   }
   MHD_TIMED(tm, K_REFLUX, s, (k_unset<<<ndep, kThreads, 0, s>>>(coarse, deps, dep_tasks)));
   return cudaGetLastError();

@@ -10,11 +10,13 @@
 #include <cstring>
 #include <string>
 #include <unordered_map>
+#include <memory>
 #include <vector>
 
 #include "amr.h"
 #include "common.cuh"
 #include "launch.h"
+#include "regrid.h"
 #include "mhd_gpu.h"
 
 using namespace mhd;
@@ -50,6 +52,10 @@ struct mhd_ctx {
   double* partials = nullptr;
   size_t partials_n = 0;
   int* d_status = nullptr;
+  unsigned long long* d_counter = nullptr;  // fallback counter of mhd_prolong_new
+  unsigned long long* d_floors = nullptr;   // cells raised by the pressure floor
+  void* rflags = nullptr;                   // refluxing's element flags, zero between calls
+  size_t rflags_bytes = 0;
   std::string err;
   std::unordered_multimap<uint64_t, TableEntry> tables;
   size_t table_bytes = 0;
@@ -344,7 +350,8 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
       params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1 ||
       params->fp64_contract < 0 || params->fp64_contract > 1 || params->advance_kernel < 0 ||
-      params->advance_kernel > 3 || params->fused_chunk < 0 || params->reserved != 0)
+      params->advance_kernel > 3 || params->fused_chunk < 0 || params->reserved != 0 || !(params->p_floor >= 0.0) ||
+      !(params->rho_floor >= 0.0))
     return MHD_EINVAL;
   mhd_ctx* c = new mhd_ctx();
   c->prm = *params;
@@ -352,9 +359,13 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_floors, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_floors, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_floors) cudaFree(c->d_floors);
     delete c;
     return MHD_ECUDA;
   }
@@ -387,6 +398,9 @@ void mhd_ctx_destroy(mhd_ctx* c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->partials) cudaFree(c->partials);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_counter) cudaFree(c->d_counter);
+  if (c->d_floors) cudaFree(c->d_floors);
+  if (c->rflags) cudaFree(c->rflags);
   delete c;
 }
 
@@ -694,10 +708,13 @@ static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_
   a.commit = true;
   a.cfl_out = cfl_dt ? (unsigned long long*)const_cast<double*>(d_dt) : nullptr;
   a.cfl = c->prm.cfl;
+  a.p_floor = c->prm.p_floor;
+  a.rho_floor = c->prm.rho_floor;
+  a.d_floors = c->d_floors;
   cudaError_t e = run_advance_args(c, dtype, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
   // fused: step constants, k_fused, k_commit; staged with the CFL dt: + reset
-  c->launches += fused ? 3 : staged_launches(elem_size(dtype)) + (cfl_dt ? 1 : 0);
+  c->launches += (fused ? 3 : staged_launches(elem_size(dtype)) + (cfl_dt ? 1 : 0)) + (c->prm.p_floor > 0.0 || c->prm.rho_floor > 0.0 ? 1 : 0);
   if (ncap > 0) {
     PackedTasks pc{};
     if ((r = packed_table(c, ccounts, false, pc))) return r;
@@ -893,6 +910,209 @@ mhd_status mhd_cfl_dt(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, cons
                                 (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cfl_dt launch");
   c->launches += tasks.empty() ? 1 : 2;
+  return MHD_OK;
+}
+
+mhd_status mhd_transfer_copy(mhd_ctx* c, const mhd_patch_desc* old, int32_t no, const mhd_patch_desc* fresh,
+                             int32_t nn, const mhd_transfer_item* items, int32_t ni, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (no < 1 || nn < 1 || !old || !fresh || ni < 0 || (ni > 0 && !items))
+    return fail(c, MHD_EINVAL, "transfer_copy: bad arguments");
+  if (ni == 0) return MHD_OK;
+  std::vector<DPatch> dold(no), dnew(nn);
+  const int dtype = old[0].dtype;
+  for (int p = 0; p < no; ++p) {
+    if ((r = convert(c, old[p], p, dold[p]))) return r;
+    if (old[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  for (int p = 0; p < nn; ++p) {
+    if ((r = convert(c, fresh[p], p, dnew[p]))) return r;
+    if (fresh[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  std::vector<DTransfer> it(ni);
+  std::vector<int64_t> counts(ni);
+  for (int t = 0; t < ni; ++t) {
+    const mhd_transfer_item& m = items[t];
+    if (m.src < 0 || m.src >= no || m.dst < 0 || m.dst >= nn || m.kind < -1 || m.kind > 2)
+      return fail(c, MHD_EINVAL, "transfer item %d: bad patch index or kind", t);
+    DTransfer& o = it[t];
+    o.src = m.src;
+    o.dst = m.dst;
+    o.kind = m.kind;
+    o.pad = 0;
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a], hi = m.box.hi[a];
+      const int top = (m.kind == a) ? 0 : -1;  // face arrays hold one more entry along their normal
+      for (const DPatch* P : {&dold[m.src], &dnew[m.dst]})
+        if (hi < lo || lo - P->glo[a] < 0 || hi - P->glo[a] > P->N[a] + top)
+          return fail(c, MHD_EINVAL, "transfer item %d: box outside the arrays", t);
+      o.lo[a] = lo;
+      o.ext[a] = hi - lo + 1;
+      cnt *= o.ext[a];
+    }
+    counts[t] = cnt;
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_o = nullptr, *d_n = nullptr, *d_i = nullptr, *d_t = nullptr;
+  if ((r = table(c, dold.data(), dold.size() * sizeof(DPatch), &d_o))) return r;
+  if ((r = table(c, dnew.data(), dnew.size() * sizeof(DPatch), &d_n))) return r;
+  if ((r = table(c, it.data(), it.size() * sizeof(DTransfer), &d_i))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = transfer_copy_launch(dtype, (const DPatch*)d_o, (const DPatch*)d_n, (const DTransfer*)d_i,
+                                       (const BlockTask*)d_t, (int)tasks.size(), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "transfer_copy launch");
+  c->launches += 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_prolong_new(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, const mhd_patch_desc* fine,
+                           int32_t nf, const mhd_prolong_new_item* items, int32_t ni, int32_t energy_mode,
+                           unsigned long long* d_fallbacks, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (nc < 1 || nf < 1 || !coarse || !fine || ni < 0 || (ni > 0 && !items) || (energy_mode != 0 && energy_mode != 1))
+    return fail(c, MHD_EINVAL, "prolong_new: bad arguments");
+  if (ni == 0) return MHD_OK;
+  std::vector<DPatch> dc(nc), df(nf);
+  const int dtype = coarse[0].dtype;
+  for (int p = 0; p < nc; ++p) {
+    if ((r = convert(c, coarse[p], p, dc[p]))) return r;
+    if (coarse[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  for (int p = 0; p < nf; ++p) {
+    if ((r = convert(c, fine[p], p, df[p]))) return r;
+    if (fine[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+  }
+  std::vector<DProlongNew> it(ni);
+  std::vector<int64_t> counts(ni);
+  for (int t = 0; t < ni; ++t) {
+    const mhd_prolong_new_item& m = items[t];
+    if (m.coarse < 0 || m.coarse >= nc || m.fine < 0 || m.fine >= nf || !m.mask)
+      return fail(c, MHD_EINVAL, "prolong_new item %d: bad patch index or mask", t);
+    const DPatch& C = dc[m.coarse];
+    const DPatch& F = df[m.fine];
+    DProlongNew& o = it[t];
+    o.coarse = m.coarse;
+    o.fine = m.fine;
+    o.mask = m.mask;
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int lo = m.box.lo[a], hi = m.box.hi[a];
+      // the coarse cells and their neighbours inside the coarse arrays, their
+      // children and the children's upper faces inside the fine arrays, the
+      // box inside the mask's box
+      if (hi < lo || lo - 1 - C.glo[a] < 0 || hi + 1 - C.glo[a] > C.N[a] - 1 || 2 * lo - F.glo[a] < 0 ||
+          2 * hi + 2 - F.glo[a] > F.N[a] || lo < m.mask_box.lo[a] || hi > m.mask_box.hi[a])
+        return fail(c, MHD_EINVAL, "prolong_new item %d: box outside the arrays or the mask", t);
+      o.lo[a] = lo;
+      o.ext[a] = hi - lo + 1;
+      o.mlo[a] = m.mask_box.lo[a];
+      o.mext[a] = m.mask_box.hi[a] - m.mask_box.lo[a] + 1;
+      cnt *= o.ext[a];
+    }
+    counts[t] = cnt;
+  }
+  unsigned long long* nfall = d_fallbacks;
+  if (!nfall) {
+    if (!c->d_counter) {
+      cudaError_t e = cudaMalloc(&c->d_counter, sizeof(unsigned long long));
+      if (e != cudaSuccess) return fail(c, MHD_ENOMEM, "counter: %s", cudaGetErrorString(e));
+    }
+    nfall = c->d_counter;
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_c = nullptr, *d_f = nullptr, *d_i = nullptr, *d_t = nullptr;
+  if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
+  if ((r = table(c, df.data(), df.size() * sizeof(DPatch), &d_f))) return r;
+  if ((r = table(c, it.data(), it.size() * sizeof(DProlongNew), &d_i))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  cudaError_t e = prolong_new_launch(dtype, (const DPatch*)d_c, (const DPatch*)d_f, (const DProlongNew*)d_i,
+                                     (const BlockTask*)d_t, (int)tasks.size(), energy_mode, nfall,
+                                     (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "prolong_new launch");
+  c->launches += 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_floor(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches) return fail(c, MHD_EINVAL, "floor: bad arguments");
+  if (!(c->prm.p_floor > 0.0 || c->prm.rho_floor > 0.0)) return MHD_OK;
+  std::vector<DPatch> dp(n);
+  std::vector<int64_t> counts(n);
+  const int dtype = patches[0].dtype;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+    dp[p].k = 0;
+    counts[p] = (int64_t)(dp[p].n[0] + 1) * (dp[p].n[1] + 1) * (dp[p].n[2] + 1);
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_p = nullptr, *d_t = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  AdvanceArgs a{};
+  a.patches = (const DPatch*)d_p;
+  a.npatches = n;
+  a.tasksu = (const BlockTask*)d_t;
+  a.nblocksu = (int)tasks.size();
+  a.gamma = c->prm.gamma;
+  a.p_floor = c->prm.p_floor;
+  a.rho_floor = c->prm.rho_floor;
+  a.d_floors = c->d_floors;
+  cudaError_t e = dtype == MHD_F32 ? floor_f32(a, (cudaStream_t)stream) : floor_f64(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "floor launch");
+  c->launches += 1;
+  return MHD_OK;
+}
+
+mhd_status mhd_floor_count(mhd_ctx* c, int64_t* out) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (!out) return fail(c, MHD_EINVAL, "floor_count: out is NULL");
+  unsigned long long v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, c->d_floors, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->d_floors, 0, sizeof v);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "floor_count");
+  *out = (int64_t)v;
+  return MHD_OK;
+}
+
+mhd_status mhd_flag_cells(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, double theta, uint8_t* d_flags,
+                          void* stream) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches || !d_flags || !(theta >= 0.0)) return fail(c, MHD_EINVAL, "flag_cells: bad arguments");
+  std::vector<DPatch> dp(n);
+  std::vector<int64_t> counts(n), off(n);
+  const int dtype = patches[0].dtype;
+  int64_t total = 0;
+  for (int p = 0; p < n; ++p) {
+    if ((r = convert(c, patches[p], p, dp[p]))) return r;
+    if (patches[p].dtype != dtype) return fail(c, MHD_EINVAL, "patches of one call must share a dtype");
+    if (patches[p].nghost < 1) return fail(c, MHD_EINVAL, "flag_cells: patch %d needs a ghost layer", p);
+    counts[p] = (int64_t)dp[p].n[0] * dp[p].n[1] * dp[p].n[2];
+    off[p] = total;
+    total += counts[p];
+  }
+  std::vector<BlockTask> tasks;
+  tasks_for(counts, tasks);
+  void *d_p = nullptr, *d_t = nullptr, *d_o = nullptr;
+  if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(BlockTask), &d_t))) return r;
+  if ((r = table(c, off.data(), off.size() * sizeof(int64_t), &d_o))) return r;
+  cudaError_t e = flag_launch(dtype, (const DPatch*)d_p, (const BlockTask*)d_t, (int)tasks.size(),
+                              (const int64_t*)d_o, c->prm.gamma, theta, d_flags, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "flag_cells launch");
+  c->launches += 1;
   return MHD_OK;
 }
 
@@ -1111,18 +1331,33 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
   int dtype = -1;
   std::vector<DPatch> dc;
   if ((r = convert_all(c, coarse, nc, dc, &dtype))) return r;
-  // element flags of the corrected patches in the arena: one byte per element
+  // element flags of the corrected patches: one byte per element in a buffer
+  // of the context that stays zero between calls (each call clears what its
+  // deposits set), so no call has to clear whole patches
   std::vector<int64_t> flag_off(nc, -1);
   int64_t flag_bytes = 0;
   std::vector<DCorr> cr;
-  std::vector<int64_t> kc;
+  std::vector<int> corr_idx(nc, -1);
   for (int p = 0; p < nc; ++p) {
     if (!corr[p]) continue;
     flag_off[p] = flag_bytes;
     flag_bytes += (dc[p].nelem + 15) / 16 * 16;
   }
-  if ((r = ensure_scratch(c, (size_t)flag_bytes + 16))) return r;
-  unsigned char* flags = (unsigned char*)c->scratch;
+  if ((size_t)flag_bytes > c->rflags_bytes) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "reflux flags resize");
+    if (c->rflags) cudaFree(c->rflags);
+    c->rflags = nullptr;
+    c->rflags_bytes = 0;
+    e = cudaMalloc(&c->rflags, (size_t)flag_bytes);
+    if (e != cudaSuccess) return fail(c, MHD_ENOMEM, "reflux flags of %lld bytes: %s", (long long)flag_bytes,
+                                      cudaGetErrorString(e));
+    e = cudaMemset(c->rflags, 0, (size_t)flag_bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "reflux flags clear");
+    c->rflags_bytes = (size_t)flag_bytes;
+  }
+  unsigned char* flags = (unsigned char*)c->rflags;
   for (int p = 0; p < nc; ++p) {
     if (!corr[p]) continue;
     DCorr k;
@@ -1131,35 +1366,39 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
     k.count = 18 * dc[p].nelem;
     k.base = corr[p];
     k.flags = flags + flag_off[p];
+    corr_idx[p] = (int)cr.size();
     cr.push_back(k);
-    kc.push_back((int64_t)(dc[p].n[0] + 1) * (dc[p].n[1] + 1) * (dc[p].n[2] + 1));
   }
   std::vector<DDeposit> dd(nd);
   std::vector<int64_t> dcount(nd);
+  int64_t marks = 0;
   for (int t = 0; t < nd; ++t) {
     const mhd_deposit& m = deps[t];
     if (m.coarse < 0 || m.coarse >= nc || !corr[m.coarse] || (m.kind != 0 && m.kind != 1) || m.axis < 0 ||
-        m.axis > 2 || !m.fine || !m.coarse_reg)
-      return fail(c, MHD_EINVAL, "deposit %d: bad coarse patch, kind, axis or register", t);
+        m.axis > 2 || !m.fine || !m.coarse_reg || (m.mode != MHD_REFLUX && m.mode != MHD_SYNC))
+      return fail(c, MHD_EINVAL, "deposit %d: bad coarse patch, kind, axis, mode or register", t);
     const DPatch& C = dc[m.coarse];
     DDeposit& o = dd[t];
     o.coarse = m.coarse;
     o.kind = m.kind;
     o.axis = m.axis;
-    o.pad = 0;
+    o.mode = m.mode;
     o.fine = m.fine;
     o.creg = m.coarse_reg;
     o.corr = corr[m.coarse];
     o.flags = (unsigned int*)(flags + flag_off[m.coarse]);
+    o.corr_idx = corr_idx[m.coarse];
+    o.pad2 = 0;
     int64_t cnt = 1;
     for (int a = 0; a < 3; ++a) {
       const int lo = m.box.lo[a], hi = m.box.hi[a];
       // the elements (face / edge index up to hi + 1) inside the coarse arrays
       if (hi < lo || lo - C.glo[a] < 0 || hi - C.glo[a] > C.N[a] - 1)
         return fail(c, MHD_EINVAL, "deposit %d: box outside the coarse arrays", t);
-      // the fine elements read: 2 lo .. 2 hi + (1 along the sub-face / segment axes)
+      // the fine elements read: 2 lo .. 2 hi + (1 along the sub-face / segment
+      // axes) when refluxing; lo .. hi of the other patch when synchronising
       const bool sub = (m.kind == 0) ? (a != m.axis) : (a == m.axis);
-      const int f0 = 2 * lo, f1 = 2 * hi + (sub ? 1 : 0);
+      const int f0 = m.mode == MHD_SYNC ? lo : 2 * lo, f1 = m.mode == MHD_SYNC ? hi : 2 * hi + (sub ? 1 : 0);
       if (f0 < m.fine_box.lo[a] || f1 > m.fine_box.hi[a])
         return fail(c, MHD_EINVAL, "deposit %d: fine register box does not hold the fine elements", t);
       o.lo[a] = lo;
@@ -1169,22 +1408,131 @@ mhd_status mhd_reflux(mhd_ctx* c, const mhd_patch_desc* coarse, int32_t nc, doub
       cnt *= o.ext[a];
     }
     dcount[t] = cnt;
+    // elements one deposit element can flag: 2 for a face, 4 for an edge
+    marks += cnt * (m.kind == 0 ? 2 : 4);
   }
-  std::vector<BlockTask> td, tk;
+  std::vector<BlockTask> td;
   tasks_for(dcount, td);
-  tasks_for(kc, tk);
-  void *d_c = nullptr, *d_r = nullptr, *d_d = nullptr, *d_td = nullptr, *d_tk = nullptr;
+  // the list of flagged elements (and its count) in the arena
+  if ((r = ensure_scratch(c, (size_t)(marks + 1) * 8))) return r;
+  RefluxList L;
+  L.count = (unsigned long long*)c->scratch;
+  L.entries = L.count + 1;
+  L.capacity = (unsigned long long)marks;
+  void *d_c = nullptr, *d_r = nullptr, *d_d = nullptr, *d_td = nullptr;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DPatch), &d_c))) return r;
   if ((r = table(c, cr.data(), cr.size() * sizeof(DCorr), &d_r))) return r;
   if ((r = table(c, dd.data(), dd.size() * sizeof(DDeposit), &d_d))) return r;
   if ((r = table(c, td.data(), td.size() * sizeof(BlockTask), &d_td))) return r;
-  if ((r = table(c, tk.data(), tk.size() * sizeof(BlockTask), &d_tk))) return r;
-  cudaError_t e = reflux_launch(dtype, (const DPatch*)d_c, (const DCorr*)d_r, flags, (size_t)flag_bytes,
-                                (const DDeposit*)d_d, (const BlockTask*)d_td, (int)td.size(), (const BlockTask*)d_tk,
-                                (int)tk.size(), timer_of(c), (cudaStream_t)stream);
+  cudaError_t e = reflux_launch(dtype, (const DPatch*)d_c, (const DCorr*)d_r, L, (const DDeposit*)d_d,
+                                (const BlockTask*)d_td, (int)td.size(), timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reflux launch");
   if (nd > 0) c->launches += 3;
   return MHD_OK;
+}
+
+
+// ---------------------------------------------------------------- flux registers
+}  // extern "C"
+
+struct mhd_fluxreg {
+  int device = 0;
+  double* base = nullptr;
+  size_t count = 0;
+  struct Item {
+    int64_t off;
+    mhd_box box;
+  };
+  std::vector<Item> faces;  // patch * 6 + 2 * axis + side
+  std::vector<Item> edges;  // patch * 12 + 2 * (2 * face axis + side) + (edge axis == face axis + 1 (mod 3) ? 0 : 1)
+};
+
+extern "C" {
+
+mhd_status mhd_fluxreg_create(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, mhd_fluxreg** out) {
+  if (!out) return MHD_EINVAL;
+  *out = nullptr;
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 1 || !patches) return fail(c, MHD_EINVAL, "fluxreg: bad arguments");
+  std::unique_ptr<mhd_fluxreg> g(new mhd_fluxreg);
+  g->device = c->device;
+  int64_t off = 0;
+  for (int p = 0; p < n; ++p) {
+    const mhd_box& in = patches[p].interior;
+    int64_t len[3];
+    for (int a = 0; a < 3; ++a) {
+      len[a] = (int64_t)in.hi[a] - in.lo[a] + 1;
+      if (len[a] < 1) return fail(c, MHD_EINVAL, "fluxreg: patch %d has an empty interior", p);
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side) {
+        mhd_fluxreg::Item it;
+        it.box = in;
+        it.box.lo[d] = it.box.hi[d] = side ? in.hi[d] + 1 : in.lo[d];
+        it.off = off;
+        g->faces.push_back(it);
+        off += 5 * (len[0] * len[1] * len[2] / len[d]);
+      }
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side)
+        for (int k = 0; k < 2; ++k) {
+          const int a = (d + 1 + k) % 3, t = (d + 2 - k) % 3;  // edge axis, remaining transverse axis
+          mhd_fluxreg::Item it;
+          it.box = in;
+          it.box.lo[d] = it.box.hi[d] = side ? in.hi[d] + 1 : in.lo[d];
+          it.box.hi[t] = in.hi[t] + 1;
+          it.off = off;
+          g->edges.push_back(it);
+          off += len[a] * (len[t] + 1);
+        }
+  }
+  g->count = (size_t)off;
+  cudaError_t e = cudaMalloc(&g->base, g->count * sizeof(double));
+  if (e != cudaSuccess) return fail(c, MHD_ENOMEM, "fluxreg: %zu doubles: %s", g->count, cudaGetErrorString(e));
+  e = cudaMemset(g->base, 0, g->count * sizeof(double));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(g->base);
+    return cuda_fail(c, e, "fluxreg: zero");
+  }
+  *out = g.release();
+  return MHD_OK;
+}
+
+void mhd_fluxreg_destroy(mhd_fluxreg* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  cudaDeviceSynchronize();
+  if (g->base) cudaFree(g->base);
+  delete g;
+}
+
+double* mhd_fluxreg_face(const mhd_fluxreg* g, int32_t patch, int32_t axis, int32_t side, mhd_box* box) {
+  if (!g || patch < 0 || axis < 0 || axis > 2 || side < 0 || side > 1) return nullptr;
+  const size_t k = (size_t)patch * 6 + 2 * axis + side;
+  if (k >= g->faces.size()) return nullptr;
+  if (box) *box = g->faces[k].box;
+  return g->base + g->faces[k].off;
+}
+
+double* mhd_fluxreg_edge(const mhd_fluxreg* g, int32_t patch, int32_t face_axis, int32_t side, int32_t edge_axis,
+                         mhd_box* box) {
+  if (!g || patch < 0 || face_axis < 0 || face_axis > 2 || side < 0 || side > 1 || edge_axis < 0 ||
+      edge_axis > 2 || edge_axis == face_axis)
+    return nullptr;
+  const int k = edge_axis == (face_axis + 1) % 3 ? 0 : 1;
+  const size_t i = (size_t)patch * 12 + 2 * (2 * face_axis + side) + k;
+  if (i >= g->edges.size()) return nullptr;
+  if (box) *box = g->edges[i].box;
+  return g->base + g->edges[i].off;
+}
+
+mhd_status mhd_fluxreg_zero(mhd_fluxreg* g, void* stream) {
+  if (!g) return MHD_EINVAL;
+  if (cudaSetDevice(g->device) != cudaSuccess) return MHD_ECUDA;
+  return cudaMemsetAsync(g->base, 0, g->count * sizeof(double), (cudaStream_t)stream) == cudaSuccess ? MHD_OK
+                                                                                                       : MHD_ECUDA;
 }
 
 }  // extern "C"

@@ -68,6 +68,8 @@ __device__ __forceinline__ void fused_prim(const DPatch& p, R* sm, int X0, int Y
     u[7] = R(0.5) * (((const R*)p.B[2])[x] + ((const R*)p.B[2])[x + p.s2]);
     R w[8];
     cons2prim(u, sc.gm1, w);
+    if (sc.rho_floor > R(0) && !(w[0] >= sc.rho_floor)) w[0] = sc.rho_floor;
+    if (sc.p_floor > R(0) && !(w[4] >= sc.p_floor)) w[4] = sc.p_floor;
     const int s = ly * L::P2 + lx;
 #pragma unroll
     for (int q = 0; q < 8; ++q) W[q * L::G2 + s] = w[q];

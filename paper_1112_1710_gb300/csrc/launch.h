@@ -38,6 +38,10 @@ struct AdvanceArgs {
   // device double (the same one as d_dt) before the step constants read it
   unsigned long long* cfl_out;
   double cfl;
+  // pressure floor after the update (0: none) and the device count of the
+  // cells it raised
+  double p_floor, rho_floor;
+  unsigned long long* d_floors;
 };
 
 // Compiled shapes of the fused advance: x-y tile and threads per CTA (one CTA
@@ -71,6 +75,10 @@ inline int staged_launches(size_t elem) { return elem == 8 ? 7 : 5; }
 cudaError_t advance_f64(const AdvanceArgs& a, cudaStream_t s);
 cudaError_t advance_f64c(const AdvanceArgs& a, cudaStream_t s);
 cudaError_t advance_f32(const AdvanceArgs& a, cudaStream_t s);
+// The floors of AdvanceArgs (p_floor, rho_floor, d_floors) over the cells of
+// each patch's interior (tasksu over [lo, hi + 1] with k = 0).
+cudaError_t floor_f64(const AdvanceArgs& a, cudaStream_t s);
+cudaError_t floor_f32(const AdvanceArgs& a, cudaStream_t s);
 
 // CFL candidate minimum over the interiors (tasks span interiors).
 cudaError_t cfl_dt_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks,
@@ -85,5 +93,10 @@ cudaError_t ghost_fill_launch(int dtype, const DPatch* patches, const DCopy* cop
 // Conservation sums (tasks span interiors); partials holds nblocks*8 doubles.
 cudaError_t sums_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks,
                         double* partials, double* d_out8, const KernelTimer* tm, cudaStream_t s);
+
+// Regridding's error flags of the interiors (tasks span interiors; flags of
+// patch p start at off[p]).
+cudaError_t flag_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks, const int64_t* off,
+                        double gamma, double theta, uint8_t* flags, cudaStream_t s);
 
 }  // namespace mhd

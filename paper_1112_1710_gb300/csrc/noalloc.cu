@@ -19,6 +19,7 @@
 // blocks it launches and reads only those, so nothing has to start at zero;
 // two calls that overlap on the GPU (different streams, no ordering between
 // them) race on the array and may return wrong sums.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,10 +48,14 @@ struct StaticSumArgs {
 };
 
 // Host-side address of g_partials, looked up once per device with that device
-// current (in host code the symbol itself is only a stand-in).
+// current (in host code the symbol itself is only a stand-in), together with
+// the CUDA context it belongs to: after cudaDeviceReset (or any other end of
+// the device's primary context) the module is loaded again, possibly at
+// another address, so a change of the current context triggers a new lookup.
 std::mutex g_mu;
 bool g_ready[kMaxDevices] = {};
 double* g_addr[kMaxDevices] = {};
+CUcontext g_ctx[kMaxDevices] = {};
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_sums_static(StaticSumArgs a, double* partials) {
@@ -157,13 +162,32 @@ extern "C" mhd_status mhd_conservation_sums_static(const mhd_patch_desc* patches
   double* partials = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ready[dev]) {
+    // cuCtxGetCurrent through the runtime's driver entry points (the library
+    // does not link the driver library itself)
+    static CUresult (*ctx_current)(CUcontext*) = nullptr;
+    if (!ctx_current) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return MHD_ECUDA;
+      }
+      ctx_current = (CUresult(*)(CUcontext*))fn;
+    }
+    CUcontext cur = nullptr;
+    if (ctx_current(&cur) != CUDA_SUCCESS) return MHD_ECUDA;
+    if (!g_ready[dev] || cur == nullptr || cur != g_ctx[dev]) {
       void* ptr = nullptr;
+      // (with no context current yet, this lookup makes the device's primary
+      // context current; the context is read again afterwards)
       if (cudaGetSymbolAddress(&ptr, g_partials) != cudaSuccess || !ptr) {
         cudaGetLastError();
         return MHD_ECUDA;
       }
+      if (ctx_current(&cur) != CUDA_SUCCESS || cur == nullptr) return MHD_ECUDA;
       g_addr[dev] = (double*)ptr;
+      g_ctx[dev] = cur;
       g_ready[dev] = true;
     }
     partials = g_addr[dev];

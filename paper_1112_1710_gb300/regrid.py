@@ -61,3 +61,111 @@ def children(cluster_boxes, coarse_boxes, ratio: int = 2):
             if all(lo[d] <= hi[d] for d in range(len(lo))):
                 out.append((tuple(ratio * v for v in lo), tuple(ratio * v + ratio - 1 for v in hi)))
     return out
+
+
+def flag(ctx, patches, theta: float, stream=None):
+    """Error flags of the interiors of `patches` (Patch objects of one
+    dtype) on the device (``mhd_flag_cells``): a list of uint8 tensors, one
+    per patch, shaped (nz, ny, nx)."""
+    import torch
+    dev = patches[0].state.device
+    total = sum(p.cells for p in patches)
+    out = torch.empty(max(1, total), dtype=torch.uint8, device=dev)
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    capi.mhd_flag_cells(ctx, [p.desc() for p in patches], theta, out.data_ptr(), s)
+    res, o = [], 0
+    for p in patches:
+        nx, ny, nz = p.n
+        res.append(out[o:o + p.cells].view(nz, ny, nx))
+        o += p.cells
+    return res
+
+
+def _cbox(lo, hi):
+    return np.asarray(lo) // 2, (np.asarray(hi) + 1) // 2 - 1
+
+
+def transfer_items(new_boxes, old_boxes):
+    """Copies of the previous iteration's data into the new patches
+    (``mhd_transfer_copy`` items): per (new, old) pair the cells of the
+    intersection of the interiors and, per axis, the faces common to both
+    face sets."""
+    out = []
+    if not old_boxes:
+        return out
+    olo = np.array([b[0] for b in old_boxes], np.int64)
+    ohi = np.array([b[1] for b in old_boxes], np.int64)
+    for i, (nlo, nhi) in enumerate(new_boxes):
+        lo = np.maximum(olo, nlo)
+        hi = np.minimum(ohi, nhi)
+        for kind in (-1, 0, 1, 2):
+            h = hi.copy()
+            if kind >= 0:
+                h[:, kind] = np.minimum(ohi[:, kind], nhi[kind]) + 1
+            for j in np.nonzero(np.all(lo <= h, axis=1))[0]:
+                it = capi.mhd_transfer_item()
+                it.src, it.dst, it.kind = int(j), int(i), kind
+                it.box = capi.box(lo[j], h[j])
+                out.append(it)
+    return out
+
+
+def transfer_mask(new_box, old_boxes):
+    """The mask of ``mhd_prolong_new`` over the coarse footprint of a new
+    patch: bit 0 where the coarse cell's children lie in an old interior,
+    bit 1 + 2 a + s where its side-s axis-a face lies in an old face set.
+    Returns (uint8 array (z, y, x), coarse lo)."""
+    clo, chi = _cbox(*new_box)
+    ext = chi - clo + 1
+    I = [np.arange(clo[d], chi[d] + 1) for d in range(3)]
+    m = np.zeros((ext[2], ext[1], ext[0]), np.uint8)
+    for olo, ohi in old_boxes:
+        ol, oh = _cbox(olo, ohi)
+        inside = [(I[d] >= ol[d]) & (I[d] <= oh[d]) for d in range(3)]
+        cell = inside[2][:, None, None] & inside[1][None, :, None] & inside[0][None, None, :]
+        m |= cell.astype(np.uint8)
+        for a in range(3):
+            for s in (0, 1):
+                f = I[a] + s
+                ok = [inside[d] if d != a else (f >= ol[a]) & (f <= oh[a] + 1) for d in range(3)]
+                face = ok[2][:, None, None] & ok[1][None, :, None] & ok[0][None, None, :]
+                m |= (face.astype(np.uint8) << (1 + 2 * a + s)).astype(np.uint8)
+    return m, tuple(int(v) for v in clo)
+
+
+def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
+    """Fills the interiors of the new patches `fresh` (Patch objects of level
+    l+1) from the previous iteration `old` (Patch objects of level l+1) and
+    the level-l patches `coarse`: the copies first, then the prolongation of
+    the rest under each new patch's mask.  Returns the device count of energy
+    fallbacks (a one-element tensor)."""
+    import torch
+    dev = fresh[0].state.device
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    nb = [(p.lo, p.hi) for p in fresh]
+    ob = [(p.lo, p.hi) for p in old]
+    items = transfer_items(nb, ob)
+    if items:
+        capi.mhd_transfer_copy(ctx, [p.desc() for p in old], [p.desc() for p in fresh], items, s)
+    masks, pitems = [], []
+    clo_all = np.array([p.lo for p in coarse], np.int64)
+    chi_all = np.array([p.hi for p in coarse], np.int64)
+    for i, (lo, hi) in enumerate(nb):
+        m, mlo = transfer_mask((lo, hi), ob)
+        dm = torch.as_tensor(m, device=dev).contiguous()
+        masks.append(dm)
+        cl, ch = _cbox(lo, hi)
+        blo = np.maximum(clo_all, cl)
+        bhi = np.minimum(chi_all, ch)
+        for k in np.nonzero(np.all(blo <= bhi, axis=1))[0]:
+            it = capi.mhd_prolong_new_item()
+            it.coarse, it.fine = int(k), i
+            it.box = capi.box(blo[k], bhi[k])
+            it.mask = dm.data_ptr()
+            it.mask_box = capi.box(mlo, tuple(int(v) for v in ch))
+            pitems.append(it)
+    nfall = torch.zeros(1, dtype=torch.int64, device=dev)
+    capi.mhd_prolong_new(ctx, [p.desc() for p in coarse], [p.desc() for p in fresh], pitems, energy_mode,
+                         nfall.data_ptr(), s)
+    transfer._keep = masks          # the masks must live until the launch has run
+    return nfall

@@ -354,3 +354,235 @@ def latency_stats(reqs):
         by_lev.setdefault(r.level, []).append(r.done - r.arrival)
     out["p50_ms_by_level"] = {int(k): float(np.percentile(v, 50) * 1e3) for k, v in sorted(by_lev.items())}
     return out
+
+
+# ---------------------------------------------------------------------------
+# Serving the level steps of a resident AMR hierarchy.
+#
+# A hierarchy held on the device (amr.Hierarchy) is advanced by requests: one
+# request per operation of a level step of the paper's life cycle (Sec. 2.2;
+# extended ghost zones, Sec. 2.3), each a captured CUDA graph of one batched
+# launch sequence over all patches of its level:
+#   start      CFL dt of every level (device scalar) and the level-0 ghost fill
+#   PF(l)      prolongation of level l (pre-advance) into level l+1's ghosts,
+#              then level l+1's same-level copies
+#   A(l,k)     advance of level l (update box grown by k) with its flux-register
+#              captures
+#   S(l)       same-level copies of level l between its two substeps
+#   RR(l)      refluxing of level l from the registers, restriction of l+1
+#              (and the floors on level l, when the hierarchy has them)
+# The requests of a coarse step form a dependency graph (a request is issued
+# once the requests it reads from are issued; the GPU orders them through
+# events).  Among the issuable requests the finer level goes first, as in the
+# paper's scheduler (Sec. 4).  The advance of a level that has children runs
+# on a slot of its own (stream and library context, so scratch arenas do not
+# collide) while the finer levels' requests proceed on the main slot, which
+# is created with the higher stream priority.  Every request is bracketed by
+# CUDA events, from which its latency (issuable-on-device to done) and the
+# per-level p50/p99 follow after the run.
+# ---------------------------------------------------------------------------
+@dataclass
+class LevelRequest:
+    tid: int
+    kind: str               # "start", "PF", "A", "S", "RR"
+    level: int
+    k: int = 0
+    first: bool = True
+    deps: tuple = ()
+    step: int = 0           # coarse step
+    slot: int = 0
+
+
+def level_requests(nlev: int, nsteps: int):
+    """The requests of `nsteps` coarse steps of an nlev-level hierarchy with
+    their dependencies, in the order the recursive step would issue them."""
+    out = []
+
+    def add(kind, level, deps, step, k=0, first=True):
+        out.append(LevelRequest(len(out), kind, level, k, first, tuple(deps), step))
+        return len(out) - 1
+
+    def level_step(l, k, first, deps, step):
+        if l + 1 >= nlev:
+            return add("A", l, deps, step, k, first)
+        pf = add("PF", l, deps, step)
+        a = add("A", l, [pf], step, k, first)
+        c1 = level_step(l + 1, 2, True, [pf], step)
+        s = add("S", l + 1, [c1], step)
+        c2 = level_step(l + 1, 0, False, [s], step)
+        return add("RR", l, [a, c2], step)
+
+    last = None
+    for c in range(nsteps):
+        st = add("start", 0, [] if last is None else [last], c)
+        last = level_step(0, 0, True, [st], c)
+    return out
+
+
+class AmrLevelServer:
+    """Serves the level-step requests of one resident hierarchy (see above).
+
+    budget_bytes: the hierarchy is admitted only if its resident device memory
+    (states, flux registers and correction planes, scratch arenas measured
+    over a warm-up coarse step) fits; otherwise the constructor raises."""
+
+    def __init__(self, h, budget_bytes=64 << 30):
+        import torch
+        self.torch = torch
+        self.h = h
+        dev = h.device
+        free0, _ = torch.cuda.mem_get_info(dev)
+        h.coarse_step()                      # sizes every arena, uploads every table
+        torch.cuda.synchronize(dev)
+        free1, _ = torch.cuda.mem_get_info(dev)
+        tensors = sum(p.state.numel() * p.state.element_size() for pats in h.levels for p in pats)
+        tensors += h.regbuf.numel() * 8 + sum(t.numel() * 8 for t in getattr(h, "_corr_keep", []))
+        self.resident_bytes = tensors + max(0, free0 - free1)
+        if self.resident_bytes > budget_bytes:
+            raise MemoryError("hierarchy needs %.1f GB, budget %.1f GB" % (self.resident_bytes / 2 ** 30,
+                                                                           budget_bytes / 2 ** 30))
+        # slots: 0 = the main stream and context; 1 + l = the side slot of level l
+        self.slots = [(h.ctx, h.stream)] + [(c, s) for c, s in h.side]
+        self.graphs = {}
+        self._capture()
+
+    def _slot_of(self, r: LevelRequest) -> int:
+        if r.kind == "A" and self.h.concurrent and r.level + 1 < self.h.nlev:
+            return 1 + r.level
+        return 0
+
+    def _body(self, key):
+        h = self.h
+        kind = key[0]
+        if kind == "start":
+            h.cfl()
+            h.fill(0)
+        elif kind == "PF":
+            h.prolong(key[1])
+            h.fill(key[1] + 1)
+        elif kind == "S":
+            h.fill(key[1])
+        elif kind == "RR":
+            h.reflux(key[1])
+            h.restrict(key[1])
+            if h.floors:
+                h.floor(key[1])
+        else:
+            _, l, k, first, slot = key
+            ctx, st = self.slots[slot]
+            h.advance(l, k, first, ctx=ctx, stream=st)
+
+    def _key(self, r: LevelRequest):
+        if r.kind == "A":
+            return ("A", r.level, r.k, r.first, self._slot_of(r))
+        return (r.kind, r.level)
+
+    def _capture(self):
+        """One CUDA graph per distinct request (kind, level, substep), each
+        captured on the stream of the slot that will replay it."""
+        torch = self.torch
+        from . import capi
+        keys = {}
+        for r in level_requests(self.h.nlev, 1):
+            keys[self._key(r)] = self._slot_of(r)
+        for key, slot in keys.items():
+            st = self.slots[slot][1]
+            n0 = sum(capi.mhd_launch_count(c) for c, _ in self.slots)
+            # a request with nothing to launch (a level without same-level
+            # neighbours has no copies) keeps no graph
+            if not self._launches(key):
+                self.graphs[key] = None
+                continue
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                self._body(key)
+            assert sum(capi.mhd_launch_count(c) for c, _ in self.slots) > n0
+            self.graphs[key] = g
+        torch.cuda.synchronize(self.h.device)
+
+    def _launches(self, key) -> bool:
+        """Whether the request's body enqueues any kernel."""
+        h = self.h
+        kind = key[0]
+        if kind == "S":
+            return bool(h._copy_arr[key[1]][1])
+        if kind == "PF":
+            return bool(h._prolong_arr[key[1]][1]) or bool(h._copy_arr[key[1] + 1][1])
+        return True
+
+    def run(self, nsteps: int, timing: bool = True):
+        """Serves `nsteps` coarse steps; returns per-request timing records and
+        latency statistics (device clock)."""
+        torch = self.torch
+        reqs = level_requests(self.h.nlev, nsteps)
+        for r in reqs:
+            r.slot = self._slot_of(r)
+        n = len(reqs)
+        ndeps = [len(r.deps) for r in reqs]
+        users = [[] for _ in range(n)]
+        for r in reqs:
+            for d in r.deps:
+                users[d].append(r.tid)
+        ready = []                            # heap: finer level first, then issue order
+        for r in reqs:
+            if not r.deps:
+                heapq.heappush(ready, (-r.level, r.tid))
+        ev_end = [None] * n
+        ev_start = [None] * n
+        base = torch.cuda.Event(enable_timing=True)
+        base.record(self.slots[0][1])
+        for _, st in self.slots[1:]:
+            st.wait_event(base)
+        issued = 0
+        while ready:
+            _, tid = heapq.heappop(ready)
+            r = reqs[tid]
+            st = self.slots[r.slot][1]
+            for d in r.deps:
+                if reqs[d].slot != r.slot:
+                    st.wait_event(ev_end[d])
+            if timing:
+                ev_start[tid] = torch.cuda.Event(enable_timing=True)
+                ev_start[tid].record(st)
+            g = self.graphs[self._key(r)]
+            if g is not None:
+                with torch.cuda.stream(st):
+                    g.replay()
+            ev_end[tid] = torch.cuda.Event(enable_timing=timing)
+            ev_end[tid].record(st)
+            issued += 1
+            for u in users[tid]:
+                ndeps[u] -= 1
+                if ndeps[u] == 0:
+                    heapq.heappush(ready, (-reqs[u].level, u))
+        if issued != n:
+            raise RuntimeError("level-request graph has a cycle")
+        main = self.slots[0][1]
+        for _, st in self.slots[1:]:
+            j = torch.cuda.Event()
+            j.record(st)
+            main.wait_event(j)
+        fin = torch.cuda.Event(enable_timing=True)
+        fin.record(main)
+        fin.synchronize()
+        total_ms = base.elapsed_time(fin)
+        out = {"requests": n, "coarse_steps": nsteps, "ms": total_ms}
+        if not timing:
+            return out
+        t0 = [base.elapsed_time(e) for e in ev_start]
+        t1 = [base.elapsed_time(e) for e in ev_end]
+        lat = []
+        per_level = {}
+        for r in reqs:
+            ready_at = max([t1[d] for d in r.deps], default=0.0)
+            ready_at = min(ready_at, t0[r.tid])
+            v = t1[r.tid] - ready_at
+            lat.append(v)
+            per_level.setdefault(r.level, []).append(v)
+        lat = np.array(lat)
+        out.update({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "max_ms": float(lat.max()),
+                    "by_level": {int(l): {"requests": len(v), "p50_ms": float(np.percentile(v, 50)),
+                                          "p99_ms": float(np.percentile(v, 99))}
+                                 for l, v in sorted(per_level.items())}})
+        return out

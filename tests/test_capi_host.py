@@ -32,7 +32,11 @@ def test_binding_struct_layouts_match_header():
     # mhd_patch_desc: 4 int32 + box (6 int32) + 8 pointers + 3 int64 + 3 double
     assert ctypes.sizeof(capi.mhd_box) == 24
     assert ctypes.sizeof(capi.mhd_patch_desc) == 16 + 24 + 64 + 24 + 24
-    assert ctypes.sizeof(capi.mhd_params) == 48
+    # mhd_params: 2 double + 2 int32 + double + 4 int32 + 2 double (floors)
+    assert ctypes.sizeof(capi.mhd_params) == 64
+    assert ctypes.sizeof(capi.mhd_deposit) == 16 + 48 + 16
+    assert ctypes.sizeof(capi.mhd_transfer_item) == 16 + 24
+    assert ctypes.sizeof(capi.mhd_prolong_new_item) == 8 + 24 + 8 + 24
     assert ctypes.sizeof(capi.mhd_copy) == 8 + 24 + 12
     assert ctypes.sizeof(capi.mhd_level_item) == ctypes.sizeof(capi.mhd_prolong_item) == 8 + 24
 

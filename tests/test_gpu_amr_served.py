@@ -1,0 +1,218 @@
+"""The served level-step path of an AMR hierarchy (serve.AmrLevelServer) and
+the FP32 error of the hierarchies against the FP64 oracle.
+
+* The served path (each level-step operation a request issued finer level
+  first, replayed from a captured graph, the advance of a level with children
+  on its own slot) gives the eager batched path's bits.
+* FP32 AMR (downscaled blast-shell hierarchy) and FP32 deep AMR (downscaled
+  k^-4 Mach-5 hierarchy, through the served path) are compared with the FP64
+  oracle after three coarse steps on the same dt sequence: the per-variable
+  L1 and L-infinity relative errors are printed and held to stated bounds
+  (FP32 rounding accumulated over the subcycled steps, refluxing included)."""
+import numpy as np
+import pytest
+import torch
+
+import synth.amr as SA
+
+pytestmark = pytest.mark.gpu
+G = 4
+NAMES = ("rho", "Mx", "My", "Mz", "E", "Bx", "By", "Bz")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1112_1710_gb300 import _build, capi as C
+    _build.build()
+    C.load()
+    return C
+
+
+def _shell(n0=16, levels=3):
+    H = SA.shell_hierarchy(n0=n0, levels=levels, size_min=4, size_max=8)
+    st = [[SA.blast_patch(lo, hi, l, n0, G, p_in=10.0)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    return H, st
+
+
+def test_served_level_steps_equal_eager_batched(capi):
+    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300.serve import AmrLevelServer
+    n0 = 16
+    H, st = _shell(n0)
+    ctx, ctx2 = capi.mhd_ctx_create(emf=1), capi.mhd_ctx_create(emf=1)
+    a = b = None
+    try:
+        a = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx, concurrent=True)
+        b = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx2,
+                      stream=torch.cuda.Stream(priority=-1), concurrent=True)
+        a.initialise()
+        b.initialise()
+        srv = AmrLevelServer(b)        # runs one eager coarse step, then captures
+        a.coarse_step()
+        out = srv.run(3)
+        for _ in range(3):
+            a.coarse_step()
+        torch.cuda.synchronize()
+        assert out["requests"] == 3 * 17 and out["p99_ms"] >= out["p50_ms"] > 0
+        assert sorted(out["by_level"]) == [0, 1, 2]
+        assert a.device_status() == 0 and b.device_status() == 0
+        for l in range(3):
+            for pa, pb in zip(a.levels[l], b.levels[l]):
+                assert np.array_equal(pa.state.cpu().numpy(), pb.state.cpu().numpy()), l
+        del srv
+    finally:
+        for h in (a, b):
+            if h is not None:
+                h.close()
+        capi.mhd_ctx_destroy(ctx)
+        capi.mhd_ctx_destroy(ctx2)
+
+
+def _error_table(oh, ph):
+    """Per-variable relative errors over every patch of every level (interior
+    cells and faces): L-inf = max |diff| / max |oracle|, L1 = sum |diff| /
+    sum |oracle|."""
+    dmax, bmax, dsum, bsum = (np.zeros(8) for _ in range(4))
+    for l in range(len(oh.levels)):
+        for P, Q in zip(oh.levels[l], ph.levels[l]):
+            got = Q.state.cpu().numpy().astype(np.float64)
+            n = P.n
+            for q in range(8):
+                ext = list(n)
+                if q >= 5:
+                    ext[q - 5] += 1
+                a = got[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                b = P.state[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                d = np.abs(a - b)
+                dmax[q] = max(dmax[q], d.max())
+                bmax[q] = max(bmax[q], np.abs(b).max())
+                dsum[q] += d.sum()
+                bsum[q] += np.abs(b).sum()
+    return dmax / np.maximum(bmax, 1e-300), dsum / np.maximum(bsum, 1e-300)
+
+
+def _print_table(capsys, title, linf, l1):
+    with capsys.disabled():
+        print("\n%s (%s)" % (title, " ".join(NAMES)))
+        print("  Linf rel : " + " ".join("%.2e" % v for v in linf))
+        print("  L1   rel : " + " ".join("%.2e" % v for v in l1))
+
+
+# Bounds: FP32 rounding (6e-8 per operation) accumulated over three coarse
+# steps of subcycled levels, refluxing and prolongation included, with a
+# factor of about 20 over the measured values (L-inf 2-4e-7, L1 2e-8-3e-7 on
+# GB300), which the test prints.
+AMR_LINF, AMR_L1 = 1e-5, 1e-6
+
+
+def test_fp32_amr_error_vs_oracle(capi, orc, capsys):
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H, st = _shell(n0)
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
+        oh.initialise()
+        ph.initialise()
+        for _ in range(3):
+            dt = oh.coarse_step()
+            ph.coarse_step(dt=dt)
+        torch.cuda.synchronize()
+        assert ph.device_status() == 0
+        linf, l1 = _error_table(oh, ph)
+        _print_table(capsys, "FP32 AMR (blast shell, base 16^3 + 2 levels) vs FP64 oracle, 3 coarse steps", linf, l1)
+        assert np.all(linf <= AMR_LINF) and np.all(l1 <= AMR_L1), (linf, l1)
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)
+
+
+DEEP_LINF, DEEP_L1 = 1e-5, 1e-6   # measured: L-inf 3-6e-7, L1 7e-8-2e-7
+
+
+def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys):
+    """The deep-AMR generator downscaled (base 16^3, 3 levels, k^-4 Mach-5
+    field, beta 1), FP32 through the served level-step path, against the
+    FP64 oracle (the served path takes its own FP32 CFL dt; the oracle is run
+    on the same dt sequence, read back from the device)."""
+    import synth.turb as ST
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300.serve import AmrLevelServer
+    n0 = 16
+    H, v, _ = ST.deep_hierarchy(n0=n0, levels=3, m=32, size_min=4, size_max=8)
+    st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx,
+                       stream=torch.cuda.Stream(priority=-1), concurrent=True)
+        oh.initialise()
+        ph.initialise()
+        srv = AmrLevelServer(ph)        # its warm-up runs one eager coarse step
+        torch.cuda.synchronize()
+        oh.coarse_step(dt=ph.d_dt.item())
+        for _ in range(2):
+            srv.run(1, timing=False)
+            torch.cuda.synchronize()
+            oh.coarse_step(dt=ph.d_dt.item())
+        assert ph.device_status() == 0
+        linf, l1 = _error_table(oh, ph)
+        _print_table(capsys, "FP32 deep AMR (k^-4 Mach 5, base 16^3 + 2 levels, served path) vs FP64 oracle, "
+                             "3 coarse steps", linf, l1)
+        assert np.all(linf <= DEEP_LINF) and np.all(l1 <= DEEP_L1), (linf, l1)
+        del srv
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)
+
+
+def test_deep_amr_floors_fp64_parity(capi, orc, capsys):
+    """The deep-AMR generator downscaled (base 16^3, 4 levels, k^-4 Mach-5
+    field), where the method without floors reaches a non-positive pressure
+    after 6 coarse steps: with the floors (reading R33; after every update and
+    after every refluxing) 10 coarse steps of the FP64 parity build through
+    the served path equal the oracle's on every patch, and the floors fired."""
+    import synth.turb as ST
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    from paper_1112_1710_gb300.serve import AmrLevelServer
+    n0 = 16
+    H, v, _ = ST.deep_hierarchy(n0=n0, levels=4, m=64, size_min=4, size_max=8)
+    st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    fl = dict(p_floor=6e-4, rho_floor=1e-3)
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G,
+                    prm=orc.params(emf=1, **fl))
+    ctx = capi.mhd_ctx_create(emf=1, **fl)
+    ph = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx,
+                       stream=torch.cuda.Stream(priority=-1), concurrent=True, floors=True)
+        oh.initialise()
+        ph.initialise()
+        srv = AmrLevelServer(ph)        # one eager coarse step
+        torch.cuda.synchronize()
+        assert oh.coarse_step() == ph.d_dt.item()
+        for _ in range(9):
+            srv.run(1, timing=False)
+            torch.cuda.synchronize()
+            assert oh.coarse_step() == ph.d_dt.item()
+        nfl = sum(capi.mhd_floor_count(c) for c in [ph.ctx] + [c for c, _ in ph.side])
+        assert ph.device_status() == 0
+        assert nfl > 0
+        linf, l1 = _error_table(oh, ph)
+        with capsys.disabled():
+            print("\nFP64 deep AMR with floors, 10 coarse steps: %d cells floored; max rel Linf vs oracle %.2e"
+                  % (nfl, linf.max()))
+        assert np.all(linf <= 1e-11), linf
+        del srv
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)

@@ -542,3 +542,53 @@ def test_field_loop_gs05_fp64_and_fp32(capi, orc, normal):
         d = np.abs(got32[5 + a, g:g + ext[2], g:g + ext[1], g:g + ext[0]] -
                    want[5 + a, g:g + ext[2], g:g + ext[1], g:g + ext[0]]).max()
         assert d <= 1e-4 * 1e-3, (a, d)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_pressure_floor_equals_oracle(capi, orc, kernel):
+    """The optional pressure floor (mhd_params.p_floor) after the staged (1)
+    and the fused (2) advance: FP64 equals the oracle bit for bit and raises
+    the same number of cells (mhd_floor_count)."""
+    pr = synth.blast(12, noise=0.01, seed=4)
+    n, g = pr.n, pr.g
+    st = pr.state.copy()
+    P = orc.patch(st, n, g, pr.dx)
+    orc.fill_periodic(P)
+    dt = orc.cfl_dt(P, orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1, p_floor=0.099, advance_kernel=kernel)
+    try:
+        p = to_patch(st, n, g, pr.dx)
+        d = torch.full((1,), dt, dtype=torch.float64, device="cuda")
+        capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr())
+        nfl = capi.mhd_floor_count(ctx)
+        assert capi.mhd_floor_count(ctx) == 0          # the count resets
+        got = p.state.cpu().numpy()
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    assert orc.advance(P, orc.params(emf=1, p_floor=0.099), dt, 0) == 0
+    assert nfl == orc.floor_count() > 0
+    err = rel_linf(got, st, n, g)
+    assert np.all(err <= TOL), err
+
+
+def test_level_floor_equals_oracle(capi, orc):
+    """mhd_floor (the floors over whole interiors, used after refluxing)
+    equals orc_floor bit for bit in FP64, cell count included."""
+    pr = synth.blast(12, noise=0.01, seed=5)
+    n, g = pr.n, pr.g
+    st = pr.state.copy()
+    P = orc.patch(st, n, g, pr.dx)
+    orc.fill_periodic(P)
+    st[0, g + 1, g + 2, g + 3] = 1e-6
+    ctx = capi.mhd_ctx_create(p_floor=0.2, rho_floor=1e-3)
+    try:
+        p = to_patch(st, n, g, pr.dx)
+        capi.mhd_floor(ctx, [p.desc()])
+        nch = capi.mhd_floor_count(ctx)
+        got = p.state.cpu().numpy()
+    finally:
+        capi.mhd_ctx_destroy(ctx)
+    want_n = orc.floor(P, orc.params(p_floor=0.2, rho_floor=1e-3))
+    assert nch == want_n > 1
+    assert np.array_equal(got[:, :n[2] + 2 * g + 1, :n[1] + 2 * g + 1, :n[0] + 2 * g + 1],
+                          st[:, :n[2] + 2 * g + 1, :n[1] + 2 * g + 1, :n[0] + 2 * g + 1])

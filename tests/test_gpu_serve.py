@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import synth
-from gpu_util import rel_linf
+from gpu_util import rel_l1, rel_linf
 
 pytestmark = pytest.mark.gpu
 G = 4
@@ -84,5 +84,67 @@ def test_poisson_latency_report(templates):
         assert st["count"] == 200 and st["p99_ms"] >= st["p50_ms"] > 0
         assert st["cell_updates_per_s"] > 0
         assert sch.resident == 0
+    finally:
+        be.close()
+
+
+def test_served_contracted_fp64_and_fp32_error_vs_oracle(templates, orc, capsys):
+    """Served FP64 requests on the contracted build (fused multiply-adds,
+    reciprocal HLLD) are within 1e-11 of the oracle per variable; served FP32
+    requests report their per-variable error against the FP64 oracle (L1 and
+    L-infinity relative), bounded by 1e-5 (one step of FP32 rounding)."""
+    from paper_1112_1710_gb300.serve import GpuBackend, Request, Scheduler
+    be = GpuBackend(templates, n_slots=2, g=G, solver=dict(SOLVER, fp64_contract=1), keep=True)
+    try:
+        reqs = [Request(0, 0.0, 24, 3, "f64"), Request(1, 0.0, 40, 5, "f64"), Request(2, 0.0, 32, 1, "f32"),
+                Request(3, 0.0, 40, 6, "f32")]
+        Scheduler(be, n_slots=2, g=G).run(reqs, t_limit=60.0)
+        torch.cuda.synchronize()
+        linf32 = np.zeros(8)
+        l1_32 = np.zeros(8)
+        for r in reqs:
+            pr = synth.blast(r.n, g=G, seed=4242 + r.n)
+            _, dt = templates[(r.n, "f64")]
+            P = orc.patch(pr.state, pr.n, G, pr.dx)
+            orc.fill_periodic(P)
+            assert orc.advance(P, orc.params(**SOLVER), dt, 0) == 0
+            got = r.result.cpu().numpy().astype(np.float64)
+            err = rel_linf(got, pr.state, pr.n, G)
+            if r.dtype == "f64":
+                assert err.max() <= 1e-11, err
+            else:
+                linf32 = np.maximum(linf32, err)
+                l1_32 = np.maximum(l1_32, rel_l1(got, pr.state, pr.n, G))
+        with capsys.disabled():
+            print("\nserved FP32 requests (32^3, 40^3 blast cubes, one step) vs FP64 oracle "
+                  "(rho Mx My Mz E Bx By Bz)")
+            print("  Linf rel : " + " ".join("%.2e" % v for v in linf32))
+            print("  L1   rel : " + " ".join("%.2e" % v for v in l1_32))
+        assert np.all(linf32 <= 1e-5) and np.all(l1_32 <= 1e-6), (linf32, l1_32)
+    finally:
+        be.close()
+
+
+def test_balanced_policy_mix_equals_alone(templates):
+    """The serving policy that sizes each slot's batch by the distribution
+    equation of Sec. 5 (balanced) on the GPU backend: every result equals
+    the same request run alone, and the batches' sizes follow the policy."""
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300.serve import GpuBackend, Scheduler
+    be = GpuBackend(templates, n_slots=3, g=G, solver=SOLVER, keep=True)
+    try:
+        sch = Scheduler(be, n_slots=3, max_batch_cells=200_000, min_batch_cells=4096, g=G, policy="balanced")
+        reqs = sch.run(_stream(60, math.inf, seed=21), t_limit=120.0)
+        torch.cuda.synchronize()
+        assert len(sch.batches) >= 3
+        for c in be.ctxs:
+            assert capi.mhd_get_device_status(c) == 0
+        by = {r.rid: r for r in reqs}
+        assert sum(len(rids) for _, rids in sch.batches) == 60
+        for _, rids in sch.batches:
+            # a batch exceeds its cell budget only when a single request does
+            assert len(rids) == 1 or sum(by[i].cells for i in rids) <= 200_000
+        for r in reqs:
+            assert torch.equal(r.result, be.alone(r)), (r.rid, r.n, r.dtype)
     finally:
         be.close()

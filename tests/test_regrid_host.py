@@ -89,3 +89,28 @@ def test_children_are_the_refined_flagged_parent_cells(R):
             got |= ck
             assert any(all(2 * g[0][d] <= k[0][d] and k[1][d] <= 2 * g[1][d] + 1 for d in range(nd)) for g in grids)
         assert got == want
+
+
+def test_transfer_items_and_masks_equal_oracle():
+    """The library's host lists of the data transfer into a new iteration
+    (copies of the previous iteration's cells and faces, and the
+    prolongation masks) equal the oracle's brute-force ones on random
+    coarse-aligned boxes."""
+    from oracle import transfer as OT
+    from paper_1112_1710_gb300 import regrid
+    rng = np.random.default_rng(9)
+
+    def box():
+        lo = 2 * rng.integers(0, 12, 3)
+        hi = lo + 2 * rng.integers(1, 6, 3) - 1
+        return tuple(int(v) for v in lo), tuple(int(v) for v in hi)
+
+    for _ in range(40):
+        old = [box() for _ in range(rng.integers(0, 4))]
+        new = box()
+        got = sorted((it.src, it.kind, tuple(it.box.lo), tuple(it.box.hi)) for it in regrid.transfer_items([new], old))
+        want = sorted((j, k, tuple(lo), tuple(hi)) for j, k, lo, hi in OT.copy_items(new, old))
+        assert got == want
+        m, mlo = regrid.transfer_mask(new, old)
+        om, omlo = OT.mask(new, old)
+        assert tuple(mlo) == tuple(omlo) and np.array_equal(m, om)
