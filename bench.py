@@ -236,6 +236,7 @@ def kernel_units(name, n):
         "k_ghost": (n + 4) ** 3 - n ** 3,
         "k_fused": n ** 3,
         "k_commit": n ** 3,
+        "k_pf": (n + 2) ** 3,
     }.get(name)
 
 
@@ -254,11 +255,14 @@ def stage_flops(name, n):
 
 def kernel_flops(name, n, launched=()):
     """Algorithmic flops of one launch.  The fused kernel does the work of all
-    six stages (its halo recomputation is not algorithmic work); where k_edge
+    six stages (its halo recomputation is not algorithmic work), the fused
+    pass that of the primitive, predictor, edge-average and flux stages; where k_edge
     and k_emf were not launched (FP32), k_flux computes the edge averages of
     E^n and k_update the edge EMFs."""
     if name == "k_fused":
         return sum(stage_flops(k, n) for k in STAGES)
+    if name == "k_pf":
+        return sum(stage_flops(k, n) for k in ("k_prim", "k_pred", "k_edge", "k_flux"))
     f = stage_flops(name, n)
     if name == "k_flux" and "k_edge" not in launched:
         f += stage_flops("k_edge", n)
@@ -273,6 +277,22 @@ def kernel_flops(name, n, launched=()):
 KERNEL_TRAFFIC = {("f32", "k_pred"): 471.1e6, ("f32", "k_flux"): 685.6e6, ("f32", "k_update"): 342.7e6,
                   ("f64", "k_pred"): 969.3e6, ("f64", "k_flux"): 1395.4e6,
                   ("f64_exact", "k_pred"): 969.2e6, ("f64_exact", "k_flux"): 1398.0e6}
+
+
+def choice_label(v):
+    """Name of an mhd_autotune_advance choice."""
+    if v <= -3:
+        return "fused pass (primitives, predictor, Riemann fluxes in one kernel), shape %d" % (-3 - v)
+    return {-2: "staged, untiled predictor", -1: "staged, tiled predictor"}.get(v, "fused kernel, shape %d" % v)
+
+
+def autotune_record(h):
+    """Lets the autotuner choose a hierarchy's advance (on its finest level's
+    batch) and returns the choice as a record."""
+    import torch
+    v, cz, ms = h.autotune()
+    torch.cuda.synchronize()
+    return {"choice": choice_label(v), "chunk": cz, "ms_per_advance_of_finest_level": ms}
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
@@ -290,15 +310,13 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         for _ in range(args.warmup):
             run.step()
         torch.cuda.synchronize()
-        # FP32: the advance (staged kernels or a fused shape) as picked by the
-        # autotuner on this patch; FP64 runs staged (its one fused shape, 8 x 8
-        # tiles for the parity tests, is about 3x slower)
+        # the advance (staged kernels, the fused pass or a fused shape) as
+        # picked by the autotuner on this patch
         tuned = None
-        if dtype == "f32" and not args.no_autotune:
+        if not args.no_autotune:
             v, cz, tms = capi.mhd_autotune_advance(ctx, run.descs, run.d_dt.data_ptr(), reps=3,
                                                    stream=stream.cuda_stream)
-            tuned = {"choice": {-2: "staged, untiled predictor", -1: "staged, tiled predictor"}.get(
-                v, "fused variant %d" % v), "chunk": cz, "ms_per_advance": tms}
+            tuned = {"choice": choice_label(v), "chunk": cz, "ms_per_advance": tms}
         status = capi.mhd_get_device_status(ctx)
         # headline: the step (fill, CFL dt, advance) replayed as one CUDA graph
         l0 = capi.mhd_launch_count(ctx)
@@ -586,10 +604,13 @@ def time_amr(H, states, dtype, steps, mode, local, concurrent=False):
     stream = torch.cuda.Stream(device=local, priority=-1)
     h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
                   device="cuda:%d" % local, concurrent=concurrent)
+    tuned = None
     try:
         h.initialise()
         if mode == "per_patch":
             h.batched = False
+        else:
+            tuned = autotune_record(h)
         if mode == "graph":
             h.capture_graph()
         else:
@@ -616,7 +637,7 @@ def time_amr(H, states, dtype, steps, mode, local, concurrent=False):
             "ms_per_coarse_step": ms / steps,
             "cell_updates_per_coarse_step": upd, "value": upd * steps / (ms * 1e-3),
             "library_launches_per_step": (launches / steps) if mode != "graph" else None,
-            "device_status": status}
+            "device_status": status, "autotune": tuned}
 
 
 def _box_vol(b):
@@ -728,6 +749,7 @@ def amr_attribution(H, states, dtype, steps, local):
                   device="cuda:%d" % local, concurrent=False)
     try:
         h.initialise()
+        autotune_record(h)
         h.coarse_step()
         torch.cuda.synchronize()
         capi.mhd_timing_enable(ctx, True)
@@ -752,6 +774,11 @@ def attribute_kernels(kt, work, dtype, steps):
     the timers' (ms, launches) and a hierarchy's algorithmic work."""
     hbm, hbm_src, sm_mhz = peaks()
     out = {}
+    fw = work["flops"]
+    if "k_pf" not in fw and all(k in fw for k in ("k_prim", "k_pred", "k_edge", "k_flux")):
+        # the fused pass does the primitive, predictor, edge-average and flux stages
+        fw = dict(fw, k_pf=fw["k_prim"] + fw["k_pred"] + fw["k_edge"] + fw["k_flux"])
+        work = dict(work, flops=fw)
     for nm, (ms, cnt) in kt.items():
         if not cnt:
             continue
@@ -1126,6 +1153,7 @@ def measure_deep(args, local):
         capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         s0 = out.cpu().numpy().copy()
+        tuned = autotune_record(h)
         srv = AmrLevelServer(h, budget_bytes=int(0.9 * total_mem))
         srv.run(1, timing=False)                       # warm-up coarse step through the server
         torch.cuda.synchronize()
@@ -1196,7 +1224,7 @@ def measure_deep(args, local):
                                       "written)"},
            "step_flops": {"achieved_tflops": sum(r.get("algorithmic_flops", 0.0) for r in rows.values()) /
                           (ms * 1e-3) / 1e12, "peak_tflops": alu_peak_tflops("f32")},
-           "kernels": rows, "conservation_drift_rel": drift,
+           "kernels": rows, "autotune": tuned, "conservation_drift_rel": drift,
            "conservation_note": "E drifts by what the floors add; rho by the density floor", "device_status": status, "clocks": clocks,
            "floors": {"p_floor": DEEP_P_FLOOR, "rho_floor": DEEP_RHO_FLOOR, "cells_changed": floored,
                               "cell_updates": upd * args.deep_steps,

@@ -103,12 +103,26 @@ typedef struct {
                         2: the fused kernel (one persistent launch over x-y
                         tiles marching along z, intermediates in shared
                         memory); 3: the staged kernels with the predictor
-                        tiled in shared memory.  All compute every element with the same
-                        expressions; a call whose captures need face fluxes
-                        outside the update box runs staged.                  */
-  int32_t fused_chunk; /* z-planes per work item of the fused kernel; 0 lets
-                        each call choose from the device's SM count          */
-  int32_t reserved;  /* must be 0                                           */
+                        tiled in shared memory; 4: the fused pass (one
+                        kernel for the primitives, the predictor and the
+                        Riemann fluxes over x-y tiles marching along z, the
+                        predicted face states kept on chip), then the staged
+                        EMF and update kernels.  All compute every element
+                        with the same expressions; a call whose captures need
+                        face fluxes outside the update box runs staged (2) or
+                        takes them from the fused pass's flux planes (4).   */
+  int32_t fused_chunk; /* z-planes per work item of the fused kernel (2) or
+                        of the fused pass (4); 0 lets each call choose (from
+                        the device's SM count for 2, 16 planes for 4)        */
+  int32_t kernel_shape; /* compiled tile shape of the fused kernel (2) or of
+                        the fused pass (4): 0 the context's choice (the first
+                        shape until mhd_autotune_advance chose one); s >= 1
+                        shape s - 1 of the element type's table: fused pass
+                        FP32 1: 16 x 16, 2: 16 x 12, 3: 24 x 8, 4: 16 x 8
+                        cells, FP64 1: 8 x 8; fused kernel FP32 1-4: 16 x 16
+                        (512 threads), 16 x 16, 16 x 12, 24 x 8 (384), FP64
+                        1: 8 x 8.  A shape outside the table of a call's
+                        element type is MHD_EINVAL at that call.            */
   double p_floor;    /* floors, applied after every update to the cells of
                         the update box (and by mhd_floor): a density below
                         rho_floor becomes rho_floor with M kept and the
@@ -253,19 +267,25 @@ mhd_status mhd_patch_step_cfl(mhd_ctx *ctx, const mhd_patch_desc *patches, int32
 
 /* Autotuner of the advance (no counterpart in the paper; it picks how the
  * patches of a call are advanced).  Times, on these patches (update box grown
- * by grow[p], may be NULL for zeros; dt from *d_dt), the staged kernels with
- * the untiled and with the shared-memory-tiled predictor, and every compiled
- * x-y tile shape of the fused kernel of the patches' element type, the latter
- * each with a few z-chunk lengths: reps launches after one
+ * by grow[p], may be NULL for zeros; dt from *d_dt), every compiled tile
+ * shape of the fused pass (advance_kernel 4), the staged kernels with the
+ * untiled and with the shared-memory-tiled predictor, and every compiled tile
+ * shape of the fused kernel of the patches' element type, the fused pass and
+ * the fused kernel each with a few z-chunk lengths: reps launches after one
  * warm-up, with the new state written to the context's scratch only, so the
- * patch state is unchanged.  The fastest becomes this context's advance for
+ * patch state is unchanged.  caps / ncap (may be NULL / 0) are the flux-
+ * register captures the real calls make, as for mhd_patch_advance: they are
+ * not written, but the candidates do the extra stores that feed them, and the
+ * fused kernel is left out when a real call could not run it.  The fastest becomes this context's advance for
  * that element type (mhd_params.advance_kernel = 0; mhd_params.fused_chunk > 0
  * still fixes the chunk).  Synchronises `stream`.  Outputs (may be NULL): the
- * choice (-2 staged with the untiled predictor, the default before tuning;
- * -1 staged with the tiled one; else the fused variant index), the chunk length
- * (0 for staged) and the time per advance in milliseconds. */
+ * choice (-3 - s: the fused pass of advance_kernel 4 in shape s of its table;
+ * -2 staged with the untiled predictor, the default before tuning; -1 staged
+ * with the tiled one; s >= 0 the fused kernel in shape s), the chunk length (0
+ * for staged) and the time per advance in milliseconds. */
 mhd_status mhd_autotune_advance(mhd_ctx *ctx, const mhd_patch_desc *patches, int32_t n,
-                                const int32_t *grow, const double *d_dt, int32_t reps,
+                                const int32_t *grow, const mhd_capture *caps, int32_t ncap,
+                                const double *d_dt, int32_t reps,
                                 int32_t *choice_out, int32_t *chunk_out, float *ms_out,
                                 void *stream);
 
@@ -594,7 +614,7 @@ int64_t mhd_launch_count(const mhd_ctx *ctx);
 /* Per-kernel event timer (diagnostics, no counterpart in the paper).  While
  * enabled, every launch of the context is bracketed by two CUDA events
  * recorded on the launching stream.  mhd_timing_read synchronises on the
- * pending events and returns, for kernel id `kernel` (0 <= id < 15, names from
+ * pending events and returns, for kernel id `kernel` (0 <= id < 16, names from
  * mhd_kernel_name), the summed device time in ms and the number of launches
  * since the last reset; mhd_timing_reset clears the sums. */
 mhd_status mhd_timing_enable(mhd_ctx *ctx, int32_t on);

@@ -483,6 +483,26 @@ class Hierarchy:
         with torch.cuda.stream(self.stream):
             self.graph.replay()
 
+    def autotune(self, reps: int = 1, dt: float = 1e-7):
+        """Lets mhd_autotune_advance choose this hierarchy's advance (staged
+        kernels, fused pass or fused kernel, tile shape and z-chunk) on the
+        finest level's batch with its first substep's update box (grown by 2
+        when subcycled), its flux-register captures and a small dt; the patch
+        state is unchanged.  The
+        contexts of the concurrent slots are cloned again so that they take
+        the same choice: call it before any step is captured.  Returns the
+        autotuner's (choice, chunk, ms)."""
+        l = self.nlev - 1
+        k = 2 if l > 0 else 0
+        d = torch.full((1,), dt, dtype=torch.float64, device=self.device)
+        out = capi.mhd_autotune_advance(self.ctx, self.descs[l], d.data_ptr(), reps=reps,
+                                        grow=[k] * len(self.descs[l]), stream=self.sp,
+                                        caps=self.caps[(l, True)])
+        for i, (c, st) in enumerate(self.side):
+            capi.mhd_ctx_destroy(c)
+            self.side[i] = (capi.mhd_ctx_clone(self.ctx), st)
+        return out
+
     def cell_updates_per_coarse_step(self) -> int:
         return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)
 

@@ -28,7 +28,7 @@ EXPORTS = ("mhd_ctx_create", "mhd_ctx_destroy", "mhd_last_error", "mhd_cfl_dt", 
            "mhd_patch_step_cfl", "mhd_cluster_flags", "mhd_alu_probe", "mhd_fluxreg_create",
            "mhd_fluxreg_destroy", "mhd_fluxreg_face", "mhd_fluxreg_edge", "mhd_fluxreg_zero", "mhd_flag_cells",
            "mhd_transfer_copy", "mhd_prolong_new", "mhd_floor_count", "mhd_floor")
-N_KERNELS = 15
+N_KERNELS = 16
 MHD_CAP_FACE, MHD_CAP_EDGE = 0, 1
 MHD_PROLONG, MHD_RESTRICT = 0, 1
 MHD_REFLUX, MHD_SYNC = 0, 1
@@ -53,7 +53,7 @@ class mhd_patch_desc(C.Structure):
 class mhd_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter", C.c_int32),
                 ("emf", C.c_int32), ("upwind_eps", C.c_double), ("fp64_contract", C.c_int32),
-                ("advance_kernel", C.c_int32), ("fused_chunk", C.c_int32), ("reserved", C.c_int32),
+                ("advance_kernel", C.c_int32), ("fused_chunk", C.c_int32), ("kernel_shape", C.c_int32),
                 ("p_floor", C.c_double), ("rho_floor", C.c_double)]
 
 
@@ -143,8 +143,8 @@ def load(build_if_missing: bool = False):
     L.mhd_restrict_prolong.argtypes = [P, i32, C.POINTER(mhd_patch_desc), i32, C.POINTER(mhd_patch_desc), i32,
                                        C.POINTER(mhd_level_item), i32, P]
     L.mhd_autotune_advance.restype = i32
-    L.mhd_autotune_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), P, i32, C.POINTER(i32),
-                                     C.POINTER(i32), C.POINTER(C.c_float), P]
+    L.mhd_autotune_advance.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(i32), C.POINTER(mhd_capture),
+                                     i32, P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float), P]
     L.mhd_reflux.restype = i32
     L.mhd_reflux.argtypes = [P, C.POINTER(mhd_patch_desc), i32, C.POINTER(C.c_void_p),
                              C.POINTER(mhd_deposit), i32, P]
@@ -232,8 +232,8 @@ def _descs(patches):
 
 # ------------------------------------------------------------------ C names
 def mhd_ctx_create(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0, upwind_eps=0.0, device=0, fp64_contract=0,
-                   advance_kernel=0, fused_chunk=0, p_floor=0.0, rho_floor=0.0):
-    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, advance_kernel, fused_chunk, 0,
+                   advance_kernel=0, fused_chunk=0, p_floor=0.0, rho_floor=0.0, kernel_shape=0):
+    prm = mhd_params(gamma, cfl, limiter, emf, upwind_eps, fp64_contract, advance_kernel, fused_chunk, kernel_shape,
                      float(p_floor), float(rho_floor))
     out = C.c_void_p()
     r = load().mhd_ctx_create(C.byref(prm), device, C.byref(out))
@@ -313,14 +313,21 @@ def mhd_restrict_prolong(ctx, mode, fine, coarse, items, stream: int = 0) -> Non
     _check(ctx, load().mhd_restrict_prolong(ctx, mode, fa, nf, ca, nc, it, ni, stream))
 
 
-def mhd_autotune_advance(ctx, patches, d_dt: int, reps: int = 3, grow=None, stream: int = 0):
-    """Returns (choice, chunk, ms per advance): choice -1 = staged kernels,
-    else the fused variant."""
+def mhd_autotune_advance(ctx, patches, d_dt: int, reps: int = 3, grow=None, stream: int = 0, caps=None):
+    """Returns (choice, chunk, ms per advance): choice -3 - s = the fused pass
+    in shape s, -2 / -1 = the staged kernels with the untiled / tiled
+    predictor, s >= 0 = the fused kernel in shape s."""
     arr, n = _descs(patches)
     gr = _arr(C.c_int32, grow) if grow is not None else None
+    if caps is None:
+        ca, nca = None, 0
+    elif isinstance(caps, tuple):  # (prebuilt ctypes array, count)
+        ca, nca = caps
+    else:
+        ca, nca = _structs(mhd_capture, caps)
     v, cz, ms = C.c_int32(), C.c_int32(), C.c_float()
-    _check(ctx, load().mhd_autotune_advance(ctx, arr, n, gr, d_dt, reps, C.byref(v), C.byref(cz), C.byref(ms),
-                                            stream))
+    _check(ctx, load().mhd_autotune_advance(ctx, arr, n, gr, ca, nca, d_dt, reps, C.byref(v), C.byref(cz),
+                                            C.byref(ms), stream))
     return int(v.value), int(cz.value), float(ms.value)
 
 

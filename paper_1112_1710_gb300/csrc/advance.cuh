@@ -200,10 +200,6 @@ __device__ __forceinline__ void store_face_state(R* g, int64_t sn, int64_t x, in
   VecIO<R>::store7(g, sn, x, v);
 }
 
-__device__ __forceinline__ void raise_status(int* status, int code) {
-  atomicCAS(status, 0, code);
-}
-
 // Per-patch step constants dt, dt/(2 dx_d), dt/dx_d, computed once per call by
 // k_stepc (one thread per patch) so that no stage thread touches the double
 // dt scalar, the double dt scale or the double cell widths (on this GPU the
@@ -892,14 +888,71 @@ __global__ void __launch_bounds__(kThreads) k_floor(const DPatch* __restrict__ P
   const DPatch& p = P[t.patch];
   Cell c;
   if (!region_cell<kMu<R>, kMuT<R>>(p, t.start + threadIdx.x, c)) return;
-  if (!in_ub(p, 0, c.i, 0, 0) || !in_ub(p, 1, c.j, 0, 0) || !in_ub(p, 2, c.k, 0, 0)) return;
-  if (floor_cell<R>(p, lin(p, c), sc)) atomicAdd(count, 1ull);
+  const bool f = in_ub(p, 0, c.i, 0, 0) && in_ub(p, 1, c.j, 0, 0) && in_ub(p, 2, c.k, 0, 0) &&
+                 floor_cell<R>(p, lin(p, c), sc);
+  // one atomic per warp with floored cells
+  const unsigned m = __ballot_sync(__activemask(), f);
+  if (m && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(count, (unsigned long long)__popc(m));
+}
+
+#include "pf.cuh"
+
+// Enqueues the step constants, the fused pass of compiled shape TX x TY and
+// the staged EMF / update / floor kernels.
+template <typename R, int TX, int TY, int MINB>
+cudaError_t launch_pf_shape(const AdvanceArgs& a, R* scr, R* K, const SolverConsts<R>& sc, cudaStream_t s) {
+  using L = PfLayout<TX, TY>;
+  if (a.npf == 0) return cudaSuccess;
+  const size_t smem = sizeof(R) * L::TOTAL;
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    e = cudaFuncSetAttribute(k_pf<R, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
+  }
+  const KernelTimer* tm = a.timer;
+  MHD_TIMED(tm, K_PF, s,
+            (k_stepc<R><<<(a.npatches + 127) / 128, 128, 0, s>>>(a.patches, a.npatches, a.d_dt, K),
+             k_pf<R, TX, TY, MINB><<<a.npf, L::NT, smem, s>>>(a.patches, a.pf_items, scr, K, sc, a.d_status)));
+  constexpr bool inl = kInlineEdges<R>;
+  const dim3 gu(a.nblocksu);
+  if (!inl) MHD_TIMED(tm, K_EMF, s, (k_emf<R><<<gu, kThreads, 0, s>>>(a.patches, a.tasksu, scr, sc)));
+  MHD_TIMED(tm, K_UPDATE, s,
+            (k_update<R, inl><<<gu, kThreads, 0, s>>>(a.patches, a.tasksu, scr, sc, K, a.commit ? 1 : 0)));
+  if (a.commit && (a.p_floor > 0.0 || a.rho_floor > 0.0))
+    MHD_TIMED(tm, K_UPDATE, s, (k_floor<R><<<gu, kThreads, 0, s>>>(a.patches, a.tasksu, sc, a.d_floors)));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pf(const AdvanceArgs& a, R* scr, R* K, const SolverConsts<R>& sc, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    static_assert(kNumPf32 == 4 && kPfVariants32[0].tx == 16 && kPfVariants32[1].ty == 12 &&
+                      kPfVariants32[2].tx == 24 && kPfVariants32[3].ty == 8,
+                  "variant table and dispatch must match");
+    switch (a.variant) {
+      case 0: return launch_pf_shape<R, 16, 16, 2>(a, scr, K, sc, s);
+      case 1: return launch_pf_shape<R, 16, 12, 3>(a, scr, K, sc, s);
+      case 2: return launch_pf_shape<R, 24, 8, 3>(a, scr, K, sc, s);
+      case 3: return launch_pf_shape<R, 16, 8, 4>(a, scr, K, sc, s);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    static_assert(kNumPf64 == 1 && kPfVariants64[0].tx == 8, "variant table and dispatch must match");
+    if (a.variant != 0) return cudaErrorInvalidValue;
+    return launch_pf_shape<R, 8, 8, 2>(a, scr, K, sc, s);
+  }
 }
 
 // Enqueues the step constants and the stages for the patches of one call;
 // K (npatch x kStepConsts elements) is scratch.
 template <typename R>
 cudaError_t launch_advance(const AdvanceArgs& a, R* scr, R* K, const SolverConsts<R>& sc, cudaStream_t s) {
+  if (a.pf) return launch_pf<R>(a, scr, K, sc, s);
   const DPatch* d_patches = a.patches;
   const int npatch = a.npatches, npblocks = a.npblocks;
   const BlockTask *d_tasks = a.tasks, *d_tasks1 = a.tasks1, *d_tasksu = a.tasksu, *d_ptasks = a.ptasks;
@@ -965,9 +1018,10 @@ cudaError_t launch_fused(const AdvanceArgs& a, const SolverConsts<R>& sc, cudaSt
              cudaMemsetAsync(a.counter, 0, sizeof(int), s),
              k_fused<R, BX, BY, NT><<<grid, NT, smem, s>>>(a.patches, a.items, a.nitems, a.counter, (R*)a.scratch,
                                                            K, sc, a.d_status)));
-  if (a.commit)
+  if (a.commit || a.commit_patches)
     MHD_TIMED(a.timer, K_COMMIT, s,
-              (k_commit<R><<<a.nctasks, kThreads, 0, s>>>(a.patches, a.ctasks, (const R*)a.scratch)));
+              (k_commit<R><<<a.nctasks, kThreads, 0, s>>>(a.commit && !a.commit_patches ? a.patches : a.commit_patches,
+                                                          a.ctasks, (const R*)a.scratch)));
   if (a.commit && (a.p_floor > 0.0 || a.rho_floor > 0.0))
     MHD_TIMED(a.timer, K_COMMIT, s,
               (k_floor<R><<<a.nctasks, kThreads, 0, s>>>(a.patches, a.ctasks, sc, a.d_floors)));

@@ -65,6 +65,8 @@ struct mhd_ctx {
   // chosen per call); staged until the autotuner measured otherwise
   bool use_fused[2] = {false, false};
   bool pred_tiled[2] = {false, false};  // staged path: the shared-memory-tiled predictor
+  bool use_pf[2] = {false, false};      // the fused primitive / predictor / Riemann pass
+  int pf_variant[2] = {0, 0};           // its shape
   int fused_variant[2] = {0, 0};
   int fused_chunk[2] = {0, 0};
   // per-kernel event timer
@@ -320,7 +322,8 @@ const KernelTimer* timer_of(mhd_ctx* c) { return c->timing ? &c->timer : nullptr
 
 const char* const kKernelNames[K_COUNT] = {"k_prim",  "k_pred",    "k_edge",     "k_flux",   "k_emf",
                                             "k_update", "k_cfl",     "k_ghost",    "k_sums",   "k_reflux",
-                                            "k_fused",  "k_commit",  "k_prolong",  "k_restrict", "k_capture"};
+                                            "k_fused",  "k_commit",  "k_prolong",  "k_restrict", "k_capture",
+                                            "k_pf"};
 
 // converts a descriptor array (all of one dtype) to device form
 mhd_status convert_all(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, std::vector<DPatch>& dp,
@@ -350,7 +353,8 @@ mhd_status mhd_ctx_create(const mhd_params* params, int32_t device, mhd_ctx** ou
   if (!params || !(params->gamma > 1.0) || !(params->cfl > 0.0) || params->cfl > 1.0 ||
       params->limiter < 0 || params->limiter > 2 || params->emf < 0 || params->emf > 1 ||
       params->fp64_contract < 0 || params->fp64_contract > 1 || params->advance_kernel < 0 ||
-      params->advance_kernel > 3 || params->fused_chunk < 0 || params->reserved != 0 || !(params->p_floor >= 0.0) ||
+      params->advance_kernel > 4 || params->fused_chunk < 0 || params->kernel_shape < 0 ||
+      params->kernel_shape > 16 || !(params->p_floor >= 0.0) ||
       !(params->rho_floor >= 0.0))
     return MHD_EINVAL;
   mhd_ctx* c = new mhd_ctx();
@@ -383,6 +387,8 @@ mhd_status mhd_ctx_clone(const mhd_ctx* src, mhd_ctx** out) {
   for (int i = 0; i < 2; ++i) {
     c->use_fused[i] = src->use_fused[i];
     c->pred_tiled[i] = src->pred_tiled[i];
+    c->use_pf[i] = src->use_pf[i];
+    c->pf_variant[i] = src->pf_variant[i];
     c->fused_variant[i] = src->fused_variant[i];
     c->fused_chunk[i] = src->fused_chunk[i];
   }
@@ -536,6 +542,37 @@ void fused_items(const std::vector<DPatch>& dp, int bx, int by, int cz, std::vec
   tasks_for(ccnt, ctasks);
 }
 
+// Work items of the fused primitive / predictor / Riemann pass: x-y tiles of
+// at most tx x ty cells over each patch's UB+1 region, the extents along each
+// axis as equal as the cell count allows, and chunks of cz of its planes.
+void pf_items(const std::vector<DPatch>& dp, int tx, int ty, int cz, std::vector<FusedItem>& items) {
+  items.clear();
+  for (size_t p = 0; p < dp.size(); ++p) {
+    const DPatch& q = dp[p];
+    const int lo = q.g - q.k - 1;
+    const int ex = q.n[0] + 2 * q.k + 2, ey = q.n[1] + 2 * q.k + 2, ez = q.n[2] + 2 * q.k + 2;
+    const int nx = (ex + tx - 1) / tx, ny = (ey + ty - 1) / ty;
+    for (int z0 = 0; z0 < ez; z0 += cz)
+      for (int j = 0, y0 = 0; j < ny; ++j) {
+        const int wy = ey / ny + (j < ey % ny ? 1 : 0);
+        for (int i = 0, x0 = 0; i < nx; ++i) {
+          const int wx = ex / nx + (i < ex % nx ? 1 : 0);
+          FusedItem it{};
+          it.patch = (int32_t)p;
+          it.x0 = lo + x0;
+          it.y0 = lo + y0;
+          it.z0 = lo + z0;
+          it.z1 = lo + (z0 + cz < ez ? z0 + cz : ez);
+          it.tx = wx;
+          it.ty = wy;
+          items.push_back(it);
+          x0 += wx;
+        }
+        y0 += wy;
+      }
+  }
+}
+
 // One block per tile of each patch's UB+1 for the tiled predictor.
 void pred_tiles(const std::vector<DPatch>& dp, int dtype, std::vector<BlockTask>& out) {
   const int* T = dtype == MHD_F32 ? kPredTile32 : kPredTile64;
@@ -580,31 +617,15 @@ cudaError_t run_advance_args(mhd_ctx* c, int dtype, const AdvanceArgs& a, cudaSt
                                 : advance_f64(a, s);
 }
 
-// The advance of mhd_patch_advance; with cfl_dt set (single-level steps, no
-// captures), the step first computes its own CFL dt into *d_dt: inside k_prim
-// for the staged kernels, by the separate reduction before the fused one.
-static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
-                        const double* d_dt, const double* dt_scale, const mhd_capture* caps, int32_t ncap,
-                        void* stream, bool cfl_dt) {
-  mhd_status r = begin(c);
-  if (r) return r;
-  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
-  if (!d_dt) return fail(c, MHD_EINVAL, "d_dt is NULL");
-  if (ncap < 0 || (ncap > 0 && !caps)) return fail(c, MHD_EINVAL, "bad capture list");
-  if (n == 0) return MHD_OK;
-  std::vector<DPatch> dp;
-  const int dtype = patches[0].dtype;
-  if ((r = advance_patches(c, patches, n, grow, dt_scale, dp))) return r;
-  // which advance: the context's (autotuned) choice, or forced staged / fused
-  bool fused = c->prm.advance_kernel == 2 || (c->prm.advance_kernel == 0 && c->use_fused[dtype == MHD_F32 ? 1 : 0]);
-  if (cfl_dt && fused) {
-    // the fused kernel has no primitive pass: the CFL reduction runs first
-    if ((r = mhd_cfl_dt(c, patches, n, nullptr, const_cast<double*>(d_dt), stream))) return r;
-    cfl_dt = false;
-  }
-  // flux-register captures: checked against the faces / edges this call computes
-  std::vector<DCapture> dc(ncap);
-  std::vector<int64_t> ccounts(ncap);
+// Checks each flux-register capture of an advance call against the faces /
+// edges the call computes, converts it to device form and marks its patch
+// (flags bit 0); fused_ok is cleared when a capture needs face fluxes outside
+// the update box (the fused kernel stores only those).
+static mhd_status scan_captures(mhd_ctx* c, std::vector<DPatch>& dp, const mhd_capture* caps, int32_t ncap,
+                                std::vector<DCapture>& dc, std::vector<int64_t>& ccounts, bool& fused_ok) {
+  const int n = (int)dp.size();
+  dc.resize(ncap);
+  ccounts.resize(ncap);
   for (int t = 0; t < ncap; ++t) {
     const mhd_capture& m = caps[t];
     if (m.patch < 0 || m.patch >= n || (m.kind != 0 && m.kind != 1) || m.axis < 0 || m.axis > 2 ||
@@ -632,7 +653,7 @@ static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_
       if (hi < lo || lo < alo || hi > ahi)
         return fail(c, MHD_EINVAL, "capture %d: box outside the elements the advance computes (axis %d)", t, d);
       // the fused kernel stores the face fluxes of the update box only
-      if (m.kind == 0 && d != m.axis && (lo < ulo || hi > uhi)) fused = false;
+      if (m.kind == 0 && d != m.axis && (lo < ulo || hi > uhi)) fused_ok = false;
       o.lo[d] = lo;
       o.ext[d] = hi - lo + 1;
       cnt *= o.ext[d];
@@ -640,6 +661,40 @@ static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_
     ccounts[t] = cnt;
     p.flags |= 1;
   }
+  return MHD_OK;
+}
+
+// The advance of mhd_patch_advance; with cfl_dt set (single-level steps, no
+// captures), the step first computes its own CFL dt into *d_dt: inside k_prim
+// for the staged kernels, by the separate reduction before the fused one.
+static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
+                        const double* d_dt, const double* dt_scale, const mhd_capture* caps, int32_t ncap,
+                        void* stream, bool cfl_dt) {
+  mhd_status r = begin(c);
+  if (r) return r;
+  if (n < 0 || (n > 0 && !patches)) return fail(c, MHD_EINVAL, "bad patch array");
+  if (!d_dt) return fail(c, MHD_EINVAL, "d_dt is NULL");
+  if (ncap < 0 || (ncap > 0 && !caps)) return fail(c, MHD_EINVAL, "bad capture list");
+  if (n == 0) return MHD_OK;
+  std::vector<DPatch> dp;
+  const int dtype = patches[0].dtype;
+  if ((r = advance_patches(c, patches, n, grow, dt_scale, dp))) return r;
+  // which advance: the context's (autotuned) choice, or forced staged / fused
+  bool fused = c->prm.advance_kernel == 2 || (c->prm.advance_kernel == 0 && c->use_fused[dtype == MHD_F32 ? 1 : 0]);
+  const bool pf = !fused && (c->prm.advance_kernel == 4 ||
+                             (c->prm.advance_kernel == 0 && c->use_pf[dtype == MHD_F32 ? 1 : 0]));
+  if (cfl_dt && (fused || pf)) {
+    // neither the fused kernel nor the fused pass has a primitive pass of its
+    // own: the CFL reduction runs first
+    if ((r = mhd_cfl_dt(c, patches, n, nullptr, const_cast<double*>(d_dt), stream))) return r;
+    cfl_dt = false;
+  }
+  // flux-register captures: checked against the faces / edges this call computes
+  std::vector<DCapture> dc(ncap);
+  std::vector<int64_t> ccounts(ncap);
+  bool fused_ok = true;
+  if ((r = scan_captures(c, dp, caps, ncap, dc, ccounts, fused_ok))) return r;
+  if (!fused_ok) fused = false;
   // arena: per patch its stage planes (staged) or its output copy, plus the
   // flux planes when it feeds captures (fused); then the step constants, then
   // the work-queue head
@@ -656,13 +711,22 @@ static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_
   std::vector<BlockTask> tasks, tasks1, tasksu, ptasks;
   std::vector<FusedItem> items;
   std::vector<BlockTask> ctasks;
-  if (!fused) {
+  const int di = dtype == MHD_F32 ? 1 : 0;
+  const int shape = c->prm.kernel_shape > 0 ? c->prm.kernel_shape - 1 : pf ? c->pf_variant[di] : c->fused_variant[di];
+  if (shape >= (pf ? (di ? kNumPf32 : kNumPf64) : (di ? kNumFused32 : kNumFused64)))
+    return fail(c, MHD_EINVAL, "kernel_shape %d is not compiled for this element type", c->prm.kernel_shape);
+  if (pf) {
+    staged_tasks(dp, elem_size(dtype), tasks, tasks1, tasksu);
+    const PfVariant& pv = di ? kPfVariants32[shape] : kPfVariants64[shape];
+    pf_items(dp, pv.tx, pv.ty,
+             c->prm.fused_chunk > 0 ? c->prm.fused_chunk : c->fused_chunk[di] > 0 ? c->fused_chunk[di] : 16, items);
+    if (items.size() > 0x7fffffff || tasksu.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
+  } else if (!fused) {
     staged_tasks(dp, elem_size(dtype), tasks, tasks1, tasksu);
     if (c->prm.advance_kernel == 3 || c->pred_tiled[dtype == MHD_F32 ? 1 : 0]) pred_tiles(dp, dtype, ptasks);
     if (tasks.size() > 0x7fffffff || ptasks.size() > 0x7fffffff) return fail(c, MHD_EINVAL, "launch too large");
   } else {
-    const int di = dtype == MHD_F32 ? 1 : 0;
-    const FusedVariant& v = fused_variant_of(dtype, c->fused_variant[di]);
+    const FusedVariant& v = fused_variant_of(dtype, shape);
     const int cz = c->prm.fused_chunk > 0   ? c->prm.fused_chunk
                    : c->fused_chunk[di] > 0 ? c->fused_chunk[di]
                                             : fused_chunk_auto(dp, v.bx, v.by, sm_count(c->device));
@@ -704,17 +768,24 @@ static mhd_status advance_impl(mhd_ctx* c, const mhd_patch_desc* patches, int32_
   a.counter = (int*)((char*)c->scratch + counter_byte);
   a.ctasks = (const BlockTask*)d_ct;
   a.nctasks = (int)ctasks.size();
-  a.variant = c->fused_variant[dtype == MHD_F32 ? 1 : 0];
+  a.variant = shape;
   a.commit = true;
   a.cfl_out = cfl_dt ? (unsigned long long*)const_cast<double*>(d_dt) : nullptr;
   a.cfl = c->prm.cfl;
   a.p_floor = c->prm.p_floor;
   a.rho_floor = c->prm.rho_floor;
   a.d_floors = c->d_floors;
+  a.pf = pf;
+  if (pf) {
+    a.pf_items = (const FusedItem*)d_i;
+    a.npf = (int)items.size();
+    a.fused = false;
+  }
   cudaError_t e = run_advance_args(c, dtype, a, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "patch advance launch");
   // fused: step constants, k_fused, k_commit; staged with the CFL dt: + reset
-  c->launches += (fused ? 3 : staged_launches(elem_size(dtype)) + (cfl_dt ? 1 : 0)) + (c->prm.p_floor > 0.0 || c->prm.rho_floor > 0.0 ? 1 : 0);
+  c->launches += (fused ? 3 : pf ? (elem_size(dtype) == 8 ? 4 : 3) : staged_launches(elem_size(dtype)) + (cfl_dt ? 1 : 0)) +
+                 (c->prm.p_floor > 0.0 || c->prm.rho_floor > 0.0 ? 1 : 0);
   if (ncap > 0) {
     PackedTasks pc{};
     if ((r = packed_table(c, ccounts, false, pc))) return r;
@@ -743,14 +814,21 @@ mhd_status mhd_patch_step_cfl(mhd_ctx* c, const mhd_patch_desc* patches, int32_t
 }
 
 mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, const int32_t* grow,
-                                const double* d_dt, int32_t reps, int32_t* variant_out, int32_t* chunk_out,
-                                float* ms_out, void* stream) {
+                                const mhd_capture* caps, int32_t ncap, const double* d_dt, int32_t reps,
+                                int32_t* variant_out, int32_t* chunk_out, float* ms_out, void* stream) {
   mhd_status r = begin(c);
   if (r) return r;
   if (n < 1 || !patches || !d_dt || reps < 1 || reps > 1000) return fail(c, MHD_EINVAL, "autotune: bad arguments");
+  if (ncap < 0 || (ncap > 0 && !caps)) return fail(c, MHD_EINVAL, "bad capture list");
   std::vector<DPatch> dp;
   const int dtype = patches[0].dtype;
   if ((r = advance_patches(c, patches, n, grow, nullptr, dp))) return r;
+  // the captures a real call would make: their patches' extra stores, and
+  // whether the fused kernel may run at all
+  std::vector<DCapture> dc;
+  std::vector<int64_t> ccounts;
+  bool fused_ok = true;
+  if ((r = scan_captures(c, dp, caps, ncap, dc, ccounts, fused_ok))) return r;
   // arena as for a staged call (the staged candidate needs its 92 planes; the
   // fused ones use the first 8 of them as output copies)
   int64_t off = 0;
@@ -776,8 +854,20 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   if ((r = table(c, tasks1.data(), tasks1.size() * sizeof(BlockTask), &d_t1))) return r;
   if ((r = table(c, tasksu.data(), tasksu.size() * sizeof(BlockTask), &d_tu))) return r;
   if ((r = table(c, ptasks.data(), ptasks.size() * sizeof(BlockTask), &d_pt))) return r;
+  // the fused kernel's copy-back goes to planes of the scratch arena the
+  // fused kernel does not use (the predicted-state planes), so that it is
+  // timed without touching the patch state
+  std::vector<DPatch> dpc = dp;
+  const size_t es0 = elem_size(dtype);
+  for (int p = 0; p < n; ++p) {
+    for (int q = 0; q < 5; ++q) dpc[p].U[q] = (char*)c->scratch + (size_t)(dp[p].scr + (SC_WF + q) * dp[p].snelem) * es0;
+    for (int a = 0; a < 3; ++a)
+      dpc[p].B[a] = (char*)c->scratch + (size_t)(dp[p].scr + (SC_WF + 5 + a) * dp[p].snelem) * es0;
+  }
+  void* d_pc = nullptr;
+  if ((r = table(c, dpc.data(), dpc.size() * sizeof(DPatch), &d_pc))) return r;
   const int di = dtype == MHD_F32 ? 1 : 0;
-  const int nv = dtype == MHD_F32 ? kNumFused32 : kNumFused64;
+  const int nv = fused_ok ? (dtype == MHD_F32 ? kNumFused32 : kNumFused64) : 0;
   const int nsm = sm_count(c->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -787,97 +877,133 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(c, e, "autotune events");
   }
+  // candidates (choice code, chunk): the fused pass in every shape (-3 - s)
+  // x chunk length; the staged kernels with the untiled (-2) and the tiled
+  // (-1) predictor; the fused kernel in every shape (s) x chunk length
+  std::vector<std::pair<int, int>> cand;
+  const int npv = dtype == MHD_F32 ? kNumPf32 : kNumPf64;
+  for (int sv = 0; sv < npv; ++sv) {
+    std::vector<int> chunks;
+    for (int cz : {6, 8, 12, 16, 24, 33}) {
+      cz = cz > zmax + 2 ? zmax + 2 : cz;
+      if (std::find(chunks.begin(), chunks.end(), cz) == chunks.end()) chunks.push_back(cz);
+    }
+    for (int cz : chunks) cand.push_back({-3 - sv, cz});
+  }
+  cand.push_back({-2, 0});
+  cand.push_back({-1, 0});
+  for (int v = 0; v < nv; ++v) {
+    const FusedVariant& fv = fused_variant_of(dtype, v);
+    std::vector<int> chunks;
+    for (int cz : {fused_chunk_auto(dp, fv.bx, fv.by, nsm), 4, 8, 16, 32, 64}) {
+      cz = cz > zmax ? zmax : cz;
+      if (std::find(chunks.begin(), chunks.end(), cz) == chunks.end()) chunks.push_back(cz);
+    }
+    for (int cz : chunks) cand.push_back({v, cz});
+  }
   float best = 3.4e38f;
-  int bv = -3, bcz = 0;
+  int bv = 0, bcz = 0;
+  bool any = false;
   std::vector<FusedItem> items;
   std::vector<BlockTask> ctasks;
-  // candidates -2 / -1: the staged kernels with the untiled / tiled
-  // predictor; then every fused variant x chunk length
-  for (int v = -2; v < nv; ++v) {
-    std::vector<int> chunks;
-    if (v < 0) {
-      chunks.push_back(0);
-    } else {
-      const FusedVariant& fv = fused_variant_of(dtype, v);
-      for (int cz : {fused_chunk_auto(dp, fv.bx, fv.by, nsm), 4, 8, 16, 32, 64}) {
-        cz = cz > zmax ? zmax : cz;
-        if (std::find(chunks.begin(), chunks.end(), cz) == chunks.end()) chunks.push_back(cz);
-      }
+  int skip_shape = -1000;  // a shape this device cannot run: its other chunks are skipped
+  for (const auto& cv : cand) {
+    const int v = cv.first, cz = cv.second;
+    if (v == skip_shape) continue;
+    AdvanceArgs a{};
+    a.patches = (const DPatch*)d_p;
+    a.npatches = n;
+    a.tasks = (const BlockTask*)d_t;
+    a.nblocks = (int)tasks.size();
+    a.tasks1 = (const BlockTask*)d_t1;
+    a.nblocks1 = (int)tasks1.size();
+    a.tasksu = (const BlockTask*)d_tu;
+    a.nblocksu = (int)tasksu.size();
+    a.scratch = c->scratch;
+    a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
+    a.gamma = c->prm.gamma;
+    a.eps_up = eps_for(c->prm, dtype);
+    a.limiter = c->prm.limiter;
+    a.emf = c->prm.emf;
+    a.d_dt = d_dt;
+    a.d_status = c->d_status;
+    a.timer = nullptr;
+    a.p_floor = c->prm.p_floor;  // the primitives' floors, as in a real call
+    a.rho_floor = c->prm.rho_floor;
+    a.d_floors = c->d_floors;
+    a.commit = false;  // every candidate leaves the patch state as it is
+    a.fused = v >= 0;
+    if (v == -1) {
+      a.ptasks = (const BlockTask*)d_pt;
+      a.npblocks = (int)ptasks.size();
     }
-    for (int cz : chunks) {
-      AdvanceArgs a{};
-      a.patches = (const DPatch*)d_p;
-      a.npatches = n;
-      a.tasks = (const BlockTask*)d_t;
-      a.nblocks = (int)tasks.size();
-      a.tasks1 = (const BlockTask*)d_t1;
-      a.nblocks1 = (int)tasks1.size();
-      a.tasksu = (const BlockTask*)d_tu;
-      a.nblocksu = (int)tasksu.size();
-      a.scratch = c->scratch;
-      a.stepc = (char*)c->scratch + (size_t)stepc_off * es;
-      a.gamma = c->prm.gamma;
-      a.eps_up = eps_for(c->prm, dtype);
-      a.limiter = c->prm.limiter;
-      a.emf = c->prm.emf;
-      a.d_dt = d_dt;
-      a.d_status = c->d_status;
-      a.timer = nullptr;
-      a.commit = false;  // both paths leave the patch state as it is
-      a.fused = v >= 0;
-      if (v == -1) {
-        a.ptasks = (const BlockTask*)d_pt;
-        a.npblocks = (int)ptasks.size();
-      }
-      if (a.fused) {
-        const FusedVariant& fv = fused_variant_of(dtype, v);
-        fused_items(dp, fv.bx, fv.by, cz, items, ctasks);
-        void *d_i = nullptr, *d_ct = nullptr;
-        if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i)) ||
-            (r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return r;
-        }
-        a.items = (const FusedItem*)d_i;
-        a.nitems = (int)items.size();
-        a.counter = (int*)((char*)c->scratch + counter_byte);
-        a.ctasks = (const BlockTask*)d_ct;
-        a.nctasks = (int)ctasks.size();
-        a.variant = v;
-      }
-      e = run_advance_args(c, dtype, a, s);
-      if (e != cudaSuccess) {  // a shape this device cannot run: skip it
-        cudaGetLastError();
-        break;
-      }
-      cudaEventRecord(e0, s);
-      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = run_advance_args(c, dtype, a, s);
-      cudaEventRecord(e1, s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
+    if (v <= -3) {
+      const PfVariant& pv = dtype == MHD_F32 ? kPfVariants32[-3 - v] : kPfVariants64[-3 - v];
+      pf_items(dp, pv.tx, pv.ty, cz, items);
+      void* d_i = nullptr;
+      if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i))) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        return cuda_fail(c, e, "autotune run");
+        return r;
       }
-      c->launches += (a.fused ? 2 : staged_launches(es)) * (reps + 1);
-      ms /= reps;
-      if (ms < best) {
-        best = ms;
-        bv = v;
-        bcz = cz;
+      a.pf = true;
+      a.pf_items = (const FusedItem*)d_i;
+      a.npf = (int)items.size();
+      a.variant = -3 - v;
+    }
+    if (a.fused) {
+      const FusedVariant& fv = fused_variant_of(dtype, v);
+      fused_items(dp, fv.bx, fv.by, cz, items, ctasks);
+      void *d_i = nullptr, *d_ct = nullptr;
+      if ((r = table(c, items.data(), items.size() * sizeof(FusedItem), &d_i)) ||
+          (r = table(c, ctasks.data(), ctasks.size() * sizeof(BlockTask), &d_ct))) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return r;
       }
+      a.items = (const FusedItem*)d_i;
+      a.nitems = (int)items.size();
+      a.counter = (int*)((char*)c->scratch + counter_byte);
+      a.ctasks = (const BlockTask*)d_ct;
+      a.nctasks = (int)ctasks.size();
+      a.variant = v;
+      a.commit_patches = (const DPatch*)d_pc;
+    }
+    e = run_advance_args(c, dtype, a, s);
+    if (e != cudaSuccess) {  // a shape this device cannot run: skip it
+      cudaGetLastError();
+      skip_shape = v;
+      continue;
+    }
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = run_advance_args(c, dtype, a, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(c, e, "autotune run");
+    }
+    c->launches += (a.fused ? 3 : a.pf ? (es == 8 ? 4 : 3) : staged_launches(es)) * (reps + 1);
+    ms /= reps;
+    if (ms < best) {
+      best = ms;
+      bv = v;
+      bcz = cz;
+      any = true;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (bv < -2) return fail(c, MHD_ECUDA, "autotune: no advance ran on this device");
+  if (!any) return fail(c, MHD_ECUDA, "autotune: no advance ran on this device");
   c->use_fused[di] = bv >= 0;
-  if (bv < 0) c->pred_tiled[di] = bv == -1;
+  c->use_pf[di] = bv <= -3;
+  if (bv == -2 || bv == -1) c->pred_tiled[di] = bv == -1;
   c->fused_variant[di] = bv >= 0 ? bv : 0;
-  c->fused_chunk[di] = bv >= 0 ? bcz : 0;
+  c->pf_variant[di] = bv <= -3 ? -3 - bv : 0;
+  c->fused_chunk[di] = bv >= 0 || bv <= -3 ? bcz : 0;
   if (variant_out) *variant_out = bv;
   if (chunk_out) *chunk_out = bcz;
   if (ms_out) *ms_out = best;

@@ -111,7 +111,8 @@ constexpr int kPredTile64[3] = {16, 4, 4};
 // lower corner (x0, y0) (array indices) and the planes [z0, z1).
 struct FusedItem {
   int32_t patch, x0, y0, z0, z1;
-  int32_t pad[3];
+  int32_t tx, ty;    // fused pass: this tile's x and y extents (at most its build's tile)
+  int32_t pad;
 };
 
 // One ghost-fill copy, resolved to array indices of both patches.
@@ -136,10 +137,17 @@ enum : int {
 };
 
 
+// Records a device status code (the first one raised wins).  The status word
+// is read first, so that once it is set the threads that meet further bad
+// cells (a whole region of them, say) issue no atomic on the one address.
+__device__ __forceinline__ void raise_status(int* status, int code) {
+  if (*(volatile int*)status == 0) atomicCAS(status, 0, code);
+}
+
 // Kernel ids of the per-kernel event timer (mhd_timing_*).
 enum KernelId : int {
   K_PRIM = 0, K_PRED, K_EDGE, K_FLUX, K_EMF, K_UPDATE, K_CFL, K_GHOST, K_SUMS, K_REFLUX, K_FUSED, K_COMMIT,
-  K_PROLONG, K_RESTRICT, K_CAPTURE, K_COUNT
+  K_PROLONG, K_RESTRICT, K_CAPTURE, K_PF, K_COUNT
 };
 
 // Optional hook that records CUDA events around each launch on its stream.

@@ -80,7 +80,7 @@ __device__ __forceinline__ void fused_prim(const DPatch& p, R* sm, int X0, int Y
     }
     if (!(w[0] > R(0)) || !(w[4] > R(0))) bad = true;
   }
-  if (bad) atomicCAS(status, 0, -4);
+  if (bad) raise_status(status, -4);
 }
 
 // Phase B (1): slopes, Hancock predictor and predicted face states of plane z.

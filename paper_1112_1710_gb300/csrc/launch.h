@@ -42,7 +42,28 @@ struct AdvanceArgs {
   // cells it raised
   double p_floor, rho_floor;
   unsigned long long* d_floors;
+  // primitive + predictor + Riemann passes fused (k_pf over x-y tiles of UB+1
+  // and z-chunks, items in the FusedItem layout; shape `variant` of
+  // kPfVariants), then the staged update
+  bool pf;
+  const FusedItem* pf_items;  // device
+  int npf;
+  // fused kernel without commit: the copy-back writes through these patches'
+  // arrays instead (device; the autotuner's scratch destinations)
+  const DPatch* commit_patches;
 };
+
+// Compiled shapes of the fused primitive / predictor / Riemann pass (k_pf):
+// the largest x-y tile and the blocks per SM its registers and shared memory
+// allow (FP32: 16 x 16 at 2, 92 KB; 16 x 12 and 24 x 8 at 3, 71-72 KB;
+// 16 x 8 at 4, 50 KB).
+struct PfVariant {
+  int tx, ty, minb;
+};
+constexpr PfVariant kPfVariants32[] = {{16, 16, 2}, {16, 12, 3}, {24, 8, 3}, {16, 8, 4}};
+constexpr PfVariant kPfVariants64[] = {{8, 8, 2}};
+constexpr int kNumPf32 = sizeof(kPfVariants32) / sizeof(kPfVariants32[0]);
+constexpr int kNumPf64 = sizeof(kPfVariants64) / sizeof(kPfVariants64[0]);
 
 // Compiled shapes of the fused advance: x-y tile and threads per CTA (one CTA
 // per SM; FP64 fits smaller tiles, its intermediates being twice as large).

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_cfl(const DPatch* __restrict__ P,
       R tt = dx_of<R>(p, d) / (Tr<R>::abs(w[1 + d]) + cf);
       m = rmin(m, tt);
     }
-    if (!(w[0] > R(0)) || !(w[4] > R(0))) atomicCAS(status, 0, -4);
+    if (!(w[0] > R(0)) || !(w[4] > R(0))) raise_status(status, -4);
   }
   for (int o = 16; o > 0; o >>= 1) {
     R u2 = __shfl_down_sync(0xffffffffu, m, o);

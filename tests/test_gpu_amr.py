@@ -78,12 +78,13 @@ def test_prolong_and_restrict_random_data(capi, orc):
         capi.mhd_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("split,kernel", [(1, 1), (2, 1), (1, 2)])
+@pytest.mark.parametrize("split,kernel", [(1, 1), (2, 1), (1, 2), (1, 4)])
 def test_amr_coarse_steps_fp64_parity(capi, orc, split, kernel):
     """Three subcycled coarse steps of a 3-level shell hierarchy (1 + 47 + 42
     patches of 4^3-8^3 cells, 4 ghost layers): every patch array equals the
-    oracle's, with the staged advance (1) and with the fused one (2), whose
-    flux-register captures come from the fluxes it stores."""
+    oracle's, with the staged advance (1), the fused one (2), whose
+    flux-register captures come from the fluxes it stores, and the fused pass
+    (4)."""
     from oracle.amr import OHierarchy
     from paper_1112_1710_gb300.amr import Hierarchy
     n0 = 16
