@@ -35,6 +35,14 @@ METRIC = "MHD cell-updates/s (FP64 vs FP32-mixed, % HBM roofline); patch p50/p99
 # upwinded Gardiner-Stone average loses positivity at this blast's
 # perpendicular shock front within a few steps)
 SOLVER = {"gamma": 5.0 / 3.0, "cfl": 0.4, "limiter": 0, "emf": 1}
+# --advance: mhd_params.advance_kernel of the contexts (0 = the autotuner's choice)
+ADVANCE_KERNELS = {"auto": 0, "staged": 1, "pf": 4, "fused": 2}
+ADVANCE = {"kernel": 0, "tune": True}
+
+
+def adv_kw():
+    """Context keywords of the advance chosen on the command line."""
+    return {"advance_kernel": ADVANCE["kernel"]} if ADVANCE["kernel"] else {}
 # deep AMR (Mach-5 turbulence): the same solver with floors at 1e-3 of the
 # initial pressure 1/gamma and density 1 (without them the method itself, FP64
 # oracle included, reaches non-positive pressure within 6-13 coarse steps)
@@ -59,6 +67,9 @@ def parse():
     ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve", "ot2d", "deep"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the staged advance (profiling runs: timings taken under a profiler mislead the tuner)")
+    ap.add_argument("--advance", default="auto", choices=list(ADVANCE_KERNELS),
+                    help="advance of the single patch and of the hierarchies: the autotuner's choice, or forced "
+                         "(staged kernels, fused pass, fused kernel)")
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests per offered load")
     ap.add_argument("--slots", type=int, default=3, help="serve: streams (one context each)")
     ap.add_argument("--batch-cells", type=int, default=4 << 20, help="serve: cell budget of one batch")
@@ -288,8 +299,10 @@ def choice_label(v):
 
 def autotune_record(h):
     """Lets the autotuner choose a hierarchy's advance (on its finest level's
-    batch) and returns the choice as a record."""
+    batch) and returns the choice as a record (or the forced one's)."""
     import torch
+    if not ADVANCE["tune"]:
+        return {"choice": "forced: advance_kernel %d" % ADVANCE["kernel"]}
     v, cz, ms = h.autotune()
     torch.cuda.synchronize()
     return {"choice": choice_label(v), "chunk": cz, "ms_per_advance_of_finest_level": ms}
@@ -302,7 +315,7 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
     from paper_1112_1710_gb300.patch import Patch
     from paper_1112_1710_gb300.runner import PeriodicRunner
 
-    ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, fp64_contract=contract, **SOLVER, **adv_kw())
     clones = []
     try:
         p = Patch.from_array(pr.state, (0, 0, 0), pr.n, pr.g, pr.dx, dtype=dtype, device="cuda:%d" % local)
@@ -313,7 +326,7 @@ def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):
         # the advance (staged kernels, the fused pass or a fused shape) as
         # picked by the autotuner on this patch
         tuned = None
-        if not args.no_autotune:
+        if ADVANCE["tune"]:
             v, cz, tms = capi.mhd_autotune_advance(ctx, run.descs, run.d_dt.data_ptr(), reps=3,
                                                    stream=stream.cuda_stream)
             tuned = {"choice": choice_label(v), "chunk": cz, "ms_per_advance": tms}
@@ -599,7 +612,7 @@ def time_amr(H, states, dtype, steps, mode, local, concurrent=False):
 
     from paper_1112_1710_gb300 import capi
     from paper_1112_1710_gb300.amr import Hierarchy
-    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER, **adv_kw())
     # the main stream carries every finer level: it gets the higher priority
     stream = torch.cuda.Stream(device=local, priority=-1)
     h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
@@ -742,7 +755,7 @@ def amr_attribution(H, states, dtype, steps, local):
 
     from paper_1112_1710_gb300 import capi
     from paper_1112_1710_gb300.amr import Hierarchy
-    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER, **adv_kw())
     stream = torch.cuda.Stream(device=local)
     # one stream and one context, so that one timer sees every launch
     h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype=dtype, ctx=ctx, stream=stream,
@@ -1139,7 +1152,7 @@ def measure_deep(args, local):
     t0 = time.time()
     H, states, sample = deep_setup(n0, G)
     dev = "cuda:%d" % local
-    ctx = capi.mhd_ctx_create(device=local, p_floor=DEEP_P_FLOOR, rho_floor=DEEP_RHO_FLOOR, **SOLVER)
+    ctx = capi.mhd_ctx_create(device=local, p_floor=DEEP_P_FLOOR, rho_floor=DEEP_RHO_FLOOR, **SOLVER, **adv_kw())
     stream = torch.cuda.Stream(device=local, priority=-1)
     h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx, stream=stream, device=dev,
                   concurrent=True, floors=True)
@@ -1352,6 +1365,8 @@ def measure_serve(args, local):
 
 def main():
     args = parse()
+    ADVANCE["kernel"] = ADVANCE_KERNELS[args.advance]
+    ADVANCE["tune"] = args.advance == "auto" and not args.no_autotune
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
