@@ -623,6 +623,7 @@ def time_amr(H, states, dtype, steps, mode, local, concurrent=False):
         if mode == "per_patch":
             h.batched = False
         else:
+            h.coarse_step()                # ghost zones filled before tuning
             tuned = autotune_record(h)
         if mode == "graph":
             h.capture_graph()
@@ -699,6 +700,7 @@ def amr_level_work(h):
     cfl = cells * 8 * es
     # advance: units per call as in kernel_units, on each patch's update box
     flops = {k: 0.0 for k in STAGES}
+    upd = 0
     for l, pats in enumerate(h.levels):
         ks = [0] if l == 0 else [2, 0]
         calls = 1 if l == 0 else 2 ** (l - 1)
@@ -714,8 +716,13 @@ def amr_level_work(h):
                      "k_update": nx * ny * nz}
                 for st in STAGES:
                     flops[st] += calls * u[st] * KERNEL_FLOPS[st]
+                # the update reads the state and the three face-flux vector
+                # groups of each cell and writes the state: 40 values per cell
+                # of the update box; the floors after it (timed with it) read
+                # the state once more
+                upd += calls * u["k_update"] * (40 + (8 if h.floors else 0)) * es
     return {"bytes": {"k_ghost": ghost, "k_prolong": prol, "k_restrict": rest, "k_capture": cap,
-                      "k_reflux": ref, "k_cfl": cfl}, "flops": flops}
+                      "k_reflux": ref, "k_cfl": cfl, "k_update": upd}, "flops": flops}
 
 
 def time_metadata(H, n0, local):
@@ -762,6 +769,7 @@ def amr_attribution(H, states, dtype, steps, local):
                   device="cuda:%d" % local, concurrent=False)
     try:
         h.initialise()
+        h.coarse_step()
         autotune_record(h)
         h.coarse_step()
         torch.cuda.synchronize()
@@ -1163,13 +1171,14 @@ def measure_deep(args, local):
     try:
         h.initialise()
         out = torch.zeros(8, dtype=torch.float64, device=dev)
-        capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
-        torch.cuda.synchronize()
-        s0 = out.cpu().numpy().copy()
+        h.coarse_step()                                # ghost zones filled before tuning
         tuned = autotune_record(h)
         srv = AmrLevelServer(h, budget_bytes=int(0.9 * total_mem))
         srv.run(1, timing=False)                       # warm-up coarse step through the server
         torch.cuda.synchronize()
+        capi.mhd_conservation_sums(ctx, h.descs[0], out.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        s0 = out.cpu().numpy().copy()
         setup_s = time.time() - t0
         for c in [h.ctx] + [c for c, _ in h.side]:
             capi.mhd_floor_count(c)                    # reset
@@ -1335,10 +1344,12 @@ def measure_serve(args, local):
     finally:
         be.close()
     flops = {k: 0.0 for k in STAGES}
+    upd = 0
     for r in f32reqs:
         for k in STAGES:
             flops[k] += KERNEL_FLOPS[k] * kernel_units(k, r.n)
-    rows = attribute_kernels(kt, {"bytes": {}, "flops": flops}, "f32", 1)
+        upd += kernel_units("k_update", r.n) * 40 * 4   # state read + written, three flux groups read
+    rows = attribute_kernels(kt, {"bytes": {"k_update": upd}, "flops": flops}, "f32", 1)
     res = {"metric": UNIT, "value": sat["cell_updates_per_s"], "unit": UNIT, "requests": nreq,
            "dtype": "f32+f64 (FP64 contracted build)",
            "config": {"workload": "serving stream: single-step requests on periodic blast-wave cubes, edges "

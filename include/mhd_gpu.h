@@ -273,7 +273,8 @@ mhd_status mhd_patch_step_cfl(mhd_ctx *ctx, const mhd_patch_desc *patches, int32
  * shape of the fused kernel of the patches' element type, the fused pass and
  * the fused kernel each with a few z-chunk lengths: reps launches after one
  * warm-up, with the new state written to the context's scratch only, so the
- * patch state is unchanged.  caps / ncap (may be NULL / 0) are the flux-
+ * patch state is unchanged, and with a status word of their own, so that the
+ * context's device status is unchanged too.  caps / ncap (may be NULL / 0) are the flux-
  * register captures the real calls make, as for mhd_patch_advance: they are
  * not written, but the candidates do the extra stores that feed them, and the
  * fused kernel is left out when a real call could not run it.  The fastest becomes this context's advance for

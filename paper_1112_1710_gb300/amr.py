@@ -490,8 +490,10 @@ class Hierarchy:
         when subcycled), its flux-register captures and a small dt; the patch
         state is unchanged.  The
         contexts of the concurrent slots are cloned again so that they take
-        the same choice: call it before any step is captured.  Returns the
-        autotuner's (choice, chunk, ms)."""
+        the same choice: call it before any step is captured, and after a
+        first coarse step (until then the fine levels' ghost zones hold
+        whatever the initial states held there).  Returns the autotuner's
+        (choice, chunk, ms)."""
         l = self.nlev - 1
         k = 2 if l > 0 else 0
         d = torch.full((1,), dt, dtype=torch.float64, device=self.device)

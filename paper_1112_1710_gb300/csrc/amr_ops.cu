@@ -383,12 +383,24 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
 // Sets flag bit `bit` of element x of a coarse patch (flags are bytes packed
 // four to a word; neighbouring elements of other threads share words); the
 // thread that sets the element's first bit appends it to the call's list.
+// The lanes of a warp that append take one run of the list with one atomic,
+// in lane order, so that the list keeps the deposits' spatial order within a
+// warp (neighbouring entries are neighbouring elements for the correction).
 __device__ __forceinline__ void mark(unsigned int* flags, int64_t x, unsigned int bit, const RefluxList& L,
                                      int corr_idx) {
   const int sh = 8 * (int)(x & 3);
   const unsigned int old = atomicOr(flags + (x >> 2), bit << sh);
-  if (((old >> sh) & 0xFFu) == 0u) {
-    const unsigned long long i = atomicAdd(L.count, 1ull);
+  const bool first = ((old >> sh) & 0xFFu) == 0u;
+  const unsigned int act = __activemask();
+  const unsigned int m = __ballot_sync(act, first);
+  if (!m) return;
+  const int lane = (int)(threadIdx.x & 31);
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(L.count, (unsigned long long)__popc(m));
+  base = __shfl_sync(act, base, leader);
+  if (first) {
+    const unsigned long long i = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
     if (i < L.capacity) L.entries[i] = ((unsigned long long)corr_idx << 40) | (unsigned long long)x;
   }
 }

@@ -843,7 +843,9 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
   off += 8 * (int64_t)n;
   const size_t es = elem_size(dtype);
   const size_t counter_byte = ((size_t)off * es + 15) / 16 * 16;
-  if ((r = ensure_scratch(c, counter_byte + 16))) return r;
+  // after the work-queue head: a status word of the candidates' own, so that
+  // their checks (on whatever the ghost zones hold) leave the context's alone
+  if ((r = ensure_scratch(c, counter_byte + 32))) return r;
   std::vector<BlockTask> tasks, tasks1, tasksu, ptasks;
   staged_tasks(dp, elem_size(dtype), tasks, tasks1, tasksu);
   pred_tiles(dp, dtype, ptasks);
@@ -926,7 +928,7 @@ mhd_status mhd_autotune_advance(mhd_ctx* c, const mhd_patch_desc* patches, int32
     a.limiter = c->prm.limiter;
     a.emf = c->prm.emf;
     a.d_dt = d_dt;
-    a.d_status = c->d_status;
+    a.d_status = (int*)((char*)c->scratch + counter_byte + 16);
     a.timer = nullptr;
     a.p_floor = c->prm.p_floor;  // the primitives' floors, as in a real call
     a.rho_floor = c->prm.rho_floor;

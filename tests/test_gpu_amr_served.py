@@ -216,3 +216,43 @@ def test_deep_amr_floors_fp64_parity(capi, orc, capsys):
         if ph is not None:
             ph.close()
         capi.mhd_ctx_destroy(ctx)
+
+
+def test_hierarchy_autotune_keeps_state_and_parity(capi, orc):
+    """Hierarchy.autotune (the autotuner on the finest level's batch with its
+    captures, after a first coarse step) changes no patch state and leaves
+    the device status alone; whatever it picks, the FP64 parity build then
+    equals the oracle bit for bit over two more coarse steps (every advance
+    computes each element with the oracle's expressions)."""
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H, st = _shell(n0)
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx,
+                       stream=torch.cuda.Stream(priority=-1), concurrent=True)
+        oh.initialise()
+        ph.initialise()
+        assert oh.coarse_step() == (ph.coarse_step() or ph.d_dt.item())
+        torch.cuda.synchronize()
+        before = [[p.state.clone() for p in lv] for lv in ph.levels]
+        v, cz, ms = ph.autotune(reps=1)
+        torch.cuda.synchronize()
+        assert ms > 0.0 and capi.mhd_get_device_status(ph.ctx) == 0
+        for lv, bl in zip(ph.levels, before):
+            for p, b in zip(lv, bl):
+                assert torch.equal(p.state, b)
+        for _ in range(2):
+            ph.coarse_step()
+            assert oh.coarse_step() == ph.d_dt.item()
+        torch.cuda.synchronize()
+        assert ph.device_status() == 0
+        linf, _ = _error_table(oh, ph)      # interiors and their faces
+        assert np.all(linf == 0.0), (v, linf)
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)
