@@ -880,6 +880,7 @@ def run_amr(args):
     torch.cuda.set_device(local)
     from paper_1112_1710_gb300 import _build
     _build.build()
+    measure_alu_peaks(local)
     H, states = amr_hierarchy()
     res = [time_amr(H, states, "f32", args.steps, "graph", local),
            time_amr(H, states, "f32", args.steps, "graph", local, concurrent=True),
