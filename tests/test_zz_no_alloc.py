@@ -63,6 +63,23 @@ def test_static_sums_match_context_sums_on_two_calls(capi, dtype):
         capi.mhd_ctx_destroy(ctx)
 
 
+def test_static_sums_leave_device_memory_unchanged(capi):
+    """After a first call (the library loaded, its fixed array resident), a
+    call changes neither the device's free memory nor torch's allocation."""
+    pr = synth.blast(32, seed=7)
+    p = _patch(pr, "f32", 0)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    capi.mhd_conservation_sums_static([p.desc()], out.data_ptr())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        capi.mhd_conservation_sums_static([p.desc()], out.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_static_sums_reject_requests_beyond_capacity(capi):
     pr = synth.blast(8)
     p = _patch(pr, "f64", 0)
