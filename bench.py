@@ -888,6 +888,7 @@ def run_amr(args):
            time_amr(H, states, "f64", max(1, args.steps // 2), "graph", local),
            time_amr(H, states, "f64", 1, "per_patch", local)]
     attribution = amr_attribution(H, states, "f32", 2, local)
+    rg = time_regrid(H, states, local)
     meta = time_metadata(H, 64, local)
     hil = time_hilbert(H, states, args.steps, local)
     if rank != 0:
@@ -910,7 +911,7 @@ def run_amr(args):
                                    sum(len(l) for l in H),
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
-            "runs": res, "kernels_f32": attribution, "metadata": meta, "hilbert": hil}
+            "runs": res, "kernels_f32": attribution, "metadata": meta, "hilbert": hil, "regrid": rg}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
@@ -1260,6 +1261,55 @@ def measure_deep(args, local):
     return res
 
 
+REGRID_THETA = 0.02
+
+
+def time_regrid(H, states, local):
+    """One regridding of the AMR hierarchy's finest level (Sec. 2.1) after a
+    first coarse step: the parent level's flags on the device, the host
+    clustering and the device data transfer (regrid.regrid_finest), then the
+    new hierarchy's metadata (device tree, lists, registers) and one coarse
+    step of it."""
+    import torch
+
+    from paper_1112_1710_gb300 import capi
+    from paper_1112_1710_gb300 import regrid as R
+    from paper_1112_1710_gb300.amr import Hierarchy
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER)
+    h = h2 = None
+    try:
+        h = Hierarchy(H, 64, states, (1.0 / 64,) * 3, g=4, dtype="f32", ctx=ctx, device="cuda:%d" % local)
+        h.initialise()
+        h.coarse_step()
+        torch.cuda.synchronize()
+        old = len(h.levels[-1])
+        t0 = time.perf_counter()
+        phases = {}
+        boxes, st, nfall = R.regrid_finest(h, REGRID_THETA, timing=phases)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h.close()
+        h2 = Hierarchy(boxes, 64, st, (1.0 / 64,) * 3, g=4, dtype="f32", ctx=ctx, device="cuda:%d" % local)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        h2.initialise()
+        h2.coarse_step()
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        new_cells = sum(p.cells for p in h2.levels[-1]) if len(boxes) == len(H) else 0
+        return {"theta": REGRID_THETA, "finest_level": len(H) - 1, "old_patches": old,
+                "new_patches": len(boxes[-1]) if len(boxes) == len(H) else 0, "new_cells": new_cells,
+                "energy_fallbacks": int(nfall.item()), "ms_flags_cluster_transfer": 1e3 * (t1 - t0),
+                "ms_new_hierarchy_metadata": 1e3 * (t2 - t1), "ms_first_coarse_step_eager": 1e3 * (t3 - t2),
+                "device_status": h2.device_status(),
+                "ms_phases": {k: 1e3 * v for k, v in phases.items()}}
+    finally:
+        for x in (h, h2):
+            if x is not None:
+                x.close()
+        capi.mhd_ctx_destroy(ctx)
+
+
 def measure_amr(args, local):
     """Config 3: the AMR blast-shell hierarchy (base 64^3 + 3 levels), one
     coarse step as a CUDA graph in FP32 and in FP64, against the plain
@@ -1269,6 +1319,7 @@ def measure_amr(args, local):
             "f64_graph": time_amr(H, states, "f64", 1, "graph", local),
             "f64_per_patch": time_amr(H, states, "f64", 1, "per_patch", local)}
     att = amr_attribution(H, states, "f32", 1, local)
+    rg = time_regrid(H, states, local)
     main = runs["f32_graph"]
     res = {"metric": UNIT, "value": main["value"], "unit": UNIT, "ms_per_coarse_step": main["ms_per_coarse_step"],
            "dtype": "f32 (FP64 registers)",
@@ -1280,7 +1331,7 @@ def measure_amr(args, local):
            "speedup_vs_per_patch_f64": {"f32_graph": main["value"] / runs["f64_per_patch"]["value"],
                                         "f64_graph": runs["f64_graph"]["value"] / runs["f64_per_patch"]["value"]},
            "roofline": roofline_of(att["kernels"], "f32", "one eager FP32 coarse step, per-launch CUDA events"),
-           "kernels": att["kernels"]}
+           "kernels": att["kernels"], "regrid": rg}
     if not args.no_cpu_baseline:
         items = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), 4, (1.0 / 64 / 2 ** l,) * 3,
                   (0,) if l == 0 else (2, 0), False)

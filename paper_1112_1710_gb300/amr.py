@@ -76,6 +76,7 @@ class Hierarchy:
         advance (reading R33)."""
         self.floors = bool(floors)
         self.n0, self.g, self.dtype = n0, g, dtype
+        self.dx0 = tuple(dx0)
         self.device = torch.device(device)
         self.gpu = self.device.type == "cuda"  # on the CPU only the metadata is built (tests)
         self.ctx = ctx if (ctx is not None or not self.gpu) else capi.mhd_ctx_create()
@@ -507,6 +508,27 @@ class Hierarchy:
 
     def cell_updates_per_coarse_step(self) -> int:
         return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)
+
+    def regrid(self, theta: float, **kw) -> "Hierarchy":
+        """The hierarchy with its finest level replaced by the next iteration
+        (regrid.regrid_finest: flags of the level below on the device,
+        Berger-Rigoutsos grids, the data transfer), built with this one's
+        context, stream and options; this hierarchy is closed (its coarser
+        levels' state tensors move to the new one).  The new hierarchy's
+        `regrid_info` holds the energy-fallback count (a device tensor) and
+        the old and new patch counts of the level."""
+        from . import regrid as R
+        boxes, states, nfall = R.regrid_finest(self, theta, **kw)
+        old = len(self.levels[-1])
+        own, self.own_ctx = self.own_ctx, False
+        conc = bool(self.side)
+        self.close()
+        h = Hierarchy(boxes, self.n0, states, self.dx0, g=self.g, dtype=self.dtype, ctx=self.ctx,
+                      stream=self.stream, device=self.device, concurrent=conc, floors=self.floors)
+        h.own_ctx = own
+        h.regrid_info = {"fallbacks": nfall, "old_patches": old,
+                         "new_patches": len(boxes[-1]) if len(boxes) == self.nlev else 0}
+        return h
 
     def close(self):
         for c, _ in self.side:

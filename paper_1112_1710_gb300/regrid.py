@@ -66,7 +66,8 @@ def children(cluster_boxes, coarse_boxes, ratio: int = 2):
 def flag(ctx, patches, theta: float, stream=None):
     """Error flags of the interiors of `patches` (Patch objects of one
     dtype) on the device (``mhd_flag_cells``): a list of uint8 tensors, one
-    per patch, shaped (nz, ny, nx)."""
+    per patch, shaped (nz, ny, nx), written on `stream` (the current stream
+    if None): synchronise with it before reading them elsewhere."""
     import torch
     dev = patches[0].state.device
     total = sum(p.cells for p in patches)
@@ -119,6 +120,13 @@ def transfer_mask(new_box, old_boxes):
     ext = chi - clo + 1
     I = [np.arange(clo[d], chi[d] + 1) for d in range(3)]
     m = np.zeros((ext[2], ext[1], ext[0]), np.uint8)
+    if len(old_boxes):
+        # only the old patches whose coarse footprint, grown by one face,
+        # meets this one's contribute
+        ol = np.array([b[0] for b in old_boxes], np.int64) // 2
+        oh = (np.array([b[1] for b in old_boxes], np.int64) + 1) // 2 - 1
+        near = np.all((ol <= chi + 1) & (oh + 1 >= clo), axis=1)
+        old_boxes = [old_boxes[k] for k in np.nonzero(near)[0]]
     for olo, ohi in old_boxes:
         ol, oh = _cbox(olo, ohi)
         inside = [(I[d] >= ol[d]) & (I[d] <= oh[d]) for d in range(3)]
@@ -165,7 +173,108 @@ def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
             it.mask_box = capi.box(mlo, tuple(int(v) for v in ch))
             pitems.append(it)
     nfall = torch.zeros(1, dtype=torch.int64, device=dev)
+    if stream is not None:
+        # the masks and the count were written on the current stream
+        stream.wait_stream(torch.cuda.current_stream(dev))
     capi.mhd_prolong_new(ctx, [p.desc() for p in coarse], [p.desc() for p in fresh], pitems, energy_mode,
                          nfall.data_ptr(), s)
     transfer._keep = masks          # the masks must live until the launch has run
     return nfall
+
+
+def _grow(m, r: int, value: bool):
+    """Separable dilation (value True) or erosion (value False) of a boolean
+    array by the cube of half-width r, the outside counting as not set."""
+    out = m
+    for ax in range(m.ndim):
+        pad = [(0, 0)] * m.ndim
+        pad[ax] = (r, r)
+        p = np.pad(out, pad, constant_values=False)
+        acc = out.copy()
+        for s in range(-r, r + 1):
+            sl = [slice(None)] * m.ndim
+            sl[ax] = slice(r + s, r + s + m.shape[ax])
+            acc = (acc | p[tuple(sl)]) if value else (acc & p[tuple(sl)])
+        out = acc
+    return out
+
+
+def regrid_finest(h, theta: float, buffer: int = 1, margin: int = 3, eff: float = 0.7, min_size: int = 2,
+                  energy_mode: int = 1, timing=None):
+    """The next iteration of a hierarchy's finest level (Sec. 2.1): the
+    level below it is flagged on the device (``mhd_flag_cells``, after its
+    ghost zones are filled from the levels below), the flags grown by
+    `buffer` cells and kept where the new level is properly nested (at least
+    `margin` parent cells inside the parent level's grids; the domain
+    boundary counts as outside), clustered into boxes (Berger-Rigoutsos),
+    cut by the parent grids and refined; the new patches take the old
+    iteration's data where they meet it and the parent's prolongation
+    elsewhere (``mhd_transfer_copy``, ``mhd_prolong_new``).  Returns (boxes,
+    states, fallbacks): every level's boxes and state tensors for a new
+    Hierarchy (the coarser levels' tensors are the hierarchy's own; with no
+    flagged cell the finest level is dropped) and the device count of energy
+    fallbacks of the prolongation.  `timing` (a dict, optional) receives the
+    seconds of each phase (flags, masks, clustering, transfer)."""
+    import time
+
+    import torch
+
+    from .patch import Patch, patch_shape
+    tm = timing if timing is not None else {}
+    t0 = time.perf_counter()
+    L = h.nlev
+    if L < 2:
+        raise ValueError("regrid_finest needs a hierarchy of at least two levels")
+    lp = L - 2                        # the parent level, whose flags make the new level
+    # ghost zones of the parent level, as at the start of its step
+    h.fill(0)
+    for k in range(1, lp + 1):
+        h.prolong(k - 1)
+        h.fill(k)
+    parents = h.levels[lp]
+    cur = torch.cuda.current_stream(h.device)
+    h.stream.wait_stream(cur)
+    fl = flag(h.ctx, parents, theta, h.stream)
+    h.stream.synchronize()
+    t1 = time.perf_counter()
+    tm["flags"] = t1 - t0
+    # flags over the bounding box of the parent grids (x, y, z -> array z, y, x)
+    blo = np.min([p.lo for p in parents], axis=0)
+    bhi = np.max([p.hi for p in parents], axis=0)
+    ext = bhi - blo + 1
+    dense = np.zeros((ext[2], ext[1], ext[0]), dtype=bool)
+    inside = np.zeros_like(dense)
+    for p, f in zip(parents, fl):
+        lo, hi = np.asarray(p.lo) - blo, np.asarray(p.hi) - blo
+        dense[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] |= f.cpu().numpy().astype(bool)
+        inside[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
+    if buffer > 0:
+        dense = _grow(dense, buffer, True)
+    dense &= _grow(inside, margin, False)
+    boxes = [[(p.lo, p.hi) for p in lv] for lv in h.levels[:L - 1]]
+    states = [[p.state for p in lv] for lv in h.levels[:L - 1]]
+    if not dense.any():
+        return boxes, states, torch.zeros(1, dtype=torch.int64, device=h.device)
+    t2 = time.perf_counter()
+    tm["masks"] = t2 - t1
+    cl = cluster(dense.astype(np.uint8), eff, min_size)            # (z, y, x) order, box-local
+    tm["clustering"] = time.perf_counter() - t2
+    cl = [(tuple(int(v) for v in np.asarray(lo[::-1]) + blo), tuple(int(v) for v in np.asarray(hi[::-1]) + blo))
+          for lo, hi in cl]
+    new = children(cl, [(p.lo, p.hi) for p in parents])
+    dx = tuple(v / 2 ** (L - 1) for v in h.dx0)
+    tdt = {"f32": torch.float32, "f64": torch.float64}[h.dtype]
+    fresh = []
+    for i, (lo, hi) in enumerate(new):
+        nn = tuple(hi[d] - lo[d] + 1 for d in range(3))
+        st = torch.zeros(patch_shape(nn, h.g), dtype=tdt, device=h.device)
+        fresh.append(Patch(st, tuple(lo), nn, h.g, dx, L - 1, i))
+    t3 = time.perf_counter()
+    h.stream.wait_stream(cur)               # the zeroed arrays
+    nfall = transfer(h.ctx, h.levels[L - 1], fresh, parents, energy_mode, h.stream)
+    cur.wait_stream(h.stream)
+    h.stream.synchronize()
+    tm["transfer"] = time.perf_counter() - t3
+    boxes.append([(tuple(lo), tuple(hi)) for lo, hi in new])
+    states.append([p.state for p in fresh])
+    return boxes, states, nfall

@@ -104,3 +104,136 @@ def test_transfer_equals_oracle(capi, orc, kind, energy_mode):
         if dtype == "f32":
             P = orc.patch(np.ascontiguousarray(got), n, T.G, dxf)
             assert orc.divb_max(P) * dxf[0] <= 1e-5 * np.abs(got[5:8]).max()
+
+
+def _interiors_equal(oh, ph, G=4):
+    for l in range(len(oh.levels)):
+        for P, Q in zip(oh.levels[l], ph.levels[l]):
+            got = Q.state.cpu().numpy()
+            for q in range(8):
+                ext = list(P.n)
+                if q >= 5:
+                    ext[q - 5] += 1
+                a = got[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                b = P.state[q, G:G + ext[2], G:G + ext[1], G:G + ext[0]]
+                if not np.array_equal(a, b):
+                    return (l, q, float(np.abs(a - b).max()))
+    return None
+
+
+@pytest.mark.parametrize("theta", [0.03, 0.1])
+def test_regrid_finest_fp64_equals_oracle_and_steps_on(capi, orc, theta):
+    """One regridding of a hierarchy's finest level (regrid.regrid_finest:
+    the parent level's flags on the device, grown, nested, clustered, cut by
+    the parent grids, and the data transfer) in the FP64 parity build: the
+    same grids and the same new patch data as the oracle's regridding step,
+    and two more coarse steps of the regridded hierarchies agree bit for
+    bit."""
+    import synth.amr as SA
+    from oracle import regrid as OR
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300 import regrid
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0, G = 16, 4
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
+    st = [[SA.blast_patch(lo, hi, l, n0, G, p_in=10.0)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = ph2 = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        oh.initialise()
+        ph.initialise()
+        assert oh.coarse_step() == (ph.coarse_step() or ph.d_dt.item())
+        boxes, states, nfall = regrid.regrid_finest(ph, theta)
+        oboxes, ostates, onfall = OR.regrid_finest(oh, theta, empty=synth.empty_patch)
+        torch.cuda.synchronize()
+        assert boxes == oboxes and len(boxes) == 3 and len(boxes[2]) > 0
+        assert int(nfall.item()) == onfall
+        for s_gpu, s_orc in zip(states[2], ostates[2]):
+            a = s_gpu.cpu().numpy()
+            assert np.array_equal(a[:, :s_orc.shape[1], :s_orc.shape[2], :s_orc.shape[3]], s_orc)
+        ph.close()
+        ph = None
+        ph2 = Hierarchy(boxes, n0, states, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        oh2 = OHierarchy(oboxes, n0, ostates, (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+        oh2.initialise()
+        ph2.initialise()
+        for _ in range(2):
+            ph2.coarse_step()
+            assert oh2.coarse_step() == ph2.d_dt.item()
+        torch.cuda.synchronize()
+        assert ph2.device_status() == 0
+        assert _interiors_equal(oh2, ph2) is None
+    finally:
+        for h in (ph, ph2):
+            if h is not None:
+                h.close()
+        capi.mhd_ctx_destroy(ctx)
+
+
+def test_regrid_finest_fp32_runs_on(capi):
+    """The same regridding on an FP32 hierarchy: the regridded hierarchy
+    steps on with a healthy status and divergence-free new patches."""
+    import synth.amr as SA
+    from paper_1112_1710_gb300 import regrid
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0, G = 16, 4
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
+    st = [[SA.blast_patch(lo, hi, l, n0, G, p_in=10.0)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    ctx = capi.mhd_ctx_create(emf=1)
+    ph = ph2 = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
+        ph.initialise()
+        ph.coarse_step()
+        boxes, states, nfall = regrid.regrid_finest(ph, 0.05)
+        assert len(boxes) == 3 and len(boxes[2]) > 0 and int(nfall.item()) == 0
+        ph.close()
+        ph = None
+        ph2 = Hierarchy(boxes, n0, states, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
+        ph2.initialise()
+        for _ in range(2):
+            ph2.coarse_step()
+        torch.cuda.synchronize()
+        assert ph2.device_status() == 0
+        dx = 1.0 / (n0 * 4)
+        worst = 0.0
+        for P in ph2.levels[2]:
+            s = P.state.cpu().numpy().astype(np.float64)
+            nx, ny, nz = P.n
+            bx = s[5, G:G + nz, G:G + ny, G:G + nx + 1]
+            by = s[6, G:G + nz, G:G + ny + 1, G:G + nx]
+            bz = s[7, G:G + nz + 1, G:G + ny, G:G + nx]
+            div = (np.diff(bx, axis=2) + np.diff(by, axis=1) + np.diff(bz, axis=0)) / dx
+            worst = max(worst, float(np.abs(div).max()))
+        assert worst < 1e-3, worst
+    finally:
+        for h in (ph, ph2):
+            if h is not None:
+                h.close()
+        capi.mhd_ctx_destroy(ctx)
+
+
+def test_hierarchy_regrid_method(capi):
+    """Hierarchy.regrid: the new hierarchy keeps the context, has the
+    regridded finest level and steps on."""
+    import synth.amr as SA
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0, G = 16, 4
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
+    st = [[SA.blast_patch(lo, hi, l, n0, G, p_in=10.0)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    h = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", concurrent=True)
+    ctx = h.ctx
+    try:
+        h.initialise()
+        h.coarse_step()
+        h2 = h.regrid(0.05)
+        h = h2
+        assert h.ctx == ctx and h.own_ctx and len(h.side) == 2
+        assert h.regrid_info["new_patches"] == len(h.levels[2]) > 0
+        h.coarse_step()
+        torch.cuda.synchronize()
+        assert h.device_status() == 0
+    finally:
+        h.close()
