@@ -1265,11 +1265,12 @@ REGRID_THETA = 0.02
 
 
 def time_regrid(H, states, local):
-    """One regridding of the AMR hierarchy's finest level (Sec. 2.1) after a
-    first coarse step: the parent level's flags on the device, the host
-    clustering and the device data transfer (regrid.regrid_finest), then the
-    new hierarchy's metadata (device tree, lists, registers) and one coarse
-    step of it."""
+    """One regridding of every refined level of the AMR hierarchy (Sec. 2.1)
+    after a first coarse step, coarsest first, each new level from the flags
+    of the new level below (regrid.regrid_levels: flags on the device, host
+    masks and clustering, the device data transfer, the intermediate
+    hierarchies' metadata), then the new hierarchy's metadata (device tree,
+    lists, registers) and one coarse step of it."""
     import torch
 
     from paper_1112_1710_gb300 import capi
@@ -1282,10 +1283,10 @@ def time_regrid(H, states, local):
         h.initialise()
         h.coarse_step()
         torch.cuda.synchronize()
-        old = len(h.levels[-1])
+        old = [len(lv) for lv in h.levels]
         t0 = time.perf_counter()
         phases = {}
-        boxes, st, nfall = R.regrid_finest(h, REGRID_THETA, timing=phases)
+        boxes, st, nfall = R.regrid_levels(h, REGRID_THETA, first=1, timing=phases)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         h.close()
@@ -1296,10 +1297,10 @@ def time_regrid(H, states, local):
         h2.coarse_step()
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        new_cells = sum(p.cells for p in h2.levels[-1]) if len(boxes) == len(H) else 0
-        return {"theta": REGRID_THETA, "finest_level": len(H) - 1, "old_patches": old,
-                "new_patches": len(boxes[-1]) if len(boxes) == len(H) else 0, "new_cells": new_cells,
-                "energy_fallbacks": int(nfall.item()), "ms_flags_cluster_transfer": 1e3 * (t1 - t0),
+        return {"theta": REGRID_THETA, "levels_regridded": list(range(1, len(H))),
+                "patches_per_level_before": old, "patches_per_level_after": [len(b) for b in boxes],
+                "cells_per_level_after": [sum(p.cells for p in lv) for lv in h2.levels],
+                "energy_fallbacks": int(nfall.item()), "ms_regrid": 1e3 * (t1 - t0),
                 "ms_new_hierarchy_metadata": 1e3 * (t2 - t1), "ms_first_coarse_step_eager": 1e3 * (t3 - t2),
                 "device_status": h2.device_status(),
                 "ms_phases": {k: 1e3 * v for k, v in phases.items()}}

@@ -509,16 +509,17 @@ class Hierarchy:
     def cell_updates_per_coarse_step(self) -> int:
         return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)
 
-    def regrid(self, theta: float, **kw) -> "Hierarchy":
-        """The hierarchy with its finest level replaced by the next iteration
-        (regrid.regrid_finest: flags of the level below on the device,
-        Berger-Rigoutsos grids, the data transfer), built with this one's
-        context, stream and options; this hierarchy is closed (its coarser
-        levels' state tensors move to the new one).  The new hierarchy's
-        `regrid_info` holds the energy-fallback count (a device tensor) and
-        the old and new patch counts of the level."""
+    def regrid(self, theta: float, first: int | None = None, **kw) -> "Hierarchy":
+        """The hierarchy with its levels from `first` (default: the finest)
+        up replaced by their next iterations (regrid.regrid_levels: each from
+        the flags of the new level below on the device, Berger-Rigoutsos
+        grids, the data transfer), built with this one's context, stream and
+        options; this hierarchy is closed (its kept levels' state tensors
+        move to the new one).  The new hierarchy's `regrid_info` holds the
+        energy-fallback count (a device tensor) and the old and new patch
+        counts of the finest level."""
         from . import regrid as R
-        boxes, states, nfall = R.regrid_finest(self, theta, **kw)
+        boxes, states, nfall = R.regrid_levels(self, theta, first=first, **kw)
         old = len(self.levels[-1])
         own, self.own_ctx = self.own_ctx, False
         conc = bool(self.side)

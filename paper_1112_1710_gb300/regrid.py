@@ -199,34 +199,53 @@ def _grow(m, r: int, value: bool):
     return out
 
 
-def regrid_finest(h, theta: float, buffer: int = 1, margin: int = 3, eff: float = 0.7, min_size: int = 2,
-                  energy_mode: int = 1, timing=None):
-    """The next iteration of a hierarchy's finest level (Sec. 2.1): the
-    level below it is flagged on the device (``mhd_flag_cells``, after its
-    ghost zones are filled from the levels below), the flags grown by
-    `buffer` cells and kept where the new level is properly nested (at least
-    `margin` parent cells inside the parent level's grids; the domain
-    boundary counts as outside), clustered into boxes (Berger-Rigoutsos),
-    cut by the parent grids and refined; the new patches take the old
-    iteration's data where they meet it and the parent's prolongation
-    elsewhere (``mhd_transfer_copy``, ``mhd_prolong_new``).  Returns (boxes,
-    states, fallbacks): every level's boxes and state tensors for a new
-    Hierarchy (the coarser levels' tensors are the hierarchy's own; with no
-    flagged cell the finest level is dropped) and the device count of energy
-    fallbacks of the prolongation.  `timing` (a dict, optional) receives the
-    seconds of each phase (flags, masks, clustering, transfer)."""
+def fit_boxes(boxes, flags, allowed):
+    """Cluster boxes (inclusive, array axis order) made to lie in `allowed`:
+    each box is shrunk to the bounding box of its flagged cells; a box with a
+    cell outside `allowed` is halved across its longest axis (the lower axis
+    on ties; the low half takes the extra slice) and both halves treated
+    again, low half first.  Every flagged cell must be allowed."""
+    out = []
+
+    def rec(lo, hi):
+        sl = tuple(slice(lo[d], hi[d] + 1) for d in range(3))
+        f = flags[sl]
+        if not f.any():
+            return
+        nz = [np.nonzero(f.any(axis=tuple(e for e in range(3) if e != d)))[0] for d in range(3)]
+        lo = tuple(lo[d] + int(nz[d][0]) for d in range(3))
+        hi = tuple(lo[d] - int(nz[d][0]) + int(nz[d][-1]) for d in range(3))
+        hi = tuple(int(v) for v in hi)
+        sl = tuple(slice(lo[d], hi[d] + 1) for d in range(3))
+        if allowed[sl].all():
+            out.append((lo, hi))
+            return
+        ext = [hi[d] - lo[d] + 1 for d in range(3)]
+        d = int(np.argmax(ext))
+        mid = lo[d] + (ext[d] - 1) // 2
+        a_hi, b_lo = list(hi), list(lo)
+        a_hi[d], b_lo[d] = mid, mid + 1
+        rec(lo, tuple(a_hi))
+        rec(tuple(b_lo), hi)
+
+    for lo, hi in boxes:
+        rec(tuple(int(v) for v in lo), tuple(int(v) for v in hi))
+    return out
+
+
+def _next_level(h, old, theta, buffer, margin, eff, min_size, energy_mode, tm):
+    """The next iteration of level h.nlev (whose previous iteration is the
+    Patch list `old`) from the flags of h's finest level, which must hold
+    its data (interiors; its ghost zones are filled here from the levels
+    below, as at the start of its step).  Returns (boxes, patches, fallbacks);
+    no boxes when nothing is flagged."""
     import time
 
     import torch
 
     from .patch import Patch, patch_shape
-    tm = timing if timing is not None else {}
     t0 = time.perf_counter()
-    L = h.nlev
-    if L < 2:
-        raise ValueError("regrid_finest needs a hierarchy of at least two levels")
-    lp = L - 2                        # the parent level, whose flags make the new level
-    # ghost zones of the parent level, as at the start of its step
+    lp = h.nlev - 1
     h.fill(0)
     for k in range(1, lp + 1):
         h.prolong(k - 1)
@@ -237,7 +256,7 @@ def regrid_finest(h, theta: float, buffer: int = 1, margin: int = 3, eff: float 
     fl = flag(h.ctx, parents, theta, h.stream)
     h.stream.synchronize()
     t1 = time.perf_counter()
-    tm["flags"] = t1 - t0
+    tm["flags"] = tm.get("flags", 0.0) + t1 - t0
     # flags over the bounding box of the parent grids (x, y, z -> array z, y, x)
     blo = np.min([p.lo for p in parents], axis=0)
     bhi = np.max([p.hi for p in parents], axis=0)
@@ -250,31 +269,105 @@ def regrid_finest(h, theta: float, buffer: int = 1, margin: int = 3, eff: float 
         inside[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
     if buffer > 0:
         dense = _grow(dense, buffer, True)
-    dense &= _grow(inside, margin, False)
-    boxes = [[(p.lo, p.hi) for p in lv] for lv in h.levels[:L - 1]]
-    states = [[p.state for p in lv] for lv in h.levels[:L - 1]]
-    if not dense.any():
-        return boxes, states, torch.zeros(1, dtype=torch.int64, device=h.device)
+    allowed = _grow(inside, margin, False)
+    dense &= allowed
     t2 = time.perf_counter()
-    tm["masks"] = t2 - t1
+    tm["masks"] = tm.get("masks", 0.0) + t2 - t1
+    if not dense.any():
+        return [], [], torch.zeros(1, dtype=torch.int64, device=h.device)
     cl = cluster(dense.astype(np.uint8), eff, min_size)            # (z, y, x) order, box-local
-    tm["clustering"] = time.perf_counter() - t2
+    cl = fit_boxes(cl, dense, allowed)
+    t3 = time.perf_counter()
+    tm["clustering"] = tm.get("clustering", 0.0) + t3 - t2
     cl = [(tuple(int(v) for v in np.asarray(lo[::-1]) + blo), tuple(int(v) for v in np.asarray(hi[::-1]) + blo))
           for lo, hi in cl]
     new = children(cl, [(p.lo, p.hi) for p in parents])
-    dx = tuple(v / 2 ** (L - 1) for v in h.dx0)
+    dx = tuple(v / 2 ** (lp + 1) for v in h.dx0)
     tdt = {"f32": torch.float32, "f64": torch.float64}[h.dtype]
     fresh = []
     for i, (lo, hi) in enumerate(new):
         nn = tuple(hi[d] - lo[d] + 1 for d in range(3))
         st = torch.zeros(patch_shape(nn, h.g), dtype=tdt, device=h.device)
-        fresh.append(Patch(st, tuple(lo), nn, h.g, dx, L - 1, i))
-    t3 = time.perf_counter()
+        fresh.append(Patch(st, tuple(lo), nn, h.g, dx, lp + 1, i))
     h.stream.wait_stream(cur)               # the zeroed arrays
-    nfall = transfer(h.ctx, h.levels[L - 1], fresh, parents, energy_mode, h.stream)
+    nfall = transfer(h.ctx, old, fresh, parents, energy_mode, h.stream)
     cur.wait_stream(h.stream)
     h.stream.synchronize()
-    tm["transfer"] = time.perf_counter() - t3
-    boxes.append([(tuple(lo), tuple(hi)) for lo, hi in new])
-    states.append([p.state for p in fresh])
+    tm["transfer"] = tm.get("transfer", 0.0) + time.perf_counter() - t3
+    return [(tuple(lo), tuple(hi)) for lo, hi in new], fresh, nfall
+
+
+def regrid_levels(h, theta: float, first: int | None = None, buffer: int = 1, margin: int = 3, eff: float = 0.7,
+                  min_size: int = 2, energy_mode: int = 1, timing=None):
+    """The next iteration of every level from `first` (default: the finest)
+    to the finest (Sec. 2.1), coarsest first: each new level is made from the
+    flags of the level below it in the new hierarchy (``mhd_flag_cells``,
+    after that level's ghost zones are filled from the levels below), the
+    flags grown by `buffer` cells and kept where the new level is properly
+    nested (at least `margin` parent cells inside the parent level's grids;
+    the domain boundary counts as outside), clustered into boxes
+    (Berger-Rigoutsos), cut by the parent grids and refined; the new patches
+    take the previous iteration of their level where they meet it and the
+    new parent level's prolongation elsewhere (``mhd_transfer_copy``,
+    ``mhd_prolong_new``).  A level with no flagged cell ends the hierarchy.
+    Returns (boxes, states, fallbacks): every level's boxes and state tensors
+    for a new Hierarchy (the kept levels' tensors are the hierarchy's own)
+    and the device count of energy fallbacks.  `timing` (a dict, optional)
+    receives the seconds of each phase (flags, masks, clustering, transfer,
+    and the metadata of the intermediate hierarchies)."""
+    import time
+
+    import torch
+    tm = timing if timing is not None else {}
+    L = h.nlev
+    first = L - 1 if first is None else first
+    if L < 2 or not 1 <= first <= L - 1:
+        raise ValueError("regridding needs levels 1 .. %d of a hierarchy of %d levels" % (L - 1, L))
+    boxes = [[(p.lo, p.hi) for p in lv] for lv in h.levels[:first]]
+    states = [[p.state for p in lv] for lv in h.levels[:first]]
+    nfall = torch.zeros(1, dtype=torch.int64, device=h.device)
+    tmp = None
+    try:
+        for m in range(first, L):
+            if m == first:
+                parent = _Prefix(h, m)          # h's own levels 0..m-1
+            else:
+                t0 = time.perf_counter()
+                if tmp is not None:
+                    tmp.close()
+                tmp = type(h)(boxes, h.n0, states, h.dx0, g=h.g, dtype=h.dtype, ctx=h.ctx, stream=h.stream,
+                              device=h.device)
+                tm["metadata"] = tm.get("metadata", 0.0) + time.perf_counter() - t0
+                parent = tmp
+            nb, fresh, nf = _next_level(parent, h.levels[m], theta, buffer, margin, eff, min_size, energy_mode, tm)
+            nfall += nf
+            if not nb:
+                break
+            boxes.append(nb)
+            states.append([p.state for p in fresh])
+    finally:
+        if tmp is not None:
+            tmp.close()
     return boxes, states, nfall
+
+
+class _Prefix:
+    """Levels 0..m-1 of a hierarchy, with its operations (the parent levels
+    of a regridding)."""
+
+    def __init__(self, h, m):
+        self._h, self.nlev = h, m
+        self.levels = h.levels[:m]
+        self.ctx, self.stream, self.device, self.dtype = h.ctx, h.stream, h.device, h.dtype
+        self.g, self.n0, self.dx0 = h.g, h.n0, h.dx0
+
+    def fill(self, l):
+        self._h.fill(l)
+
+    def prolong(self, l):
+        self._h.prolong(l)
+
+
+def regrid_finest(h, theta: float, **kw):
+    """regrid_levels of the finest level alone."""
+    return regrid_levels(h, theta, first=h.nlev - 1, **kw)

@@ -121,14 +121,15 @@ def _interiors_equal(oh, ph, G=4):
     return None
 
 
-@pytest.mark.parametrize("theta", [0.03, 0.1])
-def test_regrid_finest_fp64_equals_oracle_and_steps_on(capi, orc, theta):
-    """One regridding of a hierarchy's finest level (regrid.regrid_finest:
-    the parent level's flags on the device, grown, nested, clustered, cut by
-    the parent grids, and the data transfer) in the FP64 parity build: the
-    same grids and the same new patch data as the oracle's regridding step,
-    and two more coarse steps of the regridded hierarchies agree bit for
-    bit."""
+@pytest.mark.parametrize("theta,first", [(0.03, None), (0.1, None), (0.02, 1)])
+def test_regrid_fp64_equals_oracle_and_steps_on(capi, orc, theta, first):
+    """One regridding (regrid.regrid_levels: of the finest level, or of
+    levels 1 and 2 with level 2 made from the new level 1; each from the
+    parent level's flags on the device, grown, nested, clustered, fitted to
+    the nested region, cut by the parent grids, and the data transfer) in
+    the FP64 parity build: the same grids and the same new patch data as the
+    oracle's regridding, and two more coarse steps of the regridded
+    hierarchies agree bit for bit."""
     import synth.amr as SA
     from oracle import regrid as OR
     from oracle.amr import OHierarchy
@@ -145,14 +146,15 @@ def test_regrid_finest_fp64_equals_oracle_and_steps_on(capi, orc, theta):
         oh.initialise()
         ph.initialise()
         assert oh.coarse_step() == (ph.coarse_step() or ph.d_dt.item())
-        boxes, states, nfall = regrid.regrid_finest(ph, theta)
-        oboxes, ostates, onfall = OR.regrid_finest(oh, theta, empty=synth.empty_patch)
+        boxes, states, nfall = regrid.regrid_levels(ph, theta, first=first)
+        oboxes, ostates, onfall = OR.regrid_levels(oh, theta, first=first, empty=synth.empty_patch)
         torch.cuda.synchronize()
         assert boxes == oboxes and len(boxes) == 3 and len(boxes[2]) > 0
         assert int(nfall.item()) == onfall
-        for s_gpu, s_orc in zip(states[2], ostates[2]):
-            a = s_gpu.cpu().numpy()
-            assert np.array_equal(a[:, :s_orc.shape[1], :s_orc.shape[2], :s_orc.shape[3]], s_orc)
+        for l in range(1 if first == 1 else 2, 3):
+            for s_gpu, s_orc in zip(states[l], ostates[l]):
+                a = s_gpu.cpu().numpy()
+                assert np.array_equal(a[:, :s_orc.shape[1], :s_orc.shape[2], :s_orc.shape[3]], s_orc)
         ph.close()
         ph = None
         ph2 = Hierarchy(boxes, n0, states, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)

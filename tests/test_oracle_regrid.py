@@ -105,3 +105,28 @@ def test_regrid_without_flags_drops_the_level(orc, stepped):
     oh, H = stepped
     boxes, states, nfall = R.regrid_finest(oh, 2.0, empty=_empty)   # a normalised difference never exceeds 1
     assert len(boxes) == 1 and boxes[0] == H[0] and nfall == 0
+
+
+def test_regrid_levels_nest_each_new_level(orc):
+    """Regridding levels 1 and 2 of a 3-level hierarchy: level 1 from the
+    base's flags, then level 2 from the new level 1's; every new level-2
+    grid lies at least `margin` level-1 cells inside the new level 1."""
+    from oracle import regrid as R
+    from oracle.amr import OHierarchy
+    n0, margin = 16, 3
+    H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
+    st = [[SA.blast_patch(lo, hi, l, n0, G, p_in=10.0)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    oh = OHierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
+    oh.initialise()
+    oh.coarse_step()
+    boxes, states, nfall = R.regrid_levels(oh, 0.02, first=1, margin=margin, empty=_empty)
+    assert len(boxes) == 3 and boxes[0] == H[0] and nfall == 0
+    assert all(len(b) > 0 for b in boxes)
+    n1 = 2 * n0
+    inside = np.zeros((n1,) * 3, dtype=bool)
+    for lo, hi in boxes[1]:
+        inside[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
+    ok = _brute_inner(inside, margin)
+    for lo, hi in boxes[2]:
+        c = [(lo[d] // 2, hi[d] // 2) for d in range(3)]
+        assert ok[c[2][0]:c[2][1] + 1, c[1][0]:c[1][1] + 1, c[0][0]:c[0][1] + 1].all()

@@ -114,3 +114,34 @@ def test_transfer_items_and_masks_equal_oracle():
         m, mlo = regrid.transfer_mask(new, old)
         om, omlo = OT.mask(new, old)
         assert tuple(mlo) == tuple(omlo) and np.array_equal(m, om)
+
+
+def test_fit_boxes_equals_oracle_and_nests():
+    """regrid.fit_boxes (cluster boxes halved until they lie in the nested
+    region) against the oracle's fit on random flag fields inside random
+    L-shaped regions: the same boxes, each inside the region, together
+    covering every flag once."""
+    from oracle import cluster as OC
+    from oracle import regrid as OR
+    from paper_1112_1710_gb300 import regrid
+    rng = np.random.default_rng(11)
+    for t in range(40):
+        shape = tuple(int(v) for v in rng.integers(6, 16, size=3))
+        allowed = np.zeros(shape, dtype=bool)
+        for _ in range(2):
+            lo = [int(rng.integers(0, s // 2)) for s in shape]
+            hi = [int(rng.integers(lo[d] + 1, shape[d])) for d in range(3)]
+            allowed[lo[0]:hi[0] + 1, lo[1]:hi[1] + 1, lo[2]:hi[2] + 1] = True
+        flags = (rng.random(shape) < 0.3) & allowed
+        if not flags.any():
+            continue
+        boxes = OC.cluster(flags, 0.7, 2)
+        got = regrid.fit_boxes(boxes, flags, allowed)
+        want = OR.fit(boxes, flags, allowed)
+        assert [tuple(map(tuple, b)) for b in got] == [tuple(map(tuple, b)) for b in want], t
+        cover = np.zeros(shape, dtype=np.int32)
+        for lo, hi in got:
+            sl = tuple(slice(lo[d], hi[d] + 1) for d in range(3))
+            assert allowed[sl].all()
+            cover[sl] += 1
+        assert cover.max() <= 1 and np.all(cover[flags] == 1)
