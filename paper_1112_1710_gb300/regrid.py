@@ -141,6 +141,51 @@ def transfer_mask(new_box, old_boxes):
     return m, tuple(int(v) for v in clo)
 
 
+def transfer_masks(new_boxes, old_boxes):
+    """transfer_mask of every new patch at once: the old interiors and the
+    old face sets are painted once over the coarse bounding box of the new
+    patches (one array per mask bit's set), and each new patch's mask is
+    read off them.  Returns [(uint8 array (z, y, x), coarse lo)]."""
+    if not new_boxes:
+        return []
+    cb = [_cbox(lo, hi) for lo, hi in new_boxes]
+    glo = np.min([c[0] for c in cb], axis=0)
+    ghi = np.max([c[1] for c in cb], axis=0)
+    ext = ghi - glo + 1
+    cell = np.zeros((ext[2], ext[1], ext[0]), bool)
+    face = []
+    for a in range(3):
+        e = ext.copy()
+        e[a] += 1
+        face.append(np.zeros((e[2], e[1], e[0]), bool))
+    for olo, ohi in old_boxes:
+        ol, oh = _cbox(olo, ohi)
+        lo = np.maximum(ol, glo) - glo
+        hi = np.minimum(oh, ghi) - glo
+        if np.all(lo <= hi):
+            cell[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1] = True
+        for a in range(3):
+            flo, fhi = lo.copy(), hi.copy()
+            # faces ol_a .. oh_a + 1 along a, clipped to the painted range
+            flo[a] = max(ol[a], glo[a]) - glo[a]
+            fhi[a] = min(oh[a] + 1, ghi[a] + 1) - glo[a]
+            if np.all(flo <= fhi):
+                face[a][flo[2]:fhi[2] + 1, flo[1]:fhi[1] + 1, flo[0]:fhi[0] + 1] = True
+    out = []
+    for clo, chi in cb:
+        l, h = clo - glo, chi - glo
+        m = cell[l[2]:h[2] + 1, l[1]:h[1] + 1, l[0]:h[0] + 1].astype(np.uint8)
+        for a in range(3):
+            for sd in (0, 1):
+                sh = [0, 0, 0]
+                sh[a] = sd
+                f = face[a][l[2] + sh[2]:h[2] + sh[2] + 1, l[1] + sh[1]:h[1] + sh[1] + 1,
+                            l[0] + sh[0]:h[0] + sh[0] + 1]
+                m |= (f.astype(np.uint8) << (1 + 2 * a + sd)).astype(np.uint8)
+        out.append((m, tuple(int(v) for v in clo)))
+    return out
+
+
 def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
     """Fills the interiors of the new patches `fresh` (Patch objects of level
     l+1) from the previous iteration `old` (Patch objects of level l+1) and
@@ -155,13 +200,22 @@ def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
     items = transfer_items(nb, ob)
     if items:
         capi.mhd_transfer_copy(ctx, [p.desc() for p in old], [p.desc() for p in fresh], items, s)
-    masks, pitems = [], []
+    pitems = []
     clo_all = np.array([p.lo for p in coarse], np.int64)
     chi_all = np.array([p.hi for p in coarse], np.int64)
+    hm = transfer_masks(nb, ob)
+    # all masks in one device buffer (one copy), each at a 16-byte offset
+    offs, o = [], 0
+    for m, _ in hm:
+        offs.append(o)
+        o += (m.size + 15) // 16 * 16
+    buf = np.zeros(max(o, 16), np.uint8)
+    for (m, _), off in zip(hm, offs):
+        buf[off:off + m.size] = m.ravel()
+    dm = torch.as_tensor(buf, device=dev)
+    base = dm.data_ptr()
     for i, (lo, hi) in enumerate(nb):
-        m, mlo = transfer_mask((lo, hi), ob)
-        dm = torch.as_tensor(m, device=dev).contiguous()
-        masks.append(dm)
+        mlo = hm[i][1]
         cl, ch = _cbox(lo, hi)
         blo = np.maximum(clo_all, cl)
         bhi = np.minimum(chi_all, ch)
@@ -169,9 +223,10 @@ def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
             it = capi.mhd_prolong_new_item()
             it.coarse, it.fine = int(k), i
             it.box = capi.box(blo[k], bhi[k])
-            it.mask = dm.data_ptr()
+            it.mask = base + offs[i]
             it.mask_box = capi.box(mlo, tuple(int(v) for v in ch))
             pitems.append(it)
+    masks = [dm]
     nfall = torch.zeros(1, dtype=torch.int64, device=dev)
     if stream is not None:
         # the masks and the count were written on the current stream

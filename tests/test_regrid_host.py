@@ -145,3 +145,25 @@ def test_fit_boxes_equals_oracle_and_nests():
             assert allowed[sl].all()
             cover[sl] += 1
         assert cover.max() <= 1 and np.all(cover[flags] == 1)
+
+
+def test_transfer_masks_of_many_patches_equal_oracle():
+    """regrid.transfer_masks (the masks of all new patches read off old
+    interiors and face sets painted once) equal the oracle's brute-force
+    mask of each new patch."""
+    from oracle import transfer as OT
+    from paper_1112_1710_gb300 import regrid
+    rng = np.random.default_rng(13)
+
+    def box():
+        lo = 2 * rng.integers(0, 12, 3)
+        hi = lo + 2 * rng.integers(1, 6, 3) - 1
+        return tuple(int(v) for v in lo), tuple(int(v) for v in hi)
+
+    for _ in range(30):
+        old = [box() for _ in range(rng.integers(0, 6))]
+        new = [box() for _ in range(rng.integers(1, 5))]
+        got = regrid.transfer_masks(new, old)
+        for nb, (m, mlo) in zip(new, got):
+            om, omlo = OT.mask(nb, old)
+            assert tuple(mlo) == tuple(omlo) and np.array_equal(m, om)
