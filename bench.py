@@ -600,9 +600,10 @@ def run_ours(args):
 def amr_hierarchy():
     """The AMR workload: base 64^3 (one periodic patch) + 3 refined levels
     covering the blast shell r in [0.25, 0.35] (jittered per level) with
-    seeded uneven patches of 8^3-48^3 cells, 4 ghost layers, ratio 2."""
+    seeded uneven patches of 8^3-64^3 cells (about 2,000), 4 ghost layers,
+    ratio 2."""
     import synth.amr as SA
-    H = SA.shell_hierarchy(n0=64, levels=4, seed=1112, size_min=8, size_max=48)
+    H = SA.shell_hierarchy(n0=64, levels=4, seed=42, size_min=8, size_max=64)
     states = [[SA.blast_patch(lo, hi, l, 64, 4)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
     return H, states
 
@@ -907,7 +908,7 @@ def run_amr(args):
             "warmup": 1, "ms_per_step": main["ms_per_coarse_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "AMR blast-shell hierarchy: base 64^3 + 3 levels (ratio 2, subcycled), "
-                                   "%d patches of 8^3-48^3, 4 ghost layers; step = one coarse step" %
+                                   "%d patches of 8^3-64^3, 4 ghost layers; step = one coarse step" %
                                    sum(len(l) for l in H),
                        "patches_per_level": [len(l) for l in H],
                        "l2": "working set (GBs) larger than L2", "parallelism": "replicas"},
@@ -1325,7 +1326,7 @@ def measure_amr(args, local):
     res = {"metric": UNIT, "value": main["value"], "unit": UNIT, "ms_per_coarse_step": main["ms_per_coarse_step"],
            "dtype": "f32 (FP64 registers)",
            "config": {"workload": "AMR blast-shell hierarchy: base 64^3 + 3 levels (ratio 2, subcycled), %d patches "
-                                  "of 8^3-48^3, 4 ghost layers; step = one coarse step as a CUDA graph" %
+                                  "of 8^3-64^3, 4 ghost layers; step = one coarse step as a CUDA graph" %
                                   sum(len(l) for l in H), "patches_per_level": [len(l) for l in H],
                       "l2": "working set (GBs) larger than L2"},
            "runs": runs,

@@ -64,7 +64,7 @@ def test_box_distances_equal_oracle(PH):
 
 def test_order_of_the_amr_hierarchy_equals_oracle(PH):
     import synth.amr as SA
-    Hh = SA.shell_hierarchy(n0=64, levels=4, seed=1112, size_min=8, size_max=48)
+    Hh = SA.shell_hierarchy(n0=64, levels=4, seed=42, size_min=8, size_max=64)
     perms = PH.hilbert_order_hierarchy(Hh, 64)
     for l, bl in enumerate(Hh):
         assert list(perms[l]) == H.order_boxes(bl, H.bits_for(64 << l))

@@ -38,8 +38,8 @@ def hierarchies():
                                                              level0_split=2), 16
     H, _, _ = ST.deep_hierarchy(n0=16, levels=4, m=32, size_min=4, size_max=12)
     yield "turbulence 16^3, 4 levels", H, 16
-    yield "shell 64^3, 4 levels (the AMR bench workload)", SA.shell_hierarchy(n0=64, levels=4, seed=1112,
-                                                                              size_min=8, size_max=48), 64
+    yield "shell 64^3, 4 levels (the AMR bench workload)", SA.shell_hierarchy(n0=64, levels=4, seed=42,
+                                                                              size_min=8, size_max=64), 64
 
 
 @pytest.mark.parametrize("case", range(4))
