@@ -305,7 +305,11 @@ def autotune_record(h):
         return {"choice": "forced: advance_kernel %d" % ADVANCE["kernel"]}
     v, cz, ms = h.autotune()
     torch.cuda.synchronize()
-    return {"choice": choice_label(v), "chunk": cz, "ms_per_advance_of_finest_level": ms}
+    rec = {"choice": choice_label(v), "chunk": cz, "ms_per_advance_of_finest_level": ms}
+    if len(h.tuned) > 1:
+        rec["by_level"] = {str(l): {"choice": choice_label(t[0]), "chunk": t[1], "ms_per_advance": t[2]}
+                           for l, t in sorted(h.tuned.items())}
+    return rec
 
 
 def time_dtype(dtype, pr, args, local, world, stream, flush, contract=0):

@@ -486,25 +486,28 @@ class Hierarchy:
 
     def autotune(self, reps: int = 1, dt: float = 1e-7):
         """Lets mhd_autotune_advance choose this hierarchy's advance (staged
-        kernels, fused pass or fused kernel, tile shape and z-chunk) on the
-        finest level's batch with its first substep's update box (grown by 2
-        when subcycled), its flux-register captures and a small dt; the patch
-        state is unchanged.  The
-        contexts of the concurrent slots are cloned again so that they take
-        the same choice: call it before any step is captured, and after a
-        first coarse step (until then the fine levels' ghost zones hold
-        whatever the initial states held there).  Returns the autotuner's
-        (choice, chunk, ms)."""
-        l = self.nlev - 1
-        k = 2 if l > 0 else 0
+        kernels, fused pass or fused kernel, tile shape and z-chunk) for each
+        context on the batch it advances: the main context on the finest
+        level, and with concurrent levels each level's own slot context on
+        that level (without them the main context advances every level and
+        is tuned on the finest).  Each batch is timed with its first
+        substep's update box (grown by 2 when subcycled), its flux-register
+        captures and a small dt; the patch state is unchanged.  Call it after
+        a first coarse step (until then the fine levels' ghost zones hold
+        whatever the initial states held there) and before any step is
+        captured.  Returns the finest level's (choice, chunk, ms); every
+        level's is kept in `tuned`."""
         d = torch.full((1,), dt, dtype=torch.float64, device=self.device)
-        out = capi.mhd_autotune_advance(self.ctx, self.descs[l], d.data_ptr(), reps=reps,
-                                        grow=[k] * len(self.descs[l]), stream=self.sp,
-                                        caps=self.caps[(l, True)])
-        for i, (c, st) in enumerate(self.side):
-            capi.mhd_ctx_destroy(c)
-            self.side[i] = (capi.mhd_ctx_clone(self.ctx), st)
-        return out
+
+        def tune(ctx, l):
+            k = 2 if l > 0 else 0
+            return capi.mhd_autotune_advance(ctx, self.descs[l], d.data_ptr(), reps=reps,
+                                             grow=[k] * len(self.descs[l]), stream=self.sp,
+                                             caps=self.caps[(l, True)])
+        self.tuned = {self.nlev - 1: tune(self.ctx, self.nlev - 1)}
+        for l, (c, _) in enumerate(self.side):
+            self.tuned[l] = tune(c, l)
+        return self.tuned[self.nlev - 1]
 
     def cell_updates_per_coarse_step(self) -> int:
         return sum(p.cells * 2 ** l for l, pats in enumerate(self.levels) for p in pats)
