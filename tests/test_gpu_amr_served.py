@@ -105,13 +105,15 @@ def _print_table(capsys, title, linf, l1):
 AMR_LINF, AMR_L1 = 1e-5, 1e-6
 
 
-def test_fp32_amr_error_vs_oracle(capi, orc, capsys):
+@pytest.mark.parametrize("kernel", [1, 4])
+def test_fp32_amr_error_vs_oracle(capi, orc, capsys, kernel):
+    """With the staged kernels (1) and with the fused pass (4)."""
     from oracle.amr import OHierarchy
     from paper_1112_1710_gb300.amr import Hierarchy
     n0 = 16
     H, st = _shell(n0)
     oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
-    ctx = capi.mhd_ctx_create(emf=1)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)
     ph = None
     try:
         ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx)
@@ -123,7 +125,8 @@ def test_fp32_amr_error_vs_oracle(capi, orc, capsys):
         torch.cuda.synchronize()
         assert ph.device_status() == 0
         linf, l1 = _error_table(oh, ph)
-        _print_table(capsys, "FP32 AMR (blast shell, base 16^3 + 2 levels) vs FP64 oracle, 3 coarse steps", linf, l1)
+        _print_table(capsys, "FP32 AMR (blast shell, base 16^3 + 2 levels, advance_kernel %d) vs FP64 oracle, "
+                             "3 coarse steps" % kernel, linf, l1)
         assert np.all(linf <= AMR_LINF) and np.all(l1 <= AMR_L1), (linf, l1)
     finally:
         if ph is not None:
@@ -134,7 +137,8 @@ def test_fp32_amr_error_vs_oracle(capi, orc, capsys):
 DEEP_LINF, DEEP_L1 = 1e-5, 1e-6   # measured: L-inf 3-6e-7, L1 7e-8-2e-7
 
 
-def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys):
+@pytest.mark.parametrize("kernel", [1, 4])
+def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys, kernel):
     """The deep-AMR generator downscaled (base 16^3, 3 levels, k^-4 Mach-5
     field, beta 1), FP32 through the served level-step path, against the
     FP64 oracle (the served path takes its own FP32 CFL dt; the oracle is run
@@ -147,7 +151,7 @@ def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys):
     H, v, _ = ST.deep_hierarchy(n0=n0, levels=3, m=32, size_min=4, size_max=8)
     st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
     oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
-    ctx = capi.mhd_ctx_create(emf=1)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)
     ph = None
     try:
         ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f32", ctx=ctx,
@@ -163,8 +167,8 @@ def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys):
             oh.coarse_step(dt=ph.d_dt.item())
         assert ph.device_status() == 0
         linf, l1 = _error_table(oh, ph)
-        _print_table(capsys, "FP32 deep AMR (k^-4 Mach 5, base 16^3 + 2 levels, served path) vs FP64 oracle, "
-                             "3 coarse steps", linf, l1)
+        _print_table(capsys, "FP32 deep AMR (k^-4 Mach 5, base 16^3 + 2 levels, served path, advance_kernel %d) "
+                             "vs FP64 oracle, 3 coarse steps" % kernel, linf, l1)
         assert np.all(linf <= DEEP_LINF) and np.all(l1 <= DEEP_L1), (linf, l1)
         del srv
     finally:
