@@ -143,6 +143,52 @@ def test_orszag_tang_128_fp64_10_steps(capi, ctx, orc):
     assert capi.mhd_get_device_status(ctx) == 0
 
 
+@pytest.mark.parametrize("kernel", [2, 4])
+def test_orszag_tang_fused_paths_equal_staged(capi, kernel):
+    """The 2D Orszag-Tang patch (one cell along z, periodic z) through the
+    fused kernel (2) and the fused pass (4) in the FP64 parity build: the
+    staged kernels' bits after 5 steps with the CFL dt of each step."""
+    from paper_1112_1710_gb300.runner import PeriodicRunner
+    pr = synth.orszag_tang(64)
+    out = []
+    for k in (1, kernel):
+        ctx = capi.mhd_ctx_create(advance_kernel=k)
+        try:
+            p = to_patch(pr.state.copy(), pr.n, pr.g, pr.dx)
+            r = PeriodicRunner(p, ctx)
+            for _ in range(5):
+                r.step()
+            assert capi.mhd_get_device_status(ctx) == 0
+            out.append(p.state.cpu().numpy())
+        finally:
+            capi.mhd_ctx_destroy(ctx)
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 1), (3, 1, 2), (17, 1, 5)])
+def test_tiny_patches_every_advance_equals_staged(capi, n):
+    """Patches down to one cell (update boxes thinner than a tile, a block's
+    lower column and row outside the region): the fused kernel (2) and the
+    fused pass (4) give the staged bits in the FP64 parity build, k = 0 and
+    2."""
+    g = 4
+    for k in (0, 2):
+        st = random_state(n, g, seed=90 + k + sum(n))
+        out = []
+        for kernel in (1, 2, 4):
+            ctx = capi.mhd_ctx_create(advance_kernel=kernel)
+            try:
+                p = to_patch(st, n, g, (0.05, 0.06, 0.07))
+                d = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+                capi.mhd_patch_advance(ctx, [p.desc()], d.data_ptr(), grow=[k])
+                assert capi.mhd_get_device_status(ctx) == 0
+                out.append(p.state.cpu().numpy())
+            finally:
+                capi.mhd_ctx_destroy(ctx)
+        assert np.array_equal(out[0], out[1]), (k, "fused kernel")
+        assert np.array_equal(out[0], out[2]), (k, "fused pass")
+
+
 def test_blast_128_fp64_10_steps(capi, ctx_blast, orc):
     """3D blast, 128^3 + 2 ghosts, FP64 (the full-size 3D case, same launch
     configuration as the bench)."""
