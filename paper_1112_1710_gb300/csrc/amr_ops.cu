@@ -364,10 +364,28 @@ __global__ void __launch_bounds__(kThreads) k_capture(const DPatch* __restrict__
   const double dt = (*d_dt) * p.dt_scale;
   const int64_t x = lin3(p, ai[0], ai[1], ai[2]);
   if (cp.kind == 0) {
+    // the five components of the face's flux group as whole vectors
+    const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8) * p.snelem;
+    R f[5];
+    if constexpr (sizeof(R) == 4) {
+      const float4 a = reinterpret_cast<const float4*>(F)[x];
+      f[0] = a.x;
+      f[1] = a.y;
+      f[2] = a.z;
+      f[3] = a.w;
+      f[4] = reinterpret_cast<const float4*>(F + 4 * p.snelem)[x].x;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(F)[x];
+      const double2 b = reinterpret_cast<const double2*>(F + 2 * p.snelem)[x];
+      f[0] = a.x;
+      f[1] = a.y;
+      f[2] = b.x;
+      f[3] = b.y;
+      f[4] = *vgroup_at(F, p.snelem, x, 4);
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      const R* F = scr + p.scr + (int64_t)(SC_F + cp.axis * 8) * p.snelem;
-      const double v = dt * (double)*vgroup_at(F, p.snelem, x, q);
+      const double v = dt * (double)f[q];
       double* o = cp.dst + (int64_t)q * nv + e;
       *o = cp.mode ? *o + v : v;
     }
