@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
-    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "serve", "ot2d", "deep"])
+    ap.add_argument("--workload", default="patch", choices=["patch", "amr", "amr-step", "serve", "ot2d", "deep"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the staged advance (profiling runs: timings taken under a profiler mislead the tuner)")
     ap.add_argument("--advance", default="auto", choices=list(ADVANCE_KERNELS),
@@ -77,6 +77,7 @@ def parse():
                     help="default workload: time the single 128^3 patch only (not the deep-AMR, AMR and serving "
                          "configs)")
     ap.add_argument("--deep-steps", type=int, default=20, help="deep AMR: coarse steps through the served path")
+    ap.add_argument("--amr-base", type=int, default=64, help="amr-step: base grid of the AMR hierarchy")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="default run: requests per offered load of the serving config")
     return ap.parse_args()
@@ -610,14 +611,14 @@ def run_ours(args):
     print(json.dumps(line))
 
 
-def amr_hierarchy():
+def amr_hierarchy(n0=64):
     """The AMR workload: base 64^3 (one periodic patch) + 3 refined levels
     covering the blast shell r in [0.25, 0.35] (jittered per level) with
     seeded uneven patches of 8^3-64^3 cells (about 2,000), 4 ghost layers,
     ratio 2."""
     import synth.amr as SA
-    H = SA.shell_hierarchy(n0=64, levels=4, seed=42, size_min=8, size_max=64)
-    states = [[SA.blast_patch(lo, hi, l, 64, 4)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
+    H = SA.shell_hierarchy(n0=n0, levels=4, seed=42, size_min=8, size_max=64)
+    states = [[SA.blast_patch(lo, hi, l, n0, 4)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
     return H, states
 
 
@@ -838,16 +839,26 @@ def attribute_kernels(kt, work, dtype, steps):
     return out
 
 
-def roofline_of(rows, dtype, what):
-    """The roofline object of the dominant kernel of attribution rows."""
+# DRAM bytes per interior cell update of the AMR workload's coarse step, by
+# kernel, from one ncu capture of the same hierarchy at base 32^3
+# (profiles/k_pf_k_update_amr_dram.md); scaled by the cell updates.
+AMR_TRAFFIC_PER_UPDATE = {"k_pf": (2626.4e6 + 3329.4e6) / 24136064, "k_update": (6116.8e6 + 1434.7e6) / 24136064}
+
+
+def roofline_of(rows, dtype, what, traffic_per_update=None, updates=None):
+    """The roofline object of the dominant kernel of attribution rows (with
+    its DRAM traffic per coarse step when a per-update figure is given)."""
     hbm, hbm_src, sm_mhz = peaks()
     dom = max((k for k in rows if "bound" in rows[k]), key=lambda k: rows[k]["ms_per_coarse_step"])
     r = rows[dom]
+    traffic = None
+    if traffic_per_update and updates and dom in traffic_per_update:
+        traffic = traffic_per_update[dom] * updates
     if r["bound"] == "hbm":
         return {"kernel": dom, "bound": "hbm", "achieved": r["achieved_gbs"], "peak": r["peak_gbs"], "unit": "GB/s",
-                "frac": r["frac"], "traffic": None, "peak_source": hbm_src, "per": what}
+                "frac": r["frac"], "traffic": traffic, "peak_source": hbm_src, "per": what}
     return {"kernel": dom, "bound": "alu", "achieved": r["achieved_tflops"], "peak": r["peak_tflops"],
-            "unit": "TFLOP/s", "frac": r["frac"], "traffic": None, "peak_source": alu_peak_source(dtype, sm_mhz),
+            "unit": "TFLOP/s", "frac": r["frac"], "traffic": traffic, "peak_source": alu_peak_source(dtype, sm_mhz),
             "algorithmic_flops_per_coarse_step": r["algorithmic_flops"], "per": what}
 
 
@@ -1131,6 +1142,54 @@ def run_deep(args):
     print(json.dumps(line))
 
 
+def run_amr_step(args):
+    """`--workload amr-step`: the FP32 AMR hierarchy after initialisation,
+    tuning (or `--advance`) and `--warmup` eager coarse steps, then
+    `--steps` eager coarse steps with CUDA events around them, as one JSON
+    line: a short run of the AMR workload's kernels for profilers."""
+    import torch
+
+    from paper_1112_1710_gb300 import _build, capi
+    from paper_1112_1710_gb300.amr import Hierarchy
+    _build.build()
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    n0 = args.amr_base
+    H, states = amr_hierarchy(n0)
+    ctx = capi.mhd_ctx_create(device=local, **SOLVER, **adv_kw())
+    h = None
+    try:
+        h = Hierarchy(H, n0, states, (1.0 / n0,) * 3, g=4, dtype="f32", ctx=ctx, device="cuda:%d" % local)
+        h.initialise()
+        h.coarse_step()
+        tuned = autotune_record(h)
+        for _ in range(args.warmup):
+            h.coarse_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            h.coarse_step()
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        upd = h.cell_updates_per_coarse_step()
+        status = h.device_status()
+    finally:
+        if h is not None:
+            h.close()
+        capi.mhd_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": upd / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": "AMR hierarchy (base %d^3 + 3 levels, %d "
+                                                                      "patches), eager FP32 coarse steps (a short "
+                                                                      "run for profilers)" % (n0, sum(map(len, H))),
+                                                          "cell_updates_per_coarse_step": upd},
+                          "autotune": tuned, "device_status": status}))
+
+
 def deep_setup(n0=32, G=4, sample_every=8):
     """The deep-AMR hierarchy (base 32^3 + 7 levels on the k^-4 Mach-5 field)
     with every patch's initial state, and the oracle sample: every
@@ -1345,7 +1404,8 @@ def measure_amr(args, local):
            "runs": runs,
            "speedup_vs_per_patch_f64": {"f32_graph": main["value"] / runs["f64_per_patch"]["value"],
                                         "f64_graph": runs["f64_graph"]["value"] / runs["f64_per_patch"]["value"]},
-           "roofline": roofline_of(att["kernels"], "f32", "one eager FP32 coarse step, per-launch CUDA events"),
+           "roofline": roofline_of(att["kernels"], "f32", "one eager FP32 coarse step, per-launch CUDA events",
+                                   AMR_TRAFFIC_PER_UPDATE, main["cell_updates_per_coarse_step"]),
            "kernels": att["kernels"], "regrid": rg}
     if not args.no_cpu_baseline:
         items = [(states[l][i], tuple(hi[d] - lo[d] + 1 for d in range(3)), 4, (1.0 / 64 / 2 ** l,) * 3,
@@ -1453,6 +1513,8 @@ def main():
         run_ot2d(args)
     elif args.workload == "deep":
         run_deep(args)
+    elif args.workload == "amr-step":
+        run_amr_step(args)
     elif args.workload == "amr":
         run_amr(args)
     else:
