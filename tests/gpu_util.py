@@ -1,6 +1,5 @@
 """Helpers shared by the GPU parity tests (not collected as tests)."""
 import numpy as np
-import torch
 
 import synth
 

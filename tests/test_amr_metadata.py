@@ -1,7 +1,6 @@
 """The product's AMR metadata (ghost copies, prolongation and restriction
 items, flux-register captures and deposits) equals the oracle's, which is
 generated independently by brute-force box intersection -- no GPU."""
-import numpy as np
 import pytest
 
 import synth.amr as SA

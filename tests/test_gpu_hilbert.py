@@ -4,7 +4,6 @@ curve's properties at full size."""
 import itertools
 import random
 
-import numpy as np
 import pytest
 import torch
 
