@@ -159,7 +159,8 @@ def test_amr_fp32_conservation_and_divb(capi, capsys):
         capi.mhd_ctx_destroy(ctx)
 
 
-def test_amr_graph_replay_and_per_patch_path_equal_eager_batched(capi):
+@pytest.mark.parametrize("kernel", [0, 4])
+def test_amr_graph_replay_and_per_patch_path_equal_eager_batched(capi, kernel):
     """A captured coarse-step graph, and the plain one-call-per-patch advance,
     give the same bits as the eager batched path (the batched paths here
     advance the coarser levels on side streams, concurrently with the finer
@@ -168,8 +169,8 @@ def test_amr_graph_replay_and_per_patch_path_equal_eager_batched(capi):
     n0 = 16
     H = SA.shell_hierarchy(n0=n0, levels=3, size_min=4, size_max=8)
     st = _states(H, n0)
-    ctx = capi.mhd_ctx_create(emf=1)
-    ctx2 = capi.mhd_ctx_create(emf=1)  # one context (scratch arena) per stream
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)
+    ctx2 = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)  # one context (scratch arena) per stream
     a = b = c = None
     try:
         a = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx, concurrent=True)
@@ -200,7 +201,8 @@ def test_amr_graph_replay_and_per_patch_path_equal_eager_batched(capi):
         capi.mhd_ctx_destroy(ctx2)
 
 
-def test_turbulent_deep_hierarchy_fp64_parity(capi, orc):
+@pytest.mark.parametrize("kernel", [0, 4])
+def test_turbulent_deep_hierarchy_fp64_parity(capi, orc, kernel):
     """The deep-AMR workload's generator downscaled (base 16^3, 3 levels,
     k^-4 velocity field at Mach 5, plasma beta 1): three subcycled coarse
     steps of the FP64 parity build equal the oracle's on every patch."""
@@ -212,7 +214,7 @@ def test_turbulent_deep_hierarchy_fp64_parity(capi, orc):
     assert len(H) == 3 and all(len(l) > 0 for l in H)
     st = [[ST.turb_patch(lo, hi, l, n0, G, v)[0] for (lo, hi) in bl] for l, bl in enumerate(H)]
     oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params(emf=1))
-    ctx = capi.mhd_ctx_create(emf=1)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel)
     try:
         ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
         oh.initialise()

@@ -177,7 +177,8 @@ def test_fp32_deep_amr_served_error_vs_oracle(capi, orc, capsys, kernel):
         capi.mhd_ctx_destroy(ctx)
 
 
-def test_deep_amr_floors_fp64_parity(capi, orc, capsys):
+@pytest.mark.parametrize("kernel", [1, 4])
+def test_deep_amr_floors_fp64_parity(capi, orc, capsys, kernel):
     """The deep-AMR generator downscaled (base 16^3, 4 levels, k^-4 Mach-5
     field), where the method without floors reaches a non-positive pressure
     after 6 coarse steps: with the floors (reading R33; after every update and
@@ -193,7 +194,7 @@ def test_deep_amr_floors_fp64_parity(capi, orc, capsys):
     fl = dict(p_floor=6e-4, rho_floor=1e-3)
     oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G,
                     prm=orc.params(emf=1, **fl))
-    ctx = capi.mhd_ctx_create(emf=1, **fl)
+    ctx = capi.mhd_ctx_create(emf=1, advance_kernel=kernel, **fl)
     ph = None
     try:
         ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx,
@@ -212,8 +213,8 @@ def test_deep_amr_floors_fp64_parity(capi, orc, capsys):
         assert nfl > 0
         linf, l1 = _error_table(oh, ph)
         with capsys.disabled():
-            print("\nFP64 deep AMR with floors, 10 coarse steps: %d cells floored; max rel Linf vs oracle %.2e"
-                  % (nfl, linf.max()))
+            print("\nFP64 deep AMR with floors, 10 coarse steps, advance_kernel %d: %d cells floored; max rel "
+                  "Linf vs oracle %.2e" % (kernel, nfl, linf.max()))
         assert np.all(linf <= 1e-11), linf
         del srv
     finally:
