@@ -1462,6 +1462,9 @@ def measure_serve(args, local):
         clk.start()
         sat = serve(poisson_requests(nreq, math.inf, seed=4242))
         loads = {str(f): serve(poisson_requests(nreq, f * sat["requests_per_s"], seed=4242)) for f in (0.5, 0.8, 0.95)}
+        # the same stream at 0.8 of saturation under the batch sizing of the
+        # paper's load-balance distribution (Sec. 5; policy "balanced")
+        balanced = serve(poisson_requests(nreq, 0.8 * sat["requests_per_s"], seed=4242), "balanced")
         clocks = clk.stop()
         launches = sum(capi.mhd_launch_count(c) for c in be.ctxs) - l0
         # roofline of the FP32 requests: their kernels timed with per-launch
@@ -1497,7 +1500,7 @@ def measure_serve(args, local):
                                   "50/50, 64 GB HBM budget, seed 4242; Poisson arrivals at 0.5/0.8/0.95 of the "
                                   "saturation rate", "slots": args.slots, "batch_cells": args.batch_cells,
                       "setup_s": setup_s},
-           "saturation": sat, "offered_load": loads,
+           "saturation": sat, "offered_load": loads, "balanced_policy_at_0.8": balanced,
            "p50_ms": {k: v["p50_ms"] for k, v in loads.items()}, "p99_ms": {k: v["p99_ms"] for k, v in loads.items()},
            "fp64_sample": {"served_batched": served64, "plain_per_patch": pp,
                            "build": "FP64 contracted (fp64_contract = 1) on both paths"},
