@@ -464,13 +464,23 @@ def cpu_baseline(pr, steps):
     from oracle import oracle as O
     st = pr.state.copy()
     prm = O.params(**SOLVER)
+    O.set_threads(0)                       # every host core
+    cores = O.get_threads()
     t0 = time.perf_counter()
     O.run_periodic(st, pr.n, pr.g, pr.dx, prm, steps)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # and on one core, over two steps
+    st1 = pr.state.copy()
+    O.set_threads(1)
+    t1 = time.perf_counter()
+    O.run_periodic(st1, pr.n, pr.g, pr.dx, prm, 2)
+    dt1 = time.perf_counter() - t1
+    O.set_threads(0)
     return {"value": pr.cells * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d full FP64 steps of the %d^3 blast (ghost fill + dt + advance), %.1f s" %
-                      (steps, pr.n[0], dt)}
+                      (steps, pr.n[0], dt),
+            "single_thread": {"value": pr.cells * 2 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "2 full FP64 steps of the same blast, %.1f s" % dt1}}
 
 
 def cpu_baseline_sample(items, what):
@@ -494,7 +504,7 @@ def cpu_baseline_sample(items, what):
             O.advance(P, prm, dt, k)
             cells += n[0] * n[1] * n[2]
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.get_threads()
     return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%s: %d patch advances, %d interior cell updates, %.1f s" % (what, sum(len(i[4]) for i in items),
                                                                                   cells, dt)}
@@ -515,7 +525,7 @@ def run_reference(args):
     O.run_periodic(st, pr.n, pr.g, pr.dx, prm, args.steps)
     dt = time.perf_counter() - t0
     v = pr.cells * args.steps / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.get_threads()
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -1018,7 +1028,7 @@ def run_ot2d(args):
         O.run_periodic(st, pr.n, pr.g, pr.dx, O.params(gamma=5.0 / 3.0, cfl=0.4, limiter=0, emf=0), steps)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": pr.cells * steps / dt, "unit": UNIT,
-                                "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                                "cores": O.get_threads(),
                                 "kind": "oracle", "sample": "the whole workload (100 steps), %.1f s" % dt}
     print(json.dumps(line))
 

@@ -71,6 +71,17 @@ typedef struct {
 static int64_t orc_floored = 0;
 ORC_EXPORT int64_t orc_floor_count(void) { return orc_floored; }
 
+/* Threads of the OpenMP loops over independent cells (timing of the oracle
+ * on one core and on all; results do not depend on it).  n <= 0: all. */
+#ifdef _OPENMP
+#include <omp.h>
+ORC_EXPORT void orc_set_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+ORC_EXPORT int32_t orc_get_threads(void) { return omp_get_max_threads(); }
+#else
+ORC_EXPORT void orc_set_threads(int32_t n) { (void)n; }
+ORC_EXPORT int32_t orc_get_threads(void) { return 1; }
+#endif
+
 /* ------------------------------------------------------------------ */
 /* small helpers                                                        */
 /* ------------------------------------------------------------------ */

@@ -96,6 +96,10 @@ def bind(L):
     L.orc_floor.argtypes = [C.POINTER(_Patch), C.POINTER(_Params)]
     L.orc_floor_count.restype = C.c_int64
     L.orc_floor_count.argtypes = []
+    L.orc_set_threads.restype = None
+    L.orc_set_threads.argtypes = [C.c_int32]
+    L.orc_get_threads.restype = C.c_int32
+    L.orc_get_threads.argtypes = []
     L.orc_transfer_copy.restype = None
     L.orc_transfer_copy.argtypes = [C.POINTER(_Patch), i3, C.POINTER(_Patch), i3, C.c_int32, i3, i3]
     L.orc_prolong_new.restype = C.c_int64
@@ -289,6 +293,15 @@ def prolong_new(Pc, cglo, Pf, fglo, clo, chi, mask: np.ndarray, mlo, energy_mode
     mext = (mask.shape[2], mask.shape[1], mask.shape[0])
     return int(lib().orc_prolong_new(C.byref(Pc), _i3(cglo), C.byref(Pf), _i3(fglo), _i3(clo), _i3(chi),
                                      mask.ctypes.data, _i3(mlo), _i3(mext), int(energy_mode)))
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (n <= 0: all cores)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def flag(P: _Patch, prm: _Params, theta: float) -> np.ndarray:

@@ -230,3 +230,22 @@ def test_density_and_pressure_floor_closed_form(orc):
     keep = ~dens & ~pres
     assert np.array_equal(it[:, keep], ib[:, keep])
     assert np.array_equal(it[1:4], ib[1:4]) and np.array_equal(st[5:8], before[5:8])
+
+
+def test_thread_count_does_not_change_the_result(orc):
+    """The oracle's OpenMP loops run over independent cells (each writes its
+    own outputs; the CFL dt is a max), so one thread and all threads give the
+    same bits: the one-core and all-core timings time the same arithmetic."""
+    pr = synth.blast(16)
+    a, b = pr.state.copy(), pr.state.copy()
+    prm = orc.params()
+    try:
+        orc.set_threads(1)
+        assert orc.get_threads() == 1
+        orc.run_periodic(a, pr.n, pr.g, pr.dx, prm, 3)
+        orc.set_threads(0)
+        assert orc.get_threads() >= 1
+        orc.run_periodic(b, pr.n, pr.g, pr.dx, prm, 3)
+    finally:
+        orc.set_threads(0)
+    assert np.array_equal(a, b)
