@@ -142,12 +142,11 @@ typedef struct {
  * does every face of a box cell that exists in dst's face arrays (the outer
  * cell layer supplies the faces on the outer planes of those arrays), except
  * faces of dst's interior (normal index in [lo, hi+1], other indices inside
- * the interior).  A call writes cells and lower faces in a first pass and the
- * upper faces of each box's top layer in a second, so copies of one call
- * never write the same element in one pass; where the top face of one box is
- * the bottom face of another, the second pass wins (both sources hold that
- * face).  Source boxes must lie in src's interior and copies of one call must
- * read only interiors. */
+ * the interior).  A face that is the upper face of one box's top layer and
+ * the lower face of another box's bottom layer takes the first box's value
+ * (both sources hold that face); with that rule the copies of one call write
+ * disjoint elements, and a call is one launch.  Source boxes must lie in
+ * src's interior and copies of one call must read only interiors. */
 typedef struct {
   int32_t src, dst;    /* indices into the descriptor array                 */
   mhd_box box;         /* destination cells                                 */

@@ -65,10 +65,17 @@ struct PackedTasks {
   int packed;
 };
 
-// Ghost fill: pass 0 packed over the copies, pass 1 over (copy, axis) top
-// layers (item 3 c + a).  Restriction: the same split over the items.
-cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const PackedTasks& p0,
-                               const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s);
+// Ghost fill, one launch over the copies, one warp per task: rows row0 ..
+// row0 + ghost_rows(dtype) x (32 / W) - 1 (row = y + ext_y z) of copy `copy`
+// from x offset x0 (W = min(ext_x, 32); x0 a multiple of 32); excl holds each
+// copy's bottom-layer rectangles (DCopy.xr, nx).  Restriction: pass 0 packed
+// over the items, pass 1 over (item, axis) top layers (item 3 i + a).
+struct GhostTask {
+  int32_t copy, row0, x0, pad;
+};
+int ghost_rows(int dtype);
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const DExcl* excl,
+                               const GhostTask* tasks, int ntasks, const KernelTimer* tm, cudaStream_t s);
 cudaError_t prolong_launch(int dtype, const DPatch* coarse, const DPatch* fine, const DBoxItem* items,
                            const PackedTasks& p, const KernelTimer* tm, cudaStream_t s);
 cudaError_t restrict_launch(int dtype, const DPatch* fine, const DPatch* coarse, const DBoxItem* items,

@@ -85,6 +85,33 @@ __device__ __forceinline__ void box_cell(const int32_t* lo, const int32_t* ext, 
   c[2] = lo[2] + e / (ext[0] * ext[1]);
 }
 
+// Two consecutive elements x, x + 1 of an array (x even where vec is set),
+// each written if its flag is set; one vector store when both are.
+template <typename R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+template <typename R>
+__device__ __forceinline__ void st_pair(R* p, int64_t x, R v0, R v1, bool w0, bool w1, bool vec) {
+  if (vec && w0 && w1) {
+    typename Pair<R>::T v;
+    v.x = v0;
+    v.y = v1;
+    *reinterpret_cast<typename Pair<R>::T*>(p + x) = v;
+    return;
+  }
+  if (w0) p[x] = v0;
+  if (w1) p[x + 1] = v1;
+}
+// Are all eight arrays of p aligned for pair stores at even indices?
+template <typename R> __device__ __forceinline__ bool pair_aligned(const DPatch& p) {
+  uintptr_t o = 0;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o |= (uintptr_t)p.U[q];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o |= (uintptr_t)p.B[a];
+  return (o & (2 * sizeof(R) - 1)) == 0 && (p.s1 & 1) == 0 && (p.s2 & 1) == 0;
+}
+
 // ---------------------------------------------------------------- ghost copy
 // Cell c of the top layer of a box along axis a (the item's element e runs
 // over the two transverse axes, lower one fastest).
@@ -96,52 +123,114 @@ __device__ __forceinline__ void top_cell(const int32_t* lo, const int32_t* ext, 
   c[v] = lo[v] + e / ext[u];
 }
 
-// Pass 0: one thread per destination cell of a copy box (packed over the
-// copies): the five cell values and the lower face along each axis unless it
-// is a face of the destination's interior.  Pass 1: one thread per cell of
-// the top layer of a box along one axis (packed over copy x axis): the upper
-// face of that cell along the axis.
-template <typename R, int pass>
-__global__ void __launch_bounds__(kThreads) k_ghost2(const DPatch* __restrict__ P, const DCopy* __restrict__ C,
-                                                     const BlockTask* __restrict__ T,
-                                                     const int64_t* __restrict__ starts, int nitems, int packed) {
-  int item, e;
-  if (!list_elem(T[blockIdx.x], starts, nitems, packed, item, e)) return;
-  const int ci = pass == 0 ? item : item / 3;
-  const int ax = pass == 0 ? 0 : item - 3 * ci;
-  const DCopy cp = C[ci];
-  int di[3];
-  if constexpr (pass == 0) box_cell(cp.lo, cp.ext, e, di);
-  else top_cell(cp.lo, cp.ext, ax, e, di);
+// One launch for all copies of a fill, one warp per task: a group of rows
+// (x runs) of one copy box, the lanes along x (W = min(ext_x, 32) lanes per
+// row, 32 / W rows side by side; boxes wider than 32 are cut into x chunks),
+// kGhostRows such groups per task, their loads issued together, then their
+// stores.  Each element writes its five cell values (inside the
+// destination's arrays), its lower face along each axis, and on the box's
+// top layer along an axis its upper face; no face of the destination's
+// interior is written, nor one outside its face arrays.  A face that is the
+// upper face of one box's top layer and the lower face of another's bottom
+// layer takes the first box's value: the second skips it, from the
+// rectangles of its bottom layer the host lists (the transverse extent it
+// shares with a box whose top layer lies directly below it), so that no two
+// threads write one element.
+template <typename R> constexpr int kGhostRows = sizeof(R) == 4 ? 3 : 2;
+
+__device__ __forceinline__ bool excluded(const DCopy& cp, const DExcl* __restrict__ X, const int* di, int a) {
+  const int u = a == 0 ? 1 : 0, v = a == 2 ? 1 : 2;
+  for (int r = cp.xr; r < cp.xr + cp.nx; ++r) {
+    const DExcl x = X[r];
+    if (x.axis == a && di[u] >= x.lo[0] && di[u] <= x.hi[0] && di[v] >= x.lo[1] && di[v] <= x.hi[1]) return true;
+  }
+  return false;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 3) k_ghost2(const DPatch* __restrict__ P, const DCopy* __restrict__ C,
+                                                        const DExcl* __restrict__ X,
+                                                        const GhostTask* __restrict__ T, int ntasks) {
+  constexpr int GR = kGhostRows<R>;
+  const int wt = (int)blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5);
+  if (wt >= ntasks) return;
+  const int lane = (int)(threadIdx.x & 31);
+  const GhostTask t = T[wt];
+  const DCopy cp = C[t.copy];
   const DPatch& d = P[cp.dst];
   const DPatch& s = P[cp.src];
-  const int si[3] = {di[0] + cp.off[0], di[1] + cp.off[1], di[2] + cp.off[2]};
-  const int64_t xd = lin3(d, di[0], di[1], di[2]);
-  const int64_t xs = lin3(s, si[0], si[1], si[2]);
-  if constexpr (pass == 0) {
-    // loads first: a store would order every later load of a may-alias array
-    const bool cell_in = di[0] >= 0 && di[0] < d.N[0] && di[1] >= 0 && di[1] < d.N[1] && di[2] >= 0 && di[2] < d.N[2];
-    R u[5], b[3];
-    bool fw[3];
-    if (cell_in)
+  const int W = cp.ext[0] < 32 ? cp.ext[0] : 32;
+  const int RW = 32 / W;  // rows side by side
+  const int rr = lane / W;
+  const int xx = t.x0 + lane - rr * W;
+  const bool on = rr < RW && xx < cp.ext[0];
+  const int nrows = cp.ext[1] * cp.ext[2];
+  // the x-only conditions of the lane's element
+  const int i = cp.lo[0] + xx;
+  const bool xin = i >= 0 && i < d.N[0], xN = i == d.N[0];
+  const bool xint = i >= d.g && i < d.g + d.n[0], xtop = i == d.g + d.n[0];
+  const bool xbot = xx == 0, xlast = xx == cp.ext[0] - 1;
+  R u[GR][5], b[GR][3];
+  int64_t xd[GR];
+  unsigned w[GR];  // bit 0: the cell; bit 1 + a: the lower face along a; bit 4 + a: the upper face
+  // loads first: a store would order every later load of a may-alias array
 #pragma unroll
-      for (int q = 0; q < 5; ++q) u[q] = ((const R*)s.U[q])[xs];
+  for (int g = 0; g < GR; ++g) {
+    const int r = t.row0 + g * RW + rr;
+    w[g] = 0u;
+    xd[g] = 0;
+    if (!on || r >= nrows) continue;
+    const int yy = r % cp.ext[1], zz = r / cp.ext[1];
+    const int di[3] = {i, cp.lo[1] + yy, cp.lo[2] + zz};
+    const bool yin = di[1] >= 0 && di[1] < d.N[1], yN = di[1] == d.N[1];
+    const bool zin = di[2] >= 0 && di[2] < d.N[2], zN = di[2] == d.N[2];
+    const bool yint = di[1] >= d.g && di[1] < d.g + d.n[1], ytop = di[1] == d.g + d.n[1];
+    const bool zint = di[2] >= d.g && di[2] < d.g + d.n[2], ztop = di[2] == d.g + d.n[2];
+    xd[g] = lin3(d, di[0], di[1], di[2]);
+    const int64_t xs = lin3(s, di[0] + cp.off[0], di[1] + cp.off[1], di[2] + cp.off[2]);
+    // a face exists in the face arrays / is a face of the interior
+    const bool ex[3] = {(xin || xN) && yin && zin, xin && (yin || yN) && zin, xin && yin && (zin || zN)};
+    const bool own[3] = {(xint || xtop) && yint && zint, xint && (yint || ytop) && zint,
+                         xint && yint && (zint || ztop)};
+    const bool bot[3] = {xbot, yy == 0, zz == 0};
+    const bool last[3] = {xlast, yy == cp.ext[1] - 1, zz == cp.ext[2] - 1};
+    if (xin && yin && zin) {
+      w[g] |= 1u;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) u[g][q] = ((const R*)s.U[q])[xs];
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      fw[a] = face_exists(d, di, a) && !own_face(d, di, a);
-      if (fw[a]) b[a] = ((const R*)s.B[a])[xs];
+      if (ex[a] && !own[a] && !(bot[a] && cp.nx > 0 && excluded(cp, X, di, a))) {
+        w[g] |= 2u << a;
+        b[g][a] = ((const R*)s.B[a])[xs];
+      }
+      if (last[a]) {
+        int du[3] = {di[0], di[1], di[2]};
+        du[a] += 1;
+        if (face_exists(d, du, a) && !own_face(d, du, a)) w[g] |= 16u << a;
+      }
     }
-    if (cell_in)
+  }
 #pragma unroll
-      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd] = u[q];
+  for (int g = 0; g < GR; ++g) {
+    if (w[g] & 1u)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd[g]] = u[g][q];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (fw[a]) ((R*)d.B[a])[xd] = b[a];
-  } else {
-    int du[3] = {di[0], di[1], di[2]};
-    du[ax] += 1;
-    if (!face_exists(d, du, ax) || own_face(d, du, ax)) return;
-    ((R*)d.B[ax])[xd + sof(d, ax)] = ((const R*)s.B[ax])[xs + sof(s, ax)];
+      if (w[g] & (2u << a)) ((R*)d.B[a])[xd[g]] = b[g][a];
+  }
+  // the top layers' upper faces (a small share of the elements)
+#pragma unroll
+  for (int g = 0; g < GR; ++g) {
+    if (!(w[g] & 0x70u)) continue;
+    const int r = t.row0 + g * RW + rr;
+    const int64_t xs = lin3(s, i + cp.off[0], cp.lo[1] + r % cp.ext[1] + cp.off[1],
+                            cp.lo[2] + r / cp.ext[1] + cp.off[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (w[g] & (16u << a)) ((R*)d.B[a])[xd[g] + sof(d, a)] = ((const R*)s.B[a])[xs + sof(s, a)];
   }
 }
 
@@ -220,65 +309,86 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? MHD_PROLONG_MINB : 
     sq[a] = R(-0.5) * (crs[b][a] + crs[cc][a]);
     c0[a] = R(0.5) * (m[a][0] + m[a][1]) - sq[a];
   }
+  // The fine cells in x pairs (fa = 0, 1) for each (fb, fc), all unrolled so
+  // that every index into the reconstruction is a compile-time constant; the
+  // two values of a pair are stored together where the pair is aligned.
+  const int f0x = 2 * C3[0] - pf.glo[0];
+  const bool vec = ((f0x & 1) == 0) && pair_aligned<R>(pf);
+  // per axis and sub-index: the fine index inside the interior, on its upper
+  // face plane (a lower face of a fine cell is the patch's own when its
+  // normal index is one of the two and the other two are inside)
+  bool inI[3][2], onT[3][2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+#pragma unroll
+    for (int sb = 0; sb < 2; ++sb) {
+      const int f = 2 * C3[e] + sb - pf.glo[e];
+      inI[e][sb] = f >= pf.g && f < pf.g + pf.n[e];
+      onT[e][sb] = f == pf.g + pf.n[e];
+    }
+#pragma unroll
   for (int fc = 0; fc < 2; ++fc)
-    for (int fb = 0; fb < 2; ++fb)
+#pragma unroll
+    for (int fb = 0; fb < 2; ++fb) {
+      const int fy = 2 * C3[1] + fb - pf.glo[1], fz = 2 * C3[2] + fc - pf.glo[2];
+      const int64_t x = lin3(pf, f0x, fy, fz);
+      R uf[2][4], en[2], lf[2][3];
+#pragma unroll
       for (int fa = 0; fa < 2; ++fa) {
         const int sub[3] = {fa, fb, fc};
-        int fi[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) fi[d] = 2 * C3[d] + sub[d] - pf.glo[d];
-        const int64_t x = lin3(pf, fi[0], fi[1], fi[2]);
-        R uf[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           R u = uc[q];
           u = u + (fa ? h[q][0] : -h[q][0]);
           u = u + (fb ? h[q][1] : -h[q][1]);
           u = u + (fc ? h[q][2] : -h[q][2]);
-          uf[q] = u;
-          ((R*)pf.U[q])[x] = u;
+          uf[fa][q] = u;
         }
         R bc[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          R f0 = pface<R>(a, sub[a], sub, m, qs, lin, c0);
-          R f1 = pface<R>(a, sub[a] + 1, sub, m, qs, lin, c0);
-          bc[a] = R(0.5) * (f0 + f1);
+          lf[fa][a] = pface<R>(a, sub[a], sub, m, qs, lin, c0);
+          const R f1 = pface<R>(a, sub[a] + 1, sub, m, qs, lin, c0);
+          bc[a] = R(0.5) * (lf[fa][a] + f1);
         }
-        R en = ec;
-        en = en + (fa ? he[0] : -he[0]);
-        en = en + (fb ? he[1] : -he[1]);
-        en = en + (fc ? he[2] : -he[2]);
-        R kef = R(0.5) * (uf[1] * uf[1] + uf[2] * uf[2] + uf[3] * uf[3]) / uf[0];
-        R mef = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
-        ((R*)pf.U[4])[x] = en + kef + mef;
+        R e = ec;
+        e = e + (fa ? he[0] : -he[0]);
+        e = e + (fb ? he[1] : -he[1]);
+        e = e + (fc ? he[2] : -he[2]);
+        const R kef = R(0.5) * (uf[fa][1] * uf[fa][1] + uf[fa][2] * uf[fa][2] + uf[fa][3] * uf[fa][3]) / uf[fa][0];
+        const R mef = R(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+        en[fa] = e + kef + mef;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) st_pair<R>((R*)pf.U[q], x, uf[0][q], uf[1][q], true, true, vec);
+      st_pair<R>((R*)pf.U[4], x, en[0], en[1], true, true, vec);
+      // lower faces of both cells along each axis, never the patch's own
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        bool own[2];
+#pragma unroll
+        for (int fa = 0; fa < 2; ++fa) {
+          const int sub[3] = {fa, fb, fc};
+          const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+          own[fa] = (inI[a][sub[a]] || onT[a][sub[a]]) && inI[b1][sub[b1]] && inI[b2][sub[b2]];
+        }
+        st_pair<R>((R*)pf.B[a], x, lf[0][a], lf[1][a], !own[0], !own[1], vec);
+      }
+      // upper faces of cells in the array's last layer along an axis
+#pragma unroll
+      for (int fa = 0; fa < 2; ++fa) {
+        const int sub[3] = {fa, fb, fc};
+        const int fi[3] = {f0x + fa, fy, fz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
-          const int lo_t = t1 < t2 ? t1 : t2, hi_t = t1 < t2 ? t2 : t1;
-          for (int up = 0; up < 2; ++up) {
-            int fidx[3] = {fi[0], fi[1], fi[2]};
-            if (up) {
-              if (fi[a] != pf.N[a] - 1) continue;
-              fidx[a] += 1;
-            }
-            if (own_face(pf, fidx, a)) continue;
-            const int pos = sub[a] + up;
-            R v;
-            if (pos == 1) {
-              R sl = sub[lo_t] ? R(0.5) * lin[a][lo_t] : R(-0.5) * lin[a][lo_t];
-              R sh = sub[hi_t] ? R(0.5) * lin[a][hi_t] : R(-0.5) * lin[a][hi_t];
-              v = c0[a] + sl + sh;
-            } else {
-              const int sd = pos == 2;
-              R sl = sub[lo_t] ? qs[a][sd][lo_t] : -qs[a][sd][lo_t];
-              R sh = sub[hi_t] ? qs[a][sd][hi_t] : -qs[a][sd][hi_t];
-              v = m[a][sd] + sl + sh;
-            }
-            ((R*)pf.B[a])[lin3(pf, fidx[0], fidx[1], fidx[2])] = v;
-          }
+          if (fi[a] != pf.N[a] - 1) continue;
+          int fu[3] = {fi[0], fi[1], fi[2]};
+          fu[a] += 1;
+          if (own_face(pf, fu, a)) continue;
+          ((R*)pf.B[a])[x + fa + sof(pf, a)] = pface<R>(a, sub[a] + 1, sub, m, qs, lin, c0);
         }
       }
+    }
 }
 
 // ---------------------------------------------------------------- restriction
@@ -580,24 +690,16 @@ __global__ void __launch_bounds__(kThreads) k_correct(const DPatch* __restrict__
 
 }  // namespace
 
-cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const PackedTasks& p0,
-                               const PackedTasks& p1, const KernelTimer* tm, cudaStream_t s) {
-  if (p0.nblocks) {
-    if (dtype == 0)
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double, 0><<<p0.nblocks, kThreads, 0, s>>>(patches, copies, p0.tasks,
-                                                                                    p0.starts, p0.nitems, p0.packed)));
-    else
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float, 0><<<p0.nblocks, kThreads, 0, s>>>(patches, copies, p0.tasks,
-                                                                                   p0.starts, p0.nitems, p0.packed)));
-  }
-  if (p1.nblocks) {
-    if (dtype == 0)
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double, 1><<<p1.nblocks, kThreads, 0, s>>>(patches, copies, p1.tasks,
-                                                                                    p1.starts, p1.nitems, p1.packed)));
-    else
-      MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float, 1><<<p1.nblocks, kThreads, 0, s>>>(patches, copies, p1.tasks,
-                                                                                   p1.starts, p1.nitems, p1.packed)));
-  }
+int ghost_rows(int dtype) { return dtype == 0 ? kGhostRows<double> : kGhostRows<float>; }
+
+cudaError_t ghost_fill2_launch(int dtype, const DPatch* patches, const DCopy* copies, const DExcl* excl,
+                               const GhostTask* tasks, int ntasks, const KernelTimer* tm, cudaStream_t s) {
+  if (ntasks == 0) return cudaSuccess;
+  const int nb = (ntasks + kThreads / 32 - 1) / (kThreads / 32);
+  if (dtype == 0)
+    MHD_TIMED(tm, K_GHOST, s, (k_ghost2<double><<<nb, kThreads, 0, s>>>(patches, copies, excl, tasks, ntasks)));
+  else
+    MHD_TIMED(tm, K_GHOST, s, (k_ghost2<float><<<nb, kThreads, 0, s>>>(patches, copies, excl, tasks, ntasks)));
   return cudaGetLastError();
 }
 

@@ -1282,22 +1282,57 @@ mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, 
       o.off[a] = (m.box.lo[a] + m.offset[a] - S.glo[a]) - lo;
       cnt *= o.ext[a];
     }
-    o.start = 0;
     counts[t] = cnt;
   }
-  std::vector<std::array<int32_t, 3>> ext(nlist);
-  for (int t = 0; t < nlist; ++t)
-    for (int a = 0; a < 3; ++a) ext[t][a] = dc[t].ext[a];
-  PackedTasks p0{}, p1{};
-  if ((r = packed_table(c, counts, false, p0))) return r;
-  if ((r = packed_table(c, top_counts(ext), true, p1))) return r;
-  void *d_p = nullptr, *d_c = nullptr;
+  // Bottom-layer rectangles: where copy u's top layer along a lies directly
+  // below copy t's bottom layer (same destination), the faces between them
+  // take u's values and t skips them over the transverse extent they share.
+  std::vector<std::vector<int32_t>> by_dst(n);
+  for (int t = 0; t < nlist; ++t) by_dst[dc[t].dst].push_back(t);
+  std::vector<DExcl> ex;
+  for (int t = 0; t < nlist; ++t) {
+    DCopy& o = dc[t];
+    o.xr = (int32_t)ex.size();
+    for (int32_t u : by_dst[o.dst]) {
+      if (u == t) continue;
+      const DCopy& A = dc[u];
+      for (int a = 0; a < 3; ++a) {
+        if (A.lo[a] + A.ext[a] != o.lo[a]) continue;
+        DExcl x{};
+        x.axis = a;
+        bool meet = true;
+        for (int k = 0, e = 0; e < 3; ++e) {
+          if (e == a) continue;
+          x.lo[k] = std::max(A.lo[e], o.lo[e]);
+          x.hi[k] = std::min(A.lo[e] + A.ext[e], o.lo[e] + o.ext[e]) - 1;
+          if (x.lo[k] > x.hi[k]) meet = false;
+          ++k;
+        }
+        if (meet) ex.push_back(x);
+      }
+    }
+    o.nx = (int32_t)ex.size() - o.xr;
+  }
+  if (ex.empty()) ex.push_back(DExcl{});  // a valid table address
+  // warp tasks: groups of rows of each copy (lanes along x, see GhostTask)
+  std::vector<GhostTask> tasks;
+  const int gr = ghost_rows(dtype);
+  for (int t = 0; t < nlist; ++t) {
+    const DCopy& o = dc[t];
+    const int W = std::min(o.ext[0], 32), rows = o.ext[1] * o.ext[2], step = gr * (32 / W);
+    for (int x0 = 0; x0 < o.ext[0]; x0 += 32)
+      for (int r0 = 0; r0 < rows; r0 += step) tasks.push_back(GhostTask{t, r0, x0, 0});
+  }
+  if (tasks.size() > 0x7fffffff / kThreads) return fail(c, MHD_EINVAL, "launch too large");
+  void *d_p = nullptr, *d_c = nullptr, *d_x = nullptr, *d_t = nullptr;
   if ((r = table(c, dp.data(), dp.size() * sizeof(DPatch), &d_p))) return r;
   if ((r = table(c, dc.data(), dc.size() * sizeof(DCopy), &d_c))) return r;
-  cudaError_t e = ghost_fill2_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, p0, p1, timer_of(c),
-                                     (cudaStream_t)stream);
+  if ((r = table(c, ex.data(), ex.size() * sizeof(DExcl), &d_x))) return r;
+  if ((r = table(c, tasks.data(), tasks.size() * sizeof(GhostTask), &d_t))) return r;
+  cudaError_t e = ghost_fill2_launch(dtype, (const DPatch*)d_p, (const DCopy*)d_c, (const DExcl*)d_x,
+                                     (const GhostTask*)d_t, (int)tasks.size(), timer_of(c), (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "ghost fill launch");
-  c->launches += 2;
+  c->launches += 1;
   return MHD_OK;
 }
 

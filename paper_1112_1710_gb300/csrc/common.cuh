@@ -121,7 +121,16 @@ struct DCopy {
   int32_t lo[3];     // destination array indices of the box corner
   int32_t ext[3];    // box extents
   int32_t off[3];    // source array index = destination array index + off
-  int32_t start;     // first linear element of this copy in the launch
+  int32_t xr, nx;    // the copy's bottom-layer rectangles: DExcl xr .. xr + nx - 1
+};
+
+// A rectangle of a copy box's bottom layer along `axis` whose lower faces
+// another copy of the same destination writes (as the upper faces of its top
+// layer): the two transverse axes in increasing order, destination array
+// indices, inclusive.
+struct DExcl {
+  int32_t axis;
+  int32_t lo[2], hi[2];
 };
 
 // scratch arrays of the staged advance (offsets in units of one array)

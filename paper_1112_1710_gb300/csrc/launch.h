@@ -106,11 +106,6 @@ cudaError_t cfl_dt_launch(int dtype, const DPatch* patches, const BlockTask* tas
                           double gamma, double cfl, double* d_out, int* d_status,
                           const KernelTimer* tm, cudaStream_t s);
 
-// Ghost copies (tasks: patch field = copy index).
-cudaError_t ghost_fill_launch(int dtype, const DPatch* patches, const DCopy* copies,
-                              const BlockTask* tasks, int nblocks, const KernelTimer* tm,
-                              cudaStream_t s);
-
 // Conservation sums (tasks span interiors); partials holds nblocks*8 doubles.
 cudaError_t sums_launch(int dtype, const DPatch* patches, const BlockTask* tasks, int nblocks,
                         double* partials, double* d_out8, const KernelTimer* tm, cudaStream_t s);

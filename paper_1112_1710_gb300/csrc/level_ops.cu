@@ -98,55 +98,6 @@ cudaError_t cfl_dt_launch(int dtype, const DPatch* patches, const BlockTask* tas
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- ghost fill
-// One thread per destination cell of a copy box: the five cell values, the
-// lower face along each axis unless it is a face of the destination's
-// interior, and the array's extra upper face on the last cell of an axis.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_ghost(const DPatch* __restrict__ P,
-                                                    const DCopy* __restrict__ C,
-                                                    const BlockTask* __restrict__ T) {
-  const BlockTask t = T[blockIdx.x];
-  const DCopy cp = C[t.patch];
-  const int e = t.start + threadIdx.x;
-  if (e >= cp.ext[0] * cp.ext[1] * cp.ext[2]) return;
-  const int id[3] = {cp.lo[0] + e % cp.ext[0], cp.lo[1] + (e / cp.ext[0]) % cp.ext[1],
-                     cp.lo[2] + e / (cp.ext[0] * cp.ext[1])};
-  const DPatch& d = P[cp.dst];
-  const DPatch& s = P[cp.src];
-  const int64_t xd = (int64_t)id[0] + (int64_t)id[1] * d.s1 + (int64_t)id[2] * d.s2;
-  const int64_t xs = (int64_t)(id[0] + cp.off[0]) + (int64_t)(id[1] + cp.off[1]) * s.s1 +
-                     (int64_t)(id[2] + cp.off[2]) * s.s2;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd] = ((const R*)s.U[q])[xs];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    bool interior_face = true;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int top = (b == a) ? d.g + d.n[b] : d.g + d.n[b] - 1;
-      if (id[b] < d.g || id[b] > top) interior_face = false;
-    }
-    if (!interior_face) ((R*)d.B[a])[xd] = ((const R*)s.B[a])[xs];
-    if (id[a] == d.N[a] - 1) {
-      const int64_t sa_d = a == 0 ? 1 : (a == 1 ? d.s1 : d.s2);
-      const int64_t sa_s = a == 0 ? 1 : (a == 1 ? s.s1 : s.s2);
-      ((R*)d.B[a])[xd + sa_d] = ((const R*)s.B[a])[xs + sa_s];
-    }
-  }
-}
-
-cudaError_t ghost_fill_launch(int dtype, const DPatch* patches, const DCopy* copies,
-                              const BlockTask* tasks, int nblocks, const KernelTimer* tm,
-                              cudaStream_t s) {
-  if (nblocks == 0) return cudaSuccess;
-  if (dtype == 0)
-    MHD_TIMED(tm, K_GHOST, s, (k_ghost<double><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks)));
-  else
-    MHD_TIMED(tm, K_GHOST, s, (k_ghost<float><<<nblocks, kThreads, 0, s>>>(patches, copies, tasks)));
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------- sums
 // Two passes with a fixed reduction tree, so the result is reproducible.
 template <typename R>

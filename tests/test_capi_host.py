@@ -140,3 +140,80 @@ def test_copy_list_semantics_equal_oracle_periodic_fill(orc, n, g):
         ext = list(N)
         ext[q] += 1
         assert np.array_equal(a[5 + q, :ext[2], :ext[1], :ext[0]], b[5 + q, :ext[2], :ext[1], :ext[0]])
+
+
+def apply_copies_one_launch(st, n, g, copies, order):
+    """The rule of the one-launch ghost fill, on a numpy patch: every copy
+    writes its cells, the lower faces of its cells and the upper faces of its
+    top layer, in one pass over the copies in any `order`, except the lower
+    faces of its bottom layer along an axis over the transverse extent it
+    shares with another copy whose top layer lies directly below (that
+    copy's upper faces): the rectangles the library lists per copy."""
+    N = [v + 2 * g for v in n]
+    src = st.copy()
+
+    def interior_face(d, a):
+        return all(g <= d[b] <= (g + n[b] if b == a else g + n[b] - 1) for b in range(3))
+
+    def face_exists(d, a):
+        return all(0 <= d[b] <= (N[b] if b == a else N[b] - 1) for b in range(3))
+
+    boxes = [(list(c.box.lo), list(c.box.hi)) for c in copies]
+    rects = []
+    for t, (lo, hi) in enumerate(boxes):
+        r = []
+        for u, (ulo, uhi) in enumerate(boxes):
+            for a in range(3):
+                if u == t or uhi[a] + 1 != lo[a]:
+                    continue
+                tr = [e for e in range(3) if e != a]
+                x = [(max(ulo[e], lo[e]), min(uhi[e], hi[e])) for e in tr]
+                if all(x0 <= x1 for x0, x1 in x):
+                    r.append((a, tr, x))
+        rects.append(r)
+    for t in order:
+        c = copies[t]
+        lo, hi, off = boxes[t][0], boxes[t][1], list(c.offset)
+        for k in range(lo[2], hi[2] + 1):
+            for j in range(lo[1], hi[1] + 1):
+                for i in range(lo[0], hi[0] + 1):
+                    gl = (i, j, k)
+                    d = (i + g, j + g, k + g)
+                    s = (i + off[0] + g, j + off[1] + g, k + off[2] + g)
+                    if all(0 <= d[b] < N[b] for b in range(3)):
+                        st[:5, d[2], d[1], d[0]] = src[:5, s[2], s[1], s[0]]
+                    for a in range(3):
+                        skip = gl[a] == lo[a] and any(
+                            ra == a and all(x0 <= gl[e] <= x1 for e, (x0, x1) in zip(tr, x))
+                            for ra, tr, x in rects[t])
+                        if face_exists(d, a) and not interior_face(d, a) and not skip:
+                            st[5 + a, d[2], d[1], d[0]] = src[5 + a, s[2], s[1], s[0]]
+                        if gl[a] == hi[a]:
+                            du, su = list(d), list(s)
+                            du[a] += 1
+                            su[a] += 1
+                            if face_exists(du, a) and not interior_face(du, a):
+                                st[5 + a, du[2], du[1], du[0]] = src[5 + a, su[2], su[1], su[0]]
+
+
+@pytest.mark.parametrize("n,g", [((6, 5, 4), 2), ((7, 3, 1), 2), ((2, 3, 2), 4), ((1, 1, 1), 2)])
+def test_one_launch_copy_rule_equals_oracle_periodic_fill(orc, n, g):
+    """On random data (faces shared by two copies differ), the one-launch rule
+    gives the two-pass result in any order of the copies: no element is
+    written twice with different values."""
+    import synth
+    from paper_1112_1710_gb300.patch import periodic_copies
+    rng = np.random.default_rng(10)
+    st = rng.normal(size=synth.patch_shape(n, g))
+    b = st.copy()
+    orc.fill_periodic(orc.patch(b, n, g, (1.0, 1.0, 1.0)))
+    N = [v + 2 * g for v in n]
+    copies = periodic_copies(n, g)
+    for order in (range(len(copies)), range(len(copies) - 1, -1, -1), rng.permutation(len(copies))):
+        a = st.copy()
+        apply_copies_one_launch(a, n, g, copies, list(order))
+        assert np.array_equal(a[:5, :N[2], :N[1], :N[0]], b[:5, :N[2], :N[1], :N[0]])
+        for q in range(3):
+            ext = list(N)
+            ext[q] += 1
+            assert np.array_equal(a[5 + q, :ext[2], :ext[1], :ext[0]], b[5 + q, :ext[2], :ext[1], :ext[0]])
