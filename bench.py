@@ -493,21 +493,31 @@ def cpu_baseline_sample(items, what):
     from oracle import oracle as O
     O.build()
     prm = O.params(**SOLVER)
-    cells = 0
-    t0 = time.perf_counter()
-    for st, n, g, dx, ks, periodic in items:
-        P = O.patch(st.copy(), n, g, dx)
-        for k in ks:
-            if periodic:
-                O.fill_periodic(P)
-            dt = O.cfl_dt(P, prm)
-            O.advance(P, prm, dt, k)
-            cells += n[0] * n[1] * n[2]
-    dt = time.perf_counter() - t0
+
+    def run(sample):
+        cells = 0
+        t0 = time.perf_counter()
+        for st, n, g, dx, ks, periodic in sample:
+            P = O.patch(st.copy(), n, g, dx)
+            for k in ks:
+                if periodic:
+                    O.fill_periodic(P)
+                dt = O.cfl_dt(P, prm)
+                O.advance(P, prm, dt, k)
+                cells += n[0] * n[1] * n[2]
+        return cells, time.perf_counter() - t0
+    O.set_threads(0)                       # every host core
     cores = O.get_threads()
+    cells, dt = run(items)
+    # and on one core, over every 4th item of the sample
+    O.set_threads(1)
+    c1, dt1 = run(items[::4])
+    O.set_threads(0)
     return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%s: %d patch advances, %d interior cell updates, %.1f s" % (what, sum(len(i[4]) for i in items),
-                                                                                  cells, dt)}
+                                                                                  cells, dt),
+            "single_thread": {"value": c1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "every 4th item of that sample: %d interior cell updates, %.1f s" % (c1, dt1)}}
 
 
 def run_reference(args):
