@@ -160,77 +160,88 @@ __global__ void __launch_bounds__(kThreads, 3) k_ghost2(const DPatch* __restrict
   const DPatch& d = P[cp.dst];
   const DPatch& s = P[cp.src];
   const int W = cp.ext[0] < 32 ? cp.ext[0] : 32;
+  int xr;
+  const int rr = divmod24(lane, W, xr);
   const int RW = 32 / W;  // rows side by side
-  const int rr = lane / W;
-  const int xx = t.x0 + lane - rr * W;
+  const int xx = t.x0 + xr;
   const bool on = rr < RW && xx < cp.ext[0];
   const int nrows = cp.ext[1] * cp.ext[2];
-  // the x-only conditions of the lane's element
+  const int64_t ds1 = d.s1, ds2 = d.s2, ss1 = s.s1, ss2 = s.s2;
+  const int g = d.g;
+  // Per axis, with c the element's index along it: in the arrays (0 <= c <
+  // N), on the arrays' extra face plane (c == N), inside the interior (g <=
+  // c < g + n), on its upper face plane (c == g + n).  A lower face along a
+  // exists if c_a is in the arrays or on the extra plane and the other two
+  // are in the arrays; it is the interior's own if c_a is inside or on the
+  // upper plane and the other two are inside.  The upper face of a cell is
+  // the lower face of c_a + 1.
   const int i = cp.lo[0] + xx;
   const bool xin = i >= 0 && i < d.N[0], xN = i == d.N[0];
-  const bool xint = i >= d.g && i < d.g + d.n[0], xtop = i == d.g + d.n[0];
+  const bool xint = i >= g && i < g + d.n[0], xtop = i == g + d.n[0];
+  const bool xin1 = i >= -1 && i < d.N[0], xint1 = i >= g - 1 && i < g + d.n[0];  // for c_x + 1
   const bool xbot = xx == 0, xlast = xx == cp.ext[0] - 1;
   R u[GR][5], b[GR][3];
-  int64_t xd[GR];
+  int64_t xd[GR], xs[GR];
   unsigned w[GR];  // bit 0: the cell; bit 1 + a: the lower face along a; bit 4 + a: the upper face
   // loads first: a store would order every later load of a may-alias array
 #pragma unroll
-  for (int g = 0; g < GR; ++g) {
-    const int r = t.row0 + g * RW + rr;
-    w[g] = 0u;
-    xd[g] = 0;
+  for (int gg = 0; gg < GR; ++gg) {
+    const int r = t.row0 + gg * RW + rr;
+    w[gg] = 0u;
+    xd[gg] = xs[gg] = 0;
     if (!on || r >= nrows) continue;
-    const int yy = r % cp.ext[1], zz = r / cp.ext[1];
-    const int di[3] = {i, cp.lo[1] + yy, cp.lo[2] + zz};
-    const bool yin = di[1] >= 0 && di[1] < d.N[1], yN = di[1] == d.N[1];
-    const bool zin = di[2] >= 0 && di[2] < d.N[2], zN = di[2] == d.N[2];
-    const bool yint = di[1] >= d.g && di[1] < d.g + d.n[1], ytop = di[1] == d.g + d.n[1];
-    const bool zint = di[2] >= d.g && di[2] < d.g + d.n[2], ztop = di[2] == d.g + d.n[2];
-    xd[g] = lin3(d, di[0], di[1], di[2]);
-    const int64_t xs = lin3(s, di[0] + cp.off[0], di[1] + cp.off[1], di[2] + cp.off[2]);
-    // a face exists in the face arrays / is a face of the interior
+    int yy;
+    const int zz = divmod24(r, cp.ext[1], yy);
+    const int j = cp.lo[1] + yy, k = cp.lo[2] + zz;
+    const bool yin = j >= 0 && j < d.N[1], yN = j == d.N[1];
+    const bool zin = k >= 0 && k < d.N[2], zN = k == d.N[2];
+    const bool yint = j >= g && j < g + d.n[1], ytop = j == g + d.n[1];
+    const bool zint = k >= g && k < g + d.n[2], ztop = k == g + d.n[2];
+    xd[gg] = (int64_t)i + (int64_t)j * ds1 + (int64_t)k * ds2;
+    xs[gg] = (int64_t)(i + cp.off[0]) + (int64_t)(j + cp.off[1]) * ss1 + (int64_t)(k + cp.off[2]) * ss2;
     const bool ex[3] = {(xin || xN) && yin && zin, xin && (yin || yN) && zin, xin && yin && (zin || zN)};
     const bool own[3] = {(xint || xtop) && yint && zint, xint && (yint || ytop) && zint,
                          xint && yint && (zint || ztop)};
     const bool bot[3] = {xbot, yy == 0, zz == 0};
-    const bool last[3] = {xlast, yy == cp.ext[1] - 1, zz == cp.ext[2] - 1};
     if (xin && yin && zin) {
-      w[g] |= 1u;
+      w[gg] |= 1u;
 #pragma unroll
-      for (int q = 0; q < 5; ++q) u[g][q] = ((const R*)s.U[q])[xs];
+      for (int q = 0; q < 5; ++q) u[gg][q] = ((const R*)s.U[q])[xs[gg]];
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (ex[a] && !own[a] && !(bot[a] && cp.nx > 0 && excluded(cp, X, di, a))) {
-        w[g] |= 2u << a;
-        b[g][a] = ((const R*)s.B[a])[xs];
+      if (!ex[a] || own[a]) continue;
+      if (bot[a] && cp.nx > 0) {
+        const int di[3] = {i, j, k};
+        if (excluded(cp, X, di, a)) continue;
       }
-      if (last[a]) {
-        int du[3] = {di[0], di[1], di[2]};
-        du[a] += 1;
-        if (face_exists(d, du, a) && !own_face(d, du, a)) w[g] |= 16u << a;
-      }
+      w[gg] |= 2u << a;
+      b[gg][a] = ((const R*)s.B[a])[xs[gg]];
     }
+    // upper faces of the top layers
+    if (xlast && xin1 && yin && zin && !(xint1 && yint && zint)) w[gg] |= 16u;
+    if (yy == cp.ext[1] - 1 && xin && j >= -1 && j < d.N[1] && zin &&
+        !(xint && j >= g - 1 && j < g + d.n[1] && zint))
+      w[gg] |= 32u;
+    if (zz == cp.ext[2] - 1 && xin && yin && k >= -1 && k < d.N[2] &&
+        !(xint && yint && k >= g - 1 && k < g + d.n[2]))
+      w[gg] |= 64u;
   }
 #pragma unroll
-  for (int g = 0; g < GR; ++g) {
-    if (w[g] & 1u)
+  for (int gg = 0; gg < GR; ++gg) {
+    if (w[gg] & 1u)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd[g]] = u[g][q];
+      for (int q = 0; q < 5; ++q) ((R*)d.U[q])[xd[gg]] = u[gg][q];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      if (w[g] & (2u << a)) ((R*)d.B[a])[xd[g]] = b[g][a];
+      if (w[gg] & (2u << a)) ((R*)d.B[a])[xd[gg]] = b[gg][a];
   }
   // the top layers' upper faces (a small share of the elements)
 #pragma unroll
-  for (int g = 0; g < GR; ++g) {
-    if (!(w[g] & 0x70u)) continue;
-    const int r = t.row0 + g * RW + rr;
-    const int64_t xs = lin3(s, i + cp.off[0], cp.lo[1] + r % cp.ext[1] + cp.off[1],
-                            cp.lo[2] + r / cp.ext[1] + cp.off[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (w[g] & (16u << a)) ((R*)d.B[a])[xd[g] + sof(d, a)] = ((const R*)s.B[a])[xs + sof(s, a)];
+  for (int gg = 0; gg < GR; ++gg) {
+    if (w[gg] & 16u) ((R*)d.B[0])[xd[gg] + 1] = ((const R*)s.B[0])[xs[gg] + 1];
+    if (w[gg] & 32u) ((R*)d.B[1])[xd[gg] + ds1] = ((const R*)s.B[1])[xs[gg] + ss1];
+    if (w[gg] & 64u) ((R*)d.B[2])[xd[gg] + ds2] = ((const R*)s.B[2])[xs[gg] + ss2];
   }
 }
 

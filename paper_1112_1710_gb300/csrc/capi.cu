@@ -1319,6 +1319,8 @@ mhd_status mhd_ghost_fill(mhd_ctx* c, const mhd_patch_desc* patches, int32_t n, 
   const int gr = ghost_rows(dtype);
   for (int t = 0; t < nlist; ++t) {
     const DCopy& o = dc[t];
+    if ((int64_t)o.ext[1] * o.ext[2] >= (1 << 24))
+      return fail(c, MHD_EINVAL, "copy %d: more than 2^24 - 1 rows in one box", t);
     const int W = std::min(o.ext[0], 32), rows = o.ext[1] * o.ext[2], step = gr * (32 / W);
     for (int x0 = 0; x0 < o.ext[0]; x0 += 32)
       for (int r0 = 0; r0 < rows; r0 += step) tasks.push_back(GhostTask{t, r0, x0, 0});
