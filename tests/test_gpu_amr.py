@@ -327,3 +327,42 @@ def test_deep_hierarchy_full_size_fp32_properties(capi, capsys):
         if ph is not None:
             ph.close()
         capi.mhd_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("levels,split", [(2, 2), (3, 1)])
+def test_ghost_fill_random_faces_equals_oracle(capi, orc, levels, split):
+    """Same-level ghost copies of every level of a shell hierarchy on random
+    data, whose faces shared by two patches differ: where the top layer of
+    one copy box lies on the bottom layer of another, the two sources give
+    different values, so the one-launch fill must reproduce the two-pass
+    rule element for element (every array of every patch, ghosts included)."""
+    from oracle.amr import OHierarchy
+    from paper_1112_1710_gb300.amr import Hierarchy
+    n0 = 16
+    H = SA.shell_hierarchy(n0=n0, levels=levels, size_min=4, size_max=8, level0_split=split)
+    st = []
+    for l, bl in enumerate(H):
+        lv = []
+        for i, (lo, hi) in enumerate(bl):
+            n = tuple(hi[d] - lo[d] + 1 for d in range(3))
+            lv.append(random_state(n, G, seed=1000 * l + i))
+        st.append(lv)
+    oh = OHierarchy(H, n0, [[s.copy() for s in l] for l in st], (1.0 / n0,) * 3, g=G, prm=orc.params())
+    ctx = capi.mhd_ctx_create()
+    ph = None
+    try:
+        ph = Hierarchy(H, n0, st, (1.0 / n0,) * 3, g=G, dtype="f64", ctx=ctx)
+        shared = 0
+        for l in range(levels):
+            oh.fill(l)
+            ph.fill(l)
+            shared += len(ph.copy_lists[l])
+        assert shared > 0
+        torch.cuda.synchronize()
+        for l in range(levels):
+            for P, Q in zip(oh.levels[l], ph.levels[l]):
+                assert np.array_equal(Q.state.cpu().numpy(), P.state), (l, P.idx)
+    finally:
+        if ph is not None:
+            ph.close()
+        capi.mhd_ctx_destroy(ctx)
