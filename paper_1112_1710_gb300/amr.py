@@ -252,20 +252,16 @@ class Hierarchy:
                         cl = cl.copy()
                         ch = ch.copy()
                         cl[d] = ch[d] = cidx
-                        for k in range(len(clo_all)):
+                        # the coarse patches holding the cells outside the
+                        # side (coarse index outc along d), cut to the side's
+                        # coarse faces, in ascending order
+                        blo_a, bhi_a, ok = _isect(clo_all, chi_all, cl, ch)
+                        blo_a[:, d] = cidx
+                        bhi_a[:, d] = cidx
+                        ok = (clo_all[:, d] <= outc) & (outc <= chi_all[:, d]) & np.all(blo_a <= bhi_a, axis=1)
+                        for k in np.nonzero(ok)[0]:
                             ci = int(cand[k])
-                            if not (clo_all[k][d] <= outc <= chi_all[k][d]):
-                                continue
-                            blo, bhi = cl.copy(), ch.copy()
-                            ok = True
-                            for e in range(3):
-                                if e == d:
-                                    continue
-                                blo[e] = max(cl[e], clo_all[k][e])
-                                bhi[e] = min(ch[e], chi_all[k][e])
-                                ok = ok and blo[e] <= bhi[e]
-                            if not ok:
-                                continue
+                            blo, bhi = blo_a[k].copy(), bhi_a[k].copy()
                             rc = new_reg(5 * _vol(blo, bhi))
                             coarse_caps[l - 1].append((ci, 0, d, blo, bhi, rc))
                             deposits[l - 1].append((ci, 0, d, blo, bhi, rf, rlo, rhi, rc))
