@@ -145,8 +145,11 @@ typedef struct {
  * the interior).  A face that is the upper face of one box's top layer and
  * the lower face of another box's bottom layer takes the first box's value
  * (both sources hold that face); with that rule the copies of one call write
- * disjoint elements, and a call is one launch.  Source boxes must lie in
- * src's interior and copies of one call must read only interiors. */
+ * disjoint elements, and a call is one launch.  The boxes of one destination
+ * must not overlap (their cells would be written twice, in no fixed order),
+ * source boxes must lie in src's interior, and copies of one call must read
+ * only interiors.  A box may hold at most 2^24 - 1 rows (y-z extent
+ * product); a larger one returns MHD_EINVAL. */
 typedef struct {
   int32_t src, dst;    /* indices into the descriptor array                 */
   mhd_box box;         /* destination cells                                 */
