@@ -270,6 +270,8 @@ def mhd_cfl_dt(ctx, patches, d_dt_out: int, stream: int = 0, scale=None) -> None
 
 
 def _structs(ctype, items):
+    if isinstance(items, C.Array) and items._type_ is ctype:
+        return items, len(items)
     items = list(items)
     return (ctype * max(1, len(items)))(*items), len(items)
 

@@ -88,14 +88,15 @@ def _cbox(lo, hi):
 
 def transfer_items(new_boxes, old_boxes):
     """Copies of the previous iteration's data into the new patches
-    (``mhd_transfer_copy`` items): per (new, old) pair the cells of the
-    intersection of the interiors and, per axis, the faces common to both
-    face sets."""
-    out = []
-    if not old_boxes:
-        return out
+    (``mhd_transfer_copy`` items, as one ctypes array; [] when there is
+    none): per (new, old) pair the cells of the intersection of the
+    interiors and, per axis, the faces common to both face sets; new patch
+    by new patch, cells then the faces of each axis, old patches ascending."""
+    if not old_boxes or not new_boxes:
+        return []
     olo = np.array([b[0] for b in old_boxes], np.int64)
     ohi = np.array([b[1] for b in old_boxes], np.int64)
+    rows = []
     for i, (nlo, nhi) in enumerate(new_boxes):
         lo = np.maximum(olo, nlo)
         hi = np.minimum(ohi, nhi)
@@ -103,12 +104,58 @@ def transfer_items(new_boxes, old_boxes):
             h = hi.copy()
             if kind >= 0:
                 h[:, kind] = np.minimum(ohi[:, kind], nhi[kind]) + 1
-            for j in np.nonzero(np.all(lo <= h, axis=1))[0]:
-                it = capi.mhd_transfer_item()
-                it.src, it.dst, it.kind = int(j), int(i), kind
-                it.box = capi.box(lo[j], h[j])
-                out.append(it)
-    return out
+            js = np.nonzero(np.all(lo <= h, axis=1))[0]
+            if len(js):
+                r = np.zeros((len(js), 10), np.int32)   # src, dst, kind, pad, box lo, box hi
+                r[:, 0] = js
+                r[:, 1] = i
+                r[:, 2] = kind
+                r[:, 4:7] = lo[js]
+                r[:, 7:10] = h[js]
+                rows.append(r)
+    if not rows:
+        return []
+    a = np.ascontiguousarray(np.concatenate(rows))
+    return (capi.mhd_transfer_item * len(a)).from_buffer_copy(a)
+
+
+# numpy layout of mhd_prolong_new_item (include/mhd_gpu.h)
+_PNEW_DT = np.dtype({"names": ["coarse", "fine", "lo", "hi", "mask", "mlo", "mhi"],
+                     "formats": ["<i4", "<i4", ("<i4", 3), ("<i4", 3), "<u8", ("<i4", 3), ("<i4", 3)],
+                     "offsets": [0, 4, 8, 20, 32, 40, 52], "itemsize": 64})
+
+
+def prolong_new_items(new_boxes, coarse_boxes, mask_los, mask_ptrs):
+    """``mhd_prolong_new`` items (one ctypes array; [] when there is none):
+    per new patch i (coarse footprint of new_boxes[i]) and every coarse
+    patch k meeting it, the intersection, with the new patch's mask at
+    device address mask_ptrs[i] over the box from mask_los[i] to the
+    footprint's upper corner; new patches in order, coarse ones ascending."""
+    if not new_boxes or not coarse_boxes:
+        return []
+    clo_all = np.array([b[0] for b in coarse_boxes], np.int64)
+    chi_all = np.array([b[1] for b in coarse_boxes], np.int64)
+    parts = []
+    for i, (lo, hi) in enumerate(new_boxes):
+        cl, ch = _cbox(lo, hi)
+        blo = np.maximum(clo_all, cl)
+        bhi = np.minimum(chi_all, ch)
+        ks = np.nonzero(np.all(blo <= bhi, axis=1))[0]
+        if not len(ks):
+            continue
+        r = np.zeros(len(ks), _PNEW_DT)
+        r["coarse"] = ks
+        r["fine"] = i
+        r["lo"] = blo[ks]
+        r["hi"] = bhi[ks]
+        r["mask"] = mask_ptrs[i]
+        r["mlo"] = mask_los[i]
+        r["mhi"] = ch
+        parts.append(r)
+    if not parts:
+        return []
+    a = np.concatenate(parts)
+    return (capi.mhd_prolong_new_item * len(a)).from_buffer_copy(a)
 
 
 def transfer_mask(new_box, old_boxes):
@@ -200,9 +247,6 @@ def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
     items = transfer_items(nb, ob)
     if items:
         capi.mhd_transfer_copy(ctx, [p.desc() for p in old], [p.desc() for p in fresh], items, s)
-    pitems = []
-    clo_all = np.array([p.lo for p in coarse], np.int64)
-    chi_all = np.array([p.hi for p in coarse], np.int64)
     hm = transfer_masks(nb, ob)
     # all masks in one device buffer (one copy), each at a 16-byte offset
     offs, o = [], 0
@@ -214,18 +258,8 @@ def transfer(ctx, old, fresh, coarse, energy_mode: int = 1, stream=None):
         buf[off:off + m.size] = m.ravel()
     dm = torch.as_tensor(buf, device=dev)
     base = dm.data_ptr()
-    for i, (lo, hi) in enumerate(nb):
-        mlo = hm[i][1]
-        cl, ch = _cbox(lo, hi)
-        blo = np.maximum(clo_all, cl)
-        bhi = np.minimum(chi_all, ch)
-        for k in np.nonzero(np.all(blo <= bhi, axis=1))[0]:
-            it = capi.mhd_prolong_new_item()
-            it.coarse, it.fine = int(k), i
-            it.box = capi.box(blo[k], bhi[k])
-            it.mask = base + offs[i]
-            it.mask_box = capi.box(mlo, tuple(int(v) for v in ch))
-            pitems.append(it)
+    pitems = prolong_new_items(nb, [(p.lo, p.hi) for p in coarse], [m[1] for m in hm],
+                               [base + off for off in offs])
     masks = [dm]
     nfall = torch.zeros(1, dtype=torch.int64, device=dev)
     if stream is not None:
