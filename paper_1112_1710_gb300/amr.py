@@ -234,58 +234,73 @@ class Hierarchy:
             regs.append(nvals)
             return len(regs) - 1
 
+        eye = np.eye(3, dtype=np.int64)
         for l in range(1, L):
             for fi, (flo, fhi) in enumerate(zip(self.lo[l], self.hi[l])):
                 cand = self._coarse(l - 1, fi)
                 clo_all, chi_all = self.lo[l - 1][cand], self.hi[l - 1][cand]
-                for d in range(3):
-                    for side in (0, 1):
-                        fidx = int(flo[d]) if side == 0 else int(fhi[d]) + 1
-                        cidx = fidx // 2
-                        outc = cidx - 1 if side == 0 else cidx
-                        # fine faces of the side
-                        rlo, rhi = flo.copy(), fhi.copy()
-                        rlo[d] = rhi[d] = fidx
-                        rf = new_reg(5 * _vol(rlo, rhi))
-                        fine_caps[l].append((fi, 0, d, rlo, rhi, rf))
-                        cl, ch = flo // 2, (fhi + 1) // 2 - 1
-                        cl = cl.copy()
-                        ch = ch.copy()
-                        cl[d] = ch[d] = cidx
-                        # the coarse patches holding the cells outside the
-                        # side (coarse index outc along d), cut to the side's
-                        # coarse faces, in ascending order
-                        blo_a, bhi_a, ok = _isect(clo_all, chi_all, cl, ch)
-                        blo_a[:, d] = cidx
-                        bhi_a[:, d] = cidx
-                        ok = (clo_all[:, d] <= outc) & (outc <= chi_all[:, d]) & np.all(blo_a <= bhi_a, axis=1)
-                        for k in np.nonzero(ok)[0]:
+                # the 6 sides (d, side) and their 12 edge axes, intersected
+                # with every candidate at once; the lists are then filled
+                # side by side in the order of the registers
+                sides = [(d, side) for d in range(3) for side in (0, 1)]
+                fidx = np.array([int(flo[d]) if side == 0 else int(fhi[d]) + 1 for d, side in sides], np.int64)
+                cidx = fidx // 2
+                outc = np.array([c - 1 if side == 0 else c for c, (d, side) in zip(cidx, sides)], np.int64)
+                dd = np.array([d for d, _ in sides])
+                c0, c1 = flo // 2, (fhi + 1) // 2 - 1
+                CL = np.repeat(c0[None], 6, axis=0)
+                CH = np.repeat(c1[None], 6, axis=0)
+                CL[np.arange(6), dd] = cidx
+                CH[np.arange(6), dd] = cidx
+                # faces: the coarse patches holding the cells outside the side
+                # (coarse index outc along d), cut to the side's coarse faces
+                FLO = np.maximum(clo_all[None], CL[:, None])
+                FHI = np.minimum(chi_all[None], CH[:, None])
+                FLO[np.arange(6), :, dd] = cidx[:, None]
+                FHI[np.arange(6), :, dd] = cidx[:, None]
+                FOK = ((clo_all[:, dd].T <= outc[:, None]) & (outc[:, None] <= chi_all[:, dd].T) &
+                       np.all(FLO <= FHI, axis=2))
+                # edges along a != d in the side plane
+                edges = [(q, a) for q in range(6) for a in range(3) if a != sides[q][0]]
+                ea = np.array([a for _, a in edges])
+                eq = np.array([q for q, _ in edges])
+                ett = 3 - ea - dd[eq]
+                ECL = CL[eq].copy()
+                ECH = CH[eq].copy()
+                ECH[np.arange(12), ett] = (fhi[ett] + 1) // 2
+                top = chi_all[None] + 1 - eye[ea][:, None, :]
+                ELO = np.maximum(clo_all[None], ECL[:, None])
+                EHI = np.minimum(top, ECH[:, None])
+                EOK = np.all(ELO <= EHI, axis=2)
+                e = 0
+                for q, (d, side) in enumerate(sides):
+                    # fine faces of the side
+                    rlo, rhi = flo.copy(), fhi.copy()
+                    rlo[d] = rhi[d] = fidx[q]
+                    rf = new_reg(5 * _vol(rlo, rhi))
+                    fine_caps[l].append((fi, 0, d, rlo, rhi, rf))
+                    for k in np.nonzero(FOK[q])[0]:
+                        ci = int(cand[k])
+                        blo, bhi = FLO[q, k].copy(), FHI[q, k].copy()
+                        rc = new_reg(5 * _vol(blo, bhi))
+                        coarse_caps[l - 1].append((ci, 0, d, blo, bhi, rc))
+                        deposits[l - 1].append((ci, 0, d, blo, bhi, rf, rlo, rhi, rc))
+                    for a in range(3):
+                        if a == d:
+                            continue
+                        tt = 3 - a - d
+                        elo, ehi = flo.copy(), fhi.copy()
+                        elo[d] = ehi[d] = fidx[q]
+                        ehi[tt] = fhi[tt] + 1
+                        re = new_reg(_vol(elo, ehi))
+                        fine_caps[l].append((fi, 1, a, elo, ehi, re))
+                        for k in np.nonzero(EOK[e])[0]:
                             ci = int(cand[k])
-                            blo, bhi = blo_a[k].copy(), bhi_a[k].copy()
-                            rc = new_reg(5 * _vol(blo, bhi))
-                            coarse_caps[l - 1].append((ci, 0, d, blo, bhi, rc))
-                            deposits[l - 1].append((ci, 0, d, blo, bhi, rf, rlo, rhi, rc))
-                        # edges in the side plane
-                        for a in range(3):
-                            if a == d:
-                                continue
-                            tt = 3 - a - d
-                            elo, ehi = flo.copy(), fhi.copy()
-                            elo[d] = ehi[d] = fidx
-                            ehi[tt] = fhi[tt] + 1
-                            re = new_reg(_vol(elo, ehi))
-                            fine_caps[l].append((fi, 1, a, elo, ehi, re))
-                            cl, ch = (flo // 2).copy(), ((fhi + 1) // 2 - 1).copy()
-                            cl[d] = ch[d] = cidx
-                            ch[tt] = (fhi[tt] + 1) // 2
-                            top = chi_all + 1
-                            top[:, a] -= 1
-                            blo, bhi, ok = _isect(clo_all, top, cl, ch)
-                            for k in np.nonzero(ok)[0]:
-                                ci = int(cand[k])
-                                rc = new_reg(_vol(blo[k], bhi[k]))
-                                coarse_caps[l - 1].append((ci, 1, a, blo[k], bhi[k], rc))
-                                deposits[l - 1].append((ci, 1, a, blo[k], bhi[k], re, elo, ehi, rc))
+                            blo, bhi = ELO[e, k].copy(), EHI[e, k].copy()
+                            rc = new_reg(_vol(blo, bhi))
+                            coarse_caps[l - 1].append((ci, 1, a, blo, bhi, rc))
+                            deposits[l - 1].append((ci, 1, a, blo, bhi, re, elo, ehi, rc))
+                        e += 1
         offs = np.concatenate([[0], np.cumsum(regs)]).astype(np.int64)
         self.regbuf = torch.zeros(max(1, int(offs[-1])), dtype=torch.float64, device=self.device)
         base = self.regbuf.data_ptr()
