@@ -49,6 +49,17 @@ def _vol(lo, hi):
     return (int(hi[0]) - int(lo[0]) + 1) * (int(hi[1]) - int(lo[1]) + 1) * (int(hi[2]) - int(lo[2]) + 1)
 
 
+def _rows_array(ctype, blocks, width):
+    """One ctypes array of `ctype` (int32 fields only, `width` of them) from
+    blocks of int rows laid out like its fields; [] when there is no row."""
+    blocks = [b for b in blocks if len(b)]
+    if not blocks:
+        return []
+    a = np.ascontiguousarray(np.concatenate(blocks).astype(np.int32))
+    assert a.shape[1] == width and a.itemsize * width == C.sizeof(ctype)
+    return (ctype * len(a)).from_buffer_copy(a)
+
+
 # numpy layouts of mhd_capture and mhd_deposit (include/mhd_gpu.h), for
 # filling the ctypes arrays of long lists in one copy
 _CAP_DT = np.dtype([("patch", "<i4"), ("kind", "<i4"), ("axis", "<i4"), ("mode", "<i4"), ("lo", "<i4", 3),
@@ -127,26 +138,20 @@ class Hierarchy:
         shifts = [(0, 0, 0)]
         if near.any():
             shifts = [s for s in itertools.product((-n, 0, n), repeat=3)]
-        out = []
+        rows = []   # src, dst, box lo, box hi, offset
         for di in range(len(lo)):
             elo = lo[di] - g - 1
             ehi = hi[di] + g + 1
             for sh in shifts:
                 sh = np.array(sh)
                 blo, bhi, ok = _isect(lo + sh, hi + sh, elo, ehi)
-                if sh.any():
-                    pass
-                else:
+                if not sh.any():
                     ok[di] = False
-                for si in np.nonzero(ok)[0]:
-                    c = capi.mhd_copy()
-                    c.src = int(si)
-                    c.dst = int(di)
-                    c.box.lo[:] = [int(v) for v in blo[si]]
-                    c.box.hi[:] = [int(v) for v in bhi[si]]
-                    c.offset[:] = [int(-v) for v in sh]
-                    out.append(c)
-        return out
+                si = np.nonzero(ok)[0]
+                if len(si):
+                    rows.append(np.column_stack([si, np.full(len(si), di), blo[si], bhi[si],
+                                                 np.repeat(-sh[None], len(si), axis=0)]))
+        return _rows_array(capi.mhd_copy, rows, 11)
 
     def _copies_tree(self, l):
         """The same copies from the tree's interactions of each destination,
@@ -154,22 +159,16 @@ class Hierarchy:
         n = self.n0 * 2 ** l
         g = self.g
         lo, hi = self.lo[l], self.hi[l]
-        out = []
+        rows = []   # src, dst, box lo, box hi, offset
         for di in range(len(lo)):
             idx, s = self.tree.interactions(l, di)
             keep = (idx != di) | np.any(s != 0, axis=1)
             idx, sh = idx[keep], s[keep].astype(np.int64) * n
             blo = np.maximum(lo[idx] + sh, lo[di] - g - 1)
             bhi = np.minimum(hi[idx] + sh, hi[di] + g + 1)
-            for k in range(len(idx)):
-                c = capi.mhd_copy()
-                c.src = int(idx[k])
-                c.dst = int(di)
-                c.box.lo[:] = [int(v) for v in blo[k]]
-                c.box.hi[:] = [int(v) for v in bhi[k]]
-                c.offset[:] = [int(-v) for v in sh[k]]
-                out.append(c)
-        return out
+            if len(idx):
+                rows.append(np.column_stack([idx, np.full(len(idx), di), blo, bhi, -sh]))
+        return _rows_array(capi.mhd_copy, rows, 11)
 
     def _coarse(self, l, fi):
         """Level-l patches that can touch fine patch fi of level l+1, ascending:
@@ -196,13 +195,10 @@ class Hierarchy:
                 cl = np.array(slo) // 2
                 ch = np.array(shi) // 2
                 blo, bhi, ok = _isect(clo, chi, cl, ch)
-                for k in np.nonzero(ok)[0]:
-                    it = capi.mhd_prolong_item()
-                    it.coarse = int(cand[k])
-                    it.fine = int(fi)
-                    it.box = capi.box(blo[k], bhi[k])
-                    out.append(it)
-        return out
+                k = np.nonzero(ok)[0]
+                if len(k):
+                    out.append(np.column_stack([np.asarray(cand)[k], np.full(len(k), fi), blo[k], bhi[k]]))
+        return _rows_array(capi.mhd_prolong_item, out, 8)
 
     def _restricts(self, l):
         out = []
@@ -211,13 +207,10 @@ class Hierarchy:
             clo, chi = self.lo[l][cand], self.hi[l][cand]
             cl, ch = flo // 2, (fhi + 1) // 2 - 1
             blo, bhi, ok = _isect(clo - 1, chi + 1, cl, ch)
-            for k in np.nonzero(ok)[0]:
-                it = capi.mhd_restrict_item()
-                it.fine = int(fi)
-                it.coarse = int(cand[k])
-                it.box = capi.box(blo[k], bhi[k])
-                out.append(it)
-        return out
+            k = np.nonzero(ok)[0]
+            if len(k):
+                out.append(np.column_stack([np.full(len(k), fi), np.asarray(cand)[k], blo[k], bhi[k]]))
+        return _rows_array(capi.mhd_restrict_item, out, 8)
 
     def _build(self):
         L = self.nlev
